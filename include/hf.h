@@ -1,0 +1,242 @@
+/*
+ * hf.h -- C ABI of a B300 (sm_103a) executor for task dependency graphs.
+ *
+ * Task model (Heteroflow, "Concurrent CPU-GPU Task Programming using Modern C++",
+ * Section III-A): a graph is a DAG of tasks of four kinds -- host, pull, push and kernel --
+ * joined by explicit dependency edges; a task runs only after every task that precedes it
+ * has finished, the library adds no implicit edge, and the graph must be acyclic. Running a
+ * graph is non-blocking (Section III-B): hf_run only enqueues work on a CUDA stream.
+ *
+ * Every task carries an FP32 arrival time (timing-graph max-plus propagation, the paper's
+ * timing-analysis setting, Section IV-A): a task with no predecessor starts at its source
+ * arrival (default +0), every other task ends with
+ *         arr[v] = max over edges (u, v) of  arr[u] + d(u, v)
+ * where each sum is one binary32 add rounded to nearest even and the max uses the total
+ * order -inf < ... < -0 < +0 < ... < +inf. Results are bit-identical for every schedule.
+ *
+ * Conventions for every call:
+ *   - returns hf_status; no C++ exception crosses this boundary;
+ *   - "device" pointers are CUDA device (or managed) addresses on the current device,
+ *     "host" pointers are host addresses; pull/push host buffers must be page-locked
+ *     (cudaHostAlloc / cudaHostRegister), the executors read and write them directly;
+ *   - a stream argument is a cudaStream_t passed as void* (NULL = legacy default stream);
+ *   - the library owns every device buffer it allocates for a graph (through the allocator
+ *     installed with hf_set_allocator, else cudaMalloc/cudaFree) and frees it in
+ *     hf_graph_destroy / hf_batch_destroy;
+ *   - buffers named in payloads are BORROWED: the caller keeps them alive and leaves them
+ *     alone until the run that uses them has completed (the paper's stateful, by-reference
+ *     task arguments, Section III-A "Pull Task");
+ *   - one graph is not thread-safe for mutation; distinct graphs may run concurrently on
+ *     distinct streams.
+ */
+#ifndef HF_H
+#define HF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hf_graph hf_graph;     /* opaque, created by hf_graph_create */
+typedef struct hf_batch hf_batch;     /* opaque, created by hf_batch_create */
+typedef int32_t hf_task;              /* dense task id, 0..n-1 in creation order (a task handle) */
+
+typedef enum {
+    HF_OK = 0,
+    HF_EINVAL = 1,     /* bad argument: id out of range, NaN/inf delay, bad payload, NULL pointer */
+    HF_ENOMEM = 2,     /* host or device allocation failed */
+    HF_ECYCLE = 3,     /* the dependency edges form a cycle (self-loops included) */
+    HF_ESTATE = 4,     /* call not valid now: graph mutated while in a batch or run in flight, ... */
+    HF_ETIMEDOUT = 5,  /* the persistent executor saw no progress for spin_limit_ns and gave up */
+    HF_EQUEUE = 6,     /* a device queue overflowed (internal error; never expected) */
+    HF_ECUDA = 7,      /* a CUDA runtime call failed; hf_last_error() has its message */
+    HF_ENOTSUP = 8     /* valid request this build does not support (e.g. host tasks, persistent mode) */
+} hf_status;
+
+/* The paper's four task kinds (Section I; Section III-A). */
+typedef enum { HF_HOST = 0, HF_PULL = 1, HF_PUSH = 2, HF_KERNEL = 3 } hf_kind;
+
+/* Built-in kernel payloads. HF_K_SAXPY_I32 is Listing 1's kernel (y = a*x + y on int32,
+ * two's-complement wrap); HF_K_SAXPY_F32 its FP32 form with one fused multiply-add. */
+typedef enum { HF_K_MAXPLUS = 0, HF_K_SAXPY_F32 = 1, HF_K_SAXPY_I32 = 2 } hf_kernel_op;
+
+/* --- payloads, copied at hf_add_task time (pointers inside are borrowed) ---------------- */
+
+/* kind HF_KERNEL, op HF_K_MAXPLUS: arrival propagation only. arr0 is the arrival used when
+ * the task has no predecessor (finite; default +0 when payload is NULL). */
+typedef struct { int32_t op; float arr0; } hf_maxplus_payload;
+
+/* kind HF_KERNEL, op HF_K_SAXPY_F32 / HF_K_SAXPY_I32: y[i] = a*x[i] + y[i], i < n.
+ * x comes from pull task x_pull (its device buffer, Section III-A "Kernel Task": pull tasks
+ * are the data gateway) or, when x_pull == -1, from device pointer x_dev; likewise y.
+ * A pull used as an operand must hold at least n * 4 bytes. Device pointers must be 4-byte
+ * aligned; n >= 0. The library adds no edge from the pull: order it with hf_precede. */
+typedef struct {
+    int32_t op;
+    int32_t a_i;     /* scalar for HF_K_SAXPY_I32 */
+    float a_f;       /* scalar for HF_K_SAXPY_F32 */
+    hf_task x_pull;  /* -1: use x_dev */
+    hf_task y_pull;  /* -1: use y_dev */
+    int32_t pad_;
+    int64_t n;       /* elements */
+    void* x_dev;
+    void* y_dev;
+} hf_saxpy_payload;
+
+/* kind HF_PULL: copy `bytes` from page-locked host memory into a device buffer that the
+ * library allocates for this task (Section III-A "Pull Task"). */
+typedef struct { const void* host_ptr; size_t bytes; } hf_pull_payload;
+
+/* kind HF_PUSH: copy `bytes` into page-locked host memory from pull task src_pull's device
+ * buffer (Section III-A "Push Task") or, when src_pull == -1, from device pointer src_dev. */
+typedef struct { hf_task src_pull; int32_t pad_; const void* src_dev; void* host_ptr; size_t bytes; } hf_push_payload;
+
+/* kind HF_HOST: fn(arg) runs on a CPU thread (Section III-A "Host Task"). Supported by the
+ * level-synchronous executor only (it becomes a host node of the CUDA graph). */
+typedef struct { void (*fn)(void* arg); void* arg; } hf_host_payload;
+
+/* --- run options ---------------------------------------------------------------------- */
+
+typedef enum { HF_MODE_LEVELSYNC = 0, HF_MODE_PERSISTENT = 1, HF_MODE_AUTO = 2 } hf_mode;
+typedef enum { HF_PRIO_FIFO = 0, HF_PRIO_HEURISTIC = 1, HF_PRIO_LEARNED = 2 } hf_priority;
+
+typedef struct {
+    int32_t mode;           /* hf_mode */
+    int32_t priority;       /* hf_priority (persistent executor) */
+    int32_t ctas;           /* persistent: CTAs launched; 0 = one per SM times occupancy */
+    int32_t warps_per_cta;  /* persistent: 0 = 8 */
+    int32_t claim;          /* persistent: queue slots a warp claims at once, 1..32; 0 = 1 */
+    int32_t local_keep;     /* persistent: ready tasks a warp keeps in shared memory, 0..64;
+                               negative = default (32) */
+    int64_t chunk_elems;    /* payload split size in elements (saxpy) or 4-byte words (copies);
+                               0 = 16384 */
+    uint64_t spin_limit_ns; /* persistent: give up (HF_ETIMEDOUT) after this long without any
+                               task completing; 0 = 2 s */
+    int32_t instrument;     /* record per-task %globaltimer start/end (hf_get_task_times) */
+    int32_t validate;       /* record per-task start/finish tickets and execution counts */
+    int32_t stall_task;     /* failure-injection hook for tests: -1 = off; else this task's
+                               pending-predecessor counter starts one too high, so it never
+                               becomes ready and a persistent run ends with HF_ETIMEDOUT */
+    int32_t time_kernel;    /* record CUDA events around the executor's main work (read with
+                               hf_kernel_ms / hf_batch_kernel_ms) */
+} hf_run_opts;
+
+void hf_run_opts_default(hf_run_opts* opts);
+
+/* --- graph construction (Section III-A) ------------------------------------------------ */
+
+hf_status hf_graph_create(hf_graph** out, int64_t reserve_tasks, int64_t reserve_edges);
+hf_status hf_graph_destroy(hf_graph* g);   /* waits for the graph's last run to finish */
+
+/* Adds one task; *out receives its id. payload/payload_bytes must match the kind:
+ * HF_KERNEL: hf_maxplus_payload or hf_saxpy_payload (selected by its op field), or NULL for
+ * max-plus with arr0 = +0; HF_PULL: hf_pull_payload; HF_PUSH: hf_push_payload; HF_HOST:
+ * hf_host_payload. References to other tasks (x_pull, src_pull, ...) must name existing
+ * pull tasks. */
+hf_status hf_add_task(hf_graph* g, hf_kind kind, const void* payload, size_t payload_bytes, hf_task* out);
+
+/* Adds n max-plus kernel tasks with ids first..first+n-1; arr0 (host, n floats) or NULL. */
+hf_status hf_add_tasks_bulk(hf_graph* g, int64_t n, const float* arr0, hf_task* first_out);
+
+/* Edge a -> b ("a precedes b", Section III-A "Add a Dependency Link") with delay 0, or with
+ * the given finite delay. Duplicate edges are allowed (each counts). Cycles are reported by
+ * hf_finalize / hf_run. */
+hf_status hf_precede(hf_graph* g, hf_task a, hf_task b);
+hf_status hf_precede_w(hf_graph* g, hf_task a, hf_task b, float delay);
+
+/* m edges src[i] -> dst[i] (host arrays); delay NULL = all 0. All-or-nothing: on HF_EINVAL
+ * no edge is added. */
+hf_status hf_precede_bulk(hf_graph* g, int64_t m, const int32_t* src, const int32_t* dst, const float* delay);
+
+/* Host-side preparation: successor (CSR) and level-sorted predecessor lists, in-degrees,
+ * topological levels, cycle check. Optional: hf_run finalizes a changed graph itself. */
+hf_status hf_finalize(hf_graph* g);
+
+typedef struct {
+    int64_t tasks, edges;
+    int32_t levels;         /* 1 + longest hop count from a source; 0 before finalize */
+    int32_t sources;
+    int64_t kind_count[4];  /* indexed by hf_kind */
+    int64_t payload_tasks;  /* tasks with a saxpy or copy payload */
+    int32_t finalized;
+    int32_t pad_;
+} hf_graph_info_t;
+
+hf_status hf_graph_info(const hf_graph* g, hf_graph_info_t* info);
+/* level (longest hop count from a source) of every task, after finalize; host array of n. */
+hf_status hf_get_levels(const hf_graph* g, int32_t* level_out);
+
+/* --- execution (Section III-B) --------------------------------------------------------- */
+
+/* Enqueues one execution of the graph on `stream` and returns (non-blocking). opts NULL =
+ * defaults. Device-side failures are reported by hf_sync_status. Re-running a graph re-runs
+ * every payload (saxpy updates y again). */
+hf_status hf_run(hf_graph* g, void* stream, const hf_run_opts* opts);
+
+/* Waits for the graph's last run and returns its device status (HF_OK, HF_ETIMEDOUT, ...). */
+hf_status hf_sync_status(hf_graph* g);
+
+/* Arrival times of the last run (n floats). on_device != 0: `out` is a device pointer and the
+ * copy is enqueued on the run's stream; else `out` is host memory and the call blocks. */
+hf_status hf_get_arrivals(hf_graph* g, float* out, int on_device);
+
+/* validate runs: per-task start and finish tickets (host int64[n]; from one global counter,
+ * so finish[u] < start[v] for every edge u -> v) and execution counts (host int32[n]). */
+hf_status hf_get_stamps(hf_graph* g, int64_t* start, int64_t* finish, int32_t* exec_count);
+
+/* instrument runs: per-task %globaltimer start/end in ns (host int64[n]). */
+hf_status hf_get_task_times(hf_graph* g, int64_t* t_start_ns, int64_t* t_end_ns);
+
+/* time_kernel runs: device time (ms) of the executor's main work in the last run -- the
+ * persistent kernel, or the whole level-synchronous CUDA graph -- from CUDA events on the
+ * run's stream (the reset kernel before a persistent launch is not included). Blocks until
+ * the run has finished. */
+hf_status hf_kernel_ms(hf_graph* g, float* ms);
+
+/* Replaces every edge delay of the graph's device plan (a new timing view of the same
+ * circuit): delay[e] is the new delay of the e-th edge in the order edges were added
+ * (hf_precede*), m floats, all finite. on_device != 0: `delay` is a device pointer; else host
+ * memory (page-locked for an asynchronous copy). Enqueued on `stream`; later runs on any
+ * stream see the new delays once that stream has reached this point. The graph's own edge
+ * list keeps the delays it was built with (they return if the plan is ever rebuilt, e.g.
+ * after a mutation). Finalizes and uploads the graph first if needed. */
+hf_status hf_set_delays(hf_graph* g, const float* delay, int on_device, void* stream);
+
+/* --- batches: many independent graphs in one launch ------------------------------------- */
+
+hf_status hf_batch_create(hf_batch** out);
+hf_status hf_batch_destroy(hf_batch* b);
+/* Appends a graph (finalizing it if needed); *index_out gets its position. The graph must not
+ * be mutated while it belongs to a batch (HF_ESTATE); destroy the batch first. */
+hf_status hf_batch_add(hf_batch* b, hf_graph* g, int32_t* index_out);
+hf_status hf_batch_run(hf_batch* b, void* stream, const hf_run_opts* opts);
+hf_status hf_batch_sync_status(hf_batch* b);
+/* Arrivals of graph `index` (its n floats), as hf_get_arrivals; index -1: every graph's
+ * arrivals concatenated in batch order (sum of their task counts) in one copy. */
+hf_status hf_batch_get_arrivals(hf_batch* b, int32_t index, float* out, int on_device);
+hf_status hf_batch_get_task_times(hf_batch* b, int32_t index, int64_t* t_start_ns, int64_t* t_end_ns);
+hf_status hf_batch_get_stamps(hf_batch* b, int32_t index, int64_t* start, int64_t* finish, int32_t* exec_count);
+hf_status hf_batch_kernel_ms(hf_batch* b, float* ms);
+/* As hf_set_delays for every graph of the batch: delay holds the graphs' edge delays
+ * concatenated in batch order (sum of their edge counts). */
+hf_status hf_batch_set_delays(hf_batch* b, const float* delay, int on_device, void* stream);
+
+/* --- memory and diagnostics ------------------------------------------------------------ */
+
+/* Process-wide device allocator for library-owned buffers (NULL, NULL = cudaMalloc/cudaFree).
+ * alloc(bytes, stream, ctx) returns a device pointer aligned to 256 bytes or NULL. */
+typedef void* (*hf_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*hf_free_fn)(void* ptr, void* stream, void* ctx);
+hf_status hf_set_allocator(hf_alloc_fn alloc, hf_free_fn free_fn, void* ctx);
+
+const char* hf_status_string(hf_status s);
+/* Message of the last failure on the calling thread ("" if none). */
+const char* hf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HF_H */

@@ -105,12 +105,22 @@ def run_spec(g, with_data=True):
     ``count``, ``y`` (list of final y arrays per saxpy task) and ``push`` (list of host arrays
     per push task).
     """
+    return execute(prepare(g, with_data))
+
+
+def execute(prep):
+    """Run a graph prepared by ``prepare`` (the part the CPU baseline times)."""
+    arr, order, stamp, cnt = kahn(*prep["args"])
+    return dict(arr=arr, order=order, stamp=stamp, count=cnt, y=prep["y"], push=prep["push"], x=prep["x"])
+
+
+def prepare(g, with_data=True):
+    """Host stand-ins for every buffer of ``g`` and the argument tuple of ``kahn``."""
     from paper_2203_08395_b300.synth import KIND_SAXPY_I32  # generator constants only
 
     n = g.n
     if not with_data or g.sx_task.size == 0:
-        arr, order, stamp, cnt = kahn(n, g.src, g.dst, g.delay, g.arr0)
-        return dict(arr=arr, order=order, stamp=stamp, count=cnt, y=[], push=[])
+        return dict(args=(n, g.src, g.dst, g.delay, g.arr0), y=[], push=[], x=[])
     op = np.zeros(n, np.uint8)
     p0 = np.zeros(n, np.uint64)
     p1 = np.zeros(n, np.uint64)
@@ -151,9 +161,8 @@ def run_spec(g, with_data=True):
         p0[t] = h.ctypes.data
         p1[t] = ys[j].ctypes.data
         length[t] = h.nbytes
-    arr, order, stamp, cnt = kahn(n, g.src, g.dst, g.delay, g.arr0, op, p0, p1, length, a_f, a_i)
-    del keep
-    return dict(arr=arr, order=order, stamp=stamp, count=cnt, y=ys, push=pushes, x=xs)
+    return dict(args=(n, g.src, g.dst, g.delay, g.arr0, op, p0, p1, length, a_f, a_i), y=ys, push=pushes, x=xs,
+                keep=keep)
 
 
 def bottom_levels(n, src, dst, cost):

@@ -1,0 +1,203 @@
+// hf_internal.h -- internal data structures of the task-graph executor (host builder,
+// device plan, kernels). Not part of the C ABI; see include/hf.h for the public contract.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/hf.h"
+
+namespace hf {
+
+// ----------------------------------------------------------------------------- constants
+
+// Order-preserving map from FP32 bits to uint32 (radix-sort key): negative values have all
+// bits flipped, non-negative ones get the sign bit set; then unsigned comparison of keys
+// equals the total order -inf < ... < -0 < +0 < ... < +inf on non-NaN floats.
+constexpr uint32_t kKeyNegInf = 0x007FFFFFu;  // key(-inf)
+constexpr uint32_t kKeyPosZero = 0x80000000u;  // key(+0)
+
+enum PayOp : uint32_t { kPaySaxpyF32 = 1, kPaySaxpyI32 = 2, kPayCopy = 3 };
+
+// One device payload record (saxpy or copy), 48 bytes.
+struct DevPayload {
+    void* dst;            // saxpy: y; copy: destination
+    const void* src;      // saxpy: x; copy: source
+    int64_t n;            // saxpy: elements; copy: bytes
+    uint32_t op;          // PayOp
+    uint32_t a_bits;      // saxpy scalar (float bits or int32)
+    int32_t nchunks;      // pieces the payload is split into (>= 1)
+    int32_t chunk_first;  // first chunk-item index (multi-chunk payloads), else -1
+    int64_t chunk;        // piece size: elements (saxpy) or bytes (copy)
+};
+
+// Persistent-executor control block; hot counters on separate 128-byte lines.
+struct alignas(128) Ctrl {
+    int32_t head;
+    int32_t pad0[31];
+    int32_t tail;
+    int32_t pad1[31];
+    uint32_t done;
+    int32_t pad2[31];
+    int32_t status;
+    int32_t abort;
+    int32_t pad3[30];
+    unsigned long long ticket;  // validation tickets
+    int32_t pad4[30];
+};
+
+// Arguments of the persistent executor kernel (by value, < 4 KB).
+struct PersistArgs {
+    int32_t n_tasks;
+    int32_t qcap;
+    int32_t claim;
+    int32_t local_keep;
+    uint64_t spin_limit_ns;
+    const int32_t* row_ptr;  // n_tasks + 1
+    const int2* succ;        // edges {successor, delay bits}, CSR order
+    const int32_t* pidx;     // n_tasks payload index or -1 (NULL: no payloads)
+    const DevPayload* pay;
+    const int32_t* chunk_task;  // chunk item -> task
+    uint32_t* key;              // n_tasks arrival keys
+    int32_t* indeg;             // n_tasks pending-predecessor counters
+    int32_t* queue;             // qcap ready-queue slots (-1 = empty)
+    int32_t* chunks_left;       // per payload: pieces still running
+    Ctrl* ctrl;
+    int64_t* t_start;  // instrument: %globaltimer per task (NULL otherwise)
+    int64_t* t_end;
+    int64_t* tk_start;  // validate: tickets per task (NULL otherwise)
+    int64_t* tk_end;
+    int32_t* exec_count;
+};
+
+// Arguments of the reset kernel run before each persistent launch.
+struct ResetArgs {
+    int32_t n_tasks;
+    int32_t qcap;
+    int32_t n_seed;
+    int32_t n_pay;
+    int32_t stall_task;  // test hook: this task's counter starts one too high (-1: none)
+    int32_t pad_;
+    const int32_t* indeg0;
+    const uint32_t* key0;  // NULL: sources start at +0
+    const int32_t* seeds;
+    const DevPayload* pay;
+    uint32_t* key;
+    int32_t* indeg;
+    int32_t* queue;
+    int32_t* chunks_left;
+    Ctrl* ctrl;
+    int64_t* t_start;
+    int64_t* t_end;
+    int64_t* tk_start;
+    int64_t* tk_end;
+    int32_t* exec_count;
+};
+
+// Arguments of one level kernel of the level-synchronous executor.
+struct LevelArgs {
+    const int32_t* ls_node;  // level-sorted position -> task id
+    const int32_t* ls_ptr;   // level-sorted position -> first in-edge (n + 1)
+    const int2* ls_in;       // in-edges {predecessor, delay bits}, level-sorted order
+    const uint32_t* key0;    // NULL: sources start at +0
+    uint32_t* key;
+    const DevPayload* pay;
+    const int2* items;       // payload work items {payload index, piece index}
+    int32_t p0, p1;          // positions of this level
+    int32_t i0, i1;          // payload items of this level
+    int32_t nb_mp;           // blocks doing arrivals; the rest do payload items
+    int32_t pad_;
+};
+
+// ----------------------------------------------------------------------------- host side
+
+struct PayloadRec {
+    int32_t kind = 0;  // hf_kind
+    int32_t op = 0;    // hf_kernel_op for kernels
+    // saxpy
+    int64_t n = 0;
+    float a_f = 0.f;
+    int32_t a_i = 0;
+    int32_t x_pull = -1, y_pull = -1;
+    void* x_dev = nullptr;
+    void* y_dev = nullptr;
+    // pull / push
+    const void* host_src = nullptr;
+    void* host_dst = nullptr;
+    size_t bytes = 0;
+    int32_t src_pull = -1;
+    const void* src_dev = nullptr;
+    // host
+    void (*fn)(void*) = nullptr;
+    void* arg = nullptr;
+};
+
+// Finalized host form of one graph.
+struct Final {
+    int32_t n = 0;
+    int64_t m = 0;
+    int32_t levels = 0;
+    int32_t nsrc = 0;
+    std::vector<int32_t> row_ptr;   // n + 1 (successor CSR, edges in insertion order)
+    std::vector<int2> succ;         // m
+    std::vector<int32_t> indeg0;    // n
+    std::vector<int32_t> level;     // n
+    std::vector<int32_t> ls_node;   // n: tasks sorted by (level, id)
+    std::vector<int32_t> level_ptr; // levels + 1
+    std::vector<int32_t> ls_ptr;    // n + 1
+    std::vector<int2> ls_in;        // m
+    std::vector<int32_t> epos_csr;  // m: edge (insertion order) -> position in succ
+    std::vector<int32_t> epos_ls;   // m: edge (insertion order) -> position in ls_in
+};
+
+struct Plan;  // device-resident form of one or more graphs (plan.cu)
+
+}  // namespace hf
+
+struct hf_graph {
+    std::vector<uint8_t> kind;     // hf_kind
+    std::vector<float> arr0;
+    std::vector<int32_t> pay;      // payload index or -1
+    std::vector<hf::PayloadRec> payloads;
+    std::vector<int32_t> esrc, edst;
+    std::vector<float> edly;
+    bool dirty = true;
+    bool any_arr0 = false;
+    int in_batches = 0;
+    hf::Final fin;
+    hf::Plan* plan = nullptr;  // solo-run plan
+};
+
+struct hf_batch {
+    std::vector<hf_graph*> graphs;
+    hf::Plan* plan = nullptr;
+    bool dirty = true;
+};
+
+namespace hf {
+
+// error reporting (api.cpp)
+hf_status fail(hf_status s, const std::string& msg);
+hf_status cuda_fail(cudaError_t e, const char* what);
+
+// device memory through the installed allocator (api.cpp)
+void* dev_alloc(size_t bytes, cudaStream_t s);
+void dev_free(void* p, cudaStream_t s);
+
+// plan.cu
+hf_status plan_build(const std::vector<hf_graph*>& graphs, Plan** out);
+void plan_destroy(Plan* p);
+hf_status plan_run(Plan* p, cudaStream_t s, const hf_run_opts& o);
+hf_status plan_sync(Plan* p);
+hf_status plan_busy(Plan* p);  // HF_ESTATE while a run is in flight
+hf_status plan_get_arrivals(Plan* p, int32_t gi, float* out, int on_device);
+hf_status plan_get_times(Plan* p, int32_t gi, int64_t* a, int64_t* b);
+hf_status plan_get_stamps(Plan* p, int32_t gi, int64_t* a, int64_t* b, int32_t* c);
+hf_status plan_kernel_ms(Plan* p, float* ms);
+hf_status plan_set_delays(Plan* p, const float* delay, int on_device, cudaStream_t s);
+
+}  // namespace hf

@@ -1,0 +1,519 @@
+// kernels.cuh -- device code of the task-graph executor (sm_103a).
+//
+// Two executors share the payload code:
+//   * level-synchronous: one kernel per topological level (captured in a CUDA graph); each
+//     thread pulls the arrival of one task from its level-sorted in-edges;
+//   * persistent: one launch; every warp loops popping ready tasks (shared-memory stack
+//     first, then pre-claimed global queue slots), runs their payload pieces, and releases
+//     successors through atomic in-degree counters, pushing the ones that become ready.
+// Arrivals are kept as order-preserving uint32 keys so that the max over predecessors is
+// an unsigned integer max (an atomicMax in the persistent executor).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hf_internal.h"
+
+namespace hf {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kWarpsPerCta = 8;
+constexpr int kStackCap = 64;  // per-warp shared-memory ready stack
+
+__device__ __forceinline__ uint32_t f2key(float f) {
+    const uint32_t b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+__device__ __forceinline__ float key2f(uint32_t k) {
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
+__device__ __forceinline__ int ld_acquire(const int32_t* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ int ld_relaxed(const int32_t* p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ uint32_t ld_relaxed_u(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_relaxed(int32_t* p, int v) {
+    asm volatile("st.relaxed.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void red_max(uint32_t* p, uint32_t v) {
+    asm volatile("red.relaxed.gpu.global.max.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ int atom_dec_acq_rel(int32_t* p) {
+    int old;
+    asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], -1;" : "=r"(old) : "l"(p) : "memory");
+    return old;
+}
+
+__device__ __forceinline__ void fence_acq_rel() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
+__device__ __forceinline__ uint64_t gtimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// ------------------------------------------------------------------ payload pieces (warp-wide)
+
+// y[i] = fma(a, x[i], y[i]) for i in [0, cnt): one warp, 16-byte vector accesses when x and y
+// share their alignment, streaming cache hints (each element is touched once).
+__device__ __forceinline__ void warp_saxpy_f32(float* __restrict__ y, const float* __restrict__ x, int64_t cnt,
+                                               float a, int lane) {
+    if ((((uintptr_t)y ^ (uintptr_t)x) & 15) == 0) {
+        int64_t head = (int64_t)(((16 - ((uintptr_t)y & 15)) & 15) >> 2);
+        if (head > cnt) head = cnt;
+        if (lane < head) y[lane] = __fmaf_rn(a, __ldcg(x + lane), __ldcg(y + lane));
+        y += head;
+        x += head;
+        cnt -= head;
+        const int64_t nv = cnt >> 2;
+        float4* __restrict__ y4 = reinterpret_cast<float4*>(y);
+        const float4* __restrict__ x4 = reinterpret_cast<const float4*>(x);
+        int64_t k = lane;
+        for (; k + 96 < nv; k += 128) {
+            float4 xv[4], yv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                xv[u] = __ldcs(x4 + k + 32 * u);
+                yv[u] = __ldcs(y4 + k + 32 * u);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                yv[u].x = __fmaf_rn(a, xv[u].x, yv[u].x);
+                yv[u].y = __fmaf_rn(a, xv[u].y, yv[u].y);
+                yv[u].z = __fmaf_rn(a, xv[u].z, yv[u].z);
+                yv[u].w = __fmaf_rn(a, xv[u].w, yv[u].w);
+                __stcs(y4 + k + 32 * u, yv[u]);
+            }
+        }
+        for (; k < nv; k += 32) {
+            const float4 xv = __ldcs(x4 + k);
+            float4 yv = __ldcs(y4 + k);
+            yv.x = __fmaf_rn(a, xv.x, yv.x);
+            yv.y = __fmaf_rn(a, xv.y, yv.y);
+            yv.z = __fmaf_rn(a, xv.z, yv.z);
+            yv.w = __fmaf_rn(a, xv.w, yv.w);
+            __stcs(y4 + k, yv);
+        }
+        const int64_t done = nv << 2;
+        if (lane < cnt - done) y[done + lane] = __fmaf_rn(a, __ldcg(x + done + lane), __ldcg(y + done + lane));
+    } else {
+        for (int64_t i = lane; i < cnt; i += 32) y[i] = __fmaf_rn(a, __ldcg(x + i), __ldcg(y + i));
+    }
+}
+
+// int32 saxpy with two's-complement wrap-around (unsigned arithmetic)
+__device__ __forceinline__ void warp_saxpy_i32(int32_t* __restrict__ y, const int32_t* __restrict__ x, int64_t cnt,
+                                               uint32_t a, int lane) {
+    if ((((uintptr_t)y ^ (uintptr_t)x) & 15) == 0) {
+        int64_t head = (int64_t)(((16 - ((uintptr_t)y & 15)) & 15) >> 2);
+        if (head > cnt) head = cnt;
+        if (lane < head) y[lane] = (int32_t)(a * (uint32_t)__ldcg(x + lane) + (uint32_t)__ldcg(y + lane));
+        y += head;
+        x += head;
+        cnt -= head;
+        const int64_t nv = cnt >> 2;
+        int4* __restrict__ y4 = reinterpret_cast<int4*>(y);
+        const int4* __restrict__ x4 = reinterpret_cast<const int4*>(x);
+        for (int64_t k = lane; k < nv; k += 32) {
+            const int4 xv = __ldcs(x4 + k);
+            int4 yv = __ldcs(y4 + k);
+            yv.x = (int32_t)(a * (uint32_t)xv.x + (uint32_t)yv.x);
+            yv.y = (int32_t)(a * (uint32_t)xv.y + (uint32_t)yv.y);
+            yv.z = (int32_t)(a * (uint32_t)xv.z + (uint32_t)yv.z);
+            yv.w = (int32_t)(a * (uint32_t)xv.w + (uint32_t)yv.w);
+            __stcs(y4 + k, yv);
+        }
+        const int64_t done = nv << 2;
+        if (lane < cnt - done)
+            y[done + lane] = (int32_t)(a * (uint32_t)__ldcg(x + done + lane) + (uint32_t)__ldcg(y + done + lane));
+    } else {
+        for (int64_t i = lane; i < cnt; i += 32) y[i] = (int32_t)(a * (uint32_t)__ldcg(x + i) + (uint32_t)__ldcg(y + i));
+    }
+}
+
+// byte copy (either end may be page-locked host memory reached over the host link)
+__device__ __forceinline__ void warp_copy(char* __restrict__ d, const char* __restrict__ s, int64_t cnt, int lane) {
+    if ((((uintptr_t)d ^ (uintptr_t)s) & 15) == 0) {
+        int64_t head = (int64_t)((16 - ((uintptr_t)d & 15)) & 15);
+        if (head > cnt) head = cnt;
+        if (lane < head) d[lane] = __ldcg(s + lane);
+        d += head;
+        s += head;
+        cnt -= head;
+        const int64_t nv = cnt >> 4;
+        uint4* __restrict__ d4 = reinterpret_cast<uint4*>(d);
+        const uint4* __restrict__ s4 = reinterpret_cast<const uint4*>(s);
+        int64_t k = lane;
+        for (; k + 96 < nv; k += 128) {
+            uint4 v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) v[u] = __ldcg(s4 + k + 32 * u);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) __stcg(d4 + k + 32 * u, v[u]);
+        }
+        for (; k < nv; k += 32) __stcg(d4 + k, __ldcg(s4 + k));
+        const int64_t done = nv << 4;
+        if (lane < cnt - done) d[done + lane] = __ldcg(s + done + lane);
+    } else {
+        for (int64_t i = lane; i < cnt; i += 32) d[i] = __ldcg(s + i);
+    }
+}
+
+__device__ __forceinline__ void run_piece(const DevPayload& P, int piece, int lane) {
+    const int64_t b0 = (int64_t)piece * P.chunk;
+    int64_t b1 = b0 + P.chunk;
+    if (b1 > P.n) b1 = P.n;
+    if (b1 <= b0) return;
+    if (P.op == kPaySaxpyF32) {
+        warp_saxpy_f32((float*)P.dst + b0, (const float*)P.src + b0, b1 - b0, __uint_as_float(P.a_bits), lane);
+    } else if (P.op == kPaySaxpyI32) {
+        warp_saxpy_i32((int32_t*)P.dst + b0, (const int32_t*)P.src + b0, b1 - b0, P.a_bits, lane);
+    } else {
+        warp_copy((char*)P.dst + b0, (const char*)P.src + b0, b1 - b0, lane);
+    }
+}
+
+// ------------------------------------------------------------------ level-synchronous kernel
+
+// Arrivals of one topological level (pull form over level-sorted in-edges; no atomics) plus
+// the payload pieces of that level's tasks. Blocks [0, nb_mp) do arrivals, one thread per
+// task; the remaining blocks do payload pieces, one warp per piece.
+template <bool PAY>
+__global__ void __launch_bounds__(256) k_level(const LevelArgs a) {
+    if ((int)blockIdx.x < a.nb_mp) {
+        const int p = a.p0 + (int)blockIdx.x * 256 + (int)threadIdx.x;
+        if (p >= a.p1) return;
+        const int v = __ldg(a.ls_node + p);
+        const int e0 = __ldg(a.ls_ptr + p), e1 = __ldg(a.ls_ptr + p + 1);
+        uint32_t best;
+        if (e0 == e1) {
+            best = a.key0 ? __ldg(a.key0 + v) : kKeyPosZero;
+        } else {
+            best = 0u;
+            int e = e0;
+            for (; e + 1 < e1; e += 2) {
+                const int2 i0 = __ldg(a.ls_in + e), i1 = __ldg(a.ls_in + e + 1);
+                const uint32_t k0 = __ldcg(a.key + i0.x), k1 = __ldcg(a.key + i1.x);
+                const uint32_t c0 = f2key(__fadd_rn(key2f(k0), __int_as_float(i0.y)));
+                const uint32_t c1 = f2key(__fadd_rn(key2f(k1), __int_as_float(i1.y)));
+                best = max(best, max(c0, c1));
+            }
+            if (e < e1) {
+                const int2 i0 = __ldg(a.ls_in + e);
+                best = max(best, f2key(__fadd_rn(key2f(__ldcg(a.key + i0.x)), __int_as_float(i0.y))));
+            }
+        }
+        a.key[v] = best;
+        return;
+    }
+    if (PAY) {
+        const int lane = threadIdx.x & 31;
+        const int wg = ((int)blockIdx.x - a.nb_mp) * 8 + ((int)threadIdx.x >> 5);
+        const int nw = ((int)gridDim.x - a.nb_mp) * 8;
+        for (int it = a.i0 + wg; it < a.i1; it += nw) {
+            const int2 w = __ldg(a.items + it);
+            run_piece(a.pay[w.x], w.y, lane);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ persistent executor
+
+__global__ void k_reset(const ResetArgs a) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int64_t i = tid; i < a.n_tasks; i += stride) {
+        const int d = a.indeg0[i] + (i == a.stall_task ? 1 : 0);
+        a.indeg[i] = d;
+        a.key[i] = a.indeg0[i] ? kKeyNegInf : (a.key0 ? a.key0[i] : kKeyPosZero);
+        if (a.t_start) {
+            a.t_start[i] = INT64_MAX;
+            a.t_end[i] = 0;
+        }
+        if (a.exec_count) {
+            a.exec_count[i] = 0;
+            a.tk_start[i] = -1;
+            a.tk_end[i] = -1;
+        }
+    }
+    for (int64_t i = tid; i < a.qcap; i += stride) {
+        int v = i < a.n_seed ? a.seeds[i] : -1;
+        if (v >= 0 && v == a.stall_task) v = -2;  // never a task id: its slot is skipped
+        a.queue[i] = v;
+    }
+    for (int64_t i = tid; i < a.n_pay; i += stride) a.chunks_left[i] = a.pay[i].nchunks;
+    if (tid == 0) {
+        a.ctrl->head = 0;
+        a.ctrl->tail = a.n_seed;
+        a.ctrl->done = 0;
+        a.ctrl->status = 0;
+        a.ctrl->abort = 0;
+        a.ctrl->ticket = 0;
+    }
+}
+
+// Pushes the ready tasks of this warp (lanes with v >= 0). Single-item tasks go to the warp's
+// shared-memory stack while it has room (up to local_keep), the rest and every piece of a
+// multi-piece payload task go to the global queue with one atomicAdd on the tail per warp.
+template <bool PAY>
+__device__ __forceinline__ void push_ready(const PersistArgs& a, int v, int32_t* stk, int& top, int lane) {
+    int nitems = 0;
+    int first_item = v;
+    if (v >= 0) {
+        nitems = 1;
+        if (PAY && a.pidx) {
+            const int p = __ldg(a.pidx + v);
+            if (p >= 0) {
+                const int nc = a.pay[p].nchunks;
+                if (nc > 1) {
+                    nitems = nc;
+                    first_item = a.n_tasks + a.pay[p].chunk_first;
+                }
+            }
+        }
+    }
+    // single items into the local stack
+    const bool single = (nitems == 1);
+    const unsigned sm = __ballot_sync(kFull, single);
+    const int room = a.local_keep - top;
+    const int rank = __popc(sm & lanemask_lt());
+    bool go_global = nitems > 0;
+    if (single && rank < room) {
+        stk[top + rank] = v;
+        go_global = false;
+    }
+    const int took = min(__popc(sm), max(room, 0));
+    top += took;
+    // the rest into the global queue
+    int cnt = go_global ? nitems : 0;
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const int total = __shfl_sync(kFull, incl, 31);
+    if (total == 0) {
+        __syncwarp();
+        return;
+    }
+    int base = 0;
+    if (lane == 0) base = atomicAdd(&a.ctrl->tail, total);
+    base = __shfl_sync(kFull, base, 0);
+    if ((int64_t)base + total > (int64_t)a.qcap) {  // cannot happen with a correct capacity
+        if (lane == 0) {
+            atomicExch(&a.ctrl->status, (int)HF_EQUEUE);
+            atomicExch(&a.ctrl->abort, 1);
+        }
+        __syncwarp();
+        return;
+    }
+    // make this lane's acquired view (and the ready task's inputs) visible before publishing
+    fence_acq_rel();
+    const int start = base + incl - cnt;
+    for (int k = 0; k < cnt; ++k) st_relaxed(a.queue + start + k, first_item + (nitems > 1 ? k : 0));
+    __syncwarp();
+}
+
+template <bool PAY>
+__global__ void __launch_bounds__(kWarpsPerCta * 32) k_persist(const PersistArgs a) {
+    __shared__ int32_t s_stack[kWarpsPerCta][kStackCap];
+    const int lane = threadIdx.x & 31;
+    int32_t* stk = s_stack[threadIdx.x >> 5];
+    int top = 0;
+    int qbase = 0;
+    unsigned pend = 0;
+    uint32_t last_done = 0xffffffffu;
+    uint64_t stall_t0 = 0;
+    unsigned backoff = 32;
+    const int n_tasks = a.n_tasks;
+
+    for (;;) {
+        int item = -1;
+        if (top > 0) {
+            const int take = min(top, 32);
+            if (lane < take) item = stk[top - take + lane];
+            top -= take;
+            __syncwarp();
+        } else {
+            if (pend == 0) {
+                int b = a.qcap;
+                if (lane == 0) {
+                    const int h = ld_relaxed(&a.ctrl->head);
+                    if (h < a.qcap) b = atomicAdd(&a.ctrl->head, a.claim);
+                }
+                b = __shfl_sync(kFull, b, 0);
+                qbase = b;
+                const int k = min(a.claim, a.qcap - b);
+                pend = k <= 0 ? 0u : (k >= 32 ? kFull : ((1u << k) - 1u));
+            }
+            if (pend & (1u << lane)) {
+                const int v = ld_acquire(a.queue + qbase + lane);
+                if (v >= 0) item = v;
+            }
+            pend &= ~__ballot_sync(kFull, item >= 0);
+        }
+        const unsigned got = __ballot_sync(kFull, item >= 0);
+        if (got == 0) {
+            int quit = 0;
+            if (lane == 0) {
+                const uint32_t d = ld_relaxed_u(&a.ctrl->done);
+                if (d >= (uint32_t)n_tasks || ld_relaxed(&a.ctrl->abort)) {
+                    quit = 1;
+                } else {
+                    const uint64_t now = gtimer();
+                    if (d != last_done) {
+                        last_done = d;
+                        stall_t0 = now;
+                    } else if (now - stall_t0 > a.spin_limit_ns) {
+                        atomicCAS(&a.ctrl->status, 0, (int)HF_ETIMEDOUT);
+                        atomicExch(&a.ctrl->abort, 1);
+                        quit = 1;
+                    }
+                }
+            }
+            if (__shfl_sync(kFull, quit, 0)) break;
+            __nanosleep(backoff);
+            backoff = min(backoff * 2u, 256u);
+            continue;
+        }
+        backoff = 32;
+
+        // ---- payload pieces; find the tasks that finish in this round
+        int fin = -1;
+        if (PAY && a.pidx) {
+            int t = -1, p = -1, piece = 0;
+            if (item >= 0) {
+                if (item < n_tasks) {
+                    t = item;
+                    p = __ldg(a.pidx + t);
+                } else {
+                    const int g = item - n_tasks;
+                    t = __ldg(a.chunk_task + g);
+                    p = __ldg(a.pidx + t);
+                    piece = g - a.pay[p].chunk_first;
+                }
+                if (a.t_start) {
+                    const int64_t now = (int64_t)gtimer();
+                    if (item < n_tasks) a.t_start[t] = now;
+                    else atomicMin((long long*)(a.t_start + t), (long long)now);
+                }
+                if (a.exec_count) {
+                    const long long tk = (long long)atomicAdd(&a.ctrl->ticket, 1ull);
+                    if (item < n_tasks) a.tk_start[t] = tk;
+                    else atomicCAS((unsigned long long*)(a.tk_start + t), ~0ull, (unsigned long long)tk);
+                }
+            }
+            unsigned work = __ballot_sync(kFull, p >= 0);
+            const bool had_work = work != 0;
+            while (work) {
+                const int src = __ffs(work) - 1;
+                work &= work - 1;
+                const int pp = __shfl_sync(kFull, p, src);
+                const int pc = __shfl_sync(kFull, piece, src);
+                run_piece(a.pay[pp], pc, lane);
+            }
+            if (had_work) {
+                fence_acq_rel();  // payload writes of every lane before any release below
+                __syncwarp();
+            }
+            if (item >= 0) {
+                if (p < 0 || item < n_tasks) fin = t;
+                else if (atom_dec_acq_rel(a.chunks_left + p) == 1) fin = t;
+            }
+        } else {
+            fin = item;
+            if (item >= 0) {
+                if (a.t_start) a.t_start[item] = (int64_t)gtimer();
+                if (a.exec_count) a.tk_start[item] = (int64_t)atomicAdd(&a.ctrl->ticket, 1ull);
+            }
+        }
+
+        // ---- finish: stamps, then release successors (warp-cooperative over all edges)
+        int r0 = 0, deg = 0;
+        uint32_t kt = 0;
+        if (fin >= 0) {
+            if (a.t_end) a.t_end[fin] = (int64_t)gtimer();
+            if (a.exec_count) {
+                a.tk_end[fin] = (int64_t)atomicAdd(&a.ctrl->ticket, 1ull);
+                atomicAdd(a.exec_count + fin, 1);
+            }
+            r0 = __ldg(a.row_ptr + fin);
+            deg = __ldg(a.row_ptr + fin + 1) - r0;
+            kt = ld_relaxed_u(a.key + fin);
+        }
+        int incl = deg;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int total = __shfl_sync(kFull, incl, 31);
+        const int excl = incl - deg;
+        for (int e0 = 0; e0 < total; e0 += 32) {
+            const int e = e0 + lane;
+            int owner = 0;
+#pragma unroll
+            for (int b = 16; b >= 1; b >>= 1) {
+                const int probe = owner + b - 1;
+                const int iv = __shfl_sync(kFull, incl, probe);
+                if (iv <= e) owner += b;
+            }
+            const int o_r0 = __shfl_sync(kFull, r0, owner);
+            const int o_ex = __shfl_sync(kFull, excl, owner);
+            const uint32_t o_k = __shfl_sync(kFull, kt, owner);
+            int ready = -1;
+            if (e < total) {
+                const int2 ed = __ldg(a.succ + o_r0 + (e - o_ex));
+                const float cand = __fadd_rn(key2f(o_k), __int_as_float(ed.y));
+                red_max(a.key + ed.x, f2key(cand));
+                if (atom_dec_acq_rel(a.indeg + ed.x) == 1) ready = ed.x;
+            }
+            if (__ballot_sync(kFull, ready >= 0)) push_ready<PAY>(a, ready, stk, top, lane);
+        }
+        const unsigned fm = __ballot_sync(kFull, fin >= 0);
+        if (fm && lane == 0) atomicAdd(&a.ctrl->done, (uint32_t)__popc(fm));
+    }
+}
+
+// New edge delays: delay[e] (edges in insertion order) into both edge layouts.
+__global__ void k_set_delays(const float* __restrict__ delay, const int32_t* __restrict__ pos_csr,
+                             const int32_t* __restrict__ pos_ls, int2* succ, int2* ls_in, int64_t m) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
+        const int b = __float_as_int(__ldg(delay + i));
+        reinterpret_cast<int*>(succ)[2 * (int64_t)__ldg(pos_csr + i) + 1] = b;
+        reinterpret_cast<int*>(ls_in)[2 * (int64_t)__ldg(pos_ls + i) + 1] = b;
+    }
+}
+
+__global__ void k_keys_to_f32(const uint32_t* __restrict__ key, float* __restrict__ out, int64_t n) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) out[i] = key2f(key[i]);
+}
+
+}  // namespace hf

@@ -1,0 +1,684 @@
+// plan.cu -- device-resident execution plans and the two executors' launch logic.
+//
+// A plan is one or more finalized graphs concatenated with task/edge offsets (a batch of
+// independent DAGs runs in one persistent launch, or level by level with all graphs' level l
+// merged into one kernel). It owns every device buffer the graphs need: successor CSR,
+// level-sorted predecessor lists, payload table, pull buffers, arrival keys, in-degree
+// counters, the ready queue and the control block.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "hf_internal.h"
+#include "kernels.cuh"
+
+namespace hf {
+
+struct HostTask {
+    int32_t level;
+    void (*fn)(void*);
+    void* arg;
+};
+
+struct Plan {
+    int32_t ngraphs = 0;
+    std::vector<int32_t> task_off;  // ngraphs + 1
+    int32_t n = 0;
+    int64_t m = 0;
+    int32_t levels = 0;
+    int32_t npay = 0;
+    bool any_key0 = false;
+    std::vector<HostTask> host_tasks;
+
+    // host copies needed when the piece size changes
+    std::vector<DevPayload> hpay;   // payload table (task-ordered by creation)
+    std::vector<int32_t> pay_task;  // payload -> task
+    std::vector<int32_t> pay_level; // payload -> level
+    std::vector<int32_t> hpidx;     // task -> payload or -1
+    std::vector<int32_t> sources;   // task ids with no predecessor
+    std::vector<int32_t> level_ptr; // merged level-sorted positions (levels + 1)
+
+    // device buffers
+    std::vector<void*> owned;
+    int32_t* d_row_ptr = nullptr;
+    int2* d_succ = nullptr;
+    int32_t* d_indeg0 = nullptr;
+    uint32_t* d_key0 = nullptr;
+    int32_t* d_pidx = nullptr;
+    DevPayload* d_pay = nullptr;
+    int32_t* d_ls_node = nullptr;
+    int32_t* d_ls_ptr = nullptr;
+    int2* d_ls_in = nullptr;
+    uint32_t* d_key = nullptr;
+    int32_t* d_indeg = nullptr;
+    int32_t* d_chunks_left = nullptr;
+    Ctrl* d_ctrl = nullptr;
+    float* d_arr = nullptr;  // conversion buffer for on_device = 0 reads
+    // piece-size dependent
+    int64_t chunk_elems = -1;
+    int32_t nitems = 0;               // total pieces of multi-piece payloads
+    int32_t qcap = 0;
+    int32_t nseed = 0;
+    int32_t* d_chunk_task = nullptr;  // sized for nitems
+    int32_t* d_seeds = nullptr;
+    int32_t* d_queue = nullptr;
+    int2* d_items = nullptr;          // level-sync payload items
+    std::vector<int32_t> item_ptr;    // levels + 1
+    size_t cap_chunk_task = 0, cap_seeds = 0, cap_queue = 0, cap_items = 0;
+    // instrumentation
+    int64_t* d_t_start = nullptr;
+    int64_t* d_t_end = nullptr;
+    int64_t* d_tk_start = nullptr;
+    int64_t* d_tk_end = nullptr;
+    int32_t* d_exec = nullptr;
+    bool last_instrument = false, last_validate = false;
+    // level-sync CUDA graph
+    cudaGraph_t lgraph = nullptr;
+    cudaGraphExec_t lexec = nullptr;
+    std::vector<LevelArgs> largs;
+    // runtime
+    int num_sms = 0;
+    cudaStream_t last_stream = nullptr;
+    cudaEvent_t done_ev = nullptr;
+    cudaEvent_t kev0 = nullptr, kev1 = nullptr;  // time_kernel runs
+    bool last_timed = false;
+    int32_t* d_epos_csr = nullptr;  // edge -> succ position (m)
+    int32_t* d_epos_ls = nullptr;   // edge -> ls_in position (m)
+    float* d_dly_stage = nullptr;   // host delays staged on the device (m)
+    bool ran = false;
+    int32_t* h_status = nullptr;  // page-locked mirror of ctrl->status
+};
+
+static void* palloc(Plan* p, size_t bytes, cudaStream_t s) {
+    void* d = dev_alloc(bytes, s);
+    if (d) p->owned.push_back(d);
+    return d;
+}
+
+template <typename T>
+static hf_status upload(Plan* p, T** dst, const T* src, size_t count, cudaStream_t s, const char* what) {
+    *dst = (T*)palloc(p, std::max<size_t>(count * sizeof(T), 16), s);
+    if (!*dst) return fail(HF_ENOMEM, std::string("device allocation failed: ") + what);
+    if (count) {
+        cudaError_t e = cudaMemcpyAsync(*dst, src, count * sizeof(T), cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return cuda_fail(e, what);
+    }
+    return HF_OK;
+}
+
+static void free_owned(Plan* p, void* ptr) {
+    if (!ptr) return;
+    auto it = std::find(p->owned.begin(), p->owned.end(), ptr);
+    if (it != p->owned.end()) p->owned.erase(it);
+    dev_free(ptr, nullptr);
+}
+
+// Device-visible address of page-locked host memory (NULL if `ptr` is not page-locked or not
+// mapped for the device): kernels reach pull sources and push targets through it.
+static void* host_dev_ptr(const void* ptr) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (at.type != cudaMemoryTypeHost) return nullptr;
+    return at.devicePointer;
+}
+
+static uint32_t host_f2key(float f) {
+    uint32_t b;
+    std::memcpy(&b, &f, 4);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+void plan_destroy(Plan* p) {
+    if (!p) return;
+    if (p->ran && p->done_ev) cudaEventSynchronize(p->done_ev);
+    if (p->lexec) cudaGraphExecDestroy(p->lexec);
+    if (p->lgraph) cudaGraphDestroy(p->lgraph);
+    for (void* d : p->owned) dev_free(d, nullptr);
+    if (p->h_status) cudaFreeHost(p->h_status);
+    if (p->done_ev) cudaEventDestroy(p->done_ev);
+    if (p->kev0) cudaEventDestroy(p->kev0);
+    if (p->kev1) cudaEventDestroy(p->kev1);
+    delete p;
+}
+
+hf_status plan_build(const std::vector<hf_graph*>& graphs, Plan** out) {
+    *out = nullptr;
+    Plan* p = new (std::nothrow) Plan();
+    if (!p) return fail(HF_ENOMEM, "host allocation failed");
+    cudaStream_t s = nullptr;
+    hf_status st = HF_OK;
+    auto bail = [&](hf_status e) {
+        plan_destroy(p);
+        return e;
+    };
+    int dev = 0;
+    cudaError_t ce = cudaGetDevice(&dev);
+    if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaGetDevice"));
+    ce = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaDeviceGetAttribute"));
+    ce = cudaEventCreateWithFlags(&p->done_ev, cudaEventDisableTiming);
+    if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaEventCreate"));
+    ce = cudaEventCreate(&p->kev0);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&p->kev1);
+    if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaEventCreate"));
+    ce = cudaHostAlloc((void**)&p->h_status, 64, cudaHostAllocDefault);
+    if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaHostAlloc"));
+    std::memset(p->h_status, 0, 64);
+
+    p->ngraphs = (int32_t)graphs.size();
+    p->task_off.assign((size_t)p->ngraphs + 1, 0);
+    int64_t ntot = 0, mtot = 0;
+    for (int i = 0; i < p->ngraphs; ++i) {
+        const hf_graph* g = graphs[(size_t)i];
+        if (g->dirty) return bail(fail(HF_ESTATE, "graph not finalized"));
+        ntot += g->fin.n;
+        mtot += g->fin.m;
+        p->levels = std::max(p->levels, g->fin.levels);
+        if (g->any_arr0) p->any_key0 = true;
+        if (ntot > INT32_MAX - 1 || mtot > INT32_MAX) return bail(fail(HF_EINVAL, "batch too large for 32-bit ids"));
+        p->task_off[(size_t)i + 1] = (int32_t)ntot;
+    }
+    p->n = (int32_t)ntot;
+    p->m = mtot;
+    const int32_t n = p->n;
+
+    try {
+        // successor CSR, in-degrees, sources, source arrival keys
+        std::vector<int32_t> row_ptr((size_t)n + 1);
+        std::vector<int2> succ((size_t)p->m);
+        std::vector<int32_t> indeg0((size_t)n);
+        std::vector<int32_t> epos_csr((size_t)p->m), epos_ls((size_t)p->m);
+        std::vector<uint32_t> key0;
+        if (p->any_key0) key0.resize((size_t)n);
+        int64_t eoff = 0;
+        for (int i = 0; i < p->ngraphs; ++i) {
+            const hf_graph* g = graphs[(size_t)i];
+            const Final& f = g->fin;
+            const int32_t toff = p->task_off[(size_t)i];
+            for (int32_t v = 0; v < f.n; ++v) {
+                row_ptr[(size_t)toff + v] = (int32_t)(eoff + f.row_ptr[v]);
+                indeg0[(size_t)toff + v] = f.indeg0[v];
+                if (f.indeg0[v] == 0) p->sources.push_back(toff + v);
+                if (p->any_key0) key0[(size_t)toff + v] = host_f2key(g->arr0[v]);
+            }
+            for (int64_t e = 0; e < f.m; ++e) {
+                int2 x = f.succ[(size_t)e];
+                x.x += toff;
+                succ[(size_t)(eoff + e)] = x;
+                epos_csr[(size_t)(eoff + e)] = (int32_t)(eoff + f.epos_csr[(size_t)e]);
+            }
+            eoff += f.m;
+        }
+        row_ptr[(size_t)n] = (int32_t)eoff;
+        // merged level-sorted order: level l of graph 0, level l of graph 1, ...
+        std::vector<int32_t> ls_node((size_t)n), ls_ptr((size_t)n + 1);
+        std::vector<int2> ls_in((size_t)p->m);
+        std::vector<int64_t> geoff((size_t)p->ngraphs + 1, 0);
+        for (int i = 0; i < p->ngraphs; ++i) geoff[(size_t)i + 1] = geoff[(size_t)i] + graphs[(size_t)i]->fin.m;
+        std::vector<int32_t> ls_where((size_t)p->m);  // graph-local ls position (offset by graph) -> merged
+        p->level_ptr.assign((size_t)p->levels + 1, 0);
+        {
+            int64_t pos = 0, ein = 0;
+            for (int32_t l = 0; l < p->levels; ++l) {
+                p->level_ptr[(size_t)l] = (int32_t)pos;
+                for (int i = 0; i < p->ngraphs; ++i) {
+                    const Final& f = graphs[(size_t)i]->fin;
+                    if (l >= f.levels) continue;
+                    const int32_t toff = p->task_off[(size_t)i];
+                    for (int32_t q = f.level_ptr[(size_t)l]; q < f.level_ptr[(size_t)l + 1]; ++q) {
+                        ls_node[(size_t)pos] = toff + f.ls_node[(size_t)q];
+                        ls_ptr[(size_t)pos] = (int32_t)ein;
+                        for (int32_t e = f.ls_ptr[(size_t)q]; e < f.ls_ptr[(size_t)q + 1]; ++e) {
+                            int2 x = f.ls_in[(size_t)e];
+                            x.x += toff;
+                            ls_where[(size_t)(geoff[(size_t)i] + e)] = (int32_t)ein;
+                            ls_in[(size_t)ein++] = x;
+                        }
+                        pos++;
+                    }
+                }
+            }
+            p->level_ptr[(size_t)p->levels] = (int32_t)pos;
+            ls_ptr[(size_t)n] = (int32_t)ein;
+            for (int i = 0; i < p->ngraphs; ++i) {
+                const Final& f = graphs[(size_t)i]->fin;
+                for (int64_t e = 0; e < f.m; ++e)
+                    epos_ls[(size_t)(geoff[(size_t)i] + e)] = ls_where[(size_t)(geoff[(size_t)i] + f.epos_ls[(size_t)e])];
+            }
+        }
+        // payloads: pull buffers first (saxpy and push tasks may reference them)
+        p->hpidx.assign((size_t)n, -1);
+        std::vector<std::vector<void*>> pull_buf((size_t)p->ngraphs);
+        for (int i = 0; i < p->ngraphs; ++i) {
+            const hf_graph* g = graphs[(size_t)i];
+            pull_buf[(size_t)i].assign(g->payloads.size(), nullptr);
+            for (size_t k = 0; k < g->payloads.size(); ++k) {
+                const PayloadRec& r = g->payloads[k];
+                if (r.kind != HF_PULL) continue;
+                if (r.bytes && !host_dev_ptr(r.host_src))
+                    return bail(fail(HF_EINVAL, "pull host buffer is not page-locked"));
+                void* d = palloc(p, ((r.bytes + 15) / 16) * 16, s);
+                if (!d) return bail(fail(HF_ENOMEM, "device allocation failed: pull buffer"));
+                pull_buf[(size_t)i][k] = d;
+            }
+        }
+        for (int i = 0; i < p->ngraphs; ++i) {
+            const hf_graph* g = graphs[(size_t)i];
+            const int32_t toff = p->task_off[(size_t)i];
+            for (int32_t v = 0; v < g->fin.n; ++v) {
+                const int32_t k = g->pay[(size_t)v];
+                if (k < 0) continue;
+                const PayloadRec& r = g->payloads[(size_t)k];
+                if (r.kind == HF_HOST) {
+                    p->host_tasks.push_back(HostTask{g->fin.level[(size_t)v], r.fn, r.arg});
+                    continue;
+                }
+                DevPayload d;
+                std::memset(&d, 0, sizeof(d));
+                d.nchunks = 1;
+                d.chunk_first = -1;
+                if (r.kind == HF_KERNEL) {
+                    d.op = r.op == HF_K_SAXPY_I32 ? kPaySaxpyI32 : kPaySaxpyF32;
+                    d.n = r.n;
+                    if (r.op == HF_K_SAXPY_I32) std::memcpy(&d.a_bits, &r.a_i, 4);
+                    else std::memcpy(&d.a_bits, &r.a_f, 4);
+                    d.dst = r.y_pull >= 0 ? pull_buf[(size_t)i][(size_t)g->pay[(size_t)r.y_pull]] : r.y_dev;
+                    d.src = r.x_pull >= 0 ? pull_buf[(size_t)i][(size_t)g->pay[(size_t)r.x_pull]] : r.x_dev;
+                } else if (r.kind == HF_PULL) {
+                    d.op = kPayCopy;
+                    d.n = (int64_t)r.bytes;
+                    d.dst = pull_buf[(size_t)i][(size_t)k];
+                    d.src = r.bytes ? host_dev_ptr(r.host_src) : nullptr;
+                } else {  // HF_PUSH
+                    void* hd = r.bytes ? host_dev_ptr(r.host_dst) : nullptr;
+                    if (r.bytes && !hd) return bail(fail(HF_EINVAL, "push host buffer is not page-locked"));
+                    d.op = kPayCopy;
+                    d.n = (int64_t)r.bytes;
+                    d.dst = hd;
+                    d.src = r.src_pull >= 0 ? pull_buf[(size_t)i][(size_t)g->pay[(size_t)r.src_pull]] : r.src_dev;
+                }
+                p->hpidx[(size_t)toff + v] = (int32_t)p->hpay.size();
+                p->hpay.push_back(d);
+                p->pay_task.push_back(toff + v);
+                p->pay_level.push_back(g->fin.level[(size_t)v]);
+            }
+        }
+        p->npay = (int32_t)p->hpay.size();
+
+        // uploads
+        if ((st = upload(p, &p->d_row_ptr, row_ptr.data(), row_ptr.size(), s, "row_ptr")) != HF_OK) return bail(st);
+        if ((st = upload(p, &p->d_succ, succ.data(), succ.size(), s, "succ")) != HF_OK) return bail(st);
+        if ((st = upload(p, &p->d_indeg0, indeg0.data(), indeg0.size(), s, "indeg0")) != HF_OK) return bail(st);
+        if (p->any_key0 && (st = upload(p, &p->d_key0, key0.data(), key0.size(), s, "key0")) != HF_OK) return bail(st);
+        if (p->npay && (st = upload(p, &p->d_pidx, p->hpidx.data(), p->hpidx.size(), s, "pidx")) != HF_OK)
+            return bail(st);
+        if ((st = upload(p, &p->d_ls_node, ls_node.data(), ls_node.size(), s, "ls_node")) != HF_OK) return bail(st);
+        if ((st = upload(p, &p->d_ls_ptr, ls_ptr.data(), ls_ptr.size(), s, "ls_ptr")) != HF_OK) return bail(st);
+        if ((st = upload(p, &p->d_ls_in, ls_in.data(), ls_in.size(), s, "ls_in")) != HF_OK) return bail(st);
+        if ((st = upload(p, &p->d_epos_csr, epos_csr.data(), epos_csr.size(), s, "epos")) != HF_OK) return bail(st);
+        if ((st = upload(p, &p->d_epos_ls, epos_ls.data(), epos_ls.size(), s, "epos")) != HF_OK) return bail(st);
+        p->d_pay = (DevPayload*)palloc(p, std::max<size_t>(sizeof(DevPayload) * (size_t)p->npay, 64), s);
+        p->d_key = (uint32_t*)palloc(p, std::max<size_t>(4 * (size_t)n, 16), s);
+        p->d_indeg = (int32_t*)palloc(p, std::max<size_t>(4 * (size_t)n, 16), s);
+        p->d_chunks_left = (int32_t*)palloc(p, std::max<size_t>(4 * (size_t)p->npay, 16), s);
+        p->d_ctrl = (Ctrl*)palloc(p, sizeof(Ctrl), s);
+        if (!p->d_pay || !p->d_key || !p->d_indeg || !p->d_chunks_left || !p->d_ctrl)
+            return bail(fail(HF_ENOMEM, "device allocation failed: runtime state"));
+        ce = cudaMemsetAsync(p->d_ctrl, 0, sizeof(Ctrl), s);
+        if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaMemsetAsync"));
+        ce = cudaStreamSynchronize(s);
+        if (ce != cudaSuccess) return bail(cuda_fail(ce, "plan upload"));
+    } catch (const std::bad_alloc&) {
+        return bail(fail(HF_ENOMEM, "host allocation failed in plan build"));
+    }
+    *out = p;
+    return HF_OK;
+}
+
+// Piece layout for a payload piece size: multi-piece payloads get consecutive piece-item
+// numbers after the task ids; level-sync gets a per-level list of (payload, piece) items.
+static hf_status plan_set_chunk(Plan* p, int64_t chunk_elems, cudaStream_t s) {
+    if (chunk_elems == p->chunk_elems) return HF_OK;
+    int64_t items = 0;
+    std::vector<int32_t> chunk_task;
+    std::vector<int32_t> seeds;
+    std::vector<int2> litems;
+    std::vector<int32_t> item_ptr((size_t)p->levels + 1, 0);
+    try {
+        for (int32_t k = 0; k < p->npay; ++k) {
+            DevPayload& d = p->hpay[(size_t)k];
+            const int64_t piece = d.op == kPayCopy ? chunk_elems * 4 : chunk_elems;
+            int64_t nc = (d.n + piece - 1) / piece;
+            if (nc < 1) nc = 1;
+            if (nc > INT32_MAX / 2) return fail(HF_EINVAL, "payload too large for the piece size");
+            d.chunk = piece;
+            d.nchunks = (int32_t)nc;
+            d.chunk_first = -1;
+            if (nc > 1) {
+                d.chunk_first = (int32_t)items;
+                for (int64_t c = 0; c < nc; ++c) chunk_task.push_back(p->pay_task[(size_t)k]);
+                items += nc;
+            }
+            item_ptr[(size_t)p->pay_level[(size_t)k] + 1] += (int32_t)nc;
+        }
+        if ((int64_t)p->n + items > INT32_MAX) return fail(HF_EINVAL, "too many payload pieces");
+        for (int32_t l = 0; l < p->levels; ++l) item_ptr[(size_t)l + 1] += item_ptr[(size_t)l];
+        litems.resize((size_t)item_ptr[(size_t)p->levels]);
+        {
+            std::vector<int32_t> fill(item_ptr.begin(), item_ptr.end() - 1);
+            for (int32_t k = 0; k < p->npay; ++k) {
+                const int32_t l = p->pay_level[(size_t)k];
+                for (int32_t c = 0; c < p->hpay[(size_t)k].nchunks; ++c) litems[(size_t)fill[(size_t)l]++] = make_int2(k, c);
+            }
+        }
+        for (int32_t t : p->sources) {
+            const int32_t k = p->hpidx.empty() ? -1 : p->hpidx[(size_t)t];
+            if (k >= 0 && p->hpay[(size_t)k].nchunks > 1) {
+                for (int32_t c = 0; c < p->hpay[(size_t)k].nchunks; ++c) seeds.push_back(p->n + p->hpay[(size_t)k].chunk_first + c);
+            } else {
+                seeds.push_back(t);
+            }
+        }
+    } catch (const std::bad_alloc&) {
+        return fail(HF_ENOMEM, "host allocation failed");
+    }
+    p->nitems = (int32_t)items;
+    p->qcap = p->n + (int32_t)items;
+    p->nseed = (int32_t)seeds.size();
+    p->item_ptr = item_ptr;
+    auto grow = [&](void** ptr, size_t& cap, size_t bytes) -> bool {
+        bytes = std::max<size_t>(bytes, 16);
+        if (cap >= bytes) return true;
+        free_owned(p, *ptr);
+        *ptr = palloc(p, bytes, s);
+        cap = *ptr ? bytes : 0;
+        return *ptr != nullptr;
+    };
+    if (!grow((void**)&p->d_chunk_task, p->cap_chunk_task, 4 * chunk_task.size()) ||
+        !grow((void**)&p->d_seeds, p->cap_seeds, 4 * seeds.size()) ||
+        !grow((void**)&p->d_queue, p->cap_queue, 4 * (size_t)p->qcap) ||
+        !grow((void**)&p->d_items, p->cap_items, 8 * litems.size()))
+        return fail(HF_ENOMEM, "device allocation failed: queue");
+    cudaError_t e = cudaSuccess;
+    if (!chunk_task.empty()) e = cudaMemcpyAsync(p->d_chunk_task, chunk_task.data(), 4 * chunk_task.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && !seeds.empty()) e = cudaMemcpyAsync(p->d_seeds, seeds.data(), 4 * seeds.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && !litems.empty()) e = cudaMemcpyAsync(p->d_items, litems.data(), 8 * litems.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && p->npay) e = cudaMemcpyAsync(p->d_pay, p->hpay.data(), sizeof(DevPayload) * (size_t)p->npay, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // host vectors die at return
+    if (e != cudaSuccess) return cuda_fail(e, "piece layout upload");
+    if (p->lexec) {
+        cudaGraphExecDestroy(p->lexec);
+        p->lexec = nullptr;
+    }
+    if (p->lgraph) {
+        cudaGraphDestroy(p->lgraph);
+        p->lgraph = nullptr;
+    }
+    p->chunk_elems = chunk_elems;
+    return HF_OK;
+}
+
+static hf_status ensure_instr(Plan* p, bool instrument, bool validate, cudaStream_t s) {
+    const size_t nb = std::max<size_t>(8 * (size_t)p->n, 16);
+    if (instrument && !p->d_t_start) {
+        p->d_t_start = (int64_t*)palloc(p, nb, s);
+        p->d_t_end = (int64_t*)palloc(p, nb, s);
+        if (!p->d_t_start || !p->d_t_end) return fail(HF_ENOMEM, "device allocation failed: timers");
+    }
+    if (validate && !p->d_exec) {
+        p->d_tk_start = (int64_t*)palloc(p, nb, s);
+        p->d_tk_end = (int64_t*)palloc(p, nb, s);
+        p->d_exec = (int32_t*)palloc(p, std::max<size_t>(4 * (size_t)p->n, 16), s);
+        if (!p->d_tk_start || !p->d_tk_end || !p->d_exec) return fail(HF_ENOMEM, "device allocation failed: tickets");
+    }
+    return HF_OK;
+}
+
+// Level-synchronous executor: one kernel node per level (arrivals + payload pieces of that
+// level) and one host node per host task, chained level after level in a CUDA graph.
+static hf_status build_level_graph(Plan* p) {
+    cudaError_t e = cudaGraphCreate(&p->lgraph, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphCreate");
+    p->largs.assign((size_t)p->levels, LevelArgs());
+    std::vector<cudaGraphNode_t> prev, cur;
+    std::vector<std::vector<const HostTask*>> host_at((size_t)p->levels);
+    for (const HostTask& h : p->host_tasks) host_at[(size_t)h.level].push_back(&h);
+    const bool pay = p->npay > 0;
+    for (int32_t l = 0; l < p->levels; ++l) {
+        cur.clear();
+        LevelArgs& a = p->largs[(size_t)l];
+        a.ls_node = p->d_ls_node;
+        a.ls_ptr = p->d_ls_ptr;
+        a.ls_in = p->d_ls_in;
+        a.key0 = p->d_key0;
+        a.key = p->d_key;
+        a.pay = p->d_pay;
+        a.items = p->d_items;
+        a.p0 = p->level_ptr[(size_t)l];
+        a.p1 = p->level_ptr[(size_t)l + 1];
+        a.i0 = p->item_ptr[(size_t)l];
+        a.i1 = p->item_ptr[(size_t)l + 1];
+        a.nb_mp = (a.p1 - a.p0 + 255) / 256;
+        const int items = a.i1 - a.i0;
+        const int nb_pay = items ? std::min((items + 7) / 8, p->num_sms * 8) : 0;
+        const int grid = a.nb_mp + nb_pay;
+        if (grid > 0) {
+            cudaKernelNodeParams kp = {};
+            kp.func = pay ? (void*)k_level<true> : (void*)k_level<false>;
+            kp.gridDim = dim3((unsigned)grid);
+            kp.blockDim = dim3(256);
+            void* args[1] = {&a};
+            kp.kernelParams = args;
+            cudaGraphNode_t node;
+            e = cudaGraphAddKernelNode(&node, p->lgraph, prev.data(), prev.size(), &kp);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaGraphAddKernelNode");
+            cur.push_back(node);
+        }
+        for (const HostTask* h : host_at[(size_t)l]) {
+            cudaHostNodeParams hp;
+            hp.fn = h->fn;
+            hp.userData = h->arg;
+            cudaGraphNode_t node;
+            e = cudaGraphAddHostNode(&node, p->lgraph, prev.data(), prev.size(), &hp);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaGraphAddHostNode");
+            cur.push_back(node);
+        }
+        if (!cur.empty()) prev.swap(cur);
+    }
+    e = cudaGraphInstantiate(&p->lexec, p->lgraph, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    return HF_OK;
+}
+
+hf_status plan_busy(Plan* p) {
+    if (!p || !p->ran) return HF_OK;
+    cudaError_t e = cudaEventQuery(p->done_ev);
+    if (e == cudaErrorNotReady) {
+        cudaGetLastError();
+        return HF_ESTATE;
+    }
+    return HF_OK;
+}
+
+hf_status plan_run(Plan* p, cudaStream_t s, const hf_run_opts& o) {
+    int mode = o.mode;
+    if (mode == HF_MODE_AUTO) mode = p->host_tasks.empty() ? HF_MODE_PERSISTENT : HF_MODE_LEVELSYNC;
+    if (mode != HF_MODE_LEVELSYNC && mode != HF_MODE_PERSISTENT) return fail(HF_EINVAL, "unknown mode");
+    if (mode == HF_MODE_PERSISTENT && !p->host_tasks.empty())
+        return fail(HF_ENOTSUP, "host tasks need the level-synchronous executor");
+    if (o.priority < HF_PRIO_FIFO || o.priority > HF_PRIO_LEARNED) return fail(HF_EINVAL, "unknown priority");
+    int64_t chunk = o.chunk_elems > 0 ? o.chunk_elems : 16384;
+    chunk = ((chunk + 31) / 32) * 32;
+    hf_status st = plan_set_chunk(p, chunk, s);
+    if (st != HF_OK) return st;
+    const bool instr = o.instrument != 0, valid = o.validate != 0;
+    if ((st = ensure_instr(p, instr, valid, s)) != HF_OK) return st;
+    cudaError_t e = cudaMemsetAsync(&p->d_ctrl->status, 0, sizeof(int32_t), s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    if (p->n > 0) {
+        if (mode == HF_MODE_LEVELSYNC) {
+            if (instr || valid) return fail(HF_ENOTSUP, "instrument/validate runs need the persistent executor");
+            if (!p->lexec && (st = build_level_graph(p)) != HF_OK) return st;
+            if (o.time_kernel) cudaEventRecord(p->kev0, s);
+            e = cudaGraphLaunch(p->lexec, s);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+            if (o.time_kernel) cudaEventRecord(p->kev1, s);
+        } else {
+            ResetArgs r;
+            r.n_tasks = p->n;
+            r.qcap = p->qcap;
+            r.n_seed = p->nseed;
+            r.n_pay = p->npay;
+            r.indeg0 = p->d_indeg0;
+            r.key0 = p->d_key0;
+            r.seeds = p->d_seeds;
+            r.pay = p->d_pay;
+            r.key = p->d_key;
+            r.indeg = p->d_indeg;
+            r.queue = p->d_queue;
+            r.chunks_left = p->d_chunks_left;
+            r.ctrl = p->d_ctrl;
+            r.t_start = instr ? p->d_t_start : nullptr;
+            r.t_end = instr ? p->d_t_end : nullptr;
+            r.tk_start = valid ? p->d_tk_start : nullptr;
+            r.tk_end = valid ? p->d_tk_end : nullptr;
+            r.exec_count = valid ? p->d_exec : nullptr;
+            r.stall_task = (o.stall_task >= 0 && o.stall_task < p->n) ? o.stall_task : -1;
+            const int64_t work = std::max<int64_t>(p->n, p->qcap);
+            const int rgrid = (int)std::min<int64_t>((work + 255) / 256, (int64_t)p->num_sms * 16);
+            k_reset<<<std::max(rgrid, 1), 256, 0, s>>>(r);
+            PersistArgs a;
+            std::memset(&a, 0, sizeof(a));
+            a.n_tasks = p->n;
+            a.qcap = p->qcap;
+            a.claim = std::min(std::max(o.claim, 1), 32);
+            a.local_keep = o.local_keep < 0 ? 32 : std::min(o.local_keep, kStackCap - 32);
+            a.spin_limit_ns = o.spin_limit_ns ? o.spin_limit_ns : 2000000000ull;
+            a.row_ptr = p->d_row_ptr;
+            a.succ = p->d_succ;
+            a.pidx = p->npay ? p->d_pidx : nullptr;
+            a.pay = p->d_pay;
+            a.chunk_task = p->d_chunk_task;
+            a.key = p->d_key;
+            a.indeg = p->d_indeg;
+            a.queue = p->d_queue;
+            a.chunks_left = p->d_chunks_left;
+            a.ctrl = p->d_ctrl;
+            a.t_start = r.t_start;
+            a.t_end = r.t_end;
+            a.tk_start = r.tk_start;
+            a.tk_end = r.tk_end;
+            a.exec_count = r.exec_count;
+            int ctas = o.ctas > 0 ? o.ctas : p->num_sms * 2;
+            if (o.time_kernel) cudaEventRecord(p->kev0, s);
+            if (p->npay) k_persist<true><<<ctas, kWarpsPerCta * 32, 0, s>>>(a);
+            else k_persist<false><<<ctas, kWarpsPerCta * 32, 0, s>>>(a);
+            if (o.time_kernel) cudaEventRecord(p->kev1, s);
+        }
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+    }
+    e = cudaMemcpyAsync(p->h_status, &p->d_ctrl->status, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail(e, "status copy");
+    e = cudaEventRecord(p->done_ev, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    p->last_stream = s;
+    p->ran = true;
+    p->last_timed = o.time_kernel && p->n > 0;
+    p->last_instrument = instr && mode == HF_MODE_PERSISTENT;
+    p->last_validate = valid && mode == HF_MODE_PERSISTENT;
+    return HF_OK;
+}
+
+hf_status plan_sync(Plan* p) {
+    if (!p->ran) return fail(HF_ESTATE, "not run");
+    cudaError_t e = cudaEventSynchronize(p->done_ev);
+    if (e != cudaSuccess) return cuda_fail(e, "run");
+    const int32_t s = p->h_status[0];
+    if (s == HF_ETIMEDOUT) return fail(HF_ETIMEDOUT, "persistent executor made no progress within the spin limit");
+    if (s != 0) return fail((hf_status)s, "device status " + std::to_string(s));
+    return HF_OK;
+}
+
+hf_status plan_get_arrivals(Plan* p, int32_t gi, float* out, int on_device) {
+    if (!p->ran) return fail(HF_ESTATE, "not run");
+    const int32_t off = gi < 0 ? 0 : p->task_off[(size_t)gi];
+    const int64_t cnt = gi < 0 ? p->n : p->task_off[(size_t)gi + 1] - off;
+    if (cnt == 0) return HF_OK;
+    if (!out) return fail(HF_EINVAL, "out is NULL");
+    cudaStream_t s = p->last_stream;
+    const int grid = (int)std::min<int64_t>((cnt + 255) / 256, 4096);
+    if (on_device) {
+        k_keys_to_f32<<<grid, 256, 0, s>>>(p->d_key + off, out, cnt);
+        cudaError_t e = cudaGetLastError();
+        return e == cudaSuccess ? HF_OK : cuda_fail(e, "key conversion");
+    }
+    if (!p->d_arr) {
+        p->d_arr = (float*)palloc(p, std::max<size_t>(4 * (size_t)p->n, 16), s);
+        if (!p->d_arr) return fail(HF_ENOMEM, "device allocation failed");
+    }
+    k_keys_to_f32<<<grid, 256, 0, s>>>(p->d_key + off, p->d_arr + off, cnt);
+    cudaError_t e = cudaMemcpyAsync(out, p->d_arr + off, 4 * (size_t)cnt, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return e == cudaSuccess ? HF_OK : cuda_fail(e, "arrival copy");
+}
+
+hf_status plan_get_times(Plan* p, int32_t gi, int64_t* a, int64_t* b) {
+    if (!p->ran || !p->last_instrument) return fail(HF_ESTATE, "last run was not instrumented");
+    const int32_t off = p->task_off[(size_t)gi];
+    const int64_t cnt = p->task_off[(size_t)gi + 1] - off;
+    cudaStream_t s = p->last_stream;
+    cudaError_t e = cudaSuccess;
+    if (a && cnt) e = cudaMemcpyAsync(a, p->d_t_start + off, 8 * (size_t)cnt, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && b && cnt) e = cudaMemcpyAsync(b, p->d_t_end + off, 8 * (size_t)cnt, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return e == cudaSuccess ? HF_OK : cuda_fail(e, "timer copy");
+}
+
+hf_status plan_get_stamps(Plan* p, int32_t gi, int64_t* a, int64_t* b, int32_t* c) {
+    if (!p->ran || !p->last_validate) return fail(HF_ESTATE, "last run was not a validate run");
+    const int32_t off = p->task_off[(size_t)gi];
+    const int64_t cnt = p->task_off[(size_t)gi + 1] - off;
+    cudaStream_t s = p->last_stream;
+    cudaError_t e = cudaSuccess;
+    if (a && cnt) e = cudaMemcpyAsync(a, p->d_tk_start + off, 8 * (size_t)cnt, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && b && cnt) e = cudaMemcpyAsync(b, p->d_tk_end + off, 8 * (size_t)cnt, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && c && cnt) e = cudaMemcpyAsync(c, p->d_exec + off, 4 * (size_t)cnt, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return e == cudaSuccess ? HF_OK : cuda_fail(e, "ticket copy");
+}
+
+hf_status plan_kernel_ms(Plan* p, float* ms) {
+    if (!p->ran || !p->last_timed) return fail(HF_ESTATE, "last run was not a time_kernel run");
+    cudaError_t e = cudaEventSynchronize(p->kev1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(ms, p->kev0, p->kev1);
+    return e == cudaSuccess ? HF_OK : cuda_fail(e, "cudaEventElapsedTime");
+}
+
+hf_status plan_set_delays(Plan* p, const float* delay, int on_device, cudaStream_t s) {
+    if (p->m == 0) return HF_OK;
+    if (!delay) return fail(HF_EINVAL, "delay is NULL");
+    const float* src = delay;
+    if (!on_device) {
+        for (int64_t i = 0; i < p->m; ++i)
+            if (!std::isfinite(delay[i])) return fail(HF_EINVAL, "delay " + std::to_string(i) + " is not finite");
+        if (!p->d_dly_stage) {
+            p->d_dly_stage = (float*)palloc(p, 4 * (size_t)p->m, s);
+            if (!p->d_dly_stage) return fail(HF_ENOMEM, "device allocation failed: delay staging");
+        }
+        cudaError_t e = cudaMemcpyAsync(p->d_dly_stage, delay, 4 * (size_t)p->m, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return cuda_fail(e, "delay copy");
+        src = p->d_dly_stage;
+    }
+    const int grid = (int)std::min<int64_t>((p->m + 255) / 256, (int64_t)p->num_sms * 16);
+    k_set_delays<<<grid, 256, 0, s>>>(src, p->d_epos_csr, p->d_epos_ls, p->d_succ, p->d_ls_in, p->m);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? HF_OK : cuda_fail(e, "delay scatter");
+}
+
+}  // namespace hf

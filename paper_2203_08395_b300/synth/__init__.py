@@ -87,8 +87,13 @@ def lib():
                                      ctypes.c_double, ctypes.c_double, ctypes.c_void_p]
         L.synth_fill_i32.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64,
                                      ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p]
+        L.synth_fill_multi_f32.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_void_p, ctypes.c_double, ctypes.c_double, ctypes.c_void_p]
+        L.synth_fill_multi_i32.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p]
         for f in ("synth_layered", "synth_circuit", "synth_random", "synth_pick", "synth_loguniform",
-                  "synth_uniform_f32", "synth_fill_f32", "synth_fill_i32"):
+                  "synth_uniform_f32", "synth_fill_f32", "synth_fill_i32", "synth_fill_multi_f32",
+                  "synth_fill_multi_i32"):
             getattr(L, f).restype = ctypes.c_int
         L.synth_value_f32.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64, ctypes.c_double,
                                       ctypes.c_double]
@@ -169,6 +174,26 @@ def fill_i32(seed, stream, n, lo, hi, first=0, out=None):
         out = np.empty(n, np.int32)
     assert out.dtype == np.int32 and out.flags.c_contiguous and out.size >= n
     _check(lib().synth_fill_i32(seed, stream, first, n, lo, hi, out.ctypes.data), "fill_i32")
+    return out
+
+
+def fill_multi(seed, streams, counts, offsets, out, lo, hi):
+    """Buffer j = the counter-based data of stream streams[j] (counts[j] elements), written
+    at out[offsets[j]:]; identical to fill_f32 / fill_i32 per buffer."""
+    streams = np.ascontiguousarray(streams, np.uint64)
+    counts = np.ascontiguousarray(counts, np.int64)
+    offsets = np.ascontiguousarray(offsets, np.int64)
+    assert streams.size == counts.size == offsets.size
+    if counts.size:
+        assert int((offsets + counts).max()) <= out.size
+    if out.dtype == np.float32:
+        rc = lib().synth_fill_multi_f32(seed, streams.size, streams.ctypes.data, counts.ctypes.data,
+                                        offsets.ctypes.data, lo, hi, out.ctypes.data)
+    else:
+        assert out.dtype == np.int32
+        rc = lib().synth_fill_multi_i32(seed, streams.size, streams.ctypes.data, counts.ctypes.data,
+                                        offsets.ctypes.data, int(lo), int(hi), out.ctypes.data)
+    _check(rc, "fill_multi")
     return out
 
 
@@ -285,31 +310,34 @@ def circuit(seed=0, n=1_000_000, levels=2000, name=None):
 def _add_saxpy_mix(g: GraphSpec, seed, frac, nmin, nmax, n_copy, a=2.0, i32=False):
     """Turn a max-plus graph into a mixed one: `frac` of its tasks become saxpy kernel tasks
     with sizes log-uniform on [nmin, nmax]; `n_copy` of those get a pull task (host -> x)
-    before them and a push task (y -> host) after them, appended as new task ids."""
+    before them and a push task (y -> host) after them. Pull tasks take the lowest ids
+    (a kernel task names its pull, so the pull is created first, as in the paper's
+    listings), the original tasks follow shifted by n_copy, the push tasks come last."""
     n = g.n
     k = int(round(frac * n))
     sx = pick(seed, 11, n, k)
-    g.kind[sx] = KIND_SAXPY_I32 if i32 else KIND_SAXPY
-    g.sx_task = sx
+    kind = g.kind.copy()
+    kind[sx] = KIND_SAXPY_I32 if i32 else KIND_SAXPY
+    c = int(n_copy)
     g.sx_n = loguniform(seed, 12, k, nmin, nmax)
     g.sx_a = np.full(k, a, np.float32)
     g.sx_pull = np.full(k, -1, np.int32)
-    if n_copy:
-        sel = pick(seed, 13, k, n_copy)  # indices into the saxpy list
-        pl = np.arange(n, n + n_copy, dtype=np.int32)
-        ps = np.arange(n + n_copy, n + 2 * n_copy, dtype=np.int32)
+    src, dst, dly = g.src + c, g.dst + c, g.delay
+    g.sx_task = (sx + c).astype(np.int32)
+    if c:
+        sel = pick(seed, 13, k, c)  # indices into the saxpy list
+        pl = np.arange(0, c, dtype=np.int32)
+        ps = np.arange(n + c, n + 2 * c, dtype=np.int32)
         g.sx_pull[sel] = pl
         g.pl_task, g.pl_saxpy = pl, sel.astype(np.int32)
         g.ps_task, g.ps_saxpy = ps, sel.astype(np.int32)
-        cd = uniform_f32(seed, 14, 2 * n_copy, 0.01, 1.0)
-        esrc = np.concatenate([pl, sx[sel]]).astype(np.int32)
-        edst = np.concatenate([sx[sel], ps]).astype(np.int32)
-        g.src = np.concatenate([g.src, esrc])
-        g.dst = np.concatenate([g.dst, edst])
-        g.delay = np.concatenate([g.delay, cd])
-        g.kind = np.concatenate([g.kind, np.full(n_copy, KIND_PULL, np.uint8),
-                                 np.full(n_copy, KIND_PUSH, np.uint8)])
-        g.n = n + 2 * n_copy
+        cd = uniform_f32(seed, 14, 2 * c, 0.01, 1.0)
+        src = np.concatenate([src, pl, g.sx_task[sel]]).astype(np.int32)
+        dst = np.concatenate([dst, g.sx_task[sel], ps]).astype(np.int32)
+        dly = np.concatenate([dly, cd])
+        kind = np.concatenate([np.full(c, KIND_PULL, np.uint8), kind, np.full(c, KIND_PUSH, np.uint8)])
+    g.src, g.dst, g.delay, g.kind = src.astype(np.int32), dst.astype(np.int32), dly.astype(np.float32), kind
+    g.n = n + 2 * c
     g.data_seed = seed
     return g
 

@@ -397,3 +397,27 @@ int synth_fill_i32(uint64_t seed, uint64_t stream, int64_t first, int64_t n, int
     for (int64_t i = 0; i < n; ++i) out[i] = synth_value_i32(seed, stream, first + i, lo, hi);
     return 0;
 }
+
+/* Many counter-based buffers at once: buffer j (stream streams[j], counts[j] elements) is
+ * written at out + offsets[j]; same values as synth_fill_f32 / synth_fill_i32 per buffer. */
+int synth_fill_multi_f32(uint64_t seed, int64_t k, const uint64_t* streams, const int64_t* counts,
+                         const int64_t* offsets, double lo, double hi, float* out) {
+    if (k < 0 || (k > 0 && (!streams || !counts || !offsets || !out))) return -1;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t j = 0; j < k; ++j) {
+        float* o = out + offsets[j];
+        for (int64_t i = 0; i < counts[j]; ++i) o[i] = synth_value_f32(seed, streams[j], i, lo, hi);
+    }
+    return 0;
+}
+
+int synth_fill_multi_i32(uint64_t seed, int64_t k, const uint64_t* streams, const int64_t* counts,
+                         const int64_t* offsets, int32_t lo, int32_t hi, int32_t* out) {
+    if (k < 0 || hi < lo || (k > 0 && (!streams || !counts || !offsets || !out))) return -1;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t j = 0; j < k; ++j) {
+        int32_t* o = out + offsets[j];
+        for (int64_t i = 0; i < counts[j]; ++i) o[i] = synth_value_i32(seed, streams[j], i, lo, hi);
+    }
+    return 0;
+}

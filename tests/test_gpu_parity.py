@@ -1,0 +1,340 @@
+"""GPU parity: both executors against the CPU oracle, through the C ABI, bit for bit.
+
+Arrivals must match exactly (each sum has fixed inputs and max is exact, so every schedule
+gives the oracle's bits); saxpy and copy results must match exactly (fmaf on both sides).
+Covers the paper's worked examples (Section I saxpy graph, Section III-A eight-task graph),
+every workload shape at sizes the oracle finishes in seconds, the full-size workloads, edge
+cases (empty, single task, deep chain, wide fan-out/fan-in, ragged payload pieces) and the
+bounded-wait failure path.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2203_08395_b300 import build as B
+from paper_2203_08395_b300 import hf
+from paper_2203_08395_b300 import synth as S
+from paper_2203_08395_b300.workload import BatchOnDevice, GraphOnDevice
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+EXECUTORS = {
+    "levelsync": dict(mode=hf.HF_MODE_LEVELSYNC),
+    "persistent": dict(mode=hf.HF_MODE_PERSISTENT),
+    "persistent_claim8": dict(mode=hf.HF_MODE_PERSISTENT, claim=8),
+    "persistent_nolocal": dict(mode=hf.HF_MODE_PERSISTENT, local_keep=0),
+    "persistent_1cta": dict(mode=hf.HF_MODE_PERSISTENT, ctas=1),
+    "persistent_wide": dict(mode=hf.HF_MODE_PERSISTENT, ctas=148 * 8, claim=4),
+}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    B.build()
+    hf.load()
+    hf.install_torch_allocator()
+    torch.cuda.init()
+
+
+def bits(a):
+    return np.ascontiguousarray(a, np.float32).view(np.uint32)
+
+
+def _run(gd, **opts):
+    gd.run(**opts)
+    gd.sync()
+    return gd.arrivals()
+
+
+@pytest.mark.parametrize("ex", sorted(EXECUTORS))
+def test_layered10k_bit_exact(ex):
+    spec = S.config("layered10k").graphs[0]
+    ref = oracle.run_spec(spec)["arr"]
+    gd = GraphOnDevice(spec)
+    np.testing.assert_array_equal(bits(_run(gd, **EXECUTORS[ex])), bits(ref))
+    # a second run gives the same bits
+    np.testing.assert_array_equal(bits(_run(gd, **EXECUTORS[ex])), bits(ref))
+    gd.close()
+
+
+@pytest.mark.parametrize("ex", ["levelsync", "persistent", "persistent_claim8"])
+def test_random_graphs_100_seeds(ex):
+    rng = np.random.default_rng(5)
+    for seed in range(100):
+        n = int(rng.integers(1, 3000))
+        win = int(rng.choice([0, 4, 64]))
+        n_, _, src, dst, dly = S.random_dag(seed, n, 1, int(rng.integers(1, 9)), window=win)
+        # signed delays and signed-zero source arrivals exercise the full key order
+        if seed % 3 == 0:
+            dly = rng.normal(0, 3, dly.size).astype(np.float32)
+            dly[rng.random(dly.size) < 0.05] = -0.0
+        arr0 = rng.choice([0.0, -0.0, 2.5, -7.0], n_).astype(np.float32) if seed % 2 else None
+        spec = S.GraphSpec(name="r%d" % seed, n=n_, src=src, dst=dst, delay=dly,
+                           kind=np.zeros(n_, np.uint8), arr0=arr0)
+        ref = oracle.run_spec(spec)["arr"]
+        gd = GraphOnDevice(spec)
+        np.testing.assert_array_equal(bits(_run(gd, **EXECUTORS[ex])), bits(ref), err_msg="seed %d" % seed)
+        gd.close()
+
+
+def test_validate_exactly_once_and_order():
+    spec = S.circuit(1, 200_000, 400)
+    gd = GraphOnDevice(spec)
+    gd.run(mode=hf.HF_MODE_PERSISTENT, validate=1)
+    gd.sync()
+    s0, s1, cnt = hf.hf_get_stamps(gd.g, spec.n)
+    assert np.all(cnt == 1)
+    assert np.all(s0 >= 0) and np.all(s0 < s1)
+    assert np.all(s1[spec.src] < s0[spec.dst])
+    np.testing.assert_array_equal(bits(gd.arrivals()), bits(oracle.run_spec(spec)["arr"]))
+    gd.close()
+
+
+@pytest.mark.parametrize("ex", ["levelsync", "persistent", "persistent_claim8"])
+def test_circuit1m_full_size(ex):
+    spec = S.config("circuit1m").graphs[0]
+    ref = oracle.run_spec(spec)["arr"]
+    gd = GraphOnDevice(spec)
+    np.testing.assert_array_equal(bits(_run(gd, **EXECUTORS[ex])), bits(ref))
+    gd.close()
+
+
+def _check_payloads(gd, ref):
+    spec = gd.spec
+    for j in range(spec.sx_task.size):
+        np.testing.assert_array_equal(gd.y_of(j).cpu().numpy().view(np.uint32), ref["y"][j].view(np.uint32),
+                                      err_msg="saxpy %d" % j)
+    for i in range(spec.ps_task.size):
+        np.testing.assert_array_equal(gd.push_of(i).numpy().view(np.uint32), ref["push"][i].view(np.uint32),
+                                      err_msg="push %d" % i)
+
+
+@pytest.mark.parametrize("chunk", [0, 64, 4096])
+@pytest.mark.parametrize("ex", ["levelsync", "persistent", "persistent_claim8"])
+def test_mixed_small_with_payloads(ex, chunk):
+    spec = S.mixed(3, n=6000, nmin=1, nmax=20000, n_copy=300)
+    ref = oracle.run_spec(spec)
+    gd = GraphOnDevice(spec)
+    arr = _run(gd, chunk_elems=chunk, **EXECUTORS[ex])
+    np.testing.assert_array_equal(bits(arr), bits(ref["arr"]))
+    _check_payloads(gd, ref)
+    gd.close()
+
+
+def test_mixed100k_full_size_sampled():
+    spec = S.config("mixed100k").graphs[0]
+    ref = oracle.run_spec(spec, with_data=False)
+    gd = GraphOnDevice(spec)
+    rng = np.random.default_rng(0)
+    sample = rng.choice(spec.sx_task.size, 64, replace=False)
+    for ex in ["levelsync", "persistent"]:
+        gd.reset_y()
+        arr = _run(gd, **EXECUTORS[ex])
+        np.testing.assert_array_equal(bits(arr), bits(ref["arr"]))
+        for j in sample:
+            x = spec.pull_data(j) if spec.sx_pull[j] >= 0 else spec.init_x(j)
+            yref = oracle.saxpy_f32(spec.sx_a[j], x, spec.init_y(j))
+            np.testing.assert_array_equal(gd.y_of(j).cpu().numpy().view(np.uint32), yref.view(np.uint32))
+        for i in range(0, spec.ps_task.size, 50):
+            j = int(spec.ps_saxpy[i])
+            yref = oracle.saxpy_f32(spec.sx_a[j], spec.pull_data(j), spec.init_y(j))
+            np.testing.assert_array_equal(gd.push_of(i).numpy().view(np.uint32), yref.view(np.uint32))
+    gd.close()
+
+
+@pytest.mark.parametrize("ex", ["levelsync", "persistent"])
+def test_batch256_full_size(ex):
+    wl = S.config("batch256")
+    bd = BatchOnDevice(wl)
+    bd.run(**EXECUTORS[ex])
+    bd.sync()
+    for i, spec in enumerate(wl.graphs):
+        ref = oracle.run_spec(spec)["arr"]
+        np.testing.assert_array_equal(bits(bd.arrivals(i)), bits(ref), err_msg="graph %d" % i)
+    bd.close()
+
+
+@pytest.mark.parametrize("ex", ["levelsync", "persistent"])
+def test_batch_mixed_small(ex):
+    wl = S.batch(2, graphs=12, nmin=500, nmax=20000, frac_saxpy=0.1, sx_min=1, sx_max=3000)
+    bd = BatchOnDevice(wl)
+    bd.run(chunk_elems=256, **EXECUTORS[ex])
+    bd.sync()
+    for i, spec in enumerate(wl.graphs):
+        ref = oracle.run_spec(spec)
+        np.testing.assert_array_equal(bits(bd.arrivals(i)), bits(ref["arr"]))
+        _check_payloads(bd.graphs[i], ref)
+    bd.close()
+
+
+# ------------------------------------------------------------------ the paper's examples
+
+def test_paper_saxpy_graph_through_c_abi():
+    """Listing 1 / Figure 1: host tasks fill x with 1 and y with 2, pulls copy them to the GPU,
+    the int32 kernel computes y = 2x + y, pushes copy both back: every y is 4."""
+    from golden_io import load
+
+    gold = load("paper_saxpy_graph.txt")
+    P = gold["params"]
+    N = P["N"]
+    x = torch.zeros(N, dtype=torch.int32, pin_memory=True)
+    y = torch.zeros(N, dtype=torch.int32, pin_memory=True)
+    host = {"x": x, "y": y}
+    fills = {"x": P["x"], "y": P["y"]}
+    calls = []
+
+    def make_host(name):
+        def fn(arg):
+            host[name].fill_(fills[name])
+            calls.append(name)
+        return hf.HOST_FN(fn)
+
+    g = hf.hf_graph_create()
+    ids = {}
+    keep = []
+    for t in gold["tasks"]:
+        nm, kind = t[0], t[1]
+        if kind == "host":
+            f = make_host(t[2])
+            keep.append(f)
+            ids[nm] = hf.hf_add_task(g, hf.HF_HOST, hf.hf_host_payload(fn=f, arg=None))
+        elif kind == "pull":
+            ids[nm] = hf.hf_add_task(g, hf.HF_PULL, hf.hf_pull_payload(host_ptr=host[t[2]].data_ptr(), bytes=4 * N))
+        elif kind == "saxpy_i32":
+            p = hf.hf_saxpy_payload(op=hf.HF_K_SAXPY_I32, a_i=P["a"], n=N, x_pull=ids[t[2]], y_pull=ids[t[3]])
+            ids[nm] = hf.hf_add_task(g, hf.HF_KERNEL, p)
+        elif kind == "push":
+            p = hf.hf_push_payload(src_pull=ids[t[2]], host_ptr=host[t[3]].data_ptr(), bytes=4 * N)
+            ids[nm] = hf.hf_add_task(g, hf.HF_PUSH, p)
+    for a, b in gold["edges"]:
+        hf.hf_precede(g, ids[a], ids[b])
+    hf.hf_run(g, None, hf.hf_run_opts_default(mode=hf.HF_MODE_LEVELSYNC))
+    hf.hf_sync_status(g)
+    assert sorted(calls) == ["x", "y"]
+    assert bool((y == P["expect_y"]).all()) and bool((x == P["expect_x"]).all())
+    # host tasks are not supported by the persistent executor (reported, not silently run)
+    with pytest.raises(hf.HfError) as ei:
+        hf.hf_run(g, None, hf.hf_run_opts_default(mode=hf.HF_MODE_PERSISTENT))
+    assert ei.value.status == hf.HF_ENOTSUP
+    hf.hf_graph_destroy(g)
+
+
+def test_paper_saxpy_graph_persistent_without_host_tasks():
+    N = 65536
+    x = torch.full((N,), 1, dtype=torch.int32, pin_memory=True)
+    y = torch.full((N,), 2, dtype=torch.int32, pin_memory=True)
+    g = hf.hf_graph_create()
+    px = hf.hf_add_task(g, hf.HF_PULL, hf.hf_pull_payload(host_ptr=x.data_ptr(), bytes=4 * N))
+    py = hf.hf_add_task(g, hf.HF_PULL, hf.hf_pull_payload(host_ptr=y.data_ptr(), bytes=4 * N))
+    k = hf.hf_add_task(g, hf.HF_KERNEL, hf.hf_saxpy_payload(op=hf.HF_K_SAXPY_I32, a_i=2, n=N, x_pull=px, y_pull=py))
+    sx = hf.hf_add_task(g, hf.HF_PUSH, hf.hf_push_payload(src_pull=px, host_ptr=x.data_ptr(), bytes=4 * N))
+    sy = hf.hf_add_task(g, hf.HF_PUSH, hf.hf_push_payload(src_pull=py, host_ptr=y.data_ptr(), bytes=4 * N))
+    for a, b in [(px, k), (py, k), (k, sx), (k, sy)]:
+        hf.hf_precede(g, a, b)
+    hf.hf_run(g, None, hf.hf_run_opts_default(mode=hf.HF_MODE_PERSISTENT, chunk_elems=4096, validate=1))
+    hf.hf_sync_status(g)
+    assert bool((y == 4).all()) and bool((x == 1).all())
+    s0, s1, c = hf.hf_get_stamps(g, 5)
+    assert np.all(c == 1)
+    for a, b in [(px, k), (py, k), (k, sx), (k, sy)]:
+        assert s1[a] < s0[b]
+    hf.hf_graph_destroy(g)
+
+
+def test_paper_dependency_graph_order():
+    from golden_io import load
+
+    gold = load("paper_dependency_graph.txt")
+    names = [t[0] for t in gold["tasks"]]
+    ix = {nm: i for i, nm in enumerate(names)}
+    g = hf.hf_graph_create()
+    hf.hf_add_tasks_bulk(g, len(names))
+    for a, b in gold["edges"]:
+        hf.hf_precede_w(g, ix[a], ix[b], 1.0)
+    hf.hf_run(g, None, hf.hf_run_opts_default(mode=hf.HF_MODE_PERSISTENT, validate=1))
+    hf.hf_sync_status(g)
+    s0, s1, c = hf.hf_get_stamps(g, len(names))
+    assert np.all(c == 1)
+    for a, b in gold["edges"] + gold["reach"]:
+        assert s1[ix[a]] < s0[ix[b]]
+    arr = hf.hf_get_arrivals(g, len(names))
+    assert arr[ix["push2"]] == 4.0 and arr[ix["kernel2"]] == 3.0
+    hf.hf_graph_destroy(g)
+
+
+# ------------------------------------------------------------------ edge cases
+
+@pytest.mark.parametrize("ex", ["levelsync", "persistent"])
+def test_edge_cases(ex):
+    o = EXECUTORS[ex]
+    # empty graph
+    g = hf.hf_graph_create()
+    hf.hf_run(g, None, hf.hf_run_opts_default(**o))
+    hf.hf_sync_status(g)
+    hf.hf_graph_destroy(g)
+    # single task with a source arrival
+    g = hf.hf_graph_create()
+    hf.hf_add_task(g, hf.HF_KERNEL, hf.hf_maxplus_payload(op=hf.HF_K_MAXPLUS, arr0=-3.5))
+    hf.hf_run(g, None, hf.hf_run_opts_default(**o))
+    hf.hf_sync_status(g)
+    assert hf.hf_get_arrivals(g, 1)[0] == np.float32(-3.5)
+    hf.hf_graph_destroy(g)
+    rng = np.random.default_rng(1)
+    cases = []
+    n = 5000  # deep chain
+    cases.append((n, np.arange(n - 1), np.arange(1, n), rng.uniform(0, 1, n - 1)))
+    n = 5001  # one task fanning out to 5000, then all of them into one sink
+    src = np.concatenate([np.zeros(4999), np.arange(1, 5000)])
+    dst = np.concatenate([np.arange(1, 5000), np.full(4999, 5000)])
+    cases.append((n, src, dst, rng.normal(0, 1, src.size)))
+    n = 3000  # duplicate edges and many sources
+    src = rng.integers(0, 1500, 20000)
+    dst = rng.integers(1500, 3000, 20000)
+    cases.append((n, src, dst, rng.uniform(-1, 1, src.size)))
+    for n, src, dst, d in cases:
+        spec = S.GraphSpec(name="edge", n=n, src=np.asarray(src, np.int32), dst=np.asarray(dst, np.int32),
+                           delay=np.asarray(d, np.float32), kind=np.zeros(n, np.uint8))
+        gd = GraphOnDevice(spec)
+        np.testing.assert_array_equal(bits(_run(gd, **o)), bits(oracle.run_spec(spec)["arr"]))
+        gd.close()
+
+
+def test_arrivals_on_device():
+    spec = S.layered(7, 5000, 20, 1, 4)
+    gd = GraphOnDevice(spec)
+    gd.run(mode=hf.HF_MODE_PERSISTENT)
+    out = torch.empty(spec.n, dtype=torch.float32, device="cuda")
+    hf.hf_get_arrivals(gd.g, spec.n, out, on_device=True)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(bits(out.cpu().numpy()), bits(oracle.run_spec(spec)["arr"]))
+    gd.close()
+
+
+def test_stalled_task_times_out_and_context_survives():
+    """Failure path without a GPU fault: one task's counter starts one too high, so it never
+    becomes ready; the persistent kernel's bounded waits end the run with HF_ETIMEDOUT and the
+    next run on the same context is correct."""
+    spec = S.layered(8, 20000, 40, 1, 4)
+    gd = GraphOnDevice(spec)
+    gd.run(mode=hf.HF_MODE_PERSISTENT, stall_task=12345, spin_limit_ns=50_000_000)
+    assert gd.sync(check=False) == hf.HF_ETIMEDOUT
+    gd.run(mode=hf.HF_MODE_PERSISTENT)
+    gd.sync()
+    np.testing.assert_array_equal(bits(gd.arrivals()), bits(oracle.run_spec(spec)["arr"]))
+    gd.close()
+
+
+def test_unpinned_pull_buffer_rejected():
+    g = hf.hf_graph_create()
+    buf = np.zeros(16, np.float32)  # pageable host memory
+    hf.hf_add_task(g, hf.HF_PULL, hf.hf_pull_payload(host_ptr=buf.ctypes.data, bytes=64))
+    with pytest.raises(hf.HfError) as ei:
+        hf.hf_run(g, None, hf.hf_run_opts_default())
+    assert ei.value.status == hf.HF_EINVAL
+    hf.hf_graph_destroy(g)
