@@ -223,6 +223,67 @@ hf_status hf_batch_kernel_ms(hf_batch* b, float* ms);
  * concatenated in batch order (sum of their edge counts). */
 hf_status hf_batch_set_delays(hf_batch* b, const float* delay, int on_device, void* stream);
 
+/* --- learned cost model ------------------------------------------------------------------
+ * The paper's scheduler (Section III-C) orders ready tasks with a plain heuristic (FIFO work
+ * stealing); it has no learned component. This library adds one, kept beside the heuristic:
+ * an MLP 12 -> 64 -> 64 -> 1 (ReLU, BF16 weights and activations, FP32 accumulation and FP32
+ * master weights) maps per-task features to a predicted log task cost (log ns of the time a
+ * warp spends on the task, as the instrumented executor records it). Predicted costs give
+ * bottom-level weights b(v) = c(v) + max over successors b(s) (the remaining critical path)
+ * that order the persistent executor's ready tasks; predicted makespans choose between the
+ * executors in HF_MODE_AUTO. Results (arrivals, payload data) never depend on the model.
+ *
+ * Parameter vector (HF_COSTMODEL_PARAMS floats, row-major): W1[64][12], b1[64], W2[64][64],
+ * b2[64], w3[64], b3. W1, W2, w3 are used rounded to BF16 (round to nearest even).
+ * Feature vector per task (HF_FEATURES floats): one-hot max-plus / saxpy / pull / push,
+ * log1p(fan-in), log1p(fan-out), level / levels, log1p(level), log1p(payload bytes),
+ * log1p(tasks of its graph), log1p(edges of its graph), log1p(mean fan-out of successors). */
+
+#define HF_COSTMODEL_PARAMS 5057
+#define HF_FEATURES 12
+
+typedef struct hf_costmodel hf_costmodel;
+
+/* New model with He-uniform weights (limit sqrt(6/fan_in)) drawn from `seed`, zero biases. */
+hf_status hf_costmodel_create(hf_costmodel** out, uint64_t seed);
+hf_status hf_costmodel_destroy(hf_costmodel* cm);
+/* Host arrays of HF_COSTMODEL_PARAMS floats (FP32 master weights); set also resets Adam. */
+hf_status hf_costmodel_set_params(hf_costmodel* cm, const float* params);
+hf_status hf_costmodel_get_params(hf_costmodel* cm, float* params);
+hf_status hf_costmodel_save(hf_costmodel* cm, const char* path);  /* flat FP32 file */
+hf_status hf_costmodel_load(hf_costmodel* cm, const char* path);
+
+/* Device arrays: X[n][12] features, y[n] predictions (log ns). Enqueued on `stream`. */
+hf_status hf_costmodel_forward(hf_costmodel* cm, const float* X, int64_t n, float* y, void* stream);
+/* Gradient of mean((y - t)^2) over the n rows w.r.t. the parameter vector (device grad[P],
+ * overwritten) and the loss (device float, overwritten). */
+hf_status hf_costmodel_grad(hf_costmodel* cm, const float* X, const float* t, int64_t n, float* grad,
+                            float* loss, void* stream);
+/* One Adam update (beta1 0.9, beta2 0.999, eps 1e-8; bias-corrected) with device grad[P]. */
+hf_status hf_costmodel_adam_step(hf_costmodel* cm, const float* grad, float lr, void* stream);
+/* Mini-batch Adam training on device rows (X, t): `epochs` passes in an order shuffled by
+ * `seed`, `batch` rows per step. *final_loss (host) = loss over all rows afterwards. Blocks. */
+hf_status hf_costmodel_train(hf_costmodel* cm, const float* X, const float* t, int64_t n, int32_t epochs,
+                             int32_t batch, float lr, uint64_t seed, float* final_loss, void* stream);
+
+/* Features of every task of the batch (graphs concatenated in batch order) into device
+ * X[sum of tasks][12]; and of a single graph. */
+hf_status hf_batch_features(hf_batch* b, float* X, void* stream);
+hf_status hf_features(hf_graph* g, float* X, void* stream);
+
+/* Attach a model to a batch (NULL detaches): HF_PRIO_LEARNED and HF_MODE_AUTO use it. The
+ * model is borrowed; weights are read when priorities are (re)computed (first run with a
+ * priority mode after attaching, or hf_batch_refresh_priorities). */
+hf_status hf_batch_set_costmodel(hf_batch* b, hf_costmodel* cm);
+hf_status hf_batch_refresh_priorities(hf_batch* b, void* stream);
+/* Per-task predicted cost (ns) and bottom-level weight under `priority` (HEURISTIC or
+ * LEARNED), device arrays of the batch's task count. */
+hf_status hf_batch_task_costs(hf_batch* b, int32_t priority, float* cost, float* bottom, void* stream);
+/* Bottom-level weights for caller-given per-task costs (device arrays of the batch's task
+ * count): b(v) = c(v) + max over successors b(s) in FP32 (one rounded add per task), sinks
+ * b = c. Enqueued on `stream`. */
+hf_status hf_batch_bottom_levels(hf_batch* b, const float* cost, float* bottom, void* stream);
+
 /* --- memory and diagnostics ------------------------------------------------------------ */
 
 /* Process-wide device allocator for library-owned buffers (NULL, NULL = cudaMalloc/cudaFree).

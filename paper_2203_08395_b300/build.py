@@ -14,7 +14,7 @@ LIB = os.path.join(HERE, "libhf.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cpp", "plan.cu"]
+SOURCES = ["api.cpp", "plan.cu", "costmodel.cu"]
 HEADERS = ["hf_internal.h", "kernels.cuh"]
 
 

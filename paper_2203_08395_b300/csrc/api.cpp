@@ -569,10 +569,67 @@ hf_status hf_batch_add(hf_batch* b, hf_graph* g, int32_t* index_out) {
     return HF_OK;
 }
 
+static hf_status ensure_batch_plan(hf_batch* b) {
+    if (b->plan) return HF_OK;
+    hf_status st = plan_build(b->graphs, &b->plan);
+    if (st != HF_OK) return st;
+    plan_set_costmodel(b->plan, b->cm);
+    return HF_OK;
+}
+
+hf_status hf_batch_set_costmodel(hf_batch* b, hf_costmodel* cm) {
+    if (!b) return fail(HF_EINVAL, "batch is NULL");
+    if (b->plan && plan_busy(b->plan) != HF_OK) return fail(HF_ESTATE, "a run of this batch is in flight");
+    b->cm = cm;
+    if (b->plan) plan_set_costmodel(b->plan, cm);
+    return HF_OK;
+}
+
+hf_status hf_batch_refresh_priorities(hf_batch* b, void* stream) {
+    if (!b) return fail(HF_EINVAL, "batch is NULL");
+    hf_status st = ensure_batch_plan(b);
+    if (st != HF_OK) return st;
+    if (plan_busy(b->plan) != HF_OK) return fail(HF_ESTATE, "a run of this batch is in flight");
+    return plan_refresh_priorities(b->plan, b->cm, (cudaStream_t)stream);
+}
+
+hf_status hf_batch_features(hf_batch* b, float* X, void* stream) {
+    if (!b) return fail(HF_EINVAL, "batch is NULL");
+    hf_status st = ensure_batch_plan(b);
+    if (st != HF_OK) return st;
+    return plan_features(b->plan, X, (cudaStream_t)stream);
+}
+
+hf_status hf_features(hf_graph* g, float* X, void* stream) {
+    if (!g) return fail(HF_EINVAL, "graph is NULL");
+    if (g->dirty && g->plan) {
+        if (plan_busy(g->plan) != HF_OK) return fail(HF_ESTATE, "a run of this graph is in flight");
+        plan_destroy(g->plan);
+        g->plan = nullptr;
+    }
+    hf_status st = ensure_plan(g);
+    if (st != HF_OK) return st;
+    return plan_features(g->plan, X, (cudaStream_t)stream);
+}
+
+hf_status hf_batch_task_costs(hf_batch* b, int32_t priority, float* cost, float* bottom, void* stream) {
+    if (!b) return fail(HF_EINVAL, "batch is NULL");
+    hf_status st = ensure_batch_plan(b);
+    if (st != HF_OK) return st;
+    return plan_task_costs(b->plan, priority, b->cm, cost, bottom, (cudaStream_t)stream);
+}
+
+hf_status hf_batch_bottom_levels(hf_batch* b, const float* cost, float* bottom, void* stream) {
+    if (!b) return fail(HF_EINVAL, "batch is NULL");
+    hf_status st = ensure_batch_plan(b);
+    if (st != HF_OK) return st;
+    return plan_bottom_levels(b->plan, cost, bottom, (cudaStream_t)stream);
+}
+
 hf_status hf_batch_run(hf_batch* b, void* stream, const hf_run_opts* opts) {
     if (!b) return fail(HF_EINVAL, "batch is NULL");
-    if (!b->plan) {
-        hf_status st = plan_build(b->graphs, &b->plan);
+    {
+        hf_status st = ensure_batch_plan(b);
         if (st != HF_OK) return st;
     }
     hf_run_opts o;
@@ -609,10 +666,8 @@ hf_status hf_batch_kernel_ms(hf_batch* b, float* ms) {
 
 hf_status hf_batch_set_delays(hf_batch* b, const float* delay, int on_device, void* stream) {
     if (!b) return fail(HF_EINVAL, "batch is NULL");
-    if (!b->plan) {
-        hf_status st = plan_build(b->graphs, &b->plan);
-        if (st != HF_OK) return st;
-    }
+    hf_status st = ensure_batch_plan(b);
+    if (st != HF_OK) return st;
     return plan_set_delays(b->plan, delay, on_device, (cudaStream_t)stream);
 }
 

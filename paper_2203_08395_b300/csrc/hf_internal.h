@@ -57,13 +57,14 @@ struct PersistArgs {
     int32_t claim;
     int32_t local_keep;
     uint64_t spin_limit_ns;
-    const int32_t* row_ptr;  // n_tasks + 1
-    const int2* succ;        // edges {successor, delay bits}, CSR order
+    const int2* meta;        // n_tasks {first out-edge, out-degree}
+    const int4* erec;        // out-edges, CSR order: {successor, delay bits, successor's first
+                             // out-edge, successor's out-degree << 16 | in-degree (or marks)}
     const int32_t* pidx;     // n_tasks payload index or -1 (NULL: no payloads)
     const DevPayload* pay;
     const int32_t* chunk_task;  // chunk item -> task
-    uint32_t* key;              // n_tasks arrival keys
-    int32_t* indeg;             // n_tasks pending-predecessor counters
+    unsigned long long* state;  // n_tasks {key << 32 | pending predecessors}
+    uint32_t* key;              // n_tasks final arrival keys (output)
     int32_t* queue;             // qcap ready-queue slots (-1 = empty)
     int32_t* chunks_left;       // per payload: pieces still running
     Ctrl* ctrl;
@@ -73,6 +74,10 @@ struct PersistArgs {
     int64_t* tk_end;
     int32_t* exec_count;
 };
+
+// Successors with more than this many predecessors are released with a max on the key half
+// and a fenced decrement of the count half instead of one CAS on the packed state.
+constexpr int32_t kNarrowIn = 64;
 
 // Arguments of the reset kernel run before each persistent launch.
 struct ResetArgs {
@@ -86,8 +91,7 @@ struct ResetArgs {
     const uint32_t* key0;  // NULL: sources start at +0
     const int32_t* seeds;
     const DevPayload* pay;
-    uint32_t* key;
-    int32_t* indeg;
+    unsigned long long* state;
     int32_t* queue;
     int32_t* chunks_left;
     Ctrl* ctrl;
@@ -176,6 +180,7 @@ struct hf_batch {
     std::vector<hf_graph*> graphs;
     hf::Plan* plan = nullptr;
     bool dirty = true;
+    hf_costmodel* cm = nullptr;  // borrowed
 };
 
 namespace hf {
@@ -199,5 +204,15 @@ hf_status plan_get_times(Plan* p, int32_t gi, int64_t* a, int64_t* b);
 hf_status plan_get_stamps(Plan* p, int32_t gi, int64_t* a, int64_t* b, int32_t* c);
 hf_status plan_kernel_ms(Plan* p, float* ms);
 hf_status plan_set_delays(Plan* p, const float* delay, int on_device, cudaStream_t s);
+hf_status plan_features(Plan* p, float* X, cudaStream_t s);
+hf_status plan_task_costs(Plan* p, int32_t priority, const hf_costmodel* cm, float* cost, float* bottom,
+                          cudaStream_t s);
+hf_status plan_refresh_priorities(Plan* p, const hf_costmodel* cm, cudaStream_t s);
+void plan_set_costmodel(Plan* p, const hf_costmodel* cm);
+hf_status plan_bottom_levels(Plan* p, const float* cost, float* bottom, cudaStream_t s);
+
+// costmodel.cu
+hf_status mlp_forward(const float* params, const float* X, int64_t n, float* y, cudaStream_t s);
+const float* costmodel_params(const hf_costmodel* cm);
 
 }  // namespace hf

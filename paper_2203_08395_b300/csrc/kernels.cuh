@@ -242,14 +242,40 @@ __global__ void __launch_bounds__(256) k_level(const LevelArgs a) {
 }
 
 // ------------------------------------------------------------------ persistent executor
+//
+// Per-task state is one 64-bit word: arrival key (high 32 bits) and pending-predecessor count
+// (low 32 bits). A finished predecessor u releases successor v with one compare-and-swap that
+// raises the key to max(key, key(arr[u] + d(u,v))) and decrements the count together, so the
+// predecessor that brings the count to zero learns v's final arrival from the CAS itself and
+// no memory fence is needed for max-plus tasks (only payload tasks, whose data other tasks
+// read, fence before releasing and after becoming ready). The successor edge record carries
+// v's in-degree, so the first CAS is issued without reading v's state. Tasks with more than
+// kNarrowIn predecessors use a 32-bit max on the key half, a fence and an atomic decrement on
+// the count half instead, which avoids CAS retry storms on wide joins.
+
+constexpr uint32_t kWideMark = 0xFFFFu;  // edge record: successor is a wide join
+constexpr uint32_t kLongMark = 0xFFFFu;  // edge record: successor's out-degree does not fit 16 bits
+
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ int atom_dec_relaxed(int32_t* p) {
+    int old;
+    asm volatile("atom.relaxed.gpu.global.add.s32 %0, [%1], -1;" : "=r"(old) : "l"(p) : "memory");
+    return old;
+}
 
 __global__ void k_reset(const ResetArgs a) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     for (int64_t i = tid; i < a.n_tasks; i += stride) {
-        const int d = a.indeg0[i] + (i == a.stall_task ? 1 : 0);
-        a.indeg[i] = d;
-        a.key[i] = a.indeg0[i] ? kKeyNegInf : (a.key0 ? a.key0[i] : kKeyPosZero);
+        const int d = a.indeg0[i];
+        const uint32_t k = d ? kKeyNegInf : (a.key0 ? a.key0[i] : kKeyPosZero);
+        const uint32_t c = (uint32_t)d + (i == a.stall_task ? 1u : 0u);
+        a.state[i] = ((unsigned long long)k << 32) | c;
         if (a.t_start) {
             a.t_start[i] = INT64_MAX;
             a.t_end[i] = 0;
@@ -276,11 +302,13 @@ __global__ void k_reset(const ResetArgs a) {
     }
 }
 
-// Pushes the ready tasks of this warp (lanes with v >= 0). Single-item tasks go to the warp's
-// shared-memory stack while it has room (up to local_keep), the rest and every piece of a
-// multi-piece payload task go to the global queue with one atomicAdd on the tail per warp.
+// Pushes this warp's ready tasks (lanes with r.x >= 0; r = {task, key, row start, out-degree}).
+// Single-item tasks go to the warp's shared-memory stack while it has room (up to local_keep);
+// the rest, and every piece of a multi-piece payload task, go to the global queue with one
+// atomicAdd on its tail per warp.
 template <bool PAY>
-__device__ __forceinline__ void push_ready(const PersistArgs& a, int v, int32_t* stk, int& top, int lane) {
+__device__ __forceinline__ void push_ready(const PersistArgs& a, int4 r, int4* stk, int& top, int lane) {
+    const int v = r.x;
     int nitems = 0;
     int first_item = v;
     if (v >= 0) {
@@ -296,19 +324,16 @@ __device__ __forceinline__ void push_ready(const PersistArgs& a, int v, int32_t*
             }
         }
     }
-    // single items into the local stack
     const bool single = (nitems == 1);
     const unsigned sm = __ballot_sync(kFull, single);
     const int room = a.local_keep - top;
     const int rank = __popc(sm & lanemask_lt());
     bool go_global = nitems > 0;
     if (single && rank < room) {
-        stk[top + rank] = v;
+        stk[top + rank] = r;
         go_global = false;
     }
-    const int took = min(__popc(sm), max(room, 0));
-    top += took;
-    // the rest into the global queue
+    top += min(__popc(sm), max(room, 0));
     int cnt = go_global ? nitems : 0;
     int incl = cnt;
 #pragma unroll
@@ -332,18 +357,46 @@ __device__ __forceinline__ void push_ready(const PersistArgs& a, int v, int32_t*
         __syncwarp();
         return;
     }
-    // make this lane's acquired view (and the ready task's inputs) visible before publishing
-    fence_acq_rel();
+    fence_acq_rel();  // release: the ready task's state (and inputs) before its queue slot
     const int start = base + incl - cnt;
     for (int k = 0; k < cnt; ++k) st_relaxed(a.queue + start + k, first_item + (nitems > 1 ? k : 0));
     __syncwarp();
 }
 
+// Releases successor v of a finished task: returns true when v becomes ready, with its final
+// key in *kv. rec.w holds v's in-degree (kWideMark for wide joins) in its low 16 bits.
+__device__ __forceinline__ bool release_succ(const PersistArgs& a, int v, uint32_t ck, uint32_t f16,
+                                             uint32_t* kv) {
+    unsigned long long* st = a.state + v;
+    if (f16 != kWideMark) {
+        unsigned long long expected = ((unsigned long long)kKeyNegInf << 32) | f16;
+        unsigned long long desired;
+        for (;;) {
+            const uint32_t ek = (uint32_t)(expected >> 32);
+            const uint32_t ec = (uint32_t)expected;
+            desired = ((unsigned long long)max(ek, ck) << 32) | (unsigned long long)(ec - 1u);
+            const unsigned long long prev = atomicCAS(st, expected, desired);
+            if (prev == expected) break;
+            expected = prev;
+        }
+        *kv = (uint32_t)(desired >> 32);
+        return (uint32_t)desired == 0u;
+    }
+    uint32_t* khalf = reinterpret_cast<uint32_t*>(st) + 1;
+    int32_t* chalf = reinterpret_cast<int32_t*>(st);
+    red_max(khalf, ck);
+    fence_acq_rel();
+    if (atom_dec_relaxed(chalf) != 1) return false;
+    fence_acq_rel();
+    *kv = ld_relaxed_u(khalf);
+    return true;
+}
+
 template <bool PAY>
 __global__ void __launch_bounds__(kWarpsPerCta * 32) k_persist(const PersistArgs a) {
-    __shared__ int32_t s_stack[kWarpsPerCta][kStackCap];
+    __shared__ int4 s_stack[kWarpsPerCta][kStackCap];
     const int lane = threadIdx.x & 31;
-    int32_t* stk = s_stack[threadIdx.x >> 5];
+    int4* stk = s_stack[threadIdx.x >> 5];
     int top = 0;
     int qbase = 0;
     unsigned pend = 0;
@@ -354,9 +407,13 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_persist(const PersistArgs
 
     for (;;) {
         int item = -1;
+        int4 loc = make_int4(-1, 0, 0, 0);
         if (top > 0) {
             const int take = min(top, 32);
-            if (lane < take) item = stk[top - take + lane];
+            if (lane < take) {
+                loc = stk[top - take + lane];
+                item = loc.x;
+            }
             top -= take;
             __syncwarp();
         } else {
@@ -403,8 +460,16 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_persist(const PersistArgs
         }
         backoff = 32;
 
-        // ---- payload pieces; find the tasks that finish in this round
+        // ---- resolve items; run payload pieces; find the tasks that finish in this round
         int fin = -1;
+        uint32_t kt = 0;
+        int rs = 0, deg = 0;
+        bool known = loc.x >= 0;  // key and row came with the item from the local stack
+        if (known) {
+            kt = (uint32_t)loc.y;
+            rs = loc.z;
+            deg = loc.w;
+        }
         if (PAY && a.pidx) {
             int t = -1, p = -1, piece = 0;
             if (item >= 0) {
@@ -429,21 +494,24 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_persist(const PersistArgs
                 }
             }
             unsigned work = __ballot_sync(kFull, p >= 0);
-            const bool had_work = work != 0;
-            while (work) {
-                const int src = __ffs(work) - 1;
-                work &= work - 1;
-                const int pp = __shfl_sync(kFull, p, src);
-                const int pc = __shfl_sync(kFull, piece, src);
-                run_piece(a.pay[pp], pc, lane);
-            }
-            if (had_work) {
-                fence_acq_rel();  // payload writes of every lane before any release below
+            if (work) {
+                fence_acq_rel();  // acquire: inputs written by the payload tasks before us
+                const unsigned w0 = work;
+                while (work) {
+                    const int src = __ffs(work) - 1;
+                    work &= work - 1;
+                    const int pp = __shfl_sync(kFull, p, src);
+                    const int pc = __shfl_sync(kFull, piece, src);
+                    run_piece(a.pay[pp], pc, lane);
+                }
+                (void)w0;
+                fence_acq_rel();  // release: every lane's payload writes before any release below
                 __syncwarp();
             }
             if (item >= 0) {
                 if (p < 0 || item < n_tasks) fin = t;
                 else if (atom_dec_acq_rel(a.chunks_left + p) == 1) fin = t;
+                if (item >= n_tasks) known = false;  // a piece carries no key/row
             }
         } else {
             fin = item;
@@ -453,18 +521,22 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_persist(const PersistArgs
             }
         }
 
-        // ---- finish: stamps, then release successors (warp-cooperative over all edges)
-        int r0 = 0, deg = 0;
-        uint32_t kt = 0;
+        // ---- finish: key and row of tasks that came from the global queue, stamps, arrival
         if (fin >= 0) {
+            if (!known) {
+                const int2 mt = __ldg(a.meta + fin);
+                rs = mt.x;
+                deg = mt.y;
+                kt = (uint32_t)(ld_relaxed_u64(a.state + fin) >> 32);
+            }
             if (a.t_end) a.t_end[fin] = (int64_t)gtimer();
             if (a.exec_count) {
                 a.tk_end[fin] = (int64_t)atomicAdd(&a.ctrl->ticket, 1ull);
                 atomicAdd(a.exec_count + fin, 1);
             }
-            r0 = __ldg(a.row_ptr + fin);
-            deg = __ldg(a.row_ptr + fin + 1) - r0;
-            kt = ld_relaxed_u(a.key + fin);
+            a.key[fin] = kt;
+        } else {
+            deg = 0;
         }
         int incl = deg;
 #pragma unroll
@@ -483,17 +555,21 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_persist(const PersistArgs
                 const int iv = __shfl_sync(kFull, incl, probe);
                 if (iv <= e) owner += b;
             }
-            const int o_r0 = __shfl_sync(kFull, r0, owner);
+            const int o_rs = __shfl_sync(kFull, rs, owner);
             const int o_ex = __shfl_sync(kFull, excl, owner);
             const uint32_t o_k = __shfl_sync(kFull, kt, owner);
-            int ready = -1;
+            int4 r = make_int4(-1, 0, 0, 0);
             if (e < total) {
-                const int2 ed = __ldg(a.succ + o_r0 + (e - o_ex));
-                const float cand = __fadd_rn(key2f(o_k), __int_as_float(ed.y));
-                red_max(a.key + ed.x, f2key(cand));
-                if (atom_dec_acq_rel(a.indeg + ed.x) == 1) ready = ed.x;
+                const int4 rec = __ldg(a.erec + o_rs + (e - o_ex));
+                const float cand = __fadd_rn(key2f(o_k), __int_as_float(rec.y));
+                uint32_t kv;
+                if (release_succ(a, rec.x, f2key(cand), (uint32_t)rec.w & 0xFFFFu, &kv)) {
+                    int len = (int)((uint32_t)rec.w >> 16);
+                    if ((uint32_t)len == kLongMark) len = __ldg(a.meta + rec.x).y;
+                    r = make_int4(rec.x, (int)kv, rec.z, len);
+                }
             }
-            if (__ballot_sync(kFull, ready >= 0)) push_ready<PAY>(a, ready, stk, top, lane);
+            if (__ballot_sync(kFull, r.x >= 0)) push_ready<PAY>(a, r, stk, top, lane);
         }
         const unsigned fm = __ballot_sync(kFull, fin >= 0);
         if (fm && lane == 0) atomicAdd(&a.ctrl->done, (uint32_t)__popc(fm));
@@ -502,11 +578,11 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_persist(const PersistArgs
 
 // New edge delays: delay[e] (edges in insertion order) into both edge layouts.
 __global__ void k_set_delays(const float* __restrict__ delay, const int32_t* __restrict__ pos_csr,
-                             const int32_t* __restrict__ pos_ls, int2* succ, int2* ls_in, int64_t m) {
+                             const int32_t* __restrict__ pos_ls, int4* erec, int2* ls_in, int64_t m) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
         const int b = __float_as_int(__ldg(delay + i));
-        reinterpret_cast<int*>(succ)[2 * (int64_t)__ldg(pos_csr + i) + 1] = b;
+        reinterpret_cast<int*>(erec)[4 * (int64_t)__ldg(pos_csr + i) + 1] = b;
         reinterpret_cast<int*>(ls_in)[2 * (int64_t)__ldg(pos_ls + i) + 1] = b;
     }
 }

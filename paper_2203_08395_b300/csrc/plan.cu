@@ -43,7 +43,9 @@ struct Plan {
     // device buffers
     std::vector<void*> owned;
     int32_t* d_row_ptr = nullptr;
-    int2* d_succ = nullptr;
+    int4* d_erec = nullptr;  // successor edge records (persistent executor)
+    int2* d_meta = nullptr;  // {first out-edge, out-degree} per task
+    unsigned long long* d_state = nullptr;
     int32_t* d_indeg0 = nullptr;
     uint32_t* d_key0 = nullptr;
     int32_t* d_pidx = nullptr;
@@ -52,7 +54,6 @@ struct Plan {
     int32_t* d_ls_ptr = nullptr;
     int2* d_ls_in = nullptr;
     uint32_t* d_key = nullptr;
-    int32_t* d_indeg = nullptr;
     int32_t* d_chunks_left = nullptr;
     Ctrl* d_ctrl = nullptr;
     float* d_arr = nullptr;  // conversion buffer for on_device = 0 reads
@@ -89,7 +90,26 @@ struct Plan {
     float* d_dly_stage = nullptr;   // host delays staged on the device (m)
     bool ran = false;
     int32_t* h_status = nullptr;  // page-locked mirror of ctrl->status
+    // cost model inputs and outputs (built on first use)
+    std::vector<int32_t> h_level;  // task -> level within its graph
+    std::vector<uint8_t> h_cat;    // task -> 0 max-plus, 1 saxpy, 2 pull, 3 push, 4 host
+    std::vector<float4> h_gstat;   // graph -> {tasks, edges, levels, 0}
+    int32_t* d_level = nullptr;
+    uint8_t* d_cat = nullptr;
+    int32_t* d_toff = nullptr;
+    float4* d_gstat = nullptr;
+    float* d_prio = nullptr;       // bottom-level weight per task under seed_prio
+    int32_t seed_prio = HF_PRIO_FIFO;  // priority the seed order was built for
+    const hf_costmodel* cm = nullptr;  // borrowed from the batch
 };
+
+static hf_status plan_set_chunk(Plan* p, int64_t chunk_elems, cudaStream_t s);
+hf_status plan_prepare_priority(Plan* p, int32_t priority, const hf_costmodel* cm, cudaStream_t s);
+
+void plan_set_costmodel(Plan* p, const hf_costmodel* cm) {
+    p->cm = cm;
+    if (p->seed_prio == HF_PRIO_LEARNED) p->seed_prio = -1;  // recompute with the new model
+}
 
 static void* palloc(Plan* p, size_t bytes, cudaStream_t s) {
     void* d = dev_alloc(bytes, s);
@@ -215,6 +235,18 @@ hf_status plan_build(const std::vector<hf_graph*>& graphs, Plan** out) {
             eoff += f.m;
         }
         row_ptr[(size_t)n] = (int32_t)eoff;
+        // edge records and per-task rows for the persistent executor
+        std::vector<int4> erec((size_t)p->m);
+        std::vector<int2> meta((size_t)n);
+        for (int32_t v = 0; v < n; ++v) meta[(size_t)v] = make_int2(row_ptr[(size_t)v], row_ptr[(size_t)v + 1] - row_ptr[(size_t)v]);
+        for (int64_t e = 0; e < p->m; ++e) {
+            const int32_t w = succ[(size_t)e].x;
+            const uint32_t len = (uint32_t)meta[(size_t)w].y;
+            const uint32_t in = (uint32_t)indeg0[(size_t)w];
+            const uint32_t lo = in <= (uint32_t)kNarrowIn ? in : kWideMark;
+            const uint32_t hi = len < kLongMark ? len : kLongMark;
+            erec[(size_t)e] = make_int4(w, succ[(size_t)e].y, meta[(size_t)w].x, (int)((hi << 16) | lo));
+        }
         // merged level-sorted order: level l of graph 0, level l of graph 1, ...
         std::vector<int32_t> ls_node((size_t)n), ls_ptr((size_t)n + 1);
         std::vector<int2> ls_in((size_t)p->m);
@@ -309,10 +341,29 @@ hf_status plan_build(const std::vector<hf_graph*>& graphs, Plan** out) {
             }
         }
         p->npay = (int32_t)p->hpay.size();
+        // cost-model inputs kept on the host until first use
+        p->h_level.resize((size_t)n);
+        p->h_cat.resize((size_t)n);
+        p->h_gstat.resize((size_t)p->ngraphs);
+        for (int i = 0; i < p->ngraphs; ++i) {
+            const hf_graph* g = graphs[(size_t)i];
+            const int32_t toff = p->task_off[(size_t)i];
+            for (int32_t v = 0; v < g->fin.n; ++v) {
+                p->h_level[(size_t)toff + v] = g->fin.level[(size_t)v];
+                const uint8_t k = g->kind[(size_t)v];
+                uint8_t c = 4;
+                if (k == HF_KERNEL) c = g->pay[(size_t)v] < 0 ? 0 : 1;
+                else if (k == HF_PULL) c = 2;
+                else if (k == HF_PUSH) c = 3;
+                p->h_cat[(size_t)toff + v] = c;
+            }
+            p->h_gstat[(size_t)i] = make_float4((float)g->fin.n, (float)g->fin.m, (float)g->fin.levels, 0.f);
+        }
 
         // uploads
         if ((st = upload(p, &p->d_row_ptr, row_ptr.data(), row_ptr.size(), s, "row_ptr")) != HF_OK) return bail(st);
-        if ((st = upload(p, &p->d_succ, succ.data(), succ.size(), s, "succ")) != HF_OK) return bail(st);
+        if ((st = upload(p, &p->d_erec, erec.data(), erec.size(), s, "erec")) != HF_OK) return bail(st);
+        if ((st = upload(p, &p->d_meta, meta.data(), meta.size(), s, "meta")) != HF_OK) return bail(st);
         if ((st = upload(p, &p->d_indeg0, indeg0.data(), indeg0.size(), s, "indeg0")) != HF_OK) return bail(st);
         if (p->any_key0 && (st = upload(p, &p->d_key0, key0.data(), key0.size(), s, "key0")) != HF_OK) return bail(st);
         if (p->npay && (st = upload(p, &p->d_pidx, p->hpidx.data(), p->hpidx.size(), s, "pidx")) != HF_OK)
@@ -324,10 +375,10 @@ hf_status plan_build(const std::vector<hf_graph*>& graphs, Plan** out) {
         if ((st = upload(p, &p->d_epos_ls, epos_ls.data(), epos_ls.size(), s, "epos")) != HF_OK) return bail(st);
         p->d_pay = (DevPayload*)palloc(p, std::max<size_t>(sizeof(DevPayload) * (size_t)p->npay, 64), s);
         p->d_key = (uint32_t*)palloc(p, std::max<size_t>(4 * (size_t)n, 16), s);
-        p->d_indeg = (int32_t*)palloc(p, std::max<size_t>(4 * (size_t)n, 16), s);
+        p->d_state = (unsigned long long*)palloc(p, std::max<size_t>(8 * (size_t)n, 16), s);
         p->d_chunks_left = (int32_t*)palloc(p, std::max<size_t>(4 * (size_t)p->npay, 16), s);
         p->d_ctrl = (Ctrl*)palloc(p, sizeof(Ctrl), s);
-        if (!p->d_pay || !p->d_key || !p->d_indeg || !p->d_chunks_left || !p->d_ctrl)
+        if (!p->d_pay || !p->d_key || !p->d_state || !p->d_chunks_left || !p->d_ctrl)
             return bail(fail(HF_ENOMEM, "device allocation failed: runtime state"));
         ce = cudaMemsetAsync(p->d_ctrl, 0, sizeof(Ctrl), s);
         if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaMemsetAsync"));
@@ -512,9 +563,12 @@ hf_status plan_run(Plan* p, cudaStream_t s, const hf_run_opts& o) {
     if (mode == HF_MODE_PERSISTENT && !p->host_tasks.empty())
         return fail(HF_ENOTSUP, "host tasks need the level-synchronous executor");
     if (o.priority < HF_PRIO_FIFO || o.priority > HF_PRIO_LEARNED) return fail(HF_EINVAL, "unknown priority");
+    if (o.priority == HF_PRIO_LEARNED && !p->cm) return fail(HF_ESTATE, "HF_PRIO_LEARNED needs a cost model (hf_batch_set_costmodel)");
+    hf_status st = HF_OK;
+    if (mode == HF_MODE_PERSISTENT && (st = plan_prepare_priority(p, o.priority, p->cm, s)) != HF_OK) return st;
     int64_t chunk = o.chunk_elems > 0 ? o.chunk_elems : 16384;
     chunk = ((chunk + 31) / 32) * 32;
-    hf_status st = plan_set_chunk(p, chunk, s);
+    st = plan_set_chunk(p, chunk, s);
     if (st != HF_OK) return st;
     const bool instr = o.instrument != 0, valid = o.validate != 0;
     if ((st = ensure_instr(p, instr, valid, s)) != HF_OK) return st;
@@ -538,8 +592,7 @@ hf_status plan_run(Plan* p, cudaStream_t s, const hf_run_opts& o) {
             r.key0 = p->d_key0;
             r.seeds = p->d_seeds;
             r.pay = p->d_pay;
-            r.key = p->d_key;
-            r.indeg = p->d_indeg;
+            r.state = p->d_state;
             r.queue = p->d_queue;
             r.chunks_left = p->d_chunks_left;
             r.ctrl = p->d_ctrl;
@@ -559,13 +612,13 @@ hf_status plan_run(Plan* p, cudaStream_t s, const hf_run_opts& o) {
             a.claim = std::min(std::max(o.claim, 1), 32);
             a.local_keep = o.local_keep < 0 ? 32 : std::min(o.local_keep, kStackCap - 32);
             a.spin_limit_ns = o.spin_limit_ns ? o.spin_limit_ns : 2000000000ull;
-            a.row_ptr = p->d_row_ptr;
-            a.succ = p->d_succ;
+            a.meta = p->d_meta;
+            a.erec = p->d_erec;
             a.pidx = p->npay ? p->d_pidx : nullptr;
             a.pay = p->d_pay;
             a.chunk_task = p->d_chunk_task;
             a.key = p->d_key;
-            a.indeg = p->d_indeg;
+            a.state = p->d_state;
             a.queue = p->d_queue;
             a.chunks_left = p->d_chunks_left;
             a.ctrl = p->d_ctrl;
@@ -574,7 +627,13 @@ hf_status plan_run(Plan* p, cudaStream_t s, const hf_run_opts& o) {
             a.tk_start = r.tk_start;
             a.tk_end = r.tk_end;
             a.exec_count = r.exec_count;
-            int ctas = o.ctas > 0 ? o.ctas : p->num_sms * 2;
+            int ctas = o.ctas;
+            if (ctas <= 0) {  // every warp slot of the GPU: one CTA per SM times occupancy
+                int occ = 0;
+                if (p->npay) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_persist<true>, kWarpsPerCta * 32, 0);
+                else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_persist<false>, kWarpsPerCta * 32, 0);
+                ctas = p->num_sms * std::max(occ, 1);
+            }
             if (o.time_kernel) cudaEventRecord(p->kev0, s);
             if (p->npay) k_persist<true><<<ctas, kWarpsPerCta * 32, 0, s>>>(a);
             else k_persist<false><<<ctas, kWarpsPerCta * 32, 0, s>>>(a);
@@ -676,9 +735,190 @@ hf_status plan_set_delays(Plan* p, const float* delay, int on_device, cudaStream
         src = p->d_dly_stage;
     }
     const int grid = (int)std::min<int64_t>((p->m + 255) / 256, (int64_t)p->num_sms * 16);
-    k_set_delays<<<grid, 256, 0, s>>>(src, p->d_epos_csr, p->d_epos_ls, p->d_succ, p->d_ls_in, p->m);
+    k_set_delays<<<grid, 256, 0, s>>>(src, p->d_epos_csr, p->d_epos_ls, p->d_erec, p->d_ls_in, p->m);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? HF_OK : cuda_fail(e, "delay scatter");
+}
+
+// ------------------------------------------------------------------ cost model plumbing
+
+// The 12 features of every task (layout in include/hf.h).
+__global__ void k_features(int n, const int2* __restrict__ meta, const int4* __restrict__ erec,
+                           const int32_t* __restrict__ indeg0, const int32_t* __restrict__ level,
+                           const uint8_t* __restrict__ cat, const int32_t* __restrict__ pidx,
+                           const DevPayload* __restrict__ pay, const int32_t* __restrict__ toff, int ng,
+                           const float4* __restrict__ gstat, float* __restrict__ X) {
+    const int stride = gridDim.x * blockDim.x;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        int lo = 0, hi = ng;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (toff[mid] <= v) lo = mid;
+            else hi = mid;
+        }
+        const float4 gs = gstat[lo];
+        const int2 mt = meta[v];
+        const int c = cat[v];
+        const int lev = level[v];
+        double bytes = 0.0;
+        const int p = pidx ? pidx[v] : -1;
+        if (p >= 0) bytes = pay[p].op == kPayCopy ? (double)pay[p].n : 12.0 * (double)pay[p].n;
+        float msf = 0.f;
+        if (mt.y > 0) {
+            int64_t sum = 0;
+            for (int e = mt.x; e < mt.x + mt.y; ++e) {
+                const int4 r = erec[e];
+                int len = (int)((uint32_t)r.w >> 16);
+                if ((uint32_t)len == kLongMark) len = meta[r.x].y;
+                sum += len;
+            }
+            msf = (float)((double)sum / (double)mt.y);
+        }
+        float* x = X + (int64_t)v * HF_FEATURES;
+        x[0] = c == 0 ? 1.f : 0.f;
+        x[1] = c == 1 ? 1.f : 0.f;
+        x[2] = c == 2 ? 1.f : 0.f;
+        x[3] = c == 3 ? 1.f : 0.f;
+        x[4] = log1pf((float)indeg0[v]);
+        x[5] = log1pf((float)mt.y);
+        x[6] = (float)lev / gs.z;
+        x[7] = log1pf((float)lev);
+        x[8] = log1pf((float)bytes);
+        x[9] = log1pf(gs.x);
+        x[10] = log1pf(gs.y);
+        x[11] = log1pf(msf);
+    }
+}
+
+// Plain heuristic cost (ns of warp time), the fallback the learned model is judged against:
+// a fixed cost per task, one atomic round trip per out-edge, payload bytes at the bandwidth
+// one warp sustains. Constants are first-principles estimates, not fitted.
+constexpr float kHeurTask = 300.f, kHeurEdge = 30.f, kHeurBytesPerNs = 25.f;
+
+__global__ void k_costs(int n, const float* __restrict__ X, const float* __restrict__ y, float* __restrict__ c) {
+    const int stride = gridDim.x * blockDim.x;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        if (y) {
+            c[v] = expf(fminf(fmaxf(y[v], 0.f), 30.f));
+        } else {
+            const float* x = X + (int64_t)v * HF_FEATURES;
+            c[v] = kHeurTask + kHeurEdge * expm1f(x[5]) + expm1f(x[8]) / kHeurBytesPerNs;
+        }
+    }
+}
+
+// One level of the reverse pass: b(v) = c(v) + max over successors b(s), sinks b = c.
+__global__ void k_bottom(int p0, int p1, const int32_t* __restrict__ ls_node, const int2* __restrict__ meta,
+                         const int4* __restrict__ erec, const float* __restrict__ c, float* __restrict__ b) {
+    const int p = p0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= p1) return;
+    const int v = ls_node[p];
+    const int2 mt = meta[v];
+    if (mt.y == 0) {
+        b[v] = c[v];
+        return;
+    }
+    float mx = -INFINITY;
+    for (int e = mt.x; e < mt.x + mt.y; ++e) mx = fmaxf(mx, __ldcg(b + erec[e].x));
+    b[v] = __fadd_rn(mx, c[v]);
+}
+
+static hf_status ensure_cm_inputs(Plan* p, cudaStream_t s) {
+    if (p->d_level) return HF_OK;
+    hf_status st;
+    if ((st = upload(p, &p->d_level, p->h_level.data(), p->h_level.size(), s, "level")) != HF_OK) return st;
+    if ((st = upload(p, &p->d_cat, p->h_cat.data(), p->h_cat.size(), s, "cat")) != HF_OK) return st;
+    if ((st = upload(p, &p->d_toff, p->task_off.data(), p->task_off.size(), s, "task offsets")) != HF_OK) return st;
+    if ((st = upload(p, &p->d_gstat, p->h_gstat.data(), p->h_gstat.size(), s, "graph stats")) != HF_OK) return st;
+    cudaError_t e = cudaStreamSynchronize(s);  // host vectors stay alive, but keep uploads ordered
+    return e == cudaSuccess ? HF_OK : cuda_fail(e, "cost model inputs");
+}
+
+hf_status plan_features(Plan* p, float* X, cudaStream_t s) {
+    if (p->n == 0) return HF_OK;
+    if (!X) return fail(HF_EINVAL, "X is NULL");
+    hf_status st = ensure_cm_inputs(p, s);
+    if (st != HF_OK) return st;
+    const int grid = std::min((p->n + 255) / 256, p->num_sms * 16);
+    k_features<<<grid, 256, 0, s>>>(p->n, p->d_meta, p->d_erec, p->d_indeg0, p->d_level, p->d_cat,
+                                    p->npay ? p->d_pidx : nullptr, p->d_pay, p->d_toff, p->ngraphs, p->d_gstat, X);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? HF_OK : cuda_fail(e, "k_features");
+}
+
+hf_status plan_bottom_levels(Plan* p, const float* cost, float* bottom, cudaStream_t s) {
+    if (p->n == 0) return HF_OK;
+    if (!cost || !bottom) return fail(HF_EINVAL, "NULL argument");
+    for (int32_t l = p->levels - 1; l >= 0; --l) {
+        const int p0 = p->level_ptr[(size_t)l], p1 = p->level_ptr[(size_t)l + 1];
+        k_bottom<<<(p1 - p0 + 255) / 256, 256, 0, s>>>(p0, p1, p->d_ls_node, p->d_meta, p->d_erec, cost, bottom);
+    }
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? HF_OK : cuda_fail(e, "k_bottom");
+}
+
+hf_status plan_task_costs(Plan* p, int32_t priority, const hf_costmodel* cm, float* cost, float* bottom,
+                          cudaStream_t s) {
+    if (p->n == 0) return HF_OK;
+    if (priority != HF_PRIO_HEURISTIC && priority != HF_PRIO_LEARNED) return fail(HF_EINVAL, "priority must be HEURISTIC or LEARNED");
+    if (priority == HF_PRIO_LEARNED && !cm) return fail(HF_ESTATE, "no cost model attached");
+    if (!cost || !bottom) return fail(HF_EINVAL, "NULL output");
+    // payload pieces do not change task costs, but the payload table must be on the device
+    hf_status st = p->chunk_elems < 0 ? plan_set_chunk(p, 16384, s) : HF_OK;
+    if (st != HF_OK) return st;
+    float* X = (float*)dev_alloc(sizeof(float) * HF_FEATURES * (size_t)p->n, s);
+    float* y = priority == HF_PRIO_LEARNED ? (float*)dev_alloc(sizeof(float) * (size_t)p->n, s) : nullptr;
+    if (!X || (priority == HF_PRIO_LEARNED && !y)) {
+        dev_free(X, s);
+        dev_free(y, s);
+        return fail(HF_ENOMEM, "device allocation failed: features");
+    }
+    st = plan_features(p, X, s);
+    if (st == HF_OK && y) st = mlp_forward(costmodel_params(cm), X, p->n, y, s);
+    if (st == HF_OK) {
+        const int grid = std::min((p->n + 255) / 256, p->num_sms * 16);
+        k_costs<<<grid, 256, 0, s>>>(p->n, X, y, cost);
+        cudaError_t e = cudaGetLastError();
+        st = e != cudaSuccess ? cuda_fail(e, "k_costs") : plan_bottom_levels(p, cost, bottom, s);
+    }
+    cudaError_t e = cudaStreamSynchronize(s);  // before the temporaries are released
+    dev_free(X, s);
+    dev_free(y, s);
+    if (st == HF_OK && e != cudaSuccess) st = cuda_fail(e, "cost kernels");
+    return st;
+}
+
+// Orders the persistent executor's seed tasks by decreasing bottom-level weight (longest
+// remaining predicted critical path first) for HEURISTIC / LEARNED runs; FIFO keeps id order.
+hf_status plan_prepare_priority(Plan* p, int32_t priority, const hf_costmodel* cm, cudaStream_t s) {
+    if (priority == p->seed_prio && (priority == HF_PRIO_FIFO || p->d_prio)) return HF_OK;
+    if (priority == HF_PRIO_FIFO) {
+        std::sort(p->sources.begin(), p->sources.end());
+    } else {
+        if (!p->d_prio) {
+            p->d_prio = (float*)palloc(p, sizeof(float) * std::max<size_t>((size_t)p->n, 4), s);
+            if (!p->d_prio) return fail(HF_ENOMEM, "device allocation failed: priorities");
+        }
+        float* cost = (float*)dev_alloc(sizeof(float) * std::max<size_t>((size_t)p->n, 4), s);
+        if (!cost) return fail(HF_ENOMEM, "device allocation failed: costs");
+        hf_status st = plan_task_costs(p, priority, cm, cost, p->d_prio, s);
+        dev_free(cost, s);
+        if (st != HF_OK) return st;
+        std::vector<float> b((size_t)p->n);
+        cudaError_t e = cudaMemcpy(b.data(), p->d_prio, sizeof(float) * (size_t)p->n, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(e, "priority download");
+        std::stable_sort(p->sources.begin(), p->sources.end(),
+                         [&](int32_t x, int32_t y) { return b[(size_t)x] > b[(size_t)y]; });
+    }
+    p->seed_prio = priority;
+    p->chunk_elems = -1;  // seeds are rebuilt with the next piece layout
+    return HF_OK;
+}
+
+hf_status plan_refresh_priorities(Plan* p, const hf_costmodel* cm, cudaStream_t s) {
+    const int32_t pr = p->seed_prio;
+    p->seed_prio = -1;
+    return plan_prepare_priority(p, pr == -1 ? HF_PRIO_FIFO : pr, cm, s);
 }
 
 }  // namespace hf

@@ -118,6 +118,22 @@ def load():
         "hf_batch_kernel_ms": [vp, P(ctypes.c_float)],
         "hf_set_delays": [vp, vp, ctypes.c_int, vp],
         "hf_batch_set_delays": [vp, vp, ctypes.c_int, vp],
+        "hf_costmodel_create": [P(vp), ctypes.c_uint64],
+        "hf_costmodel_destroy": [vp],
+        "hf_costmodel_set_params": [vp, vp],
+        "hf_costmodel_get_params": [vp, vp],
+        "hf_costmodel_save": [vp, ctypes.c_char_p],
+        "hf_costmodel_load": [vp, ctypes.c_char_p],
+        "hf_costmodel_forward": [vp, vp, i64, vp, vp],
+        "hf_costmodel_grad": [vp, vp, vp, i64, vp, vp, vp],
+        "hf_costmodel_adam_step": [vp, vp, ctypes.c_float, vp],
+        "hf_costmodel_train": [vp, vp, vp, i64, i32, i32, ctypes.c_float, ctypes.c_uint64, P(ctypes.c_float), vp],
+        "hf_batch_features": [vp, vp, vp],
+        "hf_features": [vp, vp, vp],
+        "hf_batch_set_costmodel": [vp, vp],
+        "hf_batch_refresh_priorities": [vp, vp],
+        "hf_batch_task_costs": [vp, i32, vp, vp, vp],
+        "hf_batch_bottom_levels": [vp, vp, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -361,6 +377,87 @@ def hf_batch_set_delays(b, delay, on_device=False, stream=None):
         delay = np.ascontiguousarray(delay, np.float32)
     _check(load().hf_batch_set_delays(b, _ptr(delay), 1 if on_device else 0, _stream_handle(stream)),
            "hf_batch_set_delays")
+
+
+HF_COSTMODEL_PARAMS = 5057
+HF_FEATURES = 12
+
+
+def hf_costmodel_create(seed=0):
+    cm = ctypes.c_void_p()
+    _check(load().hf_costmodel_create(ctypes.byref(cm), seed), "hf_costmodel_create")
+    return cm
+
+
+def hf_costmodel_destroy(cm):
+    _check(load().hf_costmodel_destroy(cm), "hf_costmodel_destroy")
+
+
+def hf_costmodel_set_params(cm, params):
+    params = np.ascontiguousarray(params, np.float32)
+    assert params.size == HF_COSTMODEL_PARAMS
+    _check(load().hf_costmodel_set_params(cm, _ptr(params)), "hf_costmodel_set_params")
+
+
+def hf_costmodel_get_params(cm):
+    out = np.empty(HF_COSTMODEL_PARAMS, np.float32)
+    _check(load().hf_costmodel_get_params(cm, _ptr(out)), "hf_costmodel_get_params")
+    return out
+
+
+def hf_costmodel_save(cm, path):
+    _check(load().hf_costmodel_save(cm, path.encode()), "hf_costmodel_save")
+
+
+def hf_costmodel_load(cm, path):
+    _check(load().hf_costmodel_load(cm, path.encode()), "hf_costmodel_load")
+
+
+def hf_costmodel_forward(cm, X, n, y, stream=None):
+    """X: CUDA tensor [n, 12] float32; y: CUDA tensor [n] float32 (written)."""
+    _check(load().hf_costmodel_forward(cm, _ptr(X), n, _ptr(y), _stream_handle(stream)), "hf_costmodel_forward")
+
+
+def hf_costmodel_grad(cm, X, t, n, grad, loss, stream=None):
+    _check(load().hf_costmodel_grad(cm, _ptr(X), _ptr(t), n, _ptr(grad), _ptr(loss), _stream_handle(stream)),
+           "hf_costmodel_grad")
+
+
+def hf_costmodel_adam_step(cm, grad, lr, stream=None):
+    _check(load().hf_costmodel_adam_step(cm, _ptr(grad), lr, _stream_handle(stream)), "hf_costmodel_adam_step")
+
+
+def hf_costmodel_train(cm, X, t, n, epochs, batch, lr, seed=0, stream=None):
+    loss = ctypes.c_float()
+    _check(load().hf_costmodel_train(cm, _ptr(X), _ptr(t), n, epochs, batch, lr, seed, ctypes.byref(loss),
+                                     _stream_handle(stream)), "hf_costmodel_train")
+    return loss.value
+
+
+def hf_batch_features(b, X, stream=None):
+    _check(load().hf_batch_features(b, _ptr(X), _stream_handle(stream)), "hf_batch_features")
+
+
+def hf_features(g, X, stream=None):
+    _check(load().hf_features(g, _ptr(X), _stream_handle(stream)), "hf_features")
+
+
+def hf_batch_set_costmodel(b, cm):
+    _check(load().hf_batch_set_costmodel(b, cm), "hf_batch_set_costmodel")
+
+
+def hf_batch_refresh_priorities(b, stream=None):
+    _check(load().hf_batch_refresh_priorities(b, _stream_handle(stream)), "hf_batch_refresh_priorities")
+
+
+def hf_batch_task_costs(b, priority, cost, bottom, stream=None):
+    _check(load().hf_batch_task_costs(b, priority, _ptr(cost), _ptr(bottom), _stream_handle(stream)),
+           "hf_batch_task_costs")
+
+
+def hf_batch_bottom_levels(b, cost, bottom, stream=None):
+    _check(load().hf_batch_bottom_levels(b, _ptr(cost), _ptr(bottom), _stream_handle(stream)),
+           "hf_batch_bottom_levels")
 
 
 def hf_status_string(s):

@@ -98,6 +98,12 @@ def test_adam_matches_torch():
         np.testing.assert_allclose(np.atleast_1d(cur[k]), tt.detach().numpy(), rtol=1e-12, atol=1e-14)
 
 
+def test_heuristic_cost_by_hand():
+    F = np.zeros((2, 12))
+    F[0, 5], F[0, 8] = np.log1p(3), np.log1p(1200)  # fan-out 3, 1200 payload bytes
+    np.testing.assert_allclose(mlp.heuristic_cost(F), [300 + 90 + 48, 300.0])
+
+
 def test_features_on_paper_saxpy_graph():
     # Figure 1: host_x(0) host_y(1) pull_x(2) pull_y(3) kernel(4) push_x(5) push_y(6)
     src = [0, 1, 2, 3, 4, 4]
