@@ -197,7 +197,9 @@ hf_status hf_kernel_ms(hf_graph* g, float* ms);
 
 /* Replaces every edge delay of the graph's device plan (a new timing view of the same
  * circuit): delay[e] is the new delay of the e-th edge in the order edges were added
- * (hf_precede*), m floats, all finite. on_device != 0: `delay` is a device pointer; else host
+ * (hf_precede*), m floats, all finite (checked on the device: a non-finite delay is stored
+ * anyway and makes every later hf_sync_status return HF_EINVAL until delays are set again).
+ * on_device != 0: `delay` is a device pointer; else host
  * memory (page-locked for an asynchronous copy). Enqueued on `stream`; later runs on any
  * stream see the new delays once that stream has reached this point. The graph's own edge
  * list keeps the delays it was built with (they return if the plan is ever rebuilt, e.g.

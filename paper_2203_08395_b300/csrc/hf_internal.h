@@ -45,7 +45,8 @@ struct alignas(128) Ctrl {
     int32_t pad2[31];
     int32_t status;
     int32_t abort;
-    int32_t pad3[30];
+    int32_t bad_input;  // set by hf_set_delays' kernel when a delay is not finite
+    int32_t pad3[29];
     unsigned long long ticket;  // validation tickets
     int32_t pad4[30];
 };

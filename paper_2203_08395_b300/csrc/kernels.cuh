@@ -404,6 +404,9 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_persist(const PersistArgs
     uint64_t stall_t0 = 0;
     unsigned backoff = 32;
     const int n_tasks = a.n_tasks;
+    const int nwarps = (int)gridDim.x * kWarpsPerCta;
+    uint32_t ndone = 0;  // completions not yet added to ctrl->done (warp-uniform)
+    uint32_t iter = 0;
 
     for (;;) {
         int item = -1;
@@ -418,24 +421,34 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_persist(const PersistArgs
             __syncwarp();
         } else {
             if (pend == 0) {
-                int b = a.qcap;
+                // claim a fair share of the published backlog (at least 1, at most `claim`)
+                int b = a.qcap, k = 0;
                 if (lane == 0) {
                     const int h = ld_relaxed(&a.ctrl->head);
-                    if (h < a.qcap) b = atomicAdd(&a.ctrl->head, a.claim);
+                    if (h < a.qcap) {
+                        const int t = ld_relaxed(&a.ctrl->tail);
+                        k = max(1, min((t - h) / nwarps, a.claim));
+                        b = atomicAdd(&a.ctrl->head, k);
+                    }
                 }
                 b = __shfl_sync(kFull, b, 0);
+                k = __shfl_sync(kFull, k, 0);
                 qbase = b;
-                const int k = min(a.claim, a.qcap - b);
+                k = min(k, a.qcap - b);
                 pend = k <= 0 ? 0u : (k >= 32 ? kFull : ((1u << k) - 1u));
             }
             if (pend & (1u << lane)) {
-                const int v = ld_acquire(a.queue + qbase + lane);
+                const int v = ld_relaxed(a.queue + qbase + lane);
                 if (v >= 0) item = v;
             }
-            pend &= ~__ballot_sync(kFull, item >= 0);
+            const unsigned hit = __ballot_sync(kFull, item >= 0);
+            pend &= ~hit;
+            if (hit) fence_acq_rel();  // acquire: what the pusher released with the slot
         }
         const unsigned got = __ballot_sync(kFull, item >= 0);
         if (got == 0) {
+            if (ndone && lane == 0) atomicAdd(&a.ctrl->done, ndone);
+            ndone = 0;
             int quit = 0;
             if (lane == 0) {
                 const uint32_t d = ld_relaxed_u(&a.ctrl->done);
@@ -571,20 +584,31 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_persist(const PersistArgs
             }
             if (__ballot_sync(kFull, r.x >= 0)) push_ready<PAY>(a, r, stk, top, lane);
         }
-        const unsigned fm = __ballot_sync(kFull, fin >= 0);
-        if (fm && lane == 0) atomicAdd(&a.ctrl->done, (uint32_t)__popc(fm));
+        // completions reach ctrl->done in batches: when the warp goes idle, and every 32 rounds
+        // so that the stall timer of idle warps sees progress made by long-busy warps
+        ndone += (uint32_t)__popc(__ballot_sync(kFull, fin >= 0));
+        if ((++iter & 31u) == 0 && ndone) {
+            if (lane == 0) atomicAdd(&a.ctrl->done, ndone);
+            ndone = 0;
+        }
     }
 }
 
 // New edge delays: delay[e] (edges in insertion order) into both edge layouts.
+// A delay that is not finite is stored all the same and flagged in *bad (reported as
+// HF_EINVAL by the next synchronisation).
 __global__ void k_set_delays(const float* __restrict__ delay, const int32_t* __restrict__ pos_csr,
-                             const int32_t* __restrict__ pos_ls, int4* erec, int2* ls_in, int64_t m) {
+                             const int32_t* __restrict__ pos_ls, int4* erec, int2* ls_in, int64_t m,
+                             int32_t* bad) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    bool nonfinite = false;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
         const int b = __float_as_int(__ldg(delay + i));
+        nonfinite |= (b & 0x7f800000) == 0x7f800000;
         reinterpret_cast<int*>(erec)[4 * (int64_t)__ldg(pos_csr + i) + 1] = b;
         reinterpret_cast<int*>(ls_in)[2 * (int64_t)__ldg(pos_ls + i) + 1] = b;
     }
+    if (__any_sync(0xffffffffu, nonfinite) && (threadIdx.x & 31) == 0) atomicExch(bad, 1);
 }
 
 __global__ void k_keys_to_f32(const uint32_t* __restrict__ key, float* __restrict__ out, int64_t n) {

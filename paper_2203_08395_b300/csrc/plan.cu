@@ -642,7 +642,7 @@ hf_status plan_run(Plan* p, cudaStream_t s, const hf_run_opts& o) {
         e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
     }
-    e = cudaMemcpyAsync(p->h_status, &p->d_ctrl->status, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    e = cudaMemcpyAsync(p->h_status, &p->d_ctrl->status, 3 * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) return cuda_fail(e, "status copy");
     e = cudaEventRecord(p->done_ev, s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
@@ -659,6 +659,7 @@ hf_status plan_sync(Plan* p) {
     cudaError_t e = cudaEventSynchronize(p->done_ev);
     if (e != cudaSuccess) return cuda_fail(e, "run");
     const int32_t s = p->h_status[0];
+    if (p->h_status[2]) return fail(HF_EINVAL, "a delay given to hf_set_delays is not finite");
     if (s == HF_ETIMEDOUT) return fail(HF_ETIMEDOUT, "persistent executor made no progress within the spin limit");
     if (s != 0) return fail((hf_status)s, "device status " + std::to_string(s));
     return HF_OK;
@@ -724,8 +725,6 @@ hf_status plan_set_delays(Plan* p, const float* delay, int on_device, cudaStream
     if (!delay) return fail(HF_EINVAL, "delay is NULL");
     const float* src = delay;
     if (!on_device) {
-        for (int64_t i = 0; i < p->m; ++i)
-            if (!std::isfinite(delay[i])) return fail(HF_EINVAL, "delay " + std::to_string(i) + " is not finite");
         if (!p->d_dly_stage) {
             p->d_dly_stage = (float*)palloc(p, 4 * (size_t)p->m, s);
             if (!p->d_dly_stage) return fail(HF_ENOMEM, "device allocation failed: delay staging");
@@ -735,7 +734,10 @@ hf_status plan_set_delays(Plan* p, const float* delay, int on_device, cudaStream
         src = p->d_dly_stage;
     }
     const int grid = (int)std::min<int64_t>((p->m + 255) / 256, (int64_t)p->num_sms * 16);
-    k_set_delays<<<grid, 256, 0, s>>>(src, p->d_epos_csr, p->d_epos_ls, p->d_erec, p->d_ls_in, p->m);
+    cudaError_t e0 = cudaMemsetAsync(&p->d_ctrl->bad_input, 0, sizeof(int32_t), s);
+    if (e0 != cudaSuccess) return cuda_fail(e0, "cudaMemsetAsync");
+    k_set_delays<<<grid, 256, 0, s>>>(src, p->d_epos_csr, p->d_epos_ls, p->d_erec, p->d_ls_in, p->m,
+                                      &p->d_ctrl->bad_input);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? HF_OK : cuda_fail(e, "delay scatter");
 }
@@ -839,6 +841,8 @@ hf_status plan_features(Plan* p, float* X, cudaStream_t s) {
     if (!X) return fail(HF_EINVAL, "X is NULL");
     hf_status st = ensure_cm_inputs(p, s);
     if (st != HF_OK) return st;
+    // the payload table reaches the device with the first piece layout
+    if (p->chunk_elems < 0 && (st = plan_set_chunk(p, 16384, s)) != HF_OK) return st;
     const int grid = std::min((p->n + 255) / 256, p->num_sms * 16);
     k_features<<<grid, 256, 0, s>>>(p->n, p->d_meta, p->d_erec, p->d_indeg0, p->d_level, p->d_cat,
                                     p->npay ? p->d_pidx : nullptr, p->d_pay, p->d_toff, p->ngraphs, p->d_gstat, X);
@@ -863,9 +867,7 @@ hf_status plan_task_costs(Plan* p, int32_t priority, const hf_costmodel* cm, flo
     if (priority != HF_PRIO_HEURISTIC && priority != HF_PRIO_LEARNED) return fail(HF_EINVAL, "priority must be HEURISTIC or LEARNED");
     if (priority == HF_PRIO_LEARNED && !cm) return fail(HF_ESTATE, "no cost model attached");
     if (!cost || !bottom) return fail(HF_EINVAL, "NULL output");
-    // payload pieces do not change task costs, but the payload table must be on the device
-    hf_status st = p->chunk_elems < 0 ? plan_set_chunk(p, 16384, s) : HF_OK;
-    if (st != HF_OK) return st;
+    hf_status st = HF_OK;
     float* X = (float*)dev_alloc(sizeof(float) * HF_FEATURES * (size_t)p->n, s);
     float* y = priority == HF_PRIO_LEARNED ? (float*)dev_alloc(sizeof(float) * (size_t)p->n, s) : nullptr;
     if (!X || (priority == HF_PRIO_LEARNED && !y)) {

@@ -330,6 +330,36 @@ def test_stalled_task_times_out_and_context_survives():
     gd.close()
 
 
+@pytest.mark.parametrize("ex", ["levelsync", "persistent"])
+def test_new_timing_view_through_set_delays(ex):
+    """A second timing view of the same circuit: new delays in place, arrivals as the oracle
+    computes them on the new delays; a non-finite delay is reported, then recovered from."""
+    wl = S.batch(5, graphs=6, nmin=2000, nmax=20000)
+    bd = BatchOnDevice(wl)
+    bd.run(**EXECUTORS[ex])
+    bd.sync()
+    new = [S.uniform_f32(77, i, g.m, -0.5, 2.0) for i, g in enumerate(wl.graphs)]
+    allnew = torch.from_numpy(np.concatenate(new)).pin_memory()
+    hf.hf_batch_set_delays(bd.b, allnew, on_device=False)
+    bd.run(**EXECUTORS[ex])
+    bd.sync()
+    for i, g in enumerate(wl.graphs):
+        ref = oracle.kahn(g.n, g.src, g.dst, new[i])[0]
+        np.testing.assert_array_equal(bits(bd.arrivals(i)), bits(ref))
+    bad = allnew.clone()
+    bad[12345] = float("nan")
+    hf.hf_batch_set_delays(bd.b, bad.cuda(), on_device=True)
+    bd.run(**EXECUTORS[ex])
+    assert bd.sync(check=False) == hf.HF_EINVAL
+    hf.hf_batch_set_delays(bd.b, allnew.cuda(), on_device=True)
+    bd.run(**EXECUTORS[ex])
+    bd.sync()
+    allarr = hf.hf_batch_get_arrivals(bd.b, -1, wl.n_tasks)
+    ref_all = np.concatenate([oracle.kahn(g.n, g.src, g.dst, new[i])[0] for i, g in enumerate(wl.graphs)])
+    np.testing.assert_array_equal(bits(allarr), bits(ref_all))
+    bd.close()
+
+
 def test_unpinned_pull_buffer_rejected():
     g = hf.hf_graph_create()
     buf = np.zeros(16, np.float32)  # pageable host memory
