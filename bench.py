@@ -1,22 +1,26 @@
 #!/usr/bin/env python3
 """Benchmark of the task-graph executor on one B300 (one JSON line on stdout, rank 0).
 
-A step is one execution of the whole workload through the C ABI (hf_batch_run): reset of
-counters and queue, then the executor (persistent kernel, or the level-synchronous CUDA
-graph), every task's payload included. Inputs (graph structure, delays, saxpy data) are
-resident in HBM before the timed region and larger than L2 (126 MB), so no flush is needed.
+Workload (default): a batch of 256 independent layered timing DAGs of log-uniform sizes
+(1,000-200,000 tasks, ~10M tasks, ~35M edges) in which 10% of the tasks are FP32 saxpy kernel
+tasks (256-4,096 elements), run as one batch.
 
-Reported:
-  value        tasks/s of the headline executor (whole job; weak scaling over ranks)
-  edges_per_s  the same run in edges/s
-  compare      the same workload under the level-synchronous executor
-  e2e          per step through the public API with host buffers: new edge delays from
-               page-locked host memory (hf_batch_set_delays), the run, all arrivals back to
-               the host (hf_batch_get_arrivals index -1)
-  roofline     algorithmic bytes of the dominant kernel / its CUDA-event time vs measured HBM
-  cpu_baseline the CPU oracle (sequential Kahn, 1 thread) on a bounded sample of the workload
+A step is one execution of the whole batch through the C ABI (hf_batch_run): counter and
+queue reset, then the executor, every payload included. Inputs (graph structure, delays,
+saxpy data) are resident in HBM before the timed region and larger than L2 (126 MB).
 
---impl reference times the CPU oracle alone on this workload (the method's plain definition).
+Headline executor ("batched + learned"): HF_MODE_AUTO with HF_PRIO_LEARNED -- the cost model
+is first trained on timings recorded from two other seeds of the same workload family, its
+predicted costs set the ready-queue priorities and choose the executor, and the persistent
+executor's launch parameters come from the autotuner. Reported beside it: the plain
+level-synchronous executor and the persistent executor with FIFO order on the same batch.
+
+Other keys: e2e (public API with host buffers: new edge delays from page-locked host memory,
+the run, every arrival back to the host), roofline (algorithmic bytes of the dominant kernel
+over its CUDA-event time vs measured HBM bandwidth), cpu_baseline (the CPU oracle, one
+thread, on a bounded sample), clocks (nvidia-smi during the timed region).
+
+--impl reference times the CPU oracle alone (the method's plain definition) on the workload.
 """
 import argparse
 import hashlib
@@ -32,7 +36,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-DEFAULT_WORKLOAD = "batch256"
+DEFAULT_WORKLOAD = "batch256_mixed"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 KERNEL_SRC = os.path.join(ROOT, "paper_2203_08395_b300", "csrc", "kernels.cuh")
@@ -45,11 +49,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="own", choices=["own", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
-    ap.add_argument("--mode", default="persistent", choices=["persistent", "levelsync"])
-    ap.add_argument("--ctas", type=int, default=0)
-    ap.add_argument("--claim", type=int, default=1)
-    ap.add_argument("--local-keep", type=int, default=-1)
-    ap.add_argument("--chunk", type=int, default=0)
+    ap.add_argument("--no-learned", action="store_true", help="headline without the cost model (heuristic)")
+    ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -65,14 +66,17 @@ def peaks():
         return 6400.0, "fallback"
 
 
+def kernel_sha():
+    return hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()
+
+
 def traffic_for(kernel, workload):
     """Per-launch DRAM bytes from a committed ncu summary, if taken on the current kernel source."""
     try:
         with open(TRAFFIC_FILE) as f:
             t = json.load(f)
-        sha = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()
         e = t.get(kernel + "/" + workload)
-        if e and e.get("kernels_sha256") == sha:
+        if e and e.get("kernels_sha256") == kernel_sha():
             return float(e["dram_bytes_per_launch"])
     except Exception:
         pass
@@ -134,8 +138,9 @@ class Clocks:
 
 
 def algorithmic_bytes(wl):
-    """8E + 12N + 4 per graph (row pointers, successor ids+delays, counter reads, arrival writes)
-    plus 12 bytes per saxpy element (read x, read y, write y) and 2x the bytes of each copy."""
+    """Bytes the method must move per step: 8E + 12N + 4 per graph (row starts, successor ids
+    and delays, pending-counter reads, arrival writes), 12 bytes per saxpy element (read x,
+    read y, write y) and twice the bytes of every copy."""
     b = 0
     for g in wl.graphs:
         b += 8 * g.m + 12 * g.n + 4
@@ -147,8 +152,19 @@ def algorithmic_bytes(wl):
     return b
 
 
-def cpu_oracle_rate(wl, budget_s=15.0, max_graphs=None):
-    """Times the oracle (single thread) on whole graphs of the workload, in order, until about
+def train_workloads(name, seeds):
+    """Training graphs for the cost model: the same family as the benchmark workload with other
+    seeds and fewer graphs (the benchmark's own seed stays held out)."""
+    from paper_2203_08395_b300 import synth as S
+
+    if name.startswith("batch256"):
+        frac = 0.10 if name.endswith("mixed") else 0.0
+        return [S.batch(s, graphs=48, frac_saxpy=frac) for s in seeds]
+    return [S.config(name, seed=s) for s in seeds]
+
+
+def cpu_oracle_rate(wl, budget_s=15.0):
+    """The oracle (single thread) on whole graphs of the workload, in order, until about
     budget_s of oracle time. Returns (tasks/s, edges/s, description)."""
     import oracle
 
@@ -164,28 +180,28 @@ def cpu_oracle_rate(wl, budget_s=15.0, max_graphs=None):
         edges += g.m
         used += 1
         del prep
-        if spent >= budget_s or (max_graphs and used >= max_graphs):
+        if spent >= budget_s:
             break
-    desc = "%d of %d graphs (%d tasks, %d edges), %.1f s of oracle time" % (used, len(wl.graphs), tasks, edges, spent)
+    desc = "%d of %d graphs (%d tasks, %d edges, all payloads), %.1f s of oracle time" % (
+        used, len(wl.graphs), tasks, edges, spent)
     return tasks / spent, edges / spent, desc
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return
+    import oracle
     from paper_2203_08395_b300 import synth as S
 
-    wl = S.config(args.workload, seed=0)
-    # each step: the oracle over a bounded prefix of the workload's graphs
-    import oracle
-
     oracle.build()
-    per_step_graphs = max(1, min(len(wl.graphs), 8))
-    sample = S.Workload(wl.name, wl.graphs[:per_step_graphs])
-    preps = None
+    wl = S.config(args.workload, seed=0)
+    per_step = max(1, min(len(wl.graphs), 8))
+    sample = wl.graphs[:per_step]
+    n_s = sum(g.n for g in sample)
+    m_s = sum(g.m for g in sample)
     times = []
     for i in range(args.warmup + args.steps):
-        preps = [oracle.prepare(g) for g in sample.graphs]
+        preps = [oracle.prepare(g) for g in sample]
         t0 = time.perf_counter()
         for p in preps:
             oracle.execute(p)
@@ -195,18 +211,17 @@ def run_reference(args, rank, world):
         if sum(times) > 120:
             break
     ms = 1e3 * float(np.mean(times))
-    value = sample.n_tasks / (ms / 1e3)
-    desc = "%d of %d graphs per step (%d tasks, %d edges)" % (per_step_graphs, len(wl.graphs), sample.n_tasks,
-                                                                 sample.n_edges)
-    line = {
+    value = n_s / (ms / 1e3)
+    desc = "%d of %d graphs per step (%d tasks, %d edges, all payloads)" % (per_step, len(wl.graphs), n_s, m_s)
+    print(json.dumps({
         "impl": "reference", "metric": "DAG tasks/s", "value": value, "unit": "tasks/s", "n_gpus": 0,
         "steps": len(times), "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "edges_per_s": m_s / (ms / 1e3),
         "config": {"workload": args.workload, "l2": "n/a (CPU)"},
         "cpu_baseline": {"value": value, "unit": "tasks/s", "cores": 1, "kind": "oracle", "sample": desc},
         "e2e": {"value": value, "unit": "tasks/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-    }
-    print(json.dumps(line), flush=True)
+    }), flush=True)
 
 
 def main():
@@ -228,72 +243,100 @@ def main():
     import __graft_entry__
 
     __graft_entry__.build()
-    from paper_2203_08395_b300 import hf
+    from paper_2203_08395_b300 import hf, learn
     from paper_2203_08395_b300 import synth as S
     from paper_2203_08395_b300.workload import BatchOnDevice
 
     hf.install_torch_allocator()
-    t_gen = time.time()
+    stream = torch.cuda.current_stream()
+    t_setup = time.time()
     wl = S.config(args.workload, seed=rank)  # weak scaling: every rank runs its own instance
     bd = BatchOnDevice(wl)
-    t_gen = time.time() - t_gen
-    stream = torch.cuda.current_stream()
+    N, E = wl.n_tasks, wl.n_edges
 
     def barrier():
         torch.cuda.synchronize()
         if world > 1:
             torch.distributed.barrier()
 
-    mode = hf.HF_MODE_PERSISTENT if args.mode == "persistent" else hf.HF_MODE_LEVELSYNC
-    opts = dict(mode=mode, ctas=args.ctas, claim=args.claim, local_keep=args.local_keep, chunk_elems=args.chunk)
+    # ---- learned part: train on recorded timings of other seeds, evaluate on this batch
+    learned = None
+    prio = hf.HF_PRIO_HEURISTIC
+    cm = None
+    if not args.no_learned:
+        cm = hf.hf_costmodel_create(0)
+        t_tr = time.time()
+        recs = []
+        for twl in train_workloads(args.workload, (101 + 10 * rank, 102 + 10 * rank)):
+            tb = BatchOnDevice(twl)
+            recs.append(learn.record(tb, stream))
+            tb.close()
+        loss = learn.train(cm, recs)
+        t_tr = time.time() - t_tr
+        err = learn.evaluate(bd, cm, learn.record(bd, stream), stream)
+        del recs
+        hf.hf_batch_set_costmodel(bd.b, cm)
+        prio = hf.HF_PRIO_LEARNED
+        learned = {"train_mse_log": loss, "train_s": t_tr, "held_out_error": err}
 
-    def timed(opts_, steps, warmup):
+    base = hf.hf_run_opts_default(priority=prio)
+    tuned_ms = None
+    if not args.no_tune:
+        best, tuned_ms = hf.hf_batch_autotune(bd.b, stream, base)
+    else:
+        best = base
+    ls_pred, pe_pred = hf.hf_batch_predict(bd.b, prio, stream)
+    head = hf.opts_dict(best)
+    head.update(mode=hf.HF_MODE_AUTO, priority=prio)
+    chosen = hf.HF_MODE_PERSISTENT if pe_pred <= ls_pred else hf.HF_MODE_LEVELSYNC
+    bd.reset_y()
+    t_setup = time.time() - t_setup
+
+    def timed(opts_, steps, warmup, clocks=None):
         for _ in range(warmup):
             bd.run(stream, **opts_)
         bd.sync()
         barrier()
         evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
-        kms = []
+        if clocks:
+            clocks.start()
         evs[0].record(stream)
         for i in range(steps):
-            bd.run(stream, time_kernel=1, **opts_)
+            bd.run(stream, **opts_)
             evs[i + 1].record(stream)
-            kms.append(None)
         torch.cuda.synchronize()
+        clk = clocks.stop() if clocks else None
         st = bd.sync(check=False)
         barrier()
         step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(steps)]
-        kernel_ms = hf.hf_batch_kernel_ms(bd.b)  # last step's main kernel
-        return float(np.mean(step_ms)), float(np.median(step_ms)), kernel_ms, st
+        return float(np.mean(step_ms)), float(np.median(step_ms)), st, clk
 
-    # kernel-only time per step: one more pass with time_kernel, averaged
-    clocks = Clocks(local)
-    clocks.start()
-    ms_mean, ms_med, _, status = timed(opts, args.steps, args.warmup)
-    clk = clocks.stop()
-    kms = []
-    for _ in range(min(args.steps, 20)):
-        bd.run(stream, time_kernel=1, **opts)
-        kms.append(hf.hf_batch_kernel_ms(bd.b))
-    kernel_ms = float(np.mean(kms))
+    ms, ms_med, status, clk = timed(head, args.steps, args.warmup, Clocks(local))
     if status != 0:
         raise SystemExit("run failed: %s" % hf.hf_status_string(status))
-
-    ms = ms_mean
+    kms = []
+    for _ in range(min(args.steps, 20)):  # the dominant kernel alone, CUDA events on the stream
+        bd.run(stream, time_kernel=1, **head)
+        kms.append(hf.hf_batch_kernel_ms(bd.b))
+    kernel_ms = float(np.mean(kms))
     if world > 1:
         t = torch.tensor([ms], device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms = float(t.item())
-    N, E = wl.n_tasks, wl.n_edges
     value = world * N / (ms / 1e3)
 
-    compare = None
+    compare = {}
     if not args.no_compare:
-        other = dict(opts, mode=hf.HF_MODE_LEVELSYNC if mode == hf.HF_MODE_PERSISTENT else hf.HF_MODE_PERSISTENT)
-        c_mean, c_med, _, c_st = timed(other, max(5, args.steps // 4), 3)
-        compare = {"executor": "levelsync" if other["mode"] == hf.HF_MODE_LEVELSYNC else "persistent",
-                   "tasks_per_s": N / (c_mean / 1e3), "edges_per_s": E / (c_mean / 1e3), "ms_per_step": c_mean,
-                   "status": hf.hf_status_string(c_st)}
+        k = max(5, args.steps // 4)
+        for name, o in (("levelsync", dict(mode=hf.HF_MODE_LEVELSYNC)),
+                        ("persistent_fifo_default", dict(mode=hf.HF_MODE_PERSISTENT, priority=hf.HF_PRIO_FIFO)),
+                        ("persistent_fifo_tuned", dict(head, mode=hf.HF_MODE_PERSISTENT, priority=hf.HF_PRIO_FIFO)),
+                        ("persistent_heuristic_tuned", dict(head, mode=hf.HF_MODE_PERSISTENT,
+                                                            priority=hf.HF_PRIO_HEURISTIC))):
+            c_ms, c_med, c_st, _ = timed(o, k, 3)
+            compare[name] = {"ms_per_step": c_ms, "ms_median": c_med, "tasks_per_s": N / (c_ms / 1e3),
+                             "edges_per_s": E / (c_ms / 1e3), "status": hf.hf_status_string(c_st)}
+        compare["headline_over_levelsync"] = compare["levelsync"]["ms_per_step"] / ms
 
     e2e = None
     if not args.no_e2e:
@@ -305,12 +348,12 @@ def main():
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
             hf.hf_batch_set_delays(bd.b, delays, on_device=False, stream=stream)
-            bd.run(stream, **opts)
+            bd.run(stream, **head)
             hf.hf_batch_get_arrivals(bd.b, -1, N, out=arr_host.numpy())
         st = bd.sync(check=False)
         dt = (time.perf_counter() - t0) / steps
         e2e = {"value": world * N / dt, "unit": "tasks/s", "h2d_bytes_per_step": 4 * E,
-               "d2h_bytes_per_step": 4 * N + 4, "ms_per_step": 1e3 * dt, "status": hf.hf_status_string(st)}
+               "d2h_bytes_per_step": 4 * N + 12, "ms_per_step": 1e3 * dt, "status": hf.hf_status_string(st)}
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -320,30 +363,34 @@ def main():
 
     peak, peak_kind = peaks()
     b_alg = algorithmic_bytes(wl)
-    kname = "k_persist" if mode == hf.HF_MODE_PERSISTENT else "k_level"
+    kname = "k_persist" if chosen == hf.HF_MODE_PERSISTENT else "k_level"
     achieved = b_alg / (kernel_ms / 1e3) / 1e9
-    traffic = traffic_for(kname, args.workload)
     roof = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": traffic, "algorithmic_bytes": b_alg,
-            "kernel_ms": kernel_ms, "peak_source": peak_kind}
-    launches_per_step = 2 if mode == hf.HF_MODE_PERSISTENT else sum(1 for _ in range(max(g.levels for g in wl.graphs) or 1))
+            "frac": achieved / peak, "traffic": traffic_for(kname, args.workload), "algorithmic_bytes": b_alg,
+            "kernel_ms": kernel_ms, "peak_source": peak_kind + " (MEASURED_PEAKS hbm_gbs)"}
+    launches = 2 if chosen == hf.HF_MODE_PERSISTENT else max(g.levels for g in wl.graphs)
     line = {
         "metric": "DAG tasks/s", "value": value, "unit": "tasks/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "ms_per_step_median": ms_med, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "edges_per_s": world * E / (ms / 1e3),
-        "config": {"workload": args.workload, "executor": args.mode, "tasks": N, "edges": E,
-                   "graphs": len(wl.graphs), "saxpy_elems": wl.saxpy_elems, "ctas": args.ctas,
-                   "claim": args.claim, "local_keep": args.local_keep, "chunk_elems": args.chunk,
+        "config": {"workload": args.workload, "tasks": N, "edges": E, "graphs": len(wl.graphs),
+                   "saxpy_elems": wl.saxpy_elems, "executor": "auto",
+                   "chosen": "persistent" if chosen == hf.HF_MODE_PERSISTENT else "levelsync",
+                   "priority": {0: "fifo", 1: "heuristic", 2: "learned"}[prio],
+                   "launch": {k: head[k] for k in ("ctas", "claim", "local_keep", "chunk_elems")},
+                   "autotuned_ms": tuned_ms, "predicted_ms": {"levelsync": ls_pred, "persistent": pe_pred},
                    "l2": "inputs larger than L2 (graph %.0f MB + payload %.0f MB)" % (
-                       (8 * E + 16 * N) / 1e6, 8 * wl.saxpy_elems / 1e6),
-                   "setup_s": t_gen},
-        "compare": compare, "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
-        "gpu_launches": launches_per_step * args.steps,
+                       (16 * E + 24 * N) / 1e6, 8 * wl.saxpy_elems / 1e6),
+                   "setup_s": t_setup},
+        "learned": learned, "compare": compare, "e2e": e2e, "roofline": roof, "cpu_baseline": cpu,
+        "clocks": clk, "gpu_launches": launches * args.steps,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
     bd.close()
+    if cm is not None:
+        hf.hf_costmodel_destroy(cm)
     if world > 1:
         torch.distributed.destroy_process_group()
 

@@ -286,6 +286,27 @@ hf_status hf_batch_task_costs(hf_batch* b, int32_t priority, float* cost, float*
  * b = c. Enqueued on `stream`. */
 hf_status hf_batch_bottom_levels(hf_batch* b, const float* cost, float* bottom, void* stream);
 
+/* --- autotuning and executor choice ----------------------------------------------------- */
+
+/* Times trial runs of the persistent executor on this batch (coordinate descent over CTA
+ * count, queue claim size, shared-memory stack depth and payload piece size; each trial the
+ * median of 3 timed runs after one warm-up) and writes the fastest options to *best (mode
+ * PERSISTENT, other fields from `base`, NULL = defaults) and its time to *best_ms. Results are
+ * cached per size bucket (tasks, edges per task, payload share, depth), so a later call on a
+ * similar batch returns without trials unless `force`. Runs the batch many times: payloads run
+ * each time (saxpy updates y). Blocks. */
+hf_status hf_batch_autotune(hf_batch* b, void* stream, const hf_run_opts* base, int force, hf_run_opts* best,
+                            float* best_ms);
+
+/* Predicted makespans (ms) of the batch under each executor, from per-task costs of the given
+ * priority source (HEURISTIC or LEARNED) and two machine constants measured once per process
+ * on calibration graphs (level-synchronous time per level, persistent time per hop):
+ *   level-sync  = levels * t_level + sum over levels of the largest task cost in the level
+ *   persistent  = critical path of costs + depth * t_hop + total cost / warps
+ * HF_MODE_AUTO runs the executor with the smaller prediction (LEARNED costs when a model is
+ * attached, else HEURISTIC). */
+hf_status hf_batch_predict(hf_batch* b, int32_t priority, void* stream, float* levelsync_ms, float* persistent_ms);
+
 /* --- memory and diagnostics ------------------------------------------------------------ */
 
 /* Process-wide device allocator for library-owned buffers (NULL, NULL = cudaMalloc/cudaFree).

@@ -619,6 +619,24 @@ hf_status hf_batch_task_costs(hf_batch* b, int32_t priority, float* cost, float*
     return plan_task_costs(b->plan, priority, b->cm, cost, bottom, (cudaStream_t)stream);
 }
 
+hf_status hf_batch_autotune(hf_batch* b, void* stream, const hf_run_opts* base, int force, hf_run_opts* best,
+                            float* best_ms) {
+    if (!b || !best || !best_ms) return fail(HF_EINVAL, "NULL argument");
+    hf_status st = ensure_batch_plan(b);
+    if (st != HF_OK) return st;
+    hf_run_opts o;
+    if (base) o = *base;
+    else hf_run_opts_default(&o);
+    return plan_autotune(b->plan, (cudaStream_t)stream, o, force, best, best_ms);
+}
+
+hf_status hf_batch_predict(hf_batch* b, int32_t priority, void* stream, float* levelsync_ms, float* persistent_ms) {
+    if (!b || !levelsync_ms || !persistent_ms) return fail(HF_EINVAL, "NULL argument");
+    hf_status st = ensure_batch_plan(b);
+    if (st != HF_OK) return st;
+    return plan_predict(b->plan, priority, b->cm, (cudaStream_t)stream, levelsync_ms, persistent_ms);
+}
+
 hf_status hf_batch_bottom_levels(hf_batch* b, const float* cost, float* bottom, void* stream) {
     if (!b) return fail(HF_EINVAL, "batch is NULL");
     hf_status st = ensure_batch_plan(b);

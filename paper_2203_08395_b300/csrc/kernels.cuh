@@ -253,8 +253,17 @@ __global__ void __launch_bounds__(256) k_level(const LevelArgs a) {
 // kNarrowIn predecessors use a 32-bit max on the key half, a fence and an atomic decrement on
 // the count half instead, which avoids CAS retry storms on wide joins.
 
-constexpr uint32_t kWideMark = 0xFFFFu;  // edge record: successor is a wide join
-constexpr uint32_t kLongMark = 0xFFFFu;  // edge record: successor's out-degree does not fit 16 bits
+// Edge record word w: bits 0-6 successor's in-degree (kWideMark: wide join), bits 7-15 its
+// priority bucket (0 = lowest; all 0 under FIFO), bits 16-31 its out-degree (kLongMark: look it
+// up in meta).
+constexpr uint32_t kWideMark = 0x7Fu;
+constexpr uint32_t kLongMark = 0xFFFFu;
+constexpr int kPrioShift = 7;
+constexpr uint32_t kPrioMask = 0x1FFu;
+
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
 
 __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
     unsigned long long v;
@@ -307,7 +316,7 @@ __global__ void k_reset(const ResetArgs a) {
 // the rest, and every piece of a multi-piece payload task, go to the global queue with one
 // atomicAdd on its tail per warp.
 template <bool PAY>
-__device__ __forceinline__ void push_ready(const PersistArgs& a, int4 r, int4* stk, int& top, int lane) {
+__device__ __forceinline__ void push_ready(const PersistArgs& a, int4 r, int pr, int4* stk, int& top, int lane) {
     const int v = r.x;
     int nitems = 0;
     int first_item = v;
@@ -327,7 +336,17 @@ __device__ __forceinline__ void push_ready(const PersistArgs& a, int4 r, int4* s
     const bool single = (nitems == 1);
     const unsigned sm = __ballot_sync(kFull, single);
     const int room = a.local_keep - top;
-    const int rank = __popc(sm & lanemask_lt());
+    int rank;
+    if (__popc(sm) <= room) {
+        rank = __popc(sm & lanemask_lt());
+    } else {  // spill: the highest priority buckets stay in the warp's stack (ties: lane order)
+        rank = 0;
+#pragma unroll 8
+        for (int j = 0; j < 32; ++j) {
+            const int pj = __shfl_sync(kFull, pr, j);
+            if (((sm >> j) & 1u) && (pj > pr || (pj == pr && j < lane))) ++rank;
+        }
+    }
     bool go_global = nitems > 0;
     if (single && rank < room) {
         stk[top + rank] = r;
@@ -364,7 +383,7 @@ __device__ __forceinline__ void push_ready(const PersistArgs& a, int4 r, int4* s
 }
 
 // Releases successor v of a finished task: returns true when v becomes ready, with its final
-// key in *kv. rec.w holds v's in-degree (kWideMark for wide joins) in its low 16 bits.
+// key in *kv. f16 is v's in-degree from the edge record (kWideMark for wide joins).
 __device__ __forceinline__ bool release_succ(const PersistArgs& a, int v, uint32_t ck, uint32_t f16,
                                              uint32_t* kv) {
     unsigned long long* st = a.state + v;
@@ -542,8 +561,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_persist(const PersistArgs
                 deg = mt.y;
                 kt = (uint32_t)(ld_relaxed_u64(a.state + fin) >> 32);
             }
-            if (a.t_end) a.t_end[fin] = (int64_t)gtimer();
-            if (a.exec_count) {
+            if (a.exec_count) {  // finish ticket before any successor is released
                 a.tk_end[fin] = (int64_t)atomicAdd(&a.ctrl->ticket, 1ull);
                 atomicAdd(a.exec_count + fin, 1);
             }
@@ -572,18 +590,23 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_persist(const PersistArgs
             const int o_ex = __shfl_sync(kFull, excl, owner);
             const uint32_t o_k = __shfl_sync(kFull, kt, owner);
             int4 r = make_int4(-1, 0, 0, 0);
+            int pr = 0;
             if (e < total) {
                 const int4 rec = __ldg(a.erec + o_rs + (e - o_ex));
+                prefetch_l2(a.erec + rec.z);  // warm the successor's row while its CAS is in flight
                 const float cand = __fadd_rn(key2f(o_k), __int_as_float(rec.y));
+                const uint32_t w = (uint32_t)rec.w;
                 uint32_t kv;
-                if (release_succ(a, rec.x, f2key(cand), (uint32_t)rec.w & 0xFFFFu, &kv)) {
-                    int len = (int)((uint32_t)rec.w >> 16);
+                if (release_succ(a, rec.x, f2key(cand), w & kWideMark, &kv)) {
+                    int len = (int)(w >> 16);
                     if ((uint32_t)len == kLongMark) len = __ldg(a.meta + rec.x).y;
                     r = make_int4(rec.x, (int)kv, rec.z, len);
+                    pr = (int)((w >> kPrioShift) & kPrioMask);
                 }
             }
-            if (__ballot_sync(kFull, r.x >= 0)) push_ready<PAY>(a, r, stk, top, lane);
+            if (__ballot_sync(kFull, r.x >= 0)) push_ready<PAY>(a, r, pr, stk, top, lane);
         }
+        if (a.t_end && fin >= 0) a.t_end[fin] = (int64_t)gtimer();  // after its successors' release
         // completions reach ctrl->done in batches: when the warp goes idle, and every 32 rounds
         // so that the stall timer of idle warps sees progress made by long-busy warps
         ndone += (uint32_t)__popc(__ballot_sync(kFull, fin >= 0));

@@ -8,7 +8,10 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "hf_internal.h"
@@ -101,7 +104,12 @@ struct Plan {
     float* d_prio = nullptr;       // bottom-level weight per task under seed_prio
     int32_t seed_prio = HF_PRIO_FIFO;  // priority the seed order was built for
     const hf_costmodel* cm = nullptr;  // borrowed from the batch
+    int32_t auto_mode = -1;            // executor chosen by HF_MODE_AUTO (-1: not yet predicted)
+    const hf_costmodel* auto_cm = nullptr;
+    int32_t auto_ctas = 0;             // CTA count the persistent prediction assumed
 };
+
+hf_status plan_auto_mode(Plan* p, cudaStream_t s, int* mode);
 
 static hf_status plan_set_chunk(Plan* p, int64_t chunk_elems, cudaStream_t s);
 hf_status plan_prepare_priority(Plan* p, int32_t priority, const hf_costmodel* cm, cudaStream_t s);
@@ -558,7 +566,14 @@ hf_status plan_busy(Plan* p) {
 
 hf_status plan_run(Plan* p, cudaStream_t s, const hf_run_opts& o) {
     int mode = o.mode;
-    if (mode == HF_MODE_AUTO) mode = p->host_tasks.empty() ? HF_MODE_PERSISTENT : HF_MODE_LEVELSYNC;
+    if (mode == HF_MODE_AUTO) {
+        if (!p->host_tasks.empty()) {
+            mode = HF_MODE_LEVELSYNC;
+        } else {
+            hf_status st = plan_auto_mode(p, s, &mode);
+            if (st != HF_OK) return st;
+        }
+    }
     if (mode != HF_MODE_LEVELSYNC && mode != HF_MODE_PERSISTENT) return fail(HF_EINVAL, "unknown mode");
     if (mode == HF_MODE_PERSISTENT && !p->host_tasks.empty())
         return fail(HF_ENOTSUP, "host tasks need the level-synchronous executor");
@@ -825,6 +840,27 @@ __global__ void k_bottom(int p0, int p1, const int32_t* __restrict__ ls_node, co
     b[v] = __fadd_rn(mx, c[v]);
 }
 
+// Priority bucket of each edge's successor into its edge record: round(511 * b(v) / b_max)
+// (scale = 511 / b_max), or 0 everywhere when scale is 0 (FIFO).
+__global__ void k_set_prio_bits(int4* __restrict__ erec, int64_t m, const float* __restrict__ b, float scale) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
+        int4 r = erec[e];
+        uint32_t q = 0;
+        if (scale > 0.f) q = (uint32_t)fminf(fmaxf(rintf(b[r.x] * scale), 0.f), (float)kPrioMask);
+        r.w = (int)(((uint32_t)r.w & ~(kPrioMask << kPrioShift)) | (q << kPrioShift));
+        erec[e] = r;
+    }
+}
+
+static hf_status set_prio_bits(Plan* p, const float* b, float scale, cudaStream_t s) {
+    if (p->m == 0) return HF_OK;
+    const int grid = (int)std::min<int64_t>((p->m + 255) / 256, (int64_t)p->num_sms * 16);
+    k_set_prio_bits<<<grid, 256, 0, s>>>(p->d_erec, p->m, b, scale);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? HF_OK : cuda_fail(e, "k_set_prio_bits");
+}
+
 static hf_status ensure_cm_inputs(Plan* p, cudaStream_t s) {
     if (p->d_level) return HF_OK;
     hf_status st;
@@ -896,6 +932,8 @@ hf_status plan_prepare_priority(Plan* p, int32_t priority, const hf_costmodel* c
     if (priority == p->seed_prio && (priority == HF_PRIO_FIFO || p->d_prio)) return HF_OK;
     if (priority == HF_PRIO_FIFO) {
         std::sort(p->sources.begin(), p->sources.end());
+        hf_status st = set_prio_bits(p, nullptr, 0.f, s);
+        if (st != HF_OK) return st;
     } else {
         if (!p->d_prio) {
             p->d_prio = (float*)palloc(p, sizeof(float) * std::max<size_t>((size_t)p->n, 4), s);
@@ -911,6 +949,10 @@ hf_status plan_prepare_priority(Plan* p, int32_t priority, const hf_costmodel* c
         if (e != cudaSuccess) return cuda_fail(e, "priority download");
         std::stable_sort(p->sources.begin(), p->sources.end(),
                          [&](int32_t x, int32_t y) { return b[(size_t)x] > b[(size_t)y]; });
+        float bmax = 0.f;
+        for (float x : b) bmax = std::max(bmax, x);
+        st = set_prio_bits(p, p->d_prio, bmax > 0.f ? (float)kPrioMask / bmax : 0.f, s);
+        if (st != HF_OK) return st;
     }
     p->seed_prio = priority;
     p->chunk_elems = -1;  // seeds are rebuilt with the next piece layout
@@ -920,7 +962,214 @@ hf_status plan_prepare_priority(Plan* p, int32_t priority, const hf_costmodel* c
 hf_status plan_refresh_priorities(Plan* p, const hf_costmodel* cm, cudaStream_t s) {
     const int32_t pr = p->seed_prio;
     p->seed_prio = -1;
+    p->auto_mode = -1;
     return plan_prepare_priority(p, pr == -1 ? HF_PRIO_FIFO : pr, cm, s);
+}
+
+// ------------------------------------------------------------------ autotuning
+
+static hf_status time_runs(Plan* p, cudaStream_t s, const hf_run_opts& o, int reps, float* ms) {
+    hf_run_opts w = o;
+    w.time_kernel = 0;
+    hf_status st = plan_run(p, s, w);
+    if (st == HF_OK) st = plan_sync(p);
+    if (st != HF_OK) return st;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return fail(HF_ECUDA, "cudaEventCreate");
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(HF_ECUDA, "cudaEventCreate");
+    }
+    std::vector<float> t;
+    for (int i = 0; i < reps && st == HF_OK; ++i) {
+        cudaEventRecord(e0, s);
+        st = plan_run(p, s, w);
+        cudaEventRecord(e1, s);
+        if (st == HF_OK) st = plan_sync(p);
+        float x = 0.f;
+        if (st == HF_OK && cudaEventElapsedTime(&x, e0, e1) == cudaSuccess) t.push_back(x);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != HF_OK) return st;
+    std::sort(t.begin(), t.end());
+    *ms = t.empty() ? 0.f : t[t.size() / 2];
+    return HF_OK;
+}
+
+using TuneKey = std::tuple<int, int, int, int>;
+static std::mutex g_tune_mu;
+static std::map<TuneKey, std::pair<hf_run_opts, float>> g_tune_cache;
+
+static TuneKey tune_key(const Plan* p) {
+    const int logn = p->n > 0 ? (int)std::floor(std::log2((double)p->n)) : 0;
+    const int epn = p->n > 0 ? (int)std::lround(10.0 * (double)p->m / (double)p->n) : 0;
+    const int payq = p->n > 0 ? (int)std::lround(20.0 * (double)p->npay / (double)p->n) : 0;
+    const int logd = p->levels > 0 ? (int)std::floor(std::log2((double)p->levels)) : 0;
+    return TuneKey(logn, epn, payq, logd);
+}
+
+hf_status plan_autotune(Plan* p, cudaStream_t s, const hf_run_opts& base, int force, hf_run_opts* best,
+                        float* best_ms) {
+    const TuneKey key = tune_key(p);
+    if (!force) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            *best = base;
+            best->mode = HF_MODE_PERSISTENT;
+            best->ctas = it->second.first.ctas;
+            best->claim = it->second.first.claim;
+            best->local_keep = it->second.first.local_keep;
+            best->chunk_elems = it->second.first.chunk_elems;
+            *best_ms = it->second.second;
+            return HF_OK;
+        }
+    }
+    hf_run_opts cur = base;
+    cur.mode = HF_MODE_PERSISTENT;
+    cur.instrument = cur.validate = cur.time_kernel = 0;
+    cur.stall_task = -1;
+    const int sms = p->num_sms;
+    cur.ctas = 2 * sms;
+    cur.claim = 8;
+    cur.local_keep = 8;
+    if (cur.chunk_elems <= 0) cur.chunk_elems = 16384;
+    float best_t = 0.f;
+    hf_status st = time_runs(p, s, cur, 3, &best_t);
+    if (st != HF_OK) return st;
+    const std::vector<int> ctas_v{sms / 2, sms, 2 * sms, 4 * sms};
+    const std::vector<int> claim_v{1, 4, 16, 32};
+    const std::vector<int> keep_v{4, 8, 16, 32};
+    const std::vector<int64_t> chunk_v{4096, 16384, 65536};
+    for (int round = 0; round < 2; ++round) {
+        for (int dim = 0; dim < 4; ++dim) {
+            if (dim == 3 && p->npay == 0) continue;
+            const size_t nv = dim == 0 ? ctas_v.size() : dim == 1 ? claim_v.size() : dim == 2 ? keep_v.size() : chunk_v.size();
+            for (size_t i = 0; i < nv; ++i) {
+                hf_run_opts t = cur;
+                if (dim == 0) t.ctas = ctas_v[i];
+                else if (dim == 1) t.claim = claim_v[i];
+                else if (dim == 2) t.local_keep = keep_v[i];
+                else t.chunk_elems = chunk_v[i];
+                if (t.ctas == cur.ctas && t.claim == cur.claim && t.local_keep == cur.local_keep &&
+                    t.chunk_elems == cur.chunk_elems)
+                    continue;
+                float ms = 0.f;
+                if ((st = time_runs(p, s, t, 3, &ms)) != HF_OK) return st;
+                if (ms < best_t) {
+                    best_t = ms;
+                    cur = t;
+                }
+            }
+        }
+    }
+    *best = cur;
+    *best_ms = best_t;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = std::make_pair(cur, best_t);
+    return HF_OK;
+}
+
+// ------------------------------------------------------------------ executor choice
+
+// Machine constants for the makespan predictions, measured once per process on a chain of
+// tasks: the level-synchronous executor's time per level and the persistent executor's time
+// per dependent hop.
+static std::mutex g_cal_mu;
+static bool g_cal_done = false;
+static float g_t_level_ns = 0.f, g_t_hop_ns = 0.f;
+
+static hf_status calibrate(cudaStream_t s) {
+    std::lock_guard<std::mutex> lk(g_cal_mu);
+    if (g_cal_done) return HF_OK;
+    const int32_t n = 2048;
+    hf_graph* g = nullptr;
+    hf_status st = hf_graph_create(&g, n, n);
+    if (st != HF_OK) return st;
+    st = hf_add_tasks_bulk(g, n, nullptr, nullptr);
+    for (int32_t i = 0; i + 1 < n && st == HF_OK; ++i) st = hf_precede_w(g, i, i + 1, 1.0f);
+    if (st == HF_OK) st = hf_finalize(g);
+    Plan* p = nullptr;
+    if (st == HF_OK) {
+        std::vector<hf_graph*> one{g};
+        st = plan_build(one, &p);
+    }
+    float tl = 0.f, tp = 0.f;
+    if (st == HF_OK) {
+        hf_run_opts o;
+        hf_run_opts_default(&o);
+        o.mode = HF_MODE_LEVELSYNC;
+        st = time_runs(p, s, o, 3, &tl);
+        o.mode = HF_MODE_PERSISTENT;
+        o.ctas = p->num_sms;
+        if (st == HF_OK) st = time_runs(p, s, o, 3, &tp);
+    }
+    if (p) plan_destroy(p);
+    hf_graph_destroy(g);
+    if (st != HF_OK) return st;
+    g_t_level_ns = 1e6f * tl / (float)n;
+    g_t_hop_ns = 1e6f * tp / (float)n;
+    g_cal_done = true;
+    return HF_OK;
+}
+
+hf_status plan_predict(Plan* p, int32_t priority, const hf_costmodel* cm, cudaStream_t s, float* ls_ms, float* p_ms) {
+    hf_status st = calibrate(s);
+    if (st != HF_OK) return st;
+    if (p->n == 0) {
+        *ls_ms = *p_ms = 0.f;
+        return HF_OK;
+    }
+    float* c = (float*)dev_alloc(sizeof(float) * (size_t)p->n, s);
+    float* b = (float*)dev_alloc(sizeof(float) * (size_t)p->n, s);
+    if (!c || !b) {
+        dev_free(c, s);
+        dev_free(b, s);
+        return fail(HF_ENOMEM, "device allocation failed: prediction");
+    }
+    st = plan_task_costs(p, priority, cm, c, b, s);
+    std::vector<float> hc, hb;
+    if (st == HF_OK) {
+        hc.resize((size_t)p->n);
+        hb.resize((size_t)p->n);
+        cudaError_t e = cudaMemcpy(hc.data(), c, sizeof(float) * (size_t)p->n, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(hb.data(), b, sizeof(float) * (size_t)p->n, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) st = cuda_fail(e, "prediction download");
+    }
+    dev_free(c, s);
+    dev_free(b, s);
+    if (st != HF_OK) return st;
+    double cp = 0.0, work = 0.0;
+    std::vector<double> lmax((size_t)std::max(p->levels, 1), 0.0);
+    for (int32_t v = 0; v < p->n; ++v) {
+        cp = std::max(cp, (double)hb[(size_t)v]);
+        work += hc[(size_t)v];
+        double& m = lmax[(size_t)p->h_level[(size_t)v]];
+        m = std::max(m, (double)hc[(size_t)v]);
+    }
+    double lsum = 0.0;
+    for (double x : lmax) lsum += x;
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_persist<false>, kWarpsPerCta * 32, 0);
+    const double warps = (double)p->num_sms * std::max(occ, 1) * kWarpsPerCta;
+    *ls_ms = (float)(((double)p->levels * g_t_level_ns + lsum) / 1e6);
+    *p_ms = (float)((cp + (double)p->levels * g_t_hop_ns + work / warps) / 1e6);
+    return HF_OK;
+}
+
+hf_status plan_auto_mode(Plan* p, cudaStream_t s, int* mode) {
+    if (p->auto_mode >= 0 && p->auto_cm == p->cm) {
+        *mode = p->auto_mode;
+        return HF_OK;
+    }
+    float ls = 0.f, pe = 0.f;
+    hf_status st = plan_predict(p, p->cm ? HF_PRIO_LEARNED : HF_PRIO_HEURISTIC, p->cm, s, &ls, &pe);
+    if (st != HF_OK) return st;
+    p->auto_mode = pe <= ls ? HF_MODE_PERSISTENT : HF_MODE_LEVELSYNC;
+    p->auto_cm = p->cm;
+    *mode = p->auto_mode;
+    return HF_OK;
 }
 
 }  // namespace hf

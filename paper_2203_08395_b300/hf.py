@@ -134,6 +134,8 @@ def load():
         "hf_batch_refresh_priorities": [vp, vp],
         "hf_batch_task_costs": [vp, i32, vp, vp, vp],
         "hf_batch_bottom_levels": [vp, vp, vp, vp],
+        "hf_batch_autotune": [vp, vp, P(hf_run_opts), ctypes.c_int, P(hf_run_opts), P(ctypes.c_float)],
+        "hf_batch_predict": [vp, i32, vp, P(ctypes.c_float), P(ctypes.c_float)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -458,6 +460,27 @@ def hf_batch_task_costs(b, priority, cost, bottom, stream=None):
 def hf_batch_bottom_levels(b, cost, bottom, stream=None):
     _check(load().hf_batch_bottom_levels(b, _ptr(cost), _ptr(bottom), _stream_handle(stream)),
            "hf_batch_bottom_levels")
+
+
+def hf_batch_autotune(b, stream=None, base=None, force=False):
+    """Returns (best hf_run_opts, best ms)."""
+    best = hf_run_opts()
+    ms = ctypes.c_float()
+    _check(load().hf_batch_autotune(b, _stream_handle(stream), ctypes.byref(base) if base is not None else None,
+                                    1 if force else 0, ctypes.byref(best), ctypes.byref(ms)), "hf_batch_autotune")
+    return best, ms.value
+
+
+def hf_batch_predict(b, priority, stream=None):
+    """Returns (predicted level-sync ms, predicted persistent ms)."""
+    ls, pe = ctypes.c_float(), ctypes.c_float()
+    _check(load().hf_batch_predict(b, priority, _stream_handle(stream), ctypes.byref(ls), ctypes.byref(pe)),
+           "hf_batch_predict")
+    return ls.value, pe.value
+
+
+def opts_dict(o):
+    return {k: getattr(o, k) for k, _ in hf_run_opts._fields_}
 
 
 def hf_status_string(s):

@@ -1,0 +1,88 @@
+"""GPU tests of the batch executor's tuning and learned parts: the autotuner's choice runs
+bit-exact and is cached; HF_MODE_AUTO predicts and runs; a model trained on recorded timings
+predicts task costs better than the plain heuristic on held-out graphs, and its priorities
+never change results."""
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2203_08395_b300 import build as B
+from paper_2203_08395_b300 import hf, learn
+from paper_2203_08395_b300 import synth as S
+from paper_2203_08395_b300.workload import BatchOnDevice
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    B.build()
+    hf.install_torch_allocator()
+
+
+def _mixed_batch(seed, graphs=24):
+    return S.batch(seed, graphs=graphs, nmin=2000, nmax=40000, frac_saxpy=0.1, sx_min=256, sx_max=4096)
+
+
+def _check(bd):
+    for i, spec in enumerate(bd.wl.graphs):
+        ref = oracle.run_spec(spec, with_data=False)["arr"]
+        np.testing.assert_array_equal(bd.arrivals(i).view(np.uint32), ref.view(np.uint32))
+
+
+def test_autotune_choice_is_exact_and_cached():
+    bd = BatchOnDevice(S.batch(9, graphs=20, nmin=2000, nmax=50000))
+    best, ms = hf.hf_batch_autotune(bd.b)
+    assert ms > 0 and best.mode == hf.HF_MODE_PERSISTENT and best.ctas > 0
+    bd.run(**hf.opts_dict(best))
+    bd.sync()
+    _check(bd)
+    t0 = time.perf_counter()
+    again, ms2 = hf.hf_batch_autotune(bd.b)
+    assert time.perf_counter() - t0 < 0.5 and ms2 == ms
+    assert (again.ctas, again.claim, again.local_keep) == (best.ctas, best.claim, best.local_keep)
+    bd.close()
+
+
+def test_auto_mode_predicts_and_runs_exactly():
+    bd = BatchOnDevice(S.batch(10, graphs=12, nmin=1000, nmax=20000))
+    ls, pe = hf.hf_batch_predict(bd.b, hf.HF_PRIO_HEURISTIC)
+    assert ls > 0 and pe > 0
+    bd.run(mode=hf.HF_MODE_AUTO)
+    bd.sync()
+    _check(bd)
+    bd.close()
+
+
+def test_learned_model_beats_heuristic_on_held_out_graphs():
+    train = []
+    for seed in (1, 2):
+        tb = BatchOnDevice(_mixed_batch(seed))
+        train.append(learn.record(tb))
+        tb.close()
+    cm = hf.hf_costmodel_create(0)
+    loss = learn.train(cm, train, rows=131072, epochs=10)
+    assert np.isfinite(loss)
+    bd = BatchOnDevice(_mixed_batch(0))
+    err = learn.evaluate(bd, cm, learn.record(bd))
+    print("held-out cost error:", err)
+    assert err["learned"]["mse_log"] < err["heuristic"]["mse_log"]
+    assert err["learned"]["mape"] < err["heuristic"]["mape"]
+    # priorities from the model drive the run; results stay bit-exact
+    hf.hf_batch_set_costmodel(bd.b, cm)
+    times = {}
+    for name, prio in (("fifo", hf.HF_PRIO_FIFO), ("heuristic", hf.HF_PRIO_HEURISTIC),
+                       ("learned", hf.HF_PRIO_LEARNED)):
+        bd.reset_y()
+        bd.run(priority=prio, time_kernel=1)
+        bd.sync()
+        times[name] = hf.hf_batch_kernel_ms(bd.b)
+        _check(bd)
+    print("makespan ms by priority:", times)
+    bd.close()
+    hf.hf_costmodel_destroy(cm)
