@@ -286,7 +286,7 @@ def main():
     else:
         best = base
     ls_pred, pe_pred = hf.hf_batch_predict(bd.b, prio, stream)
-    head = hf.opts_dict(best)
+    head = {k: v for k, v in hf.opts_dict(best).items() if k not in ("time_kernel", "instrument", "validate")}
     head.update(mode=hf.HF_MODE_AUTO, priority=prio)
     chosen = hf.HF_MODE_PERSISTENT if pe_pred <= ls_pred else hf.HF_MODE_LEVELSYNC
     bd.reset_y()

@@ -253,13 +253,14 @@ __global__ void __launch_bounds__(256) k_level(const LevelArgs a) {
 // kNarrowIn predecessors use a 32-bit max on the key half, a fence and an atomic decrement on
 // the count half instead, which avoids CAS retry storms on wide joins.
 
-// Edge record word w: bits 0-6 successor's in-degree (kWideMark: wide join), bits 7-15 its
-// priority bucket (0 = lowest; all 0 under FIFO), bits 16-31 its out-degree (kLongMark: look it
-// up in meta).
+// Edge record word w: bits 0-6 successor's in-degree (kWideMark: wide join), bits 7-14 its
+// priority bucket (0 = lowest; all 0 under FIFO), bit 15 set when it has a payload, bits 16-31
+// its out-degree (kLongMark: look it up in meta).
 constexpr uint32_t kWideMark = 0x7Fu;
 constexpr uint32_t kLongMark = 0xFFFFu;
 constexpr int kPrioShift = 7;
-constexpr uint32_t kPrioMask = 0x1FFu;
+constexpr uint32_t kPrioMask = 0xFFu;
+constexpr uint32_t kPayBit = 1u << 15;
 
 __device__ __forceinline__ void prefetch_l2(const void* p) {
     asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
@@ -322,14 +323,12 @@ __device__ __forceinline__ void push_ready(const PersistArgs& a, int4 r, int pr,
     int first_item = v;
     if (v >= 0) {
         nitems = 1;
-        if (PAY && a.pidx) {
+        if (PAY && r.w < 0) {  // the task has a payload: split into pieces?
             const int p = __ldg(a.pidx + v);
-            if (p >= 0) {
-                const int nc = a.pay[p].nchunks;
-                if (nc > 1) {
-                    nitems = nc;
-                    first_item = a.n_tasks + a.pay[p].chunk_first;
-                }
+            const int nc = a.pay[p].nchunks;
+            if (nc > 1) {
+                nitems = nc;
+                first_item = a.n_tasks + a.pay[p].chunk_first;
             }
         }
     }
@@ -409,6 +408,61 @@ __device__ __forceinline__ bool release_succ(const PersistArgs& a, int v, uint32
     fence_acq_rel();
     *kv = ld_relaxed_u(khalf);
     return true;
+}
+
+// Releases every successor of this warp's finishing tasks (lane: task `fin` >= 0 with arrival
+// key kt, first out-edge rs, out-degree deg), flattened over the warp 32 edges at a time, and
+// pushes the ones that become ready with their key, row and payload flag.
+// Memory order: the arrival travels inside the state word, so plain releases need no fence.
+// Payload data is ordered by fences: a warp fences after running payload pieces (release) and
+// before running pieces of a task that became ready (acquire); and a window that releases a
+// task with a payload fences first, so that data written upstream by a payload task reaches it
+// through plain tasks in between (each such warp acquires what it observed, then releases).
+template <bool PAY>
+__device__ __forceinline__ void release_all(const PersistArgs& a, int fin, uint32_t kt, int rs, int deg, int4* stk,
+                                            int& top, int lane) {
+    if (fin < 0) deg = 0;
+    int incl = deg;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const int total = __shfl_sync(kFull, incl, 31);
+    const int excl = incl - deg;
+    for (int e0 = 0; e0 < total; e0 += 32) {
+        const int e = e0 + lane;
+        int owner = 0;
+#pragma unroll
+        for (int b = 16; b >= 1; b >>= 1) {
+            const int probe = owner + b - 1;
+            const int iv = __shfl_sync(kFull, incl, probe);
+            if (iv <= e) owner += b;
+        }
+        const int o_rs = __shfl_sync(kFull, rs, owner);
+        const int o_ex = __shfl_sync(kFull, excl, owner);
+        const uint32_t o_k = __shfl_sync(kFull, kt, owner);
+        int4 rec = make_int4(-1, 0, 0, 0);
+        if (e < total) {
+            rec = __ldg(a.erec + o_rs + (e - o_ex));
+            prefetch_l2(a.erec + rec.z);  // warm the successor's row while its CAS is in flight
+        }
+        const uint32_t w = (uint32_t)rec.w;
+        if (PAY && __ballot_sync(kFull, rec.x >= 0 && (w & kPayBit))) fence_acq_rel();
+        int4 r = make_int4(-1, 0, 0, 0);
+        int pr = 0;
+        if (rec.x >= 0) {
+            const float cand = __fadd_rn(key2f(o_k), __int_as_float(rec.y));
+            uint32_t kv;
+            if (release_succ(a, rec.x, f2key(cand), w & kWideMark, &kv)) {
+                int len = (int)(w >> 16);
+                if ((uint32_t)len == kLongMark) len = __ldg(a.meta + rec.x).y;
+                r = make_int4(rec.x, (int)kv, rec.z, len | ((w & kPayBit) ? (int)0x80000000u : 0));
+                pr = (int)((w >> kPrioShift) & kPrioMask);
+            }
+        }
+        if (__ballot_sync(kFull, r.x >= 0)) push_ready<PAY>(a, r, pr, stk, top, lane);
+    }
 }
 
 template <bool PAY>
@@ -492,43 +546,64 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_persist(const PersistArgs
         }
         backoff = 32;
 
-        // ---- resolve items; run payload pieces; find the tasks that finish in this round
-        int fin = -1;
+        // ---- resolve this round's items: task (with key, row, payload flag) or payload piece
+        int t = -1, p = -1, piece = 0;
         uint32_t kt = 0;
         int rs = 0, deg = 0;
-        bool known = loc.x >= 0;  // key and row came with the item from the local stack
-        if (known) {
-            kt = (uint32_t)loc.y;
-            rs = loc.z;
-            deg = loc.w;
-        }
-        if (PAY && a.pidx) {
-            int t = -1, p = -1, piece = 0;
-            if (item >= 0) {
-                if (item < n_tasks) {
-                    t = item;
-                    p = __ldg(a.pidx + t);
-                } else {
-                    const int g = item - n_tasks;
-                    t = __ldg(a.chunk_task + g);
-                    p = __ldg(a.pidx + t);
-                    piece = g - a.pay[p].chunk_first;
+        bool haspay = false;
+        if (item >= 0) {
+            if (item < n_tasks) {
+                t = item;
+                if (loc.x >= 0) {  // from the warp's stack: key, row and flag came along
+                    kt = (uint32_t)loc.y;
+                    rs = loc.z;
+                    deg = loc.w & 0x7fffffff;
+                    haspay = PAY && loc.w < 0;
+                } else {  // from the global queue
+                    const int2 mt = __ldg(a.meta + t);
+                    rs = mt.x;
+                    deg = mt.y;
+                    kt = (uint32_t)(ld_relaxed_u64(a.state + t) >> 32);
+                    haspay = PAY && a.pidx && __ldg(a.pidx + t) >= 0;
                 }
-                if (a.t_start) {
-                    const int64_t now = (int64_t)gtimer();
-                    if (item < n_tasks) a.t_start[t] = now;
-                    else atomicMin((long long*)(a.t_start + t), (long long)now);
-                }
-                if (a.exec_count) {
-                    const long long tk = (long long)atomicAdd(&a.ctrl->ticket, 1ull);
-                    if (item < n_tasks) a.tk_start[t] = tk;
-                    else atomicCAS((unsigned long long*)(a.tk_start + t), ~0ull, (unsigned long long)tk);
-                }
+                if (PAY && haspay) p = __ldg(a.pidx + t);
+            } else if (PAY) {  // a piece of a multi-piece payload task
+                const int g = item - n_tasks;
+                t = __ldg(a.chunk_task + g);
+                p = __ldg(a.pidx + t);
+                piece = g - a.pay[p].chunk_first;
+                haspay = true;
             }
-            unsigned work = __ballot_sync(kFull, p >= 0);
+            if (a.t_start) {
+                const int64_t now = (int64_t)gtimer();
+                if (item < n_tasks) a.t_start[t] = now;
+                else atomicMin((long long*)(a.t_start + t), (long long)now);
+            }
+            if (a.exec_count) {
+                const long long tk = (long long)atomicAdd(&a.ctrl->ticket, 1ull);
+                if (item < n_tasks) a.tk_start[t] = tk;
+                else atomicCAS((unsigned long long*)(a.tk_start + t), ~0ull, (unsigned long long)tk);
+            }
+        }
+
+        // ---- phase 1: tasks without payload finish now and release their successors
+        int fin = (item >= 0 && !haspay) ? t : -1;
+        if (fin >= 0) {
+            if (a.exec_count) {  // finish ticket before any successor is released
+                a.tk_end[fin] = (int64_t)atomicAdd(&a.ctrl->ticket, 1ull);
+                atomicAdd(a.exec_count + fin, 1);
+            }
+            a.key[fin] = kt;
+        }
+        if (__ballot_sync(kFull, fin >= 0)) release_all<PAY>(a, fin, kt, rs, deg, stk, top, lane);
+        if (a.t_end && fin >= 0) a.t_end[fin] = (int64_t)gtimer();
+        ndone += (uint32_t)__popc(__ballot_sync(kFull, fin >= 0));
+
+        // ---- phase 2: payload pieces, then the payload tasks that completed release theirs
+        if (PAY) {
+            unsigned work = __ballot_sync(kFull, haspay);
             if (work) {
-                fence_acq_rel();  // acquire: inputs written by the payload tasks before us
-                const unsigned w0 = work;
+                fence_acq_rel();  // acquire: inputs written by upstream payload tasks
                 while (work) {
                     const int src = __ffs(work) - 1;
                     work &= work - 1;
@@ -536,80 +611,34 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_persist(const PersistArgs
                     const int pc = __shfl_sync(kFull, piece, src);
                     run_piece(a.pay[pp], pc, lane);
                 }
-                (void)w0;
                 fence_acq_rel();  // release: every lane's payload writes before any release below
                 __syncwarp();
-            }
-            if (item >= 0) {
-                if (p < 0 || item < n_tasks) fin = t;
-                else if (atom_dec_acq_rel(a.chunks_left + p) == 1) fin = t;
-                if (item >= n_tasks) known = false;  // a piece carries no key/row
-            }
-        } else {
-            fin = item;
-            if (item >= 0) {
-                if (a.t_start) a.t_start[item] = (int64_t)gtimer();
-                if (a.exec_count) a.tk_start[item] = (int64_t)atomicAdd(&a.ctrl->ticket, 1ull);
+                int fin2 = -1;
+                if (haspay) {
+                    if (item < n_tasks) fin2 = t;
+                    else if (atom_dec_acq_rel(a.chunks_left + p) == 1) fin2 = t;
+                }
+                if (fin2 >= 0) {
+                    if (item >= n_tasks) {  // last piece: the task's key and row
+                        const int2 mt = __ldg(a.meta + t);
+                        rs = mt.x;
+                        deg = mt.y;
+                        kt = (uint32_t)(ld_relaxed_u64(a.state + t) >> 32);
+                    }
+                    if (a.exec_count) {
+                        a.tk_end[fin2] = (int64_t)atomicAdd(&a.ctrl->ticket, 1ull);
+                        atomicAdd(a.exec_count + fin2, 1);
+                    }
+                    a.key[fin2] = kt;
+                }
+                if (__ballot_sync(kFull, fin2 >= 0)) release_all<PAY>(a, fin2, kt, rs, deg, stk, top, lane);
+                if (a.t_end && fin2 >= 0) a.t_end[fin2] = (int64_t)gtimer();
+                ndone += (uint32_t)__popc(__ballot_sync(kFull, fin2 >= 0));
             }
         }
 
-        // ---- finish: key and row of tasks that came from the global queue, stamps, arrival
-        if (fin >= 0) {
-            if (!known) {
-                const int2 mt = __ldg(a.meta + fin);
-                rs = mt.x;
-                deg = mt.y;
-                kt = (uint32_t)(ld_relaxed_u64(a.state + fin) >> 32);
-            }
-            if (a.exec_count) {  // finish ticket before any successor is released
-                a.tk_end[fin] = (int64_t)atomicAdd(&a.ctrl->ticket, 1ull);
-                atomicAdd(a.exec_count + fin, 1);
-            }
-            a.key[fin] = kt;
-        } else {
-            deg = 0;
-        }
-        int incl = deg;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(kFull, incl, o);
-            if (lane >= o) incl += y;
-        }
-        const int total = __shfl_sync(kFull, incl, 31);
-        const int excl = incl - deg;
-        for (int e0 = 0; e0 < total; e0 += 32) {
-            const int e = e0 + lane;
-            int owner = 0;
-#pragma unroll
-            for (int b = 16; b >= 1; b >>= 1) {
-                const int probe = owner + b - 1;
-                const int iv = __shfl_sync(kFull, incl, probe);
-                if (iv <= e) owner += b;
-            }
-            const int o_rs = __shfl_sync(kFull, rs, owner);
-            const int o_ex = __shfl_sync(kFull, excl, owner);
-            const uint32_t o_k = __shfl_sync(kFull, kt, owner);
-            int4 r = make_int4(-1, 0, 0, 0);
-            int pr = 0;
-            if (e < total) {
-                const int4 rec = __ldg(a.erec + o_rs + (e - o_ex));
-                prefetch_l2(a.erec + rec.z);  // warm the successor's row while its CAS is in flight
-                const float cand = __fadd_rn(key2f(o_k), __int_as_float(rec.y));
-                const uint32_t w = (uint32_t)rec.w;
-                uint32_t kv;
-                if (release_succ(a, rec.x, f2key(cand), w & kWideMark, &kv)) {
-                    int len = (int)(w >> 16);
-                    if ((uint32_t)len == kLongMark) len = __ldg(a.meta + rec.x).y;
-                    r = make_int4(rec.x, (int)kv, rec.z, len);
-                    pr = (int)((w >> kPrioShift) & kPrioMask);
-                }
-            }
-            if (__ballot_sync(kFull, r.x >= 0)) push_ready<PAY>(a, r, pr, stk, top, lane);
-        }
-        if (a.t_end && fin >= 0) a.t_end[fin] = (int64_t)gtimer();  // after its successors' release
         // completions reach ctrl->done in batches: when the warp goes idle, and every 32 rounds
         // so that the stall timer of idle warps sees progress made by long-busy warps
-        ndone += (uint32_t)__popc(__ballot_sync(kFull, fin >= 0));
         if ((++iter & 31u) == 0 && ndone) {
             if (lane == 0) atomicAdd(&a.ctrl->done, ndone);
             ndone = 0;

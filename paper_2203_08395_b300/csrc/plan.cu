@@ -370,6 +370,8 @@ hf_status plan_build(const std::vector<hf_graph*>& graphs, Plan** out) {
 
         // uploads
         if ((st = upload(p, &p->d_row_ptr, row_ptr.data(), row_ptr.size(), s, "row_ptr")) != HF_OK) return bail(st);
+        for (auto& r : erec)  // flag successors that carry a payload
+            if (p->hpidx[(size_t)r.x] >= 0) r.w = (int)((uint32_t)r.w | kPayBit);
         if ((st = upload(p, &p->d_erec, erec.data(), erec.size(), s, "erec")) != HF_OK) return bail(st);
         if ((st = upload(p, &p->d_meta, meta.data(), meta.size(), s, "meta")) != HF_OK) return bail(st);
         if ((st = upload(p, &p->d_indeg0, indeg0.data(), indeg0.size(), s, "indeg0")) != HF_OK) return bail(st);
@@ -581,7 +583,9 @@ hf_status plan_run(Plan* p, cudaStream_t s, const hf_run_opts& o) {
     if (o.priority == HF_PRIO_LEARNED && !p->cm) return fail(HF_ESTATE, "HF_PRIO_LEARNED needs a cost model (hf_batch_set_costmodel)");
     hf_status st = HF_OK;
     if (mode == HF_MODE_PERSISTENT && (st = plan_prepare_priority(p, o.priority, p->cm, s)) != HF_OK) return st;
-    int64_t chunk = o.chunk_elems > 0 ? o.chunk_elems : 16384;
+    // default piece: 2,048 elements for level-sync (a level's payloads spread over many warps),
+    // 16,384 for the persistent executor (fewer queue items)
+    int64_t chunk = o.chunk_elems > 0 ? o.chunk_elems : (mode == HF_MODE_LEVELSYNC ? 2048 : 16384);
     chunk = ((chunk + 31) / 32) * 32;
     st = plan_set_chunk(p, chunk, s);
     if (st != HF_OK) return st;

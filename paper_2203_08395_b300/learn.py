@@ -5,8 +5,9 @@ record()   runs a batch with per-task %globaltimer stamps (instrument=1) and ret
            device, every task's 12 features and its log cost (log ns from start to the end of
            its successors' release);
 train()    trains a model on rows pooled from several recordings (hf_costmodel_train);
-evaluate() compares the model's and the plain heuristic's cost predictions on a recording
-           (mean absolute percentage error in ns, and MSE in log space).
+evaluate() compares the model's and the plain heuristic's cost predictions on a recording:
+           MSE of log costs, median |log(predicted / actual)| and symmetric mean absolute
+           percentage error (plain MAPE is not used: it caps under-prediction at 100%).
 """
 from __future__ import annotations
 
@@ -76,8 +77,10 @@ def evaluate(bd, cm, recording, stream=None):
     heur = cost.double()
     out = {}
     for name, pred in (("learned", learned), ("heuristic", heur)):
+        lr = torch.log(pred) - t.double()
         out[name] = {
-            "mape": float(torch.mean(torch.abs(pred - actual) / actual)),
-            "mse_log": float(torch.mean((torch.log(pred) - t.double()) ** 2)),
+            "mse_log": float(torch.mean(lr ** 2)),
+            "median_abs_log_ratio": float(torch.median(torch.abs(lr))),
+            "smape": float(torch.mean(2 * torch.abs(pred - actual) / (pred + actual))),
         }
     return out

@@ -71,8 +71,8 @@ def test_learned_model_beats_heuristic_on_held_out_graphs():
     bd = BatchOnDevice(_mixed_batch(0))
     err = learn.evaluate(bd, cm, learn.record(bd))
     print("held-out cost error:", err)
-    assert err["learned"]["mse_log"] < err["heuristic"]["mse_log"]
-    assert err["learned"]["mape"] < err["heuristic"]["mape"]
+    for k in ("mse_log", "median_abs_log_ratio", "smape"):
+        assert err["learned"][k] < err["heuristic"][k], k
     # priorities from the model drive the run; results stay bit-exact
     hf.hf_batch_set_costmodel(bd.b, cm)
     times = {}
