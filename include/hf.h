@@ -108,13 +108,14 @@ typedef struct {
     int32_t ctas;           /* persistent: CTAs launched; 0 = one per SM times occupancy */
     int32_t warps_per_cta;  /* persistent: 0 = 8 */
     int32_t claim;          /* persistent: queue slots a warp claims at once, 1..32; 0 = 1 */
-    int32_t local_keep;     /* persistent: ready tasks a warp keeps in shared memory, 0..64;
-                               negative = default (32) */
+    int32_t local_keep;     /* persistent: ready tasks a warp keeps in shared memory, 0..32;
+                               negative = default (16) */
     int64_t chunk_elems;    /* payload split size in elements (saxpy) or 4-byte words (copies);
                                0 = 16384 */
     uint64_t spin_limit_ns; /* persistent: give up (HF_ETIMEDOUT) after this long without any
                                task completing; 0 = 2 s */
-    int32_t instrument;     /* record per-task %globaltimer start/end (hf_get_task_times) */
+    int32_t instrument;     /* bit 0: record per-task %globaltimer start/end (hf_get_task_times);
+                               bit 1: record persistent-executor counters (hf_batch_get_stats) */
     int32_t validate;       /* record per-task start/finish tickets and execution counts */
     int32_t stall_task;     /* failure-injection hook for tests: -1 = off; else this task's
                                pending-predecessor counter starts one too high, so it never
@@ -221,6 +222,11 @@ hf_status hf_batch_get_arrivals(hf_batch* b, int32_t index, float* out, int on_d
 hf_status hf_batch_get_task_times(hf_batch* b, int32_t index, int64_t* t_start_ns, int64_t* t_end_ns);
 hf_status hf_batch_get_stamps(hf_batch* b, int32_t index, int64_t* start, int64_t* finish, int32_t* exec_count);
 hf_status hf_batch_kernel_ms(hf_batch* b, float* ms);
+/* Counters of the last persistent run with instrument bit 1 (host int64 out[n], n <= 16): warp
+ * rounds with work, items processed, idle polls, successor releases, CAS attempts, ready tasks
+ * kept in warp stacks, items pushed to / claims on / items popped from the global queue,
+ * payload pieces run. Diagnostics only. */
+hf_status hf_batch_get_stats(hf_batch* b, int64_t* out, int32_t n);
 /* As hf_set_delays for every graph of the batch: delay holds the graphs' edge delays
  * concatenated in batch order (sum of their edge counts). */
 hf_status hf_batch_set_delays(hf_batch* b, const float* delay, int on_device, void* stream);

@@ -676,6 +676,12 @@ hf_status hf_batch_get_task_times(hf_batch* b, int32_t index, int64_t* t0, int64
     return plan_get_times(b->plan, index, t0, t1);
 }
 
+hf_status hf_batch_get_stats(hf_batch* b, int64_t* out, int32_t n) {
+    if (!b || !out || n < 0) return fail(HF_EINVAL, "bad argument");
+    if (!b->plan) return fail(HF_ESTATE, "batch has not run");
+    return plan_get_stats(b->plan, out, n);
+}
+
 hf_status hf_batch_kernel_ms(hf_batch* b, float* ms) {
     if (!b || !ms) return fail(HF_EINVAL, "NULL argument");
     if (!b->plan) return fail(HF_ESTATE, "batch has not run");

@@ -74,6 +74,22 @@ struct PersistArgs {
     int64_t* tk_start;  // validate: tickets per task (NULL otherwise)
     int64_t* tk_end;
     int32_t* exec_count;
+    unsigned long long* stats;  // instrument & 2: executor counters (kStat*), else NULL
+};
+
+// Executor counters recorded by runs with instrument & 2 (hf_get_stats).
+enum StatIdx {
+    kStatRounds = 0,     // warp rounds that had work
+    kStatItems,          // items processed (tasks and payload pieces)
+    kStatIdle,           // idle polls
+    kStatEdges,          // successor releases
+    kStatCas,            // compare-and-swap attempts
+    kStatPushLocal,      // ready tasks kept in a warp's stack
+    kStatPushGlobal,     // items pushed to the global queue
+    kStatClaims,         // claims on the global queue
+    kStatPops,           // items taken from the global queue
+    kStatPieces,         // payload pieces run
+    kStatCount = 16
 };
 
 // Successors with more than this many predecessors are released with a max on the key half
@@ -204,6 +220,7 @@ hf_status plan_get_arrivals(Plan* p, int32_t gi, float* out, int on_device);
 hf_status plan_get_times(Plan* p, int32_t gi, int64_t* a, int64_t* b);
 hf_status plan_get_stamps(Plan* p, int32_t gi, int64_t* a, int64_t* b, int32_t* c);
 hf_status plan_kernel_ms(Plan* p, float* ms);
+hf_status plan_get_stats(Plan* p, int64_t* out, int32_t n);
 hf_status plan_set_delays(Plan* p, const float* delay, int on_device, cudaStream_t s);
 hf_status plan_features(Plan* p, float* X, cudaStream_t s);
 hf_status plan_task_costs(Plan* p, int32_t priority, const hf_costmodel* cm, float* cost, float* bottom,

@@ -19,7 +19,8 @@ namespace hf {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kWarpsPerCta = 8;
-constexpr int kStackCap = 64;  // per-warp shared-memory ready stack
+constexpr int kStackCap = 32;  // per-warp shared-memory ready stack (double-buffered)
+constexpr int kStage = 4;      // edge records staged in shared memory per stacked task
 
 __device__ __forceinline__ uint32_t f2key(float f) {
     const uint32_t b = __float_as_uint(f);
@@ -69,6 +70,16 @@ __device__ __forceinline__ uint64_t gtimer() {
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
+
+// asynchronous 16-byte global -> shared copy (completion: cp_async_wait_all by the issuer)
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned m;
@@ -316,8 +327,16 @@ __global__ void k_reset(const ResetArgs a) {
 // Single-item tasks go to the warp's shared-memory stack while it has room (up to local_keep);
 // the rest, and every piece of a multi-piece payload task, go to the global queue with one
 // atomicAdd on its tail per warp.
+// Per-warp executor counters (reported when PersistArgs::stats is set); `cas` is per lane.
+struct WStats {
+    uint32_t rounds = 0, items = 0, idle = 0, edges = 0, cas = 0, local = 0, global = 0, claims = 0, pops = 0,
+             pieces = 0;
+};
+
+// nstk / nedg: the warp's stack buffer that is being filled this round and its staging area.
 template <bool PAY>
-__device__ __forceinline__ void push_ready(const PersistArgs& a, int4 r, int pr, int4* stk, int& top, int lane) {
+__device__ __forceinline__ void push_ready(const PersistArgs& a, int4 r, int pr, int4* nstk, int4* nedg, int& top,
+                                           int lane, WStats& ws) {
     const int v = r.x;
     int nitems = 0;
     int first_item = v;
@@ -348,10 +367,17 @@ __device__ __forceinline__ void push_ready(const PersistArgs& a, int4 r, int pr,
     }
     bool go_global = nitems > 0;
     if (single && rank < room) {
-        stk[top + rank] = r;
+        const int slot = top + rank;
+        nstk[slot] = r;
+        const int len = r.w & 0x7fffffff;
+        if (len <= kStage) {  // stage its out-edges now; they are read next round
+            for (int j = 0; j < len; ++j) cp_async16(nedg + slot * kStage + j, a.erec + r.z + j);
+            cp_async_commit();
+        }
         go_global = false;
     }
     top += min(__popc(sm), max(room, 0));
+    ws.local += (uint32_t)min(__popc(sm), max(room, 0));
     int cnt = go_global ? nitems : 0;
     int incl = cnt;
 #pragma unroll
@@ -365,6 +391,7 @@ __device__ __forceinline__ void push_ready(const PersistArgs& a, int4 r, int pr,
         return;
     }
     int base = 0;
+    ws.global += (uint32_t)total;
     if (lane == 0) base = atomicAdd(&a.ctrl->tail, total);
     base = __shfl_sync(kFull, base, 0);
     if ((int64_t)base + total > (int64_t)a.qcap) {  // cannot happen with a correct capacity
@@ -384,7 +411,7 @@ __device__ __forceinline__ void push_ready(const PersistArgs& a, int4 r, int pr,
 // Releases successor v of a finished task: returns true when v becomes ready, with its final
 // key in *kv. f16 is v's in-degree from the edge record (kWideMark for wide joins).
 __device__ __forceinline__ bool release_succ(const PersistArgs& a, int v, uint32_t ck, uint32_t f16,
-                                             uint32_t* kv) {
+                                             uint32_t* kv, uint32_t& ncas) {
     unsigned long long* st = a.state + v;
     if (f16 != kWideMark) {
         unsigned long long expected = ((unsigned long long)kKeyNegInf << 32) | f16;
@@ -394,6 +421,7 @@ __device__ __forceinline__ bool release_succ(const PersistArgs& a, int v, uint32
             const uint32_t ec = (uint32_t)expected;
             desired = ((unsigned long long)max(ek, ck) << 32) | (unsigned long long)(ec - 1u);
             const unsigned long long prev = atomicCAS(st, expected, desired);
+            ++ncas;
             if (prev == expected) break;
             expected = prev;
         }
@@ -418,9 +446,12 @@ __device__ __forceinline__ bool release_succ(const PersistArgs& a, int v, uint32
 // before running pieces of a task that became ready (acquire); and a window that releases a
 // task with a payload fences first, so that data written upstream by a payload task reaches it
 // through plain tasks in between (each such warp acquires what it observed, then releases).
+// staged: this lane's task came from the warp's stack with its out-edges staged in
+// cedg[lane * kStage ...]; nstk / nedg receive the tasks that become ready.
 template <bool PAY>
-__device__ __forceinline__ void release_all(const PersistArgs& a, int fin, uint32_t kt, int rs, int deg, int4* stk,
-                                            int& top, int lane) {
+__device__ __forceinline__ void release_all(const PersistArgs& a, int fin, uint32_t kt, int rs, int deg, bool staged,
+                                            const int4* cedg, int4* nstk, int4* nedg, int& top, int lane,
+                                            WStats& ws) {
     if (fin < 0) deg = 0;
     int incl = deg;
 #pragma unroll
@@ -430,6 +461,7 @@ __device__ __forceinline__ void release_all(const PersistArgs& a, int fin, uint3
     }
     const int total = __shfl_sync(kFull, incl, 31);
     const int excl = incl - deg;
+    ws.edges += (uint32_t)total;
     for (int e0 = 0; e0 < total; e0 += 32) {
         const int e = e0 + lane;
         int owner = 0;
@@ -442,9 +474,10 @@ __device__ __forceinline__ void release_all(const PersistArgs& a, int fin, uint3
         const int o_rs = __shfl_sync(kFull, rs, owner);
         const int o_ex = __shfl_sync(kFull, excl, owner);
         const uint32_t o_k = __shfl_sync(kFull, kt, owner);
+        const bool o_st = __shfl_sync(kFull, staged ? 1 : 0, owner) != 0;
         int4 rec = make_int4(-1, 0, 0, 0);
         if (e < total) {
-            rec = __ldg(a.erec + o_rs + (e - o_ex));
+            rec = o_st ? cedg[owner * kStage + (e - o_ex)] : __ldg(a.erec + o_rs + (e - o_ex));
             prefetch_l2(a.erec + rec.z);  // warm the successor's row while its CAS is in flight
         }
         const uint32_t w = (uint32_t)rec.w;
@@ -454,22 +487,24 @@ __device__ __forceinline__ void release_all(const PersistArgs& a, int fin, uint3
         if (rec.x >= 0) {
             const float cand = __fadd_rn(key2f(o_k), __int_as_float(rec.y));
             uint32_t kv;
-            if (release_succ(a, rec.x, f2key(cand), w & kWideMark, &kv)) {
+            if (release_succ(a, rec.x, f2key(cand), w & kWideMark, &kv, ws.cas)) {
                 int len = (int)(w >> 16);
                 if ((uint32_t)len == kLongMark) len = __ldg(a.meta + rec.x).y;
                 r = make_int4(rec.x, (int)kv, rec.z, len | ((w & kPayBit) ? (int)0x80000000u : 0));
                 pr = (int)((w >> kPrioShift) & kPrioMask);
             }
         }
-        if (__ballot_sync(kFull, r.x >= 0)) push_ready<PAY>(a, r, pr, stk, top, lane);
+        if (__ballot_sync(kFull, r.x >= 0)) push_ready<PAY>(a, r, pr, nstk, nedg, top, lane, ws);
     }
 }
 
 template <bool PAY>
-__global__ void __launch_bounds__(kWarpsPerCta * 32) k_persist(const PersistArgs a) {
-    __shared__ int4 s_stack[kWarpsPerCta][kStackCap];
+__global__ void __launch_bounds__(kWarpsPerCta * 32, 2) k_persist(const PersistArgs a) {
+    __shared__ int4 s_stack[kWarpsPerCta][2][kStackCap];
+    __shared__ int4 s_edges[kWarpsPerCta][2][kStackCap * kStage];
     const int lane = threadIdx.x & 31;
-    int4* stk = s_stack[threadIdx.x >> 5];
+    const int wid = threadIdx.x >> 5;
+    int pb = 0;  // buffer holding the stacked tasks; a round pops all of it and fills the other
     int top = 0;
     int qbase = 0;
     unsigned pend = 0;
@@ -480,17 +515,21 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_persist(const PersistArgs
     const int nwarps = (int)gridDim.x * kWarpsPerCta;
     uint32_t ndone = 0;  // completions not yet added to ctrl->done (warp-uniform)
     uint32_t iter = 0;
+    WStats ws;
 
     for (;;) {
         int item = -1;
         int4 loc = make_int4(-1, 0, 0, 0);
+        const int cb = pb;  // staged edges of this round's stacked tasks stay in buffer cb
         if (top > 0) {
-            const int take = min(top, 32);
-            if (lane < take) {
-                loc = stk[top - take + lane];
+            cp_async_wait_all();
+            __syncwarp();
+            if (lane < top) {
+                loc = s_stack[wid][cb][lane];
                 item = loc.x;
             }
-            top -= take;
+            top = 0;
+            pb ^= 1;
             __syncwarp();
         } else {
             if (pend == 0) {
@@ -502,6 +541,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_persist(const PersistArgs
                         const int t = ld_relaxed(&a.ctrl->tail);
                         k = max(1, min((t - h) / nwarps, a.claim));
                         b = atomicAdd(&a.ctrl->head, k);
+                        ws.claims++;
                     }
                 }
                 b = __shfl_sync(kFull, b, 0);
@@ -516,6 +556,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_persist(const PersistArgs
             }
             const unsigned hit = __ballot_sync(kFull, item >= 0);
             pend &= ~hit;
+            ws.pops += (uint32_t)__popc(hit);
             if (hit) fence_acq_rel();  // acquire: what the pusher released with the slot
         }
         const unsigned got = __ballot_sync(kFull, item >= 0);
@@ -540,17 +581,20 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_persist(const PersistArgs
                 }
             }
             if (__shfl_sync(kFull, quit, 0)) break;
+            ws.idle++;
             __nanosleep(backoff);
             backoff = min(backoff * 2u, 256u);
             continue;
         }
         backoff = 32;
+        ws.rounds++;
+        ws.items += (uint32_t)__popc(got);
 
         // ---- resolve this round's items: task (with key, row, payload flag) or payload piece
         int t = -1, p = -1, piece = 0;
         uint32_t kt = 0;
         int rs = 0, deg = 0;
-        bool haspay = false;
+        bool haspay = false, staged = false;
         if (item >= 0) {
             if (item < n_tasks) {
                 t = item;
@@ -559,6 +603,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_persist(const PersistArgs
                     rs = loc.z;
                     deg = loc.w & 0x7fffffff;
                     haspay = PAY && loc.w < 0;
+                    staged = deg <= kStage;
                 } else {  // from the global queue
                     const int2 mt = __ldg(a.meta + t);
                     rs = mt.x;
@@ -595,7 +640,9 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_persist(const PersistArgs
             }
             a.key[fin] = kt;
         }
-        if (__ballot_sync(kFull, fin >= 0)) release_all<PAY>(a, fin, kt, rs, deg, stk, top, lane);
+        if (__ballot_sync(kFull, fin >= 0))
+            release_all<PAY>(a, fin, kt, rs, deg, staged, s_edges[wid][cb], s_stack[wid][pb], s_edges[wid][pb], top,
+                             lane, ws);
         if (a.t_end && fin >= 0) a.t_end[fin] = (int64_t)gtimer();
         ndone += (uint32_t)__popc(__ballot_sync(kFull, fin >= 0));
 
@@ -603,6 +650,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_persist(const PersistArgs
         if (PAY) {
             unsigned work = __ballot_sync(kFull, haspay);
             if (work) {
+                ws.pieces += (uint32_t)__popc(work);
                 fence_acq_rel();  // acquire: inputs written by upstream payload tasks
                 while (work) {
                     const int src = __ffs(work) - 1;
@@ -631,7 +679,9 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_persist(const PersistArgs
                     }
                     a.key[fin2] = kt;
                 }
-                if (__ballot_sync(kFull, fin2 >= 0)) release_all<PAY>(a, fin2, kt, rs, deg, stk, top, lane);
+                if (__ballot_sync(kFull, fin2 >= 0))
+                    release_all<PAY>(a, fin2, kt, rs, deg, staged && item < n_tasks, s_edges[wid][cb], s_stack[wid][pb],
+                                     s_edges[wid][pb], top, lane, ws);
                 if (a.t_end && fin2 >= 0) a.t_end[fin2] = (int64_t)gtimer();
                 ndone += (uint32_t)__popc(__ballot_sync(kFull, fin2 >= 0));
             }
@@ -642,6 +692,22 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_persist(const PersistArgs
         if ((++iter & 31u) == 0 && ndone) {
             if (lane == 0) atomicAdd(&a.ctrl->done, ndone);
             ndone = 0;
+        }
+    }
+    if (a.stats) {
+        uint32_t cas = ws.cas;
+        for (int o = 16; o > 0; o >>= 1) cas += __shfl_xor_sync(kFull, cas, o);
+        if (lane == 0) {
+            atomicAdd(a.stats + kStatRounds, (unsigned long long)ws.rounds);
+            atomicAdd(a.stats + kStatItems, (unsigned long long)ws.items);
+            atomicAdd(a.stats + kStatIdle, (unsigned long long)ws.idle);
+            atomicAdd(a.stats + kStatEdges, (unsigned long long)ws.edges);
+            atomicAdd(a.stats + kStatCas, (unsigned long long)cas);
+            atomicAdd(a.stats + kStatPushLocal, (unsigned long long)ws.local);
+            atomicAdd(a.stats + kStatPushGlobal, (unsigned long long)ws.global);
+            atomicAdd(a.stats + kStatClaims, (unsigned long long)ws.claims);
+            atomicAdd(a.stats + kStatPops, (unsigned long long)ws.pops);
+            atomicAdd(a.stats + kStatPieces, (unsigned long long)ws.pieces);
         }
     }
 }

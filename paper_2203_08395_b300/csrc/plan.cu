@@ -77,6 +77,8 @@ struct Plan {
     int64_t* d_tk_start = nullptr;
     int64_t* d_tk_end = nullptr;
     int32_t* d_exec = nullptr;
+    unsigned long long* d_stats = nullptr;  // executor counters (instrument & 2)
+    bool last_stats = false;
     bool last_instrument = false, last_validate = false;
     // level-sync CUDA graph
     cudaGraph_t lgraph = nullptr;
@@ -589,7 +591,7 @@ hf_status plan_run(Plan* p, cudaStream_t s, const hf_run_opts& o) {
     chunk = ((chunk + 31) / 32) * 32;
     st = plan_set_chunk(p, chunk, s);
     if (st != HF_OK) return st;
-    const bool instr = o.instrument != 0, valid = o.validate != 0;
+    const bool instr = (o.instrument & 1) != 0, valid = o.validate != 0;
     if ((st = ensure_instr(p, instr, valid, s)) != HF_OK) return st;
     cudaError_t e = cudaMemsetAsync(&p->d_ctrl->status, 0, sizeof(int32_t), s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
@@ -629,7 +631,7 @@ hf_status plan_run(Plan* p, cudaStream_t s, const hf_run_opts& o) {
             a.n_tasks = p->n;
             a.qcap = p->qcap;
             a.claim = std::min(std::max(o.claim, 1), 32);
-            a.local_keep = o.local_keep < 0 ? 32 : std::min(o.local_keep, kStackCap - 32);
+            a.local_keep = o.local_keep < 0 ? 16 : std::min(o.local_keep, kStackCap);
             a.spin_limit_ns = o.spin_limit_ns ? o.spin_limit_ns : 2000000000ull;
             a.meta = p->d_meta;
             a.erec = p->d_erec;
@@ -646,6 +648,17 @@ hf_status plan_run(Plan* p, cudaStream_t s, const hf_run_opts& o) {
             a.tk_start = r.tk_start;
             a.tk_end = r.tk_end;
             a.exec_count = r.exec_count;
+            a.stats = nullptr;
+            if (o.instrument & 2) {
+                if (!p->d_stats) {
+                    p->d_stats = (unsigned long long*)palloc(p, sizeof(unsigned long long) * kStatCount, s);
+                    if (!p->d_stats) return fail(HF_ENOMEM, "device allocation failed: stats");
+                }
+                e = cudaMemsetAsync(p->d_stats, 0, sizeof(unsigned long long) * kStatCount, s);
+                if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+                a.stats = p->d_stats;
+            }
+            p->last_stats = a.stats != nullptr;
             int ctas = o.ctas;
             if (ctas <= 0) {  // every warp slot of the GPU: one CTA per SM times occupancy
                 int occ = 0;
@@ -730,6 +743,16 @@ hf_status plan_get_stamps(Plan* p, int32_t gi, int64_t* a, int64_t* b, int32_t* 
     if (e == cudaSuccess && c && cnt) e = cudaMemcpyAsync(c, p->d_exec + off, 4 * (size_t)cnt, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     return e == cudaSuccess ? HF_OK : cuda_fail(e, "ticket copy");
+}
+
+hf_status plan_get_stats(Plan* p, int64_t* out, int32_t n) {
+    if (!p->ran || !p->last_stats) return fail(HF_ESTATE, "last run did not record executor counters");
+    unsigned long long h[kStatCount];
+    cudaError_t e = cudaStreamSynchronize(p->last_stream);
+    if (e == cudaSuccess) e = cudaMemcpy(h, p->d_stats, sizeof(h), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "stats copy");
+    for (int32_t i = 0; i < n && i < kStatCount; ++i) out[i] = (int64_t)h[i];
+    return HF_OK;
 }
 
 hf_status plan_kernel_ms(Plan* p, float* ms) {

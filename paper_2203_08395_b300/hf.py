@@ -135,6 +135,7 @@ def load():
         "hf_batch_task_costs": [vp, i32, vp, vp, vp],
         "hf_batch_bottom_levels": [vp, vp, vp, vp],
         "hf_batch_autotune": [vp, vp, P(hf_run_opts), ctypes.c_int, P(hf_run_opts), P(ctypes.c_float)],
+        "hf_batch_get_stats": [vp, vp, i32],
         "hf_batch_predict": [vp, i32, vp, P(ctypes.c_float), P(ctypes.c_float)],
     }
     for name, args in sig.items():
@@ -477,6 +478,15 @@ def hf_batch_predict(b, priority, stream=None):
     _check(load().hf_batch_predict(b, priority, _stream_handle(stream), ctypes.byref(ls), ctypes.byref(pe)),
            "hf_batch_predict")
     return ls.value, pe.value
+
+
+STAT_NAMES = ["rounds", "items", "idle", "edges", "cas", "push_local", "push_global", "claims", "pops", "pieces"]
+
+
+def hf_batch_get_stats(b):
+    out = np.zeros(16, np.int64)
+    _check(load().hf_batch_get_stats(b, _ptr(out), 16), "hf_batch_get_stats")
+    return {nm: int(out[i]) for i, nm in enumerate(STAT_NAMES)}
 
 
 def opts_dict(o):
