@@ -122,6 +122,9 @@ typedef struct {
                                becomes ready and a persistent run ends with HF_ETIMEDOUT */
     int32_t time_kernel;    /* record CUDA events around the executor's main work (read with
                                hf_kernel_ms / hf_batch_kernel_ms) */
+    int32_t payload_warps;  /* persistent: warps per CTA (0..7) that only run payload tasks,
+                               taken from a separate payload queue; 0 = every warp runs both */
+    int32_t pad_;
 } hf_run_opts;
 
 void hf_run_opts_default(hf_run_opts* opts);

@@ -49,6 +49,10 @@ struct alignas(128) Ctrl {
     int32_t pad3[29];
     unsigned long long ticket;  // validation tickets
     int32_t pad4[30];
+    int32_t phead;  // payload queue (warp-specialised runs)
+    int32_t pad5[31];
+    int32_t ptail;
+    int32_t pad6[31];
 };
 
 // Arguments of the persistent executor kernel (by value, < 4 KB).
@@ -67,6 +71,9 @@ struct PersistArgs {
     unsigned long long* state;  // n_tasks {key << 32 | pending predecessors}
     uint32_t* key;              // n_tasks final arrival keys (output)
     int32_t* queue;             // qcap ready-queue slots (-1 = empty)
+    int32_t* pqueue;            // pqcap payload-queue slots (used when pay_warps > 0)
+    int32_t pqcap;
+    int32_t pay_warps;          // warps per CTA that only run payload tasks (0: none)
     int32_t* chunks_left;       // per payload: pieces still running
     Ctrl* ctrl;
     int64_t* t_start;  // instrument: %globaltimer per task (NULL otherwise)
@@ -103,10 +110,14 @@ struct ResetArgs {
     int32_t n_seed;
     int32_t n_pay;
     int32_t stall_task;  // test hook: this task's counter starts one too high (-1: none)
-    int32_t pad_;
+    int32_t n_pseed;     // payload seed items
+    int32_t pqcap;
+    int32_t split;       // payload seeds go to the payload queue (else to the main queue)
     const int32_t* indeg0;
     const uint32_t* key0;  // NULL: sources start at +0
-    const int32_t* seeds;
+    const int32_t* seeds;   // items of sources without payload
+    const int32_t* pseeds;  // items of sources with a payload
+    int32_t* pqueue;
     const DevPayload* pay;
     unsigned long long* state;
     int32_t* queue;

@@ -307,15 +307,28 @@ __global__ void k_reset(const ResetArgs a) {
             a.tk_end[i] = -1;
         }
     }
+    // sources without payload seed the main queue; sources with one seed the payload queue in
+    // warp-specialised runs, else they follow in the main queue
+    const int64_t nmain = a.split ? a.n_seed : (int64_t)a.n_seed + a.n_pseed;
     for (int64_t i = tid; i < a.qcap; i += stride) {
-        int v = i < a.n_seed ? a.seeds[i] : -1;
+        int v = -1;
+        if (i < a.n_seed) v = a.seeds[i];
+        else if (i < nmain) v = a.pseeds[i - a.n_seed];
         if (v >= 0 && v == a.stall_task) v = -2;  // never a task id: its slot is skipped
         a.queue[i] = v;
     }
+    if (a.split)
+        for (int64_t i = tid; i < a.pqcap; i += stride) {
+            int v = i < a.n_pseed ? a.pseeds[i] : -1;
+            if (v >= 0 && v == a.stall_task) v = -2;
+            a.pqueue[i] = v;
+        }
     for (int64_t i = tid; i < a.n_pay; i += stride) a.chunks_left[i] = a.pay[i].nchunks;
     if (tid == 0) {
         a.ctrl->head = 0;
-        a.ctrl->tail = a.n_seed;
+        a.ctrl->tail = (int32_t)nmain;
+        a.ctrl->phead = 0;
+        a.ctrl->ptail = a.split ? a.n_pseed : 0;
         a.ctrl->done = 0;
         a.ctrl->status = 0;
         a.ctrl->abort = 0;
@@ -332,6 +345,39 @@ struct WStats {
     uint32_t rounds = 0, items = 0, idle = 0, edges = 0, cas = 0, local = 0, global = 0, claims = 0, pops = 0,
              pieces = 0;
 };
+
+// Appends each lane's `cnt` items (first_item, first_item+1, ... when multi, else first_item)
+// to a global queue with one atomicAdd on its tail per warp, then publishes them.
+__device__ __forceinline__ void push_items(const PersistArgs& a, int32_t* slots, int32_t cap, int32_t* tailp, int cnt,
+                                           int first_item, bool multi, int lane, WStats& ws) {
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const int total = __shfl_sync(kFull, incl, 31);
+    if (total == 0) {
+        __syncwarp();
+        return;
+    }
+    int base = 0;
+    ws.global += (uint32_t)total;
+    if (lane == 0) base = atomicAdd(tailp, total);
+    base = __shfl_sync(kFull, base, 0);
+    if ((int64_t)base + total > (int64_t)cap) {  // cannot happen with a correct capacity
+        if (lane == 0) {
+            atomicExch(&a.ctrl->status, (int)HF_EQUEUE);
+            atomicExch(&a.ctrl->abort, 1);
+        }
+        __syncwarp();
+        return;
+    }
+    fence_acq_rel();  // release: the ready task's state (and inputs) before its queue slot
+    const int start = base + incl - cnt;
+    for (int k = 0; k < cnt; ++k) st_relaxed(slots + start + k, first_item + (multi ? k : 0));
+    __syncwarp();
+}
 
 // nstk / nedg: the warp's stack buffer that is being filled this round and its staging area.
 template <bool PAY>
@@ -351,7 +397,9 @@ __device__ __forceinline__ void push_ready(const PersistArgs& a, int4 r, int pr,
             }
         }
     }
-    const bool single = (nitems == 1);
+    // warp-specialised runs send every payload task to the payload queue
+    const bool topay = PAY && a.pay_warps > 0 && v >= 0 && r.w < 0;
+    const bool single = (nitems == 1) && !topay;
     const unsigned sm = __ballot_sync(kFull, single);
     const int room = a.local_keep - top;
     int rank;
@@ -378,34 +426,10 @@ __device__ __forceinline__ void push_ready(const PersistArgs& a, int4 r, int pr,
     }
     top += min(__popc(sm), max(room, 0));
     ws.local += (uint32_t)min(__popc(sm), max(room, 0));
-    int cnt = go_global ? nitems : 0;
-    int incl = cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(kFull, incl, o);
-        if (lane >= o) incl += y;
-    }
-    const int total = __shfl_sync(kFull, incl, 31);
-    if (total == 0) {
-        __syncwarp();
-        return;
-    }
-    int base = 0;
-    ws.global += (uint32_t)total;
-    if (lane == 0) base = atomicAdd(&a.ctrl->tail, total);
-    base = __shfl_sync(kFull, base, 0);
-    if ((int64_t)base + total > (int64_t)a.qcap) {  // cannot happen with a correct capacity
-        if (lane == 0) {
-            atomicExch(&a.ctrl->status, (int)HF_EQUEUE);
-            atomicExch(&a.ctrl->abort, 1);
-        }
-        __syncwarp();
-        return;
-    }
-    fence_acq_rel();  // release: the ready task's state (and inputs) before its queue slot
-    const int start = base + incl - cnt;
-    for (int k = 0; k < cnt; ++k) st_relaxed(a.queue + start + k, first_item + (nitems > 1 ? k : 0));
-    __syncwarp();
+    const int cnt = go_global ? nitems : 0;
+    push_items(a, a.queue, a.qcap, &a.ctrl->tail, topay ? 0 : cnt, first_item, nitems > 1, lane, ws);
+    if (PAY && a.pay_warps > 0)
+        push_items(a, a.pqueue, a.pqcap, &a.ctrl->ptail, topay ? cnt : 0, first_item, nitems > 1, lane, ws);
 }
 
 // Releases successor v of a finished task: returns true when v becomes ready, with its final
@@ -481,7 +505,8 @@ __device__ __forceinline__ void release_all(const PersistArgs& a, int fin, uint3
             prefetch_l2(a.erec + rec.z);  // warm the successor's row while its CAS is in flight
         }
         const uint32_t w = (uint32_t)rec.w;
-        if (PAY && __ballot_sync(kFull, rec.x >= 0 && (w & kPayBit))) fence_acq_rel();
+        // (warp-specialised runs publish payload tasks through a queue, which fences already)
+        if (PAY && a.pay_warps == 0 && __ballot_sync(kFull, rec.x >= 0 && (w & kPayBit))) fence_acq_rel();
         int4 r = make_int4(-1, 0, 0, 0);
         int pr = 0;
         if (rec.x >= 0) {
@@ -512,7 +537,15 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 2) k_persist(const PersistA
     uint64_t stall_t0 = 0;
     unsigned backoff = 32;
     const int n_tasks = a.n_tasks;
-    const int nwarps = (int)gridDim.x * kWarpsPerCta;
+    // role: in warp-specialised runs the last pay_warps warps of each CTA take their work from
+    // the payload queue (payload tasks and pieces), the others from the main queue
+    const bool payw = PAY && a.pay_warps > 0 && wid >= kWarpsPerCta - a.pay_warps;
+    int32_t* const qslots = payw ? a.pqueue : a.queue;
+    const int qcap = payw ? a.pqcap : a.qcap;
+    int32_t* const qhead = payw ? &a.ctrl->phead : &a.ctrl->head;
+    int32_t* const qtail = payw ? &a.ctrl->ptail : &a.ctrl->tail;
+    const int nwarps = (int)gridDim.x * (PAY && a.pay_warps > 0 ? (payw ? a.pay_warps : kWarpsPerCta - a.pay_warps)
+                                                                  : kWarpsPerCta);
     uint32_t ndone = 0;  // completions not yet added to ctrl->done (warp-uniform)
     uint32_t iter = 0;
     WStats ws;
@@ -534,24 +567,24 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 2) k_persist(const PersistA
         } else {
             if (pend == 0) {
                 // claim a fair share of the published backlog (at least 1, at most `claim`)
-                int b = a.qcap, k = 0;
+                int b = qcap, k = 0;
                 if (lane == 0) {
-                    const int h = ld_relaxed(&a.ctrl->head);
-                    if (h < a.qcap) {
-                        const int t = ld_relaxed(&a.ctrl->tail);
+                    const int h = ld_relaxed(qhead);
+                    if (h < qcap) {
+                        const int t = ld_relaxed(qtail);
                         k = max(1, min((t - h) / nwarps, a.claim));
-                        b = atomicAdd(&a.ctrl->head, k);
+                        b = atomicAdd(qhead, k);
                         ws.claims++;
                     }
                 }
                 b = __shfl_sync(kFull, b, 0);
                 k = __shfl_sync(kFull, k, 0);
                 qbase = b;
-                k = min(k, a.qcap - b);
+                k = min(k, qcap - b);
                 pend = k <= 0 ? 0u : (k >= 32 ? kFull : ((1u << k) - 1u));
             }
             if (pend & (1u << lane)) {
-                const int v = ld_relaxed(a.queue + qbase + lane);
+                const int v = ld_relaxed(qslots + qbase + lane);
                 if (v >= 0) item = v;
             }
             const unsigned hit = __ballot_sync(kFull, item >= 0);

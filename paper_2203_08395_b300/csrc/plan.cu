@@ -67,10 +67,13 @@ struct Plan {
     int32_t nseed = 0;
     int32_t* d_chunk_task = nullptr;  // sized for nitems
     int32_t* d_seeds = nullptr;
+    int32_t* d_pseeds = nullptr;  // items of sources with a payload
+    int32_t* d_pqueue = nullptr;  // payload queue (warp-specialised runs)
+    int32_t npseed = 0, pqcap = 0;
     int32_t* d_queue = nullptr;
     int2* d_items = nullptr;          // level-sync payload items
     std::vector<int32_t> item_ptr;    // levels + 1
-    size_t cap_chunk_task = 0, cap_seeds = 0, cap_queue = 0, cap_items = 0;
+    size_t cap_chunk_task = 0, cap_seeds = 0, cap_queue = 0, cap_items = 0, cap_pseeds = 0, cap_pqueue = 0;
     // instrumentation
     int64_t* d_t_start = nullptr;
     int64_t* d_t_end = nullptr;
@@ -409,7 +412,7 @@ static hf_status plan_set_chunk(Plan* p, int64_t chunk_elems, cudaStream_t s) {
     if (chunk_elems == p->chunk_elems) return HF_OK;
     int64_t items = 0;
     std::vector<int32_t> chunk_task;
-    std::vector<int32_t> seeds;
+    std::vector<int32_t> seeds, pseeds;
     std::vector<int2> litems;
     std::vector<int32_t> item_ptr((size_t)p->levels + 1, 0);
     try {
@@ -441,11 +444,11 @@ static hf_status plan_set_chunk(Plan* p, int64_t chunk_elems, cudaStream_t s) {
         }
         for (int32_t t : p->sources) {
             const int32_t k = p->hpidx.empty() ? -1 : p->hpidx[(size_t)t];
-            if (k >= 0 && p->hpay[(size_t)k].nchunks > 1) {
-                for (int32_t c = 0; c < p->hpay[(size_t)k].nchunks; ++c) seeds.push_back(p->n + p->hpay[(size_t)k].chunk_first + c);
-            } else {
-                seeds.push_back(t);
-            }
+            if (k < 0) seeds.push_back(t);
+            else if (p->hpay[(size_t)k].nchunks == 1) pseeds.push_back(t);
+            else
+                for (int32_t c = 0; c < p->hpay[(size_t)k].nchunks; ++c)
+                    pseeds.push_back(p->n + p->hpay[(size_t)k].chunk_first + c);
         }
     } catch (const std::bad_alloc&) {
         return fail(HF_ENOMEM, "host allocation failed");
@@ -453,6 +456,8 @@ static hf_status plan_set_chunk(Plan* p, int64_t chunk_elems, cudaStream_t s) {
     p->nitems = (int32_t)items;
     p->qcap = p->n + (int32_t)items;
     p->nseed = (int32_t)seeds.size();
+    p->npseed = (int32_t)pseeds.size();
+    p->pqcap = p->npay + (int32_t)items;
     p->item_ptr = item_ptr;
     auto grow = [&](void** ptr, size_t& cap, size_t bytes) -> bool {
         bytes = std::max<size_t>(bytes, 16);
@@ -464,12 +469,15 @@ static hf_status plan_set_chunk(Plan* p, int64_t chunk_elems, cudaStream_t s) {
     };
     if (!grow((void**)&p->d_chunk_task, p->cap_chunk_task, 4 * chunk_task.size()) ||
         !grow((void**)&p->d_seeds, p->cap_seeds, 4 * seeds.size()) ||
+        !grow((void**)&p->d_pseeds, p->cap_pseeds, 4 * pseeds.size()) ||
+        !grow((void**)&p->d_pqueue, p->cap_pqueue, 4 * (size_t)p->pqcap) ||
         !grow((void**)&p->d_queue, p->cap_queue, 4 * (size_t)p->qcap) ||
         !grow((void**)&p->d_items, p->cap_items, 8 * litems.size()))
         return fail(HF_ENOMEM, "device allocation failed: queue");
     cudaError_t e = cudaSuccess;
     if (!chunk_task.empty()) e = cudaMemcpyAsync(p->d_chunk_task, chunk_task.data(), 4 * chunk_task.size(), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && !seeds.empty()) e = cudaMemcpyAsync(p->d_seeds, seeds.data(), 4 * seeds.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && !pseeds.empty()) e = cudaMemcpyAsync(p->d_pseeds, pseeds.data(), 4 * pseeds.size(), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && !litems.empty()) e = cudaMemcpyAsync(p->d_items, litems.data(), 8 * litems.size(), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && p->npay) e = cudaMemcpyAsync(p->d_pay, p->hpay.data(), sizeof(DevPayload) * (size_t)p->npay, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // host vectors die at return
@@ -612,6 +620,12 @@ hf_status plan_run(Plan* p, cudaStream_t s, const hf_run_opts& o) {
             r.indeg0 = p->d_indeg0;
             r.key0 = p->d_key0;
             r.seeds = p->d_seeds;
+            r.pseeds = p->d_pseeds;
+            r.n_pseed = p->npseed;
+            r.pqcap = p->pqcap;
+            r.pqueue = p->d_pqueue;
+            const int pay_warps = p->npay ? std::min(std::max(o.payload_warps, 0), kWarpsPerCta - 1) : 0;
+            r.split = pay_warps > 0 ? 1 : 0;
             r.pay = p->d_pay;
             r.state = p->d_state;
             r.queue = p->d_queue;
@@ -641,6 +655,9 @@ hf_status plan_run(Plan* p, cudaStream_t s, const hf_run_opts& o) {
             a.key = p->d_key;
             a.state = p->d_state;
             a.queue = p->d_queue;
+            a.pqueue = p->d_pqueue;
+            a.pqcap = p->pqcap;
+            a.pay_warps = pay_warps;
             a.chunks_left = p->d_chunks_left;
             a.ctrl = p->d_ctrl;
             a.t_start = r.t_start;
@@ -1049,6 +1066,7 @@ hf_status plan_autotune(Plan* p, cudaStream_t s, const hf_run_opts& base, int fo
             best->claim = it->second.first.claim;
             best->local_keep = it->second.first.local_keep;
             best->chunk_elems = it->second.first.chunk_elems;
+            best->payload_warps = it->second.first.payload_warps;
             *best_ms = it->second.second;
             return HF_OK;
         }
@@ -1068,19 +1086,22 @@ hf_status plan_autotune(Plan* p, cudaStream_t s, const hf_run_opts& base, int fo
     const std::vector<int> ctas_v{sms / 2, sms, 2 * sms, 4 * sms};
     const std::vector<int> claim_v{1, 4, 16, 32};
     const std::vector<int> keep_v{4, 8, 16, 32};
-    const std::vector<int64_t> chunk_v{4096, 16384, 65536};
+    const std::vector<int64_t> chunk_v{1024, 4096, 16384};
+    const std::vector<int> payw_v{0, 1, 2, 4};
     for (int round = 0; round < 2; ++round) {
-        for (int dim = 0; dim < 4; ++dim) {
-            if (dim == 3 && p->npay == 0) continue;
-            const size_t nv = dim == 0 ? ctas_v.size() : dim == 1 ? claim_v.size() : dim == 2 ? keep_v.size() : chunk_v.size();
+        for (int dim = 0; dim < 5; ++dim) {
+            if (dim >= 3 && p->npay == 0) continue;
+            const size_t nv = dim == 0 ? ctas_v.size() : dim == 1 ? claim_v.size() : dim == 2 ? keep_v.size()
+                              : dim == 3 ? chunk_v.size() : payw_v.size();
             for (size_t i = 0; i < nv; ++i) {
                 hf_run_opts t = cur;
                 if (dim == 0) t.ctas = ctas_v[i];
                 else if (dim == 1) t.claim = claim_v[i];
                 else if (dim == 2) t.local_keep = keep_v[i];
-                else t.chunk_elems = chunk_v[i];
+                else if (dim == 3) t.chunk_elems = chunk_v[i];
+                else t.payload_warps = payw_v[i];
                 if (t.ctas == cur.ctas && t.claim == cur.claim && t.local_keep == cur.local_keep &&
-                    t.chunk_elems == cur.chunk_elems)
+                    t.chunk_elems == cur.chunk_elems && t.payload_warps == cur.payload_warps)
                     continue;
                 float ms = 0.f;
                 if ((st = time_runs(p, s, t, 3, &ms)) != HF_OK) return st;

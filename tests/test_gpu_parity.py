@@ -29,6 +29,8 @@ EXECUTORS = {
     "persistent_nolocal": dict(mode=hf.HF_MODE_PERSISTENT, local_keep=0),
     "persistent_1cta": dict(mode=hf.HF_MODE_PERSISTENT, ctas=1),
     "persistent_wide": dict(mode=hf.HF_MODE_PERSISTENT, ctas=148 * 8, claim=4),
+    "persistent_payw2": dict(mode=hf.HF_MODE_PERSISTENT, payload_warps=2, claim=8, local_keep=8),
+    "persistent_payw7": dict(mode=hf.HF_MODE_PERSISTENT, payload_warps=7, ctas=16),
 }
 
 
@@ -116,7 +118,7 @@ def _check_payloads(gd, ref):
 
 
 @pytest.mark.parametrize("chunk", [0, 64, 4096])
-@pytest.mark.parametrize("ex", ["levelsync", "persistent", "persistent_claim8"])
+@pytest.mark.parametrize("ex", ["levelsync", "persistent", "persistent_claim8", "persistent_payw2", "persistent_payw7"])
 def test_mixed_small_with_payloads(ex, chunk):
     spec = S.mixed(3, n=6000, nmin=1, nmax=20000, n_copy=300)
     ref = oracle.run_spec(spec)
@@ -160,7 +162,7 @@ def test_batch256_full_size(ex):
     bd.close()
 
 
-@pytest.mark.parametrize("ex", ["levelsync", "persistent"])
+@pytest.mark.parametrize("ex", ["levelsync", "persistent", "persistent_payw2"])
 def test_batch_mixed_small(ex):
     wl = S.batch(2, graphs=12, nmin=500, nmax=20000, frac_saxpy=0.1, sx_min=1, sx_max=3000)
     bd = BatchOnDevice(wl)
