@@ -96,6 +96,10 @@ enum StatIdx {
     kStatClaims,         // claims on the global queue
     kStatPops,           // items taken from the global queue
     kStatPieces,         // payload pieces run
+    kStatCycRound,       // SM cycles in rounds with work (from items in hand to round end)
+    kStatCycRelease,     // ... of which releasing successors (pushes included)
+    kStatCycCas,         // ... of which the compare-and-swap sections
+    kStatCycPush,        // ... of which pushing ready tasks
     kStatCount = 16
 };
 

@@ -344,7 +344,11 @@ __global__ void k_reset(const ResetArgs a) {
 struct WStats {
     uint32_t rounds = 0, items = 0, idle = 0, edges = 0, cas = 0, local = 0, global = 0, claims = 0, pops = 0,
              pieces = 0;
+    unsigned long long cyc_round = 0, cyc_release = 0, cyc_cas = 0, cyc_push = 0;
+    bool on = false;  // cycle counts are taken only when counters are recorded
 };
+
+__device__ __forceinline__ long long clk(const WStats& ws) { return ws.on ? clock64() : 0; }
 
 // Appends each lane's `cnt` items (first_item, first_item+1, ... when multi, else first_item)
 // to a global queue with one atomicAdd on its tail per warp, then publishes them.
@@ -383,6 +387,7 @@ __device__ __forceinline__ void push_items(const PersistArgs& a, int32_t* slots,
 template <bool PAY>
 __device__ __forceinline__ void push_ready(const PersistArgs& a, int4 r, int pr, int4* nstk, int4* nedg, int& top,
                                            int lane, WStats& ws) {
+    const long long c_push = clk(ws);
     const int v = r.x;
     int nitems = 0;
     int first_item = v;
@@ -430,6 +435,7 @@ __device__ __forceinline__ void push_ready(const PersistArgs& a, int4 r, int pr,
     push_items(a, a.queue, a.qcap, &a.ctrl->tail, topay ? 0 : cnt, first_item, nitems > 1, lane, ws);
     if (PAY && a.pay_warps > 0)
         push_items(a, a.pqueue, a.pqcap, &a.ctrl->ptail, topay ? cnt : 0, first_item, nitems > 1, lane, ws);
+    if (ws.on) ws.cyc_push += (unsigned long long)(clk(ws) - c_push);
 }
 
 // Releases successor v of a finished task: returns true when v becomes ready, with its final
@@ -476,6 +482,7 @@ template <bool PAY>
 __device__ __forceinline__ void release_all(const PersistArgs& a, int fin, uint32_t kt, int rs, int deg, bool staged,
                                             const int4* cedg, int4* nstk, int4* nedg, int& top, int lane,
                                             WStats& ws) {
+    const long long c_rel = clk(ws);
     if (fin < 0) deg = 0;
     int incl = deg;
 #pragma unroll
@@ -507,6 +514,7 @@ __device__ __forceinline__ void release_all(const PersistArgs& a, int fin, uint3
         const uint32_t w = (uint32_t)rec.w;
         // (warp-specialised runs publish payload tasks through a queue, which fences already)
         if (PAY && a.pay_warps == 0 && __ballot_sync(kFull, rec.x >= 0 && (w & kPayBit))) fence_acq_rel();
+        const long long c_cas = clk(ws);
         int4 r = make_int4(-1, 0, 0, 0);
         int pr = 0;
         if (rec.x >= 0) {
@@ -519,8 +527,11 @@ __device__ __forceinline__ void release_all(const PersistArgs& a, int fin, uint3
                 pr = (int)((w >> kPrioShift) & kPrioMask);
             }
         }
-        if (__ballot_sync(kFull, r.x >= 0)) push_ready<PAY>(a, r, pr, nstk, nedg, top, lane, ws);
+        const bool any_ready = __ballot_sync(kFull, r.x >= 0) != 0;
+        if (ws.on) ws.cyc_cas += (unsigned long long)(clk(ws) - c_cas);
+        if (any_ready) push_ready<PAY>(a, r, pr, nstk, nedg, top, lane, ws);
     }
+    if (ws.on) ws.cyc_release += (unsigned long long)(clk(ws) - c_rel);
 }
 
 template <bool PAY>
@@ -549,6 +560,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 2) k_persist(const PersistA
     uint32_t ndone = 0;  // completions not yet added to ctrl->done (warp-uniform)
     uint32_t iter = 0;
     WStats ws;
+    ws.on = a.stats != nullptr;
 
     for (;;) {
         int item = -1;
@@ -621,6 +633,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 2) k_persist(const PersistA
         }
         backoff = 32;
         ws.rounds++;
+        const long long c_round = clk(ws);
         ws.items += (uint32_t)__popc(got);
 
         // ---- resolve this round's items: task (with key, row, payload flag) or payload piece
@@ -722,6 +735,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 2) k_persist(const PersistA
 
         // completions reach ctrl->done in batches: when the warp goes idle, and every 32 rounds
         // so that the stall timer of idle warps sees progress made by long-busy warps
+        if (ws.on) ws.cyc_round += (unsigned long long)(clk(ws) - c_round);
         if ((++iter & 31u) == 0 && ndone) {
             if (lane == 0) atomicAdd(&a.ctrl->done, ndone);
             ndone = 0;
@@ -741,6 +755,10 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 2) k_persist(const PersistA
             atomicAdd(a.stats + kStatClaims, (unsigned long long)ws.claims);
             atomicAdd(a.stats + kStatPops, (unsigned long long)ws.pops);
             atomicAdd(a.stats + kStatPieces, (unsigned long long)ws.pieces);
+            atomicAdd(a.stats + kStatCycRound, ws.cyc_round);
+            atomicAdd(a.stats + kStatCycRelease, ws.cyc_release);
+            atomicAdd(a.stats + kStatCycCas, ws.cyc_cas);
+            atomicAdd(a.stats + kStatCycPush, ws.cyc_push);
         }
     }
 }

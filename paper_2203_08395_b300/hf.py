@@ -481,7 +481,8 @@ def hf_batch_predict(b, priority, stream=None):
     return ls.value, pe.value
 
 
-STAT_NAMES = ["rounds", "items", "idle", "edges", "cas", "push_local", "push_global", "claims", "pops", "pieces"]
+STAT_NAMES = ["rounds", "items", "idle", "edges", "cas", "push_local", "push_global", "claims", "pops", "pieces",
+              "cyc_round", "cyc_release", "cyc_cas", "cyc_push"]
 
 
 def hf_batch_get_stats(b):
