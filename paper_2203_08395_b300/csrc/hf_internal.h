@@ -23,7 +23,8 @@ constexpr uint32_t kKeyPosZero = 0x80000000u;  // key(+0)
 
 enum PayOp : uint32_t { kPaySaxpyF32 = 1, kPaySaxpyI32 = 2, kPayCopy = 3 };
 
-// One device payload record (saxpy or copy), 48 bytes.
+// One device payload record (saxpy or copy), 64 bytes. It also carries its task's id and row so
+// that a warp holding only the payload index has everything it needs after one load.
 struct DevPayload {
     void* dst;            // saxpy: y; copy: destination
     const void* src;      // saxpy: x; copy: source
@@ -31,8 +32,12 @@ struct DevPayload {
     uint32_t op;          // PayOp
     uint32_t a_bits;      // saxpy scalar (float bits or int32)
     int32_t nchunks;      // pieces the payload is split into (>= 1)
-    int32_t chunk_first;  // first chunk-item index (multi-chunk payloads), else -1
+    int32_t chunk_first;  // first piece-item index (multi-piece payloads), else -1
     int64_t chunk;        // piece size: elements (saxpy) or bytes (copy)
+    int32_t task;         // the task carrying this payload
+    int32_t row;          // its first out-edge
+    int32_t deg;          // its out-degree
+    int32_t pad_;
 };
 
 // Persistent-executor control block; hot counters on separate 128-byte lines.
@@ -67,7 +72,9 @@ struct PersistArgs {
                              // out-edge, successor's out-degree << 16 | in-degree (or marks)}
     const int32_t* pidx;     // n_tasks payload index or -1 (NULL: no payloads)
     const DevPayload* pay;
-    const int32_t* chunk_task;  // chunk item -> task
+    const int32_t* chunk_pay;   // piece item -> payload index
+    int32_t npieces;            // piece items (queue items n .. n+npieces-1; payload starts follow)
+    int32_t pad2_;
     unsigned long long* state;  // n_tasks {key << 32 | pending predecessors}
     uint32_t* key;              // n_tasks final arrival keys (output)
     int32_t* queue;             // qcap ready-queue slots (-1 = empty)

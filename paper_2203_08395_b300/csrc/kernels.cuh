@@ -336,10 +336,6 @@ __global__ void k_reset(const ResetArgs a) {
     }
 }
 
-// Pushes this warp's ready tasks (lanes with r.x >= 0; r = {task, key, row start, out-degree}).
-// Single-item tasks go to the warp's shared-memory stack while it has room (up to local_keep);
-// the rest, and every piece of a multi-piece payload task, go to the global queue with one
-// atomicAdd on its tail per warp.
 // Per-warp executor counters (reported when PersistArgs::stats is set); `cas` is per lane.
 struct WStats {
     uint32_t rounds = 0, items = 0, idle = 0, edges = 0, cas = 0, local = 0, global = 0, claims = 0, pops = 0,
@@ -350,10 +346,15 @@ struct WStats {
 
 __device__ __forceinline__ long long clk(const WStats& ws) { return ws.on ? clock64() : 0; }
 
+// Queue items: [0, n) a task without payload; [n, n + npieces) one piece of a multi-piece
+// payload; [n + npieces, n + npieces + npay) the start of payload p (the warp that pops it
+// pushes the payload's other pieces, if any, and runs the first).
+
 // Appends each lane's `cnt` items (first_item, first_item+1, ... when multi, else first_item)
 // to a global queue with one atomicAdd on its tail per warp, then publishes them.
 __device__ __forceinline__ void push_items(const PersistArgs& a, int32_t* slots, int32_t cap, int32_t* tailp, int cnt,
                                            int first_item, bool multi, int lane, WStats& ws) {
+    if (__ballot_sync(kFull, cnt > 0) == 0) return;
     int incl = cnt;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -361,10 +362,6 @@ __device__ __forceinline__ void push_items(const PersistArgs& a, int32_t* slots,
         if (lane >= o) incl += y;
     }
     const int total = __shfl_sync(kFull, incl, 31);
-    if (total == 0) {
-        __syncwarp();
-        return;
-    }
     int base = 0;
     ws.global += (uint32_t)total;
     if (lane == 0) base = atomicAdd(tailp, total);
@@ -383,28 +380,20 @@ __device__ __forceinline__ void push_items(const PersistArgs& a, int32_t* slots,
     __syncwarp();
 }
 
-// nstk / nedg: the warp's stack buffer that is being filled this round and its staging area.
+// Pushes this warp's ready tasks (lane: r.x >= 0 with r = {task, key, first out-edge (payload
+// index for payload tasks), out-degree | payload flag << 31}). Tasks go to the warp's stack
+// while it has room (up to local_keep) -- plain tasks with their first kStage out-edges staged
+// in shared memory for the next round -- except payload tasks in warp-specialised runs, which
+// go to the payload queue; the rest go to the main queue. nstk / nedg: the stack buffer filled
+// this round and its staging area.
 template <bool PAY>
 __device__ __forceinline__ void push_ready(const PersistArgs& a, int4 r, int pr, int4* nstk, int4* nedg, int& top,
                                            int lane, WStats& ws) {
     const long long c_push = clk(ws);
     const int v = r.x;
-    int nitems = 0;
-    int first_item = v;
-    if (v >= 0) {
-        nitems = 1;
-        if (PAY && r.w < 0) {  // the task has a payload: split into pieces?
-            const int p = __ldg(a.pidx + v);
-            const int nc = a.pay[p].nchunks;
-            if (nc > 1) {
-                nitems = nc;
-                first_item = a.n_tasks + a.pay[p].chunk_first;
-            }
-        }
-    }
-    // warp-specialised runs send every payload task to the payload queue
-    const bool topay = PAY && a.pay_warps > 0 && v >= 0 && r.w < 0;
-    const bool single = (nitems == 1) && !topay;
+    const bool haspay = PAY && v >= 0 && r.w < 0;
+    const bool topay = haspay && a.pay_warps > 0;
+    const bool single = v >= 0 && !topay;
     const unsigned sm = __ballot_sync(kFull, single);
     const int room = a.local_keep - top;
     int rank;
@@ -418,12 +407,12 @@ __device__ __forceinline__ void push_ready(const PersistArgs& a, int4 r, int pr,
             if (((sm >> j) & 1u) && (pj > pr || (pj == pr && j < lane))) ++rank;
         }
     }
-    bool go_global = nitems > 0;
+    bool go_global = v >= 0;
     if (single && rank < room) {
         const int slot = top + rank;
         nstk[slot] = r;
         const int len = r.w & 0x7fffffff;
-        if (len <= kStage) {  // stage its out-edges now; they are read next round
+        if (!haspay && len <= kStage) {  // stage its out-edges now; they are read next round
             for (int j = 0; j < len; ++j) cp_async16(nedg + slot * kStage + j, a.erec + r.z + j);
             cp_async_commit();
         }
@@ -431,10 +420,9 @@ __device__ __forceinline__ void push_ready(const PersistArgs& a, int4 r, int pr,
     }
     top += min(__popc(sm), max(room, 0));
     ws.local += (uint32_t)min(__popc(sm), max(room, 0));
-    const int cnt = go_global ? nitems : 0;
-    push_items(a, a.queue, a.qcap, &a.ctrl->tail, topay ? 0 : cnt, first_item, nitems > 1, lane, ws);
-    if (PAY && a.pay_warps > 0)
-        push_items(a, a.pqueue, a.pqcap, &a.ctrl->ptail, topay ? cnt : 0, first_item, nitems > 1, lane, ws);
+    const int item = haspay ? a.n_tasks + a.npieces + r.z : v;
+    push_items(a, a.queue, a.qcap, &a.ctrl->tail, (go_global && !topay) ? 1 : 0, item, false, lane, ws);
+    if (PAY && a.pay_warps > 0) push_items(a, a.pqueue, a.pqcap, &a.ctrl->ptail, topay ? 1 : 0, item, false, lane, ws);
     if (ws.on) ws.cyc_push += (unsigned long long)(clk(ws) - c_push);
 }
 
@@ -470,12 +458,13 @@ __device__ __forceinline__ bool release_succ(const PersistArgs& a, int v, uint32
 
 // Releases every successor of this warp's finishing tasks (lane: task `fin` >= 0 with arrival
 // key kt, first out-edge rs, out-degree deg), flattened over the warp 32 edges at a time, and
-// pushes the ones that become ready with their key, row and payload flag.
+// pushes the ones that become ready with their key, row (payload index) and payload flag.
 // Memory order: the arrival travels inside the state word, so plain releases need no fence.
 // Payload data is ordered by fences: a warp fences after running payload pieces (release) and
-// before running pieces of a task that became ready (acquire); and a window that releases a
-// task with a payload fences first, so that data written upstream by a payload task reaches it
-// through plain tasks in between (each such warp acquires what it observed, then releases).
+// before running pieces of a task that became ready (acquire); queue publication fences; and
+// without warp specialisation a window that releases a payload task fences first, so that data
+// written upstream by a payload task reaches it through plain tasks in between (each such warp
+// acquires what it observed, then releases).
 // staged: this lane's task came from the warp's stack with its out-edges staged in
 // cedg[lane * kStage ...]; nstk / nedg receive the tasks that become ready.
 template <bool PAY>
@@ -509,7 +498,9 @@ __device__ __forceinline__ void release_all(const PersistArgs& a, int fin, uint3
         int4 rec = make_int4(-1, 0, 0, 0);
         if (e < total) {
             rec = o_st ? cedg[owner * kStage + (e - o_ex)] : __ldg(a.erec + o_rs + (e - o_ex));
-            prefetch_l2(a.erec + rec.z);  // warm the successor's row while its CAS is in flight
+            // warm what the successor needs next while its CAS is in flight
+            if ((uint32_t)rec.w & kPayBit) prefetch_l2(a.pay + rec.z);
+            else prefetch_l2(a.erec + rec.z);
         }
         const uint32_t w = (uint32_t)rec.w;
         // (warp-specialised runs publish payload tasks through a queue, which fences already)
@@ -548,8 +539,9 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 2) k_persist(const PersistA
     uint64_t stall_t0 = 0;
     unsigned backoff = 32;
     const int n_tasks = a.n_tasks;
+    const int start_base = n_tasks + a.npieces;  // payload-start items begin here
     // role: in warp-specialised runs the last pay_warps warps of each CTA take their work from
-    // the payload queue (payload tasks and pieces), the others from the main queue
+    // the payload queue (payload starts and pieces), the others from the main queue
     const bool payw = PAY && a.pay_warps > 0 && wid >= kWarpsPerCta - a.pay_warps;
     int32_t* const qslots = payw ? a.pqueue : a.queue;
     const int qcap = payw ? a.pqcap : a.qcap;
@@ -636,43 +628,54 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 2) k_persist(const PersistA
         const long long c_round = clk(ws);
         ws.items += (uint32_t)__popc(got);
 
-        // ---- resolve this round's items: task (with key, row, payload flag) or payload piece
+        // ---- resolve this round's items: a task (with key, row, payload flag), a payload start
+        // (to expand) or a payload piece
         int t = -1, p = -1, piece = 0;
         uint32_t kt = 0;
         int rs = 0, deg = 0;
-        bool haspay = false, staged = false;
+        bool haspay = false, staged = false, expand = false, key_known = false;
         if (item >= 0) {
             if (item < n_tasks) {
                 t = item;
                 if (loc.x >= 0) {  // from the warp's stack: key, row and flag came along
                     kt = (uint32_t)loc.y;
-                    rs = loc.z;
+                    key_known = true;
                     deg = loc.w & 0x7fffffff;
                     haspay = PAY && loc.w < 0;
-                    staged = deg <= kStage;
-                } else {  // from the global queue
+                    if (haspay) {
+                        p = loc.z;
+                        expand = true;
+                    } else {
+                        rs = loc.z;
+                        staged = deg <= kStage;
+                    }
+                } else {  // a task without payload from the main queue
                     const int2 mt = __ldg(a.meta + t);
                     rs = mt.x;
                     deg = mt.y;
                     kt = (uint32_t)(ld_relaxed_u64(a.state + t) >> 32);
-                    haspay = PAY && a.pidx && __ldg(a.pidx + t) >= 0;
+                    key_known = true;
                 }
-                if (PAY && haspay) p = __ldg(a.pidx + t);
-            } else if (PAY) {  // a piece of a multi-piece payload task
-                const int g = item - n_tasks;
-                t = __ldg(a.chunk_task + g);
-                p = __ldg(a.pidx + t);
-                piece = g - a.pay[p].chunk_first;
+            } else if (PAY) {
                 haspay = true;
+                if (item < start_base) {  // one piece of a multi-piece payload
+                    const int g = item - n_tasks;
+                    p = __ldg(a.chunk_pay + g);
+                    piece = g - a.pay[p].chunk_first;
+                } else {  // a payload start
+                    p = item - start_base;
+                    expand = true;
+                }
+                t = a.pay[p].task;
             }
             if (a.t_start) {
                 const int64_t now = (int64_t)gtimer();
-                if (item < n_tasks) a.t_start[t] = now;
+                if (expand || !haspay) a.t_start[t] = now;
                 else atomicMin((long long*)(a.t_start + t), (long long)now);
             }
             if (a.exec_count) {
                 const long long tk = (long long)atomicAdd(&a.ctrl->ticket, 1ull);
-                if (item < n_tasks) a.tk_start[t] = tk;
+                if (expand || !haspay) a.tk_start[t] = tk;
                 else atomicCAS((unsigned long long*)(a.tk_start + t), ~0ull, (unsigned long long)tk);
             }
         }
@@ -696,6 +699,14 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 2) k_persist(const PersistA
         if (PAY) {
             unsigned work = __ballot_sync(kFull, haspay);
             if (work) {
+                // expansion: a payload start (or a stacked payload task) of several pieces puts
+                // pieces 1.. on the queue this warp serves and runs piece 0 here
+                int nc = 1, cf = 0;
+                if (haspay) {
+                    nc = a.pay[p].nchunks;
+                    cf = a.pay[p].chunk_first;
+                }
+                push_items(a, qslots, qcap, qtail, (expand && nc > 1) ? nc - 1 : 0, n_tasks + cf + 1, true, lane, ws);
                 ws.pieces += (uint32_t)__popc(work);
                 fence_acq_rel();  // acquire: inputs written by upstream payload tasks
                 while (work) {
@@ -709,16 +720,13 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 2) k_persist(const PersistA
                 __syncwarp();
                 int fin2 = -1;
                 if (haspay) {
-                    if (item < n_tasks) fin2 = t;
+                    if (nc == 1) fin2 = t;
                     else if (atom_dec_acq_rel(a.chunks_left + p) == 1) fin2 = t;
                 }
                 if (fin2 >= 0) {
-                    if (item >= n_tasks) {  // last piece: the task's key and row
-                        const int2 mt = __ldg(a.meta + t);
-                        rs = mt.x;
-                        deg = mt.y;
-                        kt = (uint32_t)(ld_relaxed_u64(a.state + t) >> 32);
-                    }
+                    rs = a.pay[p].row;
+                    deg = a.pay[p].deg;
+                    if (!key_known) kt = (uint32_t)(ld_relaxed_u64(a.state + t) >> 32);
                     if (a.exec_count) {
                         a.tk_end[fin2] = (int64_t)atomicAdd(&a.ctrl->ticket, 1ull);
                         atomicAdd(a.exec_count + fin2, 1);
@@ -726,16 +734,16 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 2) k_persist(const PersistA
                     a.key[fin2] = kt;
                 }
                 if (__ballot_sync(kFull, fin2 >= 0))
-                    release_all<PAY>(a, fin2, kt, rs, deg, staged && item < n_tasks, s_edges[wid][cb], s_stack[wid][pb],
+                    release_all<PAY>(a, fin2, kt, rs, deg, false, s_edges[wid][cb], s_stack[wid][pb],
                                      s_edges[wid][pb], top, lane, ws);
                 if (a.t_end && fin2 >= 0) a.t_end[fin2] = (int64_t)gtimer();
                 ndone += (uint32_t)__popc(__ballot_sync(kFull, fin2 >= 0));
             }
         }
 
+        if (ws.on) ws.cyc_round += (unsigned long long)(clk(ws) - c_round);
         // completions reach ctrl->done in batches: when the warp goes idle, and every 32 rounds
         // so that the stall timer of idle warps sees progress made by long-busy warps
-        if (ws.on) ws.cyc_round += (unsigned long long)(clk(ws) - c_round);
         if ((++iter & 31u) == 0 && ndone) {
             if (lane == 0) atomicAdd(&a.ctrl->done, ndone);
             ndone = 0;

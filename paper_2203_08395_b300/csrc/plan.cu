@@ -327,6 +327,9 @@ hf_status plan_build(const std::vector<hf_graph*>& graphs, Plan** out) {
                 std::memset(&d, 0, sizeof(d));
                 d.nchunks = 1;
                 d.chunk_first = -1;
+                d.task = toff + v;
+                d.row = row_ptr[(size_t)toff + v];
+                d.deg = row_ptr[(size_t)toff + v + 1] - row_ptr[(size_t)toff + v];
                 if (r.kind == HF_KERNEL) {
                     d.op = r.op == HF_K_SAXPY_I32 ? kPaySaxpyI32 : kPaySaxpyF32;
                     d.n = r.n;
@@ -375,8 +378,13 @@ hf_status plan_build(const std::vector<hf_graph*>& graphs, Plan** out) {
 
         // uploads
         if ((st = upload(p, &p->d_row_ptr, row_ptr.data(), row_ptr.size(), s, "row_ptr")) != HF_OK) return bail(st);
-        for (auto& r : erec)  // flag successors that carry a payload
-            if (p->hpidx[(size_t)r.x] >= 0) r.w = (int)((uint32_t)r.w | kPayBit);
+        for (auto& r : erec) {  // successors with a payload: flag, and their payload index
+            const int32_t k = p->hpidx[(size_t)r.x];
+            if (k >= 0) {
+                r.w = (int)((uint32_t)r.w | kPayBit);
+                r.z = k;
+            }
+        }
         if ((st = upload(p, &p->d_erec, erec.data(), erec.size(), s, "erec")) != HF_OK) return bail(st);
         if ((st = upload(p, &p->d_meta, meta.data(), meta.size(), s, "meta")) != HF_OK) return bail(st);
         if ((st = upload(p, &p->d_indeg0, indeg0.data(), indeg0.size(), s, "indeg0")) != HF_OK) return bail(st);
@@ -427,12 +435,12 @@ static hf_status plan_set_chunk(Plan* p, int64_t chunk_elems, cudaStream_t s) {
             d.chunk_first = -1;
             if (nc > 1) {
                 d.chunk_first = (int32_t)items;
-                for (int64_t c = 0; c < nc; ++c) chunk_task.push_back(p->pay_task[(size_t)k]);
+                for (int64_t c = 0; c < nc; ++c) chunk_task.push_back(k);  // piece item -> payload
                 items += nc;
             }
             item_ptr[(size_t)p->pay_level[(size_t)k] + 1] += (int32_t)nc;
         }
-        if ((int64_t)p->n + items > INT32_MAX) return fail(HF_EINVAL, "too many payload pieces");
+        if ((int64_t)p->n + items + p->npay > INT32_MAX) return fail(HF_EINVAL, "too many payload pieces");
         for (int32_t l = 0; l < p->levels; ++l) item_ptr[(size_t)l + 1] += item_ptr[(size_t)l];
         litems.resize((size_t)item_ptr[(size_t)p->levels]);
         {
@@ -442,19 +450,16 @@ static hf_status plan_set_chunk(Plan* p, int64_t chunk_elems, cudaStream_t s) {
                 for (int32_t c = 0; c < p->hpay[(size_t)k].nchunks; ++c) litems[(size_t)fill[(size_t)l]++] = make_int2(k, c);
             }
         }
-        for (int32_t t : p->sources) {
+        for (int32_t t : p->sources) {  // payload sources enter the queues as payload starts
             const int32_t k = p->hpidx.empty() ? -1 : p->hpidx[(size_t)t];
             if (k < 0) seeds.push_back(t);
-            else if (p->hpay[(size_t)k].nchunks == 1) pseeds.push_back(t);
-            else
-                for (int32_t c = 0; c < p->hpay[(size_t)k].nchunks; ++c)
-                    pseeds.push_back(p->n + p->hpay[(size_t)k].chunk_first + c);
+            else pseeds.push_back(p->n + (int32_t)items + k);
         }
     } catch (const std::bad_alloc&) {
         return fail(HF_ENOMEM, "host allocation failed");
     }
     p->nitems = (int32_t)items;
-    p->qcap = p->n + (int32_t)items;
+    p->qcap = p->n + (int32_t)items + p->npay;  // tasks, pieces and payload starts
     p->nseed = (int32_t)seeds.size();
     p->npseed = (int32_t)pseeds.size();
     p->pqcap = p->npay + (int32_t)items;
@@ -651,7 +656,8 @@ hf_status plan_run(Plan* p, cudaStream_t s, const hf_run_opts& o) {
             a.erec = p->d_erec;
             a.pidx = p->npay ? p->d_pidx : nullptr;
             a.pay = p->d_pay;
-            a.chunk_task = p->d_chunk_task;
+            a.chunk_pay = p->d_chunk_task;  // piece item -> payload index
+            a.npieces = p->nitems;
             a.key = p->d_key;
             a.state = p->d_state;
             a.queue = p->d_queue;
