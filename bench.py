@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="own", choices=["own", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--executor", default="auto", choices=["auto", "persistent", "levelsync"],
+                    help="headline executor (auto: the cost model's choice)")
     ap.add_argument("--no-learned", action="store_true", help="headline without the cost model (heuristic)")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
@@ -287,8 +289,12 @@ def main():
         best = base
     ls_pred, pe_pred = hf.hf_batch_predict(bd.b, prio, stream)
     head = {k: v for k, v in hf.opts_dict(best).items() if k not in ("time_kernel", "instrument", "validate")}
-    head.update(mode=hf.HF_MODE_AUTO, priority=prio)
-    chosen = hf.HF_MODE_PERSISTENT if pe_pred <= ls_pred else hf.HF_MODE_LEVELSYNC
+    forced = {"auto": hf.HF_MODE_AUTO, "persistent": hf.HF_MODE_PERSISTENT, "levelsync": hf.HF_MODE_LEVELSYNC}
+    head.update(mode=forced[args.executor], priority=prio)
+    if args.executor == "auto":
+        chosen = hf.HF_MODE_PERSISTENT if pe_pred <= ls_pred else hf.HF_MODE_LEVELSYNC
+    else:
+        chosen = forced[args.executor]
     bd.reset_y()
     t_setup = time.time() - t_setup
 
@@ -375,7 +381,7 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "edges_per_s": world * E / (ms / 1e3),
         "config": {"workload": args.workload, "tasks": N, "edges": E, "graphs": len(wl.graphs),
-                   "saxpy_elems": wl.saxpy_elems, "executor": "auto",
+                   "saxpy_elems": wl.saxpy_elems, "executor": args.executor,
                    "chosen": "persistent" if chosen == hf.HF_MODE_PERSISTENT else "levelsync",
                    "priority": {0: "fifo", 1: "heuristic", 2: "learned"}[prio],
                    "launch": {k: head[k] for k in ("ctas", "claim", "local_keep", "chunk_elems")},

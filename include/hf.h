@@ -108,7 +108,7 @@ typedef struct {
     int32_t ctas;           /* persistent: CTAs launched; 0 = one per SM times occupancy */
     int32_t warps_per_cta;  /* persistent: 0 = 8 */
     int32_t claim;          /* persistent: queue slots a warp claims at once, 1..32; 0 = 1 */
-    int32_t local_keep;     /* persistent: ready tasks a warp keeps in shared memory, 0..32;
+    int32_t local_keep;     /* persistent: ready tasks a warp keeps in shared memory, 0..16;
                                negative = default (16) */
     int64_t chunk_elems;    /* payload split size in elements (saxpy) or 4-byte words (copies);
                                0 = 16384 */

@@ -19,8 +19,8 @@ namespace hf {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kWarpsPerCta = 8;
-constexpr int kStackCap = 32;  // per-warp shared-memory ready stack (double-buffered)
-constexpr int kStage = 4;      // edge records staged in shared memory per stacked task
+constexpr int kStackCap = 16;  // per-warp shared-memory ready stack (double-buffered)
+constexpr int kStage = 8;      // edge records staged in shared memory per stacked task
 
 __device__ __forceinline__ uint32_t f2key(float f) {
     const uint32_t b = __float_as_uint(f);
@@ -411,8 +411,8 @@ __device__ __forceinline__ void push_ready(const PersistArgs& a, int4 r, int pr,
     if (single && rank < room) {
         const int slot = top + rank;
         nstk[slot] = r;
-        const int len = r.w & 0x7fffffff;
-        if (!haspay && len <= kStage) {  // stage its out-edges now; they are read next round
+        const int len = min(r.w & 0x7fffffff, kStage);
+        if (!haspay) {  // stage its first out-edges now; they are read next round
             for (int j = 0; j < len; ++j) cp_async16(nedg + slot * kStage + j, a.erec + r.z + j);
             cp_async_commit();
         }
@@ -497,7 +497,8 @@ __device__ __forceinline__ void release_all(const PersistArgs& a, int fin, uint3
         const bool o_st = __shfl_sync(kFull, staged ? 1 : 0, owner) != 0;
         int4 rec = make_int4(-1, 0, 0, 0);
         if (e < total) {
-            rec = o_st ? cedg[owner * kStage + (e - o_ex)] : __ldg(a.erec + o_rs + (e - o_ex));
+            const int j = e - o_ex;  // the first kStage edges of a stacked task are staged
+            rec = (o_st && j < kStage) ? cedg[owner * kStage + j] : __ldg(a.erec + o_rs + j);
             // warm what the successor needs next while its CAS is in flight
             if ((uint32_t)rec.w & kPayBit) prefetch_l2(a.pay + rec.z);
             else prefetch_l2(a.erec + rec.z);
@@ -647,7 +648,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 2) k_persist(const PersistA
                         expand = true;
                     } else {
                         rs = loc.z;
-                        staged = deg <= kStage;
+                        staged = true;
                     }
                 } else {  // a task without payload from the main queue
                     const int2 mt = __ldg(a.meta + t);

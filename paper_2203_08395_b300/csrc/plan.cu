@@ -1091,7 +1091,7 @@ hf_status plan_autotune(Plan* p, cudaStream_t s, const hf_run_opts& base, int fo
     if (st != HF_OK) return st;
     const std::vector<int> ctas_v{sms / 2, sms, 2 * sms, 4 * sms};
     const std::vector<int> claim_v{1, 4, 16, 32};
-    const std::vector<int> keep_v{4, 8, 16, 32};
+    const std::vector<int> keep_v{4, 8, 12, 16};
     const std::vector<int64_t> chunk_v{1024, 4096, 16384};
     const std::vector<int> payw_v{0, 1, 2, 4};
     for (int round = 0; round < 2; ++round) {
