@@ -287,7 +287,9 @@ def main():
         best, tuned_ms = hf.hf_batch_autotune(bd.b, stream, base)
     else:
         best = base
-    ls_pred, pe_pred = hf.hf_batch_predict(bd.b, prio, stream)
+    ls_pred = pe_pred = None
+    if args.executor == "auto":
+        ls_pred, pe_pred = hf.hf_batch_predict(bd.b, prio, stream)
     head = {k: v for k, v in hf.opts_dict(best).items() if k not in ("time_kernel", "instrument", "validate")}
     forced = {"auto": hf.HF_MODE_AUTO, "persistent": hf.HF_MODE_PERSISTENT, "levelsync": hf.HF_MODE_LEVELSYNC}
     head.update(mode=forced[args.executor], priority=prio)

@@ -105,13 +105,15 @@ typedef enum { HF_PRIO_FIFO = 0, HF_PRIO_HEURISTIC = 1, HF_PRIO_LEARNED = 2 } hf
 typedef struct {
     int32_t mode;           /* hf_mode */
     int32_t priority;       /* hf_priority (persistent executor) */
-    int32_t ctas;           /* persistent: CTAs launched; 0 = one per SM times occupancy */
-    int32_t warps_per_cta;  /* persistent: 0 = 8 */
-    int32_t claim;          /* persistent: queue slots a warp claims at once, 1..32; 0 = 1 */
+    int32_t ctas;           /* persistent: CTAs launched; 0 = two per SM (within occupancy) */
+    int32_t warps_per_cta;  /* persistent: fixed at 8 in this build (the field is ignored) */
+    int32_t claim;          /* persistent: most queue slots a warp claims at once (it claims its
+                               fair share of the backlog), 1..32; default 8 */
     int32_t local_keep;     /* persistent: ready tasks a warp keeps in shared memory, 0..16;
                                negative = default (16) */
     int64_t chunk_elems;    /* payload split size in elements (saxpy) or 4-byte words (copies);
-                               0 = 16384 */
+                               0 = 16384 (persistent) / 512 (level-sync); in HF_MODE_AUTO it
+                               applies only when the persistent executor is chosen */
     uint64_t spin_limit_ns; /* persistent: give up (HF_ETIMEDOUT) after this long without any
                                task completing; 0 = 2 s */
     int32_t instrument;     /* bit 0: record per-task %globaltimer start/end (hf_get_task_times);

@@ -183,7 +183,7 @@ void hf_run_opts_default(hf_run_opts* o) {
     std::memset(o, 0, sizeof(*o));
     o->mode = HF_MODE_PERSISTENT;
     o->priority = HF_PRIO_FIFO;
-    o->claim = 1;
+    o->claim = 8;
     o->local_keep = -1;
     o->stall_task = -1;
 }

@@ -598,9 +598,11 @@ hf_status plan_run(Plan* p, cudaStream_t s, const hf_run_opts& o) {
     if (o.priority == HF_PRIO_LEARNED && !p->cm) return fail(HF_ESTATE, "HF_PRIO_LEARNED needs a cost model (hf_batch_set_costmodel)");
     hf_status st = HF_OK;
     if (mode == HF_MODE_PERSISTENT && (st = plan_prepare_priority(p, o.priority, p->cm, s)) != HF_OK) return st;
-    // default piece: 2,048 elements for level-sync (a level's payloads spread over many warps),
-    // 16,384 for the persistent executor (fewer queue items)
-    int64_t chunk = o.chunk_elems > 0 ? o.chunk_elems : (mode == HF_MODE_LEVELSYNC ? 2048 : 16384);
+    // default piece: 512 elements for level-sync (a level's payloads spread over many warps),
+    // 16,384 for the persistent executor (fewer queue items); in AUTO mode the caller's piece
+    // size applies to the persistent executor only
+    const bool own_chunk = o.chunk_elems > 0 && !(o.mode == HF_MODE_AUTO && mode == HF_MODE_LEVELSYNC);
+    int64_t chunk = own_chunk ? o.chunk_elems : (mode == HF_MODE_LEVELSYNC ? 512 : 16384);
     chunk = ((chunk + 31) / 32) * 32;
     st = plan_set_chunk(p, chunk, s);
     if (st != HF_OK) return st;
@@ -683,11 +685,12 @@ hf_status plan_run(Plan* p, cudaStream_t s, const hf_run_opts& o) {
             }
             p->last_stats = a.stats != nullptr;
             int ctas = o.ctas;
-            if (ctas <= 0) {  // every warp slot of the GPU: one CTA per SM times occupancy
+            if (ctas <= 0) {  // two CTAs (16 warps) per SM, capped by occupancy: more idle warps
+                              // only add polling traffic (the autotuner searches around this)
                 int occ = 0;
                 if (p->npay) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_persist<true>, kWarpsPerCta * 32, 0);
                 else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_persist<false>, kWarpsPerCta * 32, 0);
-                ctas = p->num_sms * std::max(occ, 1);
+                ctas = p->num_sms * std::min(std::max(occ, 1), 2);
             }
             if (o.time_kernel) cudaEventRecord(p->kev0, s);
             if (p->npay) k_persist<true><<<ctas, kWarpsPerCta * 32, 0, s>>>(a);

@@ -39,7 +39,7 @@ def test_every_declared_symbol_is_exported():
 def test_defaults_and_status_strings():
     o = hf.hf_run_opts_default()
     assert o.mode == hf.HF_MODE_PERSISTENT and o.priority == hf.HF_PRIO_FIFO
-    assert o.claim == 1 and o.local_keep == -1 and o.stall_task == -1
+    assert o.claim == 8 and o.local_keep == -1 and o.stall_task == -1
     for s in range(9):
         assert hf.hf_status_string(s).startswith(hf.STATUS_NAMES[s])
 
