@@ -318,6 +318,41 @@ hf_status hf_batch_autotune(hf_batch* b, void* stream, const hf_run_opts* base, 
  * attached, else HEURISTIC). */
 hf_status hf_batch_predict(hf_batch* b, int32_t priority, void* stream, float* levelsync_ms, float* persistent_ms);
 
+/* --- allocation-free entry point -------------------------------------------------------
+ * The paper has no counterpart to this call; it exists for callers that cannot allocate
+ * device memory: code that runs inside another framework's memory pool or under a fixed
+ * memory budget, plug-ins whose host application forbids cudaMalloc, and loops where an
+ * allocation, or the device-wide synchronisation cudaFree can bring, is not acceptable.
+ *
+ * hf_run_csr_noalloc computes the arrivals of one max-plus graph (the same result, bit for
+ * bit, as hf_run on a graph of max-plus tasks with these edges) without any allocation: no
+ * cudaMalloc, no cudaFree, no allocator hook, no graph object. Its scratch (12 bytes per task
+ * plus 512 bytes) is a fixed device array inside the library, HF_NOALLOC_MAX_TASKS tasks
+ * large (12 MiB), that every GPU where the library is loaded holds until the process exits.
+ * Arguments (device pointers on the current device, all owned by the caller):
+ *   n_tasks  tasks 0..n_tasks-1, 0 <= n_tasks <= HF_NOALLOC_MAX_TASKS (larger: HF_EINVAL);
+ *   n_edges  edges, >= 0;
+ *   row_ptr  int32[n_tasks + 1], CSR row starts: the successors of task v are
+ *            succ[row_ptr[v] .. row_ptr[v+1]), row_ptr[0] = 0, row_ptr[n_tasks] = n_edges;
+ *   succ     int32[n_edges] successor ids; delay float[n_edges] finite edge delays d(u, v);
+ *   arr0     float[n_tasks] finite source arrivals (read for tasks without predecessors),
+ *            or NULL for +0;
+ *   arr      float[n_tasks] output arrivals;
+ *   spin_limit_ns  give up with HF_ETIMEDOUT after this long without progress (0 = 2 s);
+ *   stream   cudaStream_t the work is enqueued on; the call then waits for that stream.
+ * Errors: HF_EINVAL for sizes, NULL pointers or (found on the device) a malformed CSR, an
+ * out-of-range successor or a non-finite delay/arr0, with arr left unwritten; HF_ETIMEDOUT
+ * when the edges form a cycle (arr partly written); HF_ECUDA for a CUDA failure.
+ * The first call on each device looks up the array's device address and sizes the grid
+ * (with that device current); make that first call before any stream capture. Every call
+ * on a device uses the same array: it clears what it reads before use, but two calls whose
+ * work overlaps on the GPU (other streams, other host threads) race and corrupt each
+ * other's results, so serialise them. */
+#define HF_NOALLOC_MAX_TASKS 1048576
+hf_status hf_run_csr_noalloc(int32_t n_tasks, int32_t n_edges, const int32_t* row_ptr, const int32_t* succ,
+                             const float* delay, const float* arr0, float* arr, uint64_t spin_limit_ns,
+                             void* stream);
+
 /* --- memory and diagnostics ------------------------------------------------------------ */
 
 /* Process-wide device allocator for library-owned buffers (NULL, NULL = cudaMalloc/cudaFree).

@@ -1,6 +1,7 @@
 """Builds the CUDA library libhf.so (sm_103a) in-tree with nvcc.
 
-Sources: csrc/api.cpp (C ABI, host graph builder) and csrc/plan.cu (plans, executors, kernels).
+Sources: csrc/api.cpp (C ABI, host graph builder), csrc/plan.cu (plans, executors, kernels),
+csrc/costmodel.cu (learned cost model) and csrc/noalloc.cu (the allocation-free entry point).
 The CUDA runtime is linked as a shared library so that, inside a process that already loaded
 PyTorch's libcudart.so.13, both use one runtime instance.
 """
@@ -14,7 +15,7 @@ LIB = os.path.join(HERE, "libhf.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cpp", "plan.cu", "costmodel.cu"]
+SOURCES = ["api.cpp", "plan.cu", "costmodel.cu", "noalloc.cu"]
 HEADERS = ["hf_internal.h", "kernels.cuh"]
 
 

@@ -138,6 +138,7 @@ def load():
         "hf_batch_autotune": [vp, vp, P(hf_run_opts), ctypes.c_int, P(hf_run_opts), P(ctypes.c_float)],
         "hf_batch_get_stats": [vp, vp, i32],
         "hf_batch_predict": [vp, i32, vp, P(ctypes.c_float), P(ctypes.c_float)],
+        "hf_run_csr_noalloc": [i32, i32, vp, vp, vp, vp, vp, ctypes.c_uint64, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -489,6 +490,18 @@ def hf_batch_get_stats(b):
     out = np.zeros(16, np.int64)
     _check(load().hf_batch_get_stats(b, _ptr(out), 16), "hf_batch_get_stats")
     return {nm: int(out[i]) for i, nm in enumerate(STAT_NAMES)}
+
+
+HF_NOALLOC_MAX_TASKS = 1048576
+
+
+def hf_run_csr_noalloc(n_tasks, n_edges, row_ptr, succ, delay, arr0, arr, spin_limit_ns=0, stream=None):
+    """Arrivals of one max-plus graph given as a successor CSR, with no allocation by the
+    library (its scratch is a fixed device array). row_ptr (int32, n_tasks + 1), succ (int32),
+    delay (float32), arr0 (float32 or None) and arr (float32, written) are device buffers the
+    caller owns (CUDA tensors or raw addresses). Blocks until the result is in arr."""
+    _check(load().hf_run_csr_noalloc(n_tasks, n_edges, _ptr(row_ptr), _ptr(succ), _ptr(delay), _ptr(arr0),
+                                     _ptr(arr), spin_limit_ns, _stream_handle(stream)), "hf_run_csr_noalloc")
 
 
 def opts_dict(o):
