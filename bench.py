@@ -39,7 +39,7 @@ sys.path.insert(0, ROOT)
 DEFAULT_WORKLOAD = "batch256_mixed"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
-KERNEL_SRC = os.path.join(ROOT, "paper_2203_08395_b300", "csrc", "kernels.cuh")
+KERNEL_SRC = [os.path.join(ROOT, "paper_2203_08395_b300", "csrc", f) for f in ("kernels.cuh", "team.cuh")]
 
 
 def parse():
@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="own", choices=["own", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
-    ap.add_argument("--executor", default="auto", choices=["auto", "persistent", "levelsync"],
+    ap.add_argument("--executor", default="auto", choices=["auto", "persistent", "levelsync", "team"],
                     help="headline executor (auto: the cost model's choice)")
     ap.add_argument("--no-learned", action="store_true", help="headline without the cost model (heuristic)")
     ap.add_argument("--no-tune", action="store_true")
@@ -69,7 +69,10 @@ def peaks():
 
 
 def kernel_sha():
-    return hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()
+    h = hashlib.sha256()
+    for f in KERNEL_SRC:
+        h.update(open(f, "rb").read())
+    return h.hexdigest()
 
 
 def traffic_for(kernel, workload):
@@ -291,7 +294,8 @@ def main():
     if args.executor == "auto":
         ls_pred, pe_pred = hf.hf_batch_predict(bd.b, prio, stream)
     head = {k: v for k, v in hf.opts_dict(best).items() if k not in ("time_kernel", "instrument", "validate")}
-    forced = {"auto": hf.HF_MODE_AUTO, "persistent": hf.HF_MODE_PERSISTENT, "levelsync": hf.HF_MODE_LEVELSYNC}
+    forced = {"auto": hf.HF_MODE_AUTO, "persistent": hf.HF_MODE_PERSISTENT, "levelsync": hf.HF_MODE_LEVELSYNC,
+              "team": hf.HF_MODE_TEAM}
     head.update(mode=forced[args.executor], priority=prio)
     if args.executor == "auto":
         chosen = hf.HF_MODE_PERSISTENT if pe_pred <= ls_pred else hf.HF_MODE_LEVELSYNC
@@ -340,7 +344,9 @@ def main():
                         ("persistent_fifo_default", dict(mode=hf.HF_MODE_PERSISTENT, priority=hf.HF_PRIO_FIFO)),
                         ("persistent_fifo_tuned", dict(head, mode=hf.HF_MODE_PERSISTENT, priority=hf.HF_PRIO_FIFO)),
                         ("persistent_heuristic_tuned", dict(head, mode=hf.HF_MODE_PERSISTENT,
-                                                            priority=hf.HF_PRIO_HEURISTIC))):
+                                                            priority=hf.HF_PRIO_HEURISTIC)),
+                        ("team_fifo", dict(mode=hf.HF_MODE_TEAM, priority=hf.HF_PRIO_FIFO)),
+                        ("team_heuristic", dict(mode=hf.HF_MODE_TEAM, priority=hf.HF_PRIO_HEURISTIC))):
             c_ms, c_med, c_st, _ = timed(o, k, 3)
             compare[name] = {"ms_per_step": c_ms, "ms_median": c_med, "tasks_per_s": N / (c_ms / 1e3),
                              "edges_per_s": E / (c_ms / 1e3), "status": hf.hf_status_string(c_st)}
@@ -371,15 +377,15 @@ def main():
 
     peak, peak_kind = peaks()
     b_alg = algorithmic_bytes(wl)
-    kname = "k_persist" if chosen == hf.HF_MODE_PERSISTENT else "k_level"
+    kname = {hf.HF_MODE_PERSISTENT: "k_persist", hf.HF_MODE_TEAM: "k_team"}.get(chosen, "k_level")
     # per launch of the dominant kernel: one k_persist per step, or one k_level per merged level
-    k_launches = 1 if chosen == hf.HF_MODE_PERSISTENT else max(g.levels for g in wl.graphs)
+    k_launches = 1 if chosen in (hf.HF_MODE_PERSISTENT, hf.HF_MODE_TEAM) else max(g.levels for g in wl.graphs)
     achieved = (b_alg / k_launches) / (kernel_ms / k_launches / 1e3) / 1e9
     roof = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": traffic_for(kname, args.workload),
             "algorithmic_bytes": b_alg / k_launches, "launches_per_step": k_launches,
             "ms_per_launch": kernel_ms / k_launches, "peak_source": peak_kind + " (MEASURED_PEAKS hbm_gbs)"}
-    launches = 2 if chosen == hf.HF_MODE_PERSISTENT else k_launches
+    launches = 2 if chosen == hf.HF_MODE_PERSISTENT else k_launches  # persistent: k_reset + k_persist
     line = {
         "metric": "DAG tasks/s", "value": value, "unit": "tasks/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "ms_per_step_median": ms_med, "higher_is_better": True,
@@ -387,7 +393,7 @@ def main():
         "edges_per_s": world * E / (ms / 1e3),
         "config": {"workload": args.workload, "tasks": N, "edges": E, "graphs": len(wl.graphs),
                    "saxpy_elems": wl.saxpy_elems, "executor": args.executor,
-                   "chosen": "persistent" if chosen == hf.HF_MODE_PERSISTENT else "levelsync",
+                   "chosen": {hf.HF_MODE_PERSISTENT: "persistent", hf.HF_MODE_TEAM: "team"}.get(chosen, "levelsync"),
                    "priority": {0: "fifo", 1: "heuristic", 2: "learned"}[prio],
                    "launch": {k: head[k] for k in ("ctas", "claim", "local_keep", "chunk_elems")},
                    "autotuned_ms": tuned_ms, "predicted_ms": {"levelsync": ls_pred, "persistent": pe_pred},

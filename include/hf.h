@@ -99,7 +99,15 @@ typedef struct { void (*fn)(void* arg); void* arg; } hf_host_payload;
 
 /* --- run options ---------------------------------------------------------------------- */
 
-typedef enum { HF_MODE_LEVELSYNC = 0, HF_MODE_PERSISTENT = 1, HF_MODE_AUTO = 2 } hf_mode;
+/* HF_MODE_TEAM: persistent executor for batches of independent graphs. One launch; each graph
+ * is a job, taken from a job queue longest predicted first and run level by level with a
+ * barrier between levels instead of a kernel boundary: one CTA and CTA barriers for most
+ * graphs, the CTAs of one thread-block cluster and the hardware cluster barrier for the longest
+ * ones. The next levels' task lists and in-edges are staged in shared memory by TMA bulk
+ * copies while the current level runs. The cluster size and which graphs get a cluster come
+ * from predicted task costs (HF_PRIO_HEURISTIC, or HF_PRIO_LEARNED with a cost model attached;
+ * HF_PRIO_FIFO: one CTA per graph in batch order). Payload pieces default to 512 elements. */
+typedef enum { HF_MODE_LEVELSYNC = 0, HF_MODE_PERSISTENT = 1, HF_MODE_AUTO = 2, HF_MODE_TEAM = 3 } hf_mode;
 typedef enum { HF_PRIO_FIFO = 0, HF_PRIO_HEURISTIC = 1, HF_PRIO_LEARNED = 2 } hf_priority;
 
 typedef struct {
@@ -126,7 +134,9 @@ typedef struct {
                                hf_kernel_ms / hf_batch_kernel_ms) */
     int32_t payload_warps;  /* persistent: warps per CTA (0..7) that only run payload tasks,
                                taken from a separate payload queue; 0 = every warp runs both */
-    int32_t pad_;
+    int32_t team_size;      /* team: thread-block cluster size for every graph, 1..16 (above 16:
+                               16); 0 = cluster size and clustered graphs chosen from predicted
+                               costs (one CTA per graph under HF_PRIO_FIFO) */
 } hf_run_opts;
 
 void hf_run_opts_default(hf_run_opts* opts);

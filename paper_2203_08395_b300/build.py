@@ -16,7 +16,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["api.cpp", "plan.cu", "costmodel.cu", "noalloc.cu"]
-HEADERS = ["hf_internal.h", "kernels.cuh"]
+HEADERS = ["hf_internal.h", "kernels.cuh", "team.cuh"]
 
 
 def _stale():

@@ -141,6 +141,39 @@ struct ResetArgs {
     int32_t* exec_count;
 };
 
+// Team executor: a job is one graph, run by one CTA (solo job) or by the CTAs of one thread-block
+// cluster (cluster job; jobs [0, ncjobs) of the list).
+struct TeamJob {
+    int32_t graph;
+    int32_t pad_;
+    int32_t seg0;    // first (graph, level) segment of the graph
+    int32_t levels;  // levels of the graph
+};
+
+// Team-executor control words (zeroed before every run): solo-job counter, cluster-job counter.
+constexpr int kTeamNext = 0;
+constexpr int kTeamNextC = 32;
+constexpr int kTeamWords = 64;
+
+// Arguments of the team executor kernel.
+struct TeamArgs {
+    const int32_t* ls_node;  // merged level-sorted order (as the level-synchronous executor)
+    const int32_t* ls_ptr;
+    const int2* ls_in;
+    const uint32_t* key0;
+    uint32_t* key;
+    const DevPayload* pay;
+    const int2* items;       // payload work items {payload index, piece index}
+    const int4* seg;         // (graph, level) segment -> {p0, p1, e0, e1}
+    const int2* seg_items;   // (graph, level) segment -> payload items {i0, i1}
+    const TeamJob* jobs;     // cluster jobs first, then solo jobs
+    int32_t njobs;
+    int32_t ncjobs;
+    int32_t* team;           // control words (kTeam*)
+    Ctrl* ctrl;              // status word (HF_ETIMEDOUT when a staged copy never lands)
+    uint64_t spin_limit_ns;
+};
+
 // Arguments of one level kernel of the level-synchronous executor.
 struct LevelArgs {
     const int32_t* ls_node;  // level-sorted position -> task id

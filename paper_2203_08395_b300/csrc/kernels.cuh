@@ -90,26 +90,38 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 // ------------------------------------------------------------------ payload pieces (warp-wide)
 
 // y[i] = fma(a, x[i], y[i]) for i in [0, cnt): one warp, 16-byte vector accesses when x and y
-// share their alignment, streaming cache hints (each element is touched once).
+// share their alignment, streaming cache hints (each element is touched once). The unaligned
+// head and the ragged tail are loaded together with the first 512-element block, so a piece of
+// up to 512 elements costs one round trip; lanes past the end of a block load its last vector
+// again and store nothing.
 __device__ __forceinline__ void warp_saxpy_f32(float* __restrict__ y, const float* __restrict__ x, int64_t cnt,
                                                float a, int lane) {
     if ((((uintptr_t)y ^ (uintptr_t)x) & 15) == 0) {
         int64_t head = (int64_t)(((16 - ((uintptr_t)y & 15)) & 15) >> 2);
         if (head > cnt) head = cnt;
-        if (lane < head) y[lane] = __fmaf_rn(a, __ldcg(x + lane), __ldcg(y + lane));
-        y += head;
-        x += head;
-        cnt -= head;
-        const int64_t nv = cnt >> 2;
-        float4* __restrict__ y4 = reinterpret_cast<float4*>(y);
-        const float4* __restrict__ x4 = reinterpret_cast<const float4*>(x);
-        int64_t k = lane;
-        for (; k + 96 < nv; k += 128) {
+        float hx = 0.f, hy = 0.f, tx = 0.f, ty = 0.f;
+        if (lane < head) {
+            hx = __ldcg(x + lane);
+            hy = __ldcg(y + lane);
+        }
+        float* yb = y + head;
+        const float* xb = x + head;
+        const int64_t body = cnt - head;
+        const int64_t nv = body >> 2;
+        const int64_t done = nv << 2;
+        if (lane < body - done) {
+            tx = __ldcg(xb + done + lane);
+            ty = __ldcg(yb + done + lane);
+        }
+        float4* __restrict__ y4 = reinterpret_cast<float4*>(yb);
+        const float4* __restrict__ x4 = reinterpret_cast<const float4*>(xb);
+        for (int64_t k = lane; k - lane < nv; k += 128) {
             float4 xv[4], yv[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                xv[u] = __ldcs(x4 + k + 32 * u);
-                yv[u] = __ldcs(y4 + k + 32 * u);
+                const int64_t i = k + 32 * u < nv ? k + 32 * u : nv - 1;
+                xv[u] = __ldcs(x4 + i);
+                yv[u] = __ldcs(y4 + i);
             }
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
@@ -117,78 +129,88 @@ __device__ __forceinline__ void warp_saxpy_f32(float* __restrict__ y, const floa
                 yv[u].y = __fmaf_rn(a, xv[u].y, yv[u].y);
                 yv[u].z = __fmaf_rn(a, xv[u].z, yv[u].z);
                 yv[u].w = __fmaf_rn(a, xv[u].w, yv[u].w);
-                __stcs(y4 + k + 32 * u, yv[u]);
+                if (k + 32 * u < nv) __stcs(y4 + k + 32 * u, yv[u]);
             }
         }
-        for (; k < nv; k += 32) {
-            const float4 xv = __ldcs(x4 + k);
-            float4 yv = __ldcs(y4 + k);
-            yv.x = __fmaf_rn(a, xv.x, yv.x);
-            yv.y = __fmaf_rn(a, xv.y, yv.y);
-            yv.z = __fmaf_rn(a, xv.z, yv.z);
-            yv.w = __fmaf_rn(a, xv.w, yv.w);
-            __stcs(y4 + k, yv);
-        }
-        const int64_t done = nv << 2;
-        if (lane < cnt - done) y[done + lane] = __fmaf_rn(a, __ldcg(x + done + lane), __ldcg(y + done + lane));
+        if (lane < head) y[lane] = __fmaf_rn(a, hx, hy);
+        if (lane < body - done) yb[done + lane] = __fmaf_rn(a, tx, ty);
     } else {
         for (int64_t i = lane; i < cnt; i += 32) y[i] = __fmaf_rn(a, __ldcg(x + i), __ldcg(y + i));
     }
 }
 
-// int32 saxpy with two's-complement wrap-around (unsigned arithmetic)
+// int32 saxpy with two's-complement wrap-around (unsigned arithmetic), same access pattern
 __device__ __forceinline__ void warp_saxpy_i32(int32_t* __restrict__ y, const int32_t* __restrict__ x, int64_t cnt,
                                                uint32_t a, int lane) {
     if ((((uintptr_t)y ^ (uintptr_t)x) & 15) == 0) {
         int64_t head = (int64_t)(((16 - ((uintptr_t)y & 15)) & 15) >> 2);
         if (head > cnt) head = cnt;
-        if (lane < head) y[lane] = (int32_t)(a * (uint32_t)__ldcg(x + lane) + (uint32_t)__ldcg(y + lane));
-        y += head;
-        x += head;
-        cnt -= head;
-        const int64_t nv = cnt >> 2;
-        int4* __restrict__ y4 = reinterpret_cast<int4*>(y);
-        const int4* __restrict__ x4 = reinterpret_cast<const int4*>(x);
-        for (int64_t k = lane; k < nv; k += 32) {
-            const int4 xv = __ldcs(x4 + k);
-            int4 yv = __ldcs(y4 + k);
-            yv.x = (int32_t)(a * (uint32_t)xv.x + (uint32_t)yv.x);
-            yv.y = (int32_t)(a * (uint32_t)xv.y + (uint32_t)yv.y);
-            yv.z = (int32_t)(a * (uint32_t)xv.z + (uint32_t)yv.z);
-            yv.w = (int32_t)(a * (uint32_t)xv.w + (uint32_t)yv.w);
-            __stcs(y4 + k, yv);
+        uint32_t hx = 0, hy = 0, tx = 0, ty = 0;
+        if (lane < head) {
+            hx = (uint32_t)__ldcg(x + lane);
+            hy = (uint32_t)__ldcg(y + lane);
         }
+        int32_t* yb = y + head;
+        const int32_t* xb = x + head;
+        const int64_t body = cnt - head;
+        const int64_t nv = body >> 2;
         const int64_t done = nv << 2;
-        if (lane < cnt - done)
-            y[done + lane] = (int32_t)(a * (uint32_t)__ldcg(x + done + lane) + (uint32_t)__ldcg(y + done + lane));
+        if (lane < body - done) {
+            tx = (uint32_t)__ldcg(xb + done + lane);
+            ty = (uint32_t)__ldcg(yb + done + lane);
+        }
+        int4* __restrict__ y4 = reinterpret_cast<int4*>(yb);
+        const int4* __restrict__ x4 = reinterpret_cast<const int4*>(xb);
+        for (int64_t k = lane; k - lane < nv; k += 128) {
+            int4 xv[4], yv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t i = k + 32 * u < nv ? k + 32 * u : nv - 1;
+                xv[u] = __ldcs(x4 + i);
+                yv[u] = __ldcs(y4 + i);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                yv[u].x = (int32_t)(a * (uint32_t)xv[u].x + (uint32_t)yv[u].x);
+                yv[u].y = (int32_t)(a * (uint32_t)xv[u].y + (uint32_t)yv[u].y);
+                yv[u].z = (int32_t)(a * (uint32_t)xv[u].z + (uint32_t)yv[u].z);
+                yv[u].w = (int32_t)(a * (uint32_t)xv[u].w + (uint32_t)yv[u].w);
+                if (k + 32 * u < nv) __stcs(y4 + k + 32 * u, yv[u]);
+            }
+        }
+        if (lane < head) y[lane] = (int32_t)(a * hx + hy);
+        if (lane < body - done) yb[done + lane] = (int32_t)(a * tx + ty);
     } else {
         for (int64_t i = lane; i < cnt; i += 32) y[i] = (int32_t)(a * (uint32_t)__ldcg(x + i) + (uint32_t)__ldcg(y + i));
     }
 }
 
-// byte copy (either end may be page-locked host memory reached over the host link)
+// byte copy (either end may be page-locked host memory reached over the host link), same
+// access pattern with 16-byte vectors
 __device__ __forceinline__ void warp_copy(char* __restrict__ d, const char* __restrict__ s, int64_t cnt, int lane) {
     if ((((uintptr_t)d ^ (uintptr_t)s) & 15) == 0) {
         int64_t head = (int64_t)((16 - ((uintptr_t)d & 15)) & 15);
         if (head > cnt) head = cnt;
-        if (lane < head) d[lane] = __ldcg(s + lane);
-        d += head;
-        s += head;
-        cnt -= head;
-        const int64_t nv = cnt >> 4;
-        uint4* __restrict__ d4 = reinterpret_cast<uint4*>(d);
-        const uint4* __restrict__ s4 = reinterpret_cast<const uint4*>(s);
-        int64_t k = lane;
-        for (; k + 96 < nv; k += 128) {
+        char hc = 0, tc = 0;
+        if (lane < head) hc = __ldcg(s + lane);
+        char* db = d + head;
+        const char* sb = s + head;
+        const int64_t body = cnt - head;
+        const int64_t nv = body >> 4;
+        const int64_t done = nv << 4;
+        if (lane < body - done) tc = __ldcg(sb + done + lane);
+        uint4* __restrict__ d4 = reinterpret_cast<uint4*>(db);
+        const uint4* __restrict__ s4 = reinterpret_cast<const uint4*>(sb);
+        for (int64_t k = lane; k - lane < nv; k += 128) {
             uint4 v[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) v[u] = __ldcg(s4 + k + 32 * u);
+            for (int u = 0; u < 4; ++u) v[u] = __ldcg(s4 + (k + 32 * u < nv ? k + 32 * u : nv - 1));
 #pragma unroll
-            for (int u = 0; u < 4; ++u) __stcg(d4 + k + 32 * u, v[u]);
+            for (int u = 0; u < 4; ++u)
+                if (k + 32 * u < nv) __stcg(d4 + k + 32 * u, v[u]);
         }
-        for (; k < nv; k += 32) __stcg(d4 + k, __ldcg(s4 + k));
-        const int64_t done = nv << 4;
-        if (lane < cnt - done) d[done + lane] = __ldcg(s + done + lane);
+        if (lane < head) d[lane] = hc;
+        if (lane < body - done) db[done + lane] = tc;
     } else {
         for (int64_t i = lane; i < cnt; i += 32) d[i] = __ldcg(s + i);
     }
@@ -224,18 +246,22 @@ __global__ void __launch_bounds__(256) k_level(const LevelArgs a) {
         if (e0 == e1) {
             best = a.key0 ? __ldg(a.key0 + v) : kKeyPosZero;
         } else {
+            // batches of up to 8 in-edges: every key load of a batch is issued before the first
+            // is used, so a task's gather costs one round trip
             best = 0u;
-            int e = e0;
-            for (; e + 1 < e1; e += 2) {
-                const int2 i0 = __ldg(a.ls_in + e), i1 = __ldg(a.ls_in + e + 1);
-                const uint32_t k0 = __ldcg(a.key + i0.x), k1 = __ldcg(a.key + i1.x);
-                const uint32_t c0 = f2key(__fadd_rn(key2f(k0), __int_as_float(i0.y)));
-                const uint32_t c1 = f2key(__fadd_rn(key2f(k1), __int_as_float(i1.y)));
-                best = max(best, max(c0, c1));
-            }
-            if (e < e1) {
-                const int2 i0 = __ldg(a.ls_in + e);
-                best = max(best, f2key(__fadd_rn(key2f(__ldcg(a.key + i0.x)), __int_as_float(i0.y))));
+            for (int e = e0; e < e1; e += 8) {
+                const int cnt = e1 - e < 8 ? e1 - e : 8;
+                int2 ie[8];
+                uint32_t kk[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    if (j < cnt) ie[j] = __ldg(a.ls_in + e + j);
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    if (j < cnt) kk[j] = __ldcg(a.key + ie[j].x);
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    if (j < cnt) best = max(best, f2key(__fadd_rn(key2f(kk[j]), __int_as_float(ie[j].y))));
             }
         }
         a.key[v] = best;

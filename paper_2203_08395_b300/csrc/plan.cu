@@ -10,12 +10,14 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <queue>
 #include <string>
 #include <tuple>
 #include <vector>
 
 #include "hf_internal.h"
 #include "kernels.cuh"
+#include "team.cuh"
 
 namespace hf {
 
@@ -42,6 +44,21 @@ struct Plan {
     std::vector<int32_t> hpidx;     // task -> payload or -1
     std::vector<int32_t> sources;   // task ids with no predecessor
     std::vector<int32_t> level_ptr; // merged level-sorted positions (levels + 1)
+    // team executor
+    std::vector<int4> h_seg;          // (graph, level) segment -> {p0, p1, e0, e1}
+    std::vector<int32_t> seg_first;   // graph -> first segment (ngraphs + 1)
+    std::vector<int32_t> glevels;     // graph -> levels
+    int4* d_seg = nullptr;
+    int2* d_seg_items = nullptr;      // segment -> payload items {i0, i1} (per piece size)
+    size_t cap_seg_items = 0;
+    TeamJob* d_jobs = nullptr;
+    size_t cap_jobs = 0;
+    int32_t njobs = 0;
+    int32_t ncjobs = 0;               // cluster jobs (the first ncjobs of the list)
+    int32_t team_k = 1;               // cluster size of the launch
+    int32_t* d_team = nullptr;        // control words (job counters)
+    int32_t team_for[3] = {-1, -1, -1};  // priority, team_size, CTAs the job list was built for
+    const hf_costmodel* team_cm = nullptr;
 
     // device buffers
     std::vector<void*> owned;
@@ -117,6 +134,8 @@ struct Plan {
 hf_status plan_auto_mode(Plan* p, cudaStream_t s, int* mode);
 
 static hf_status plan_set_chunk(Plan* p, int64_t chunk_elems, cudaStream_t s);
+static hf_status plan_team_jobs(Plan* p, const hf_run_opts& o, cudaStream_t s);
+static int team_capacity(const Plan* p, int k);
 hf_status plan_prepare_priority(Plan* p, int32_t priority, const hf_costmodel* cm, cudaStream_t s);
 
 void plan_set_costmodel(Plan* p, const hf_costmodel* cm) {
@@ -130,9 +149,11 @@ static void* palloc(Plan* p, size_t bytes, cudaStream_t s) {
     return d;
 }
 
+// slack: extra bytes after the data (the team executor's bulk copies round ends up to 16 bytes)
 template <typename T>
-static hf_status upload(Plan* p, T** dst, const T* src, size_t count, cudaStream_t s, const char* what) {
-    *dst = (T*)palloc(p, std::max<size_t>(count * sizeof(T), 16), s);
+static hf_status upload(Plan* p, T** dst, const T* src, size_t count, cudaStream_t s, const char* what,
+                        size_t slack = 0) {
+    *dst = (T*)palloc(p, std::max<size_t>(count * sizeof(T) + slack, 16), s);
     if (!*dst) return fail(HF_ENOMEM, std::string("device allocation failed: ") + what);
     if (count) {
         cudaError_t e = cudaMemcpyAsync(*dst, src, count * sizeof(T), cudaMemcpyHostToDevice, s);
@@ -267,6 +288,14 @@ hf_status plan_build(const std::vector<hf_graph*>& graphs, Plan** out) {
         for (int i = 0; i < p->ngraphs; ++i) geoff[(size_t)i + 1] = geoff[(size_t)i] + graphs[(size_t)i]->fin.m;
         std::vector<int32_t> ls_where((size_t)p->m);  // graph-local ls position (offset by graph) -> merged
         p->level_ptr.assign((size_t)p->levels + 1, 0);
+        // (graph, level) segments of the merged order for the team executor
+        p->seg_first.assign((size_t)p->ngraphs + 1, 0);
+        p->glevels.assign((size_t)p->ngraphs, 0);
+        for (int i = 0; i < p->ngraphs; ++i) {
+            p->glevels[(size_t)i] = graphs[(size_t)i]->fin.levels;
+            p->seg_first[(size_t)i + 1] = p->seg_first[(size_t)i] + graphs[(size_t)i]->fin.levels;
+        }
+        p->h_seg.assign((size_t)p->seg_first[(size_t)p->ngraphs], make_int4(0, 0, 0, 0));
         {
             int64_t pos = 0, ein = 0;
             for (int32_t l = 0; l < p->levels; ++l) {
@@ -274,6 +303,9 @@ hf_status plan_build(const std::vector<hf_graph*>& graphs, Plan** out) {
                 for (int i = 0; i < p->ngraphs; ++i) {
                     const Final& f = graphs[(size_t)i]->fin;
                     if (l >= f.levels) continue;
+                    int4& sgm = p->h_seg[(size_t)(p->seg_first[(size_t)i] + l)];
+                    sgm.x = (int32_t)pos;
+                    sgm.z = (int32_t)ein;
                     const int32_t toff = p->task_off[(size_t)i];
                     for (int32_t q = f.level_ptr[(size_t)l]; q < f.level_ptr[(size_t)l + 1]; ++q) {
                         ls_node[(size_t)pos] = toff + f.ls_node[(size_t)q];
@@ -286,6 +318,8 @@ hf_status plan_build(const std::vector<hf_graph*>& graphs, Plan** out) {
                         }
                         pos++;
                     }
+                    sgm.y = (int32_t)pos;
+                    sgm.w = (int32_t)ein;
                 }
             }
             p->level_ptr[(size_t)p->levels] = (int32_t)pos;
@@ -391,9 +425,10 @@ hf_status plan_build(const std::vector<hf_graph*>& graphs, Plan** out) {
         if (p->any_key0 && (st = upload(p, &p->d_key0, key0.data(), key0.size(), s, "key0")) != HF_OK) return bail(st);
         if (p->npay && (st = upload(p, &p->d_pidx, p->hpidx.data(), p->hpidx.size(), s, "pidx")) != HF_OK)
             return bail(st);
-        if ((st = upload(p, &p->d_ls_node, ls_node.data(), ls_node.size(), s, "ls_node")) != HF_OK) return bail(st);
-        if ((st = upload(p, &p->d_ls_ptr, ls_ptr.data(), ls_ptr.size(), s, "ls_ptr")) != HF_OK) return bail(st);
-        if ((st = upload(p, &p->d_ls_in, ls_in.data(), ls_in.size(), s, "ls_in")) != HF_OK) return bail(st);
+        if ((st = upload(p, &p->d_ls_node, ls_node.data(), ls_node.size(), s, "ls_node", 64)) != HF_OK) return bail(st);
+        if ((st = upload(p, &p->d_ls_ptr, ls_ptr.data(), ls_ptr.size(), s, "ls_ptr", 64)) != HF_OK) return bail(st);
+        if ((st = upload(p, &p->d_ls_in, ls_in.data(), ls_in.size(), s, "ls_in", 64)) != HF_OK) return bail(st);
+        if ((st = upload(p, &p->d_seg, p->h_seg.data(), p->h_seg.size(), s, "seg")) != HF_OK) return bail(st);
         if ((st = upload(p, &p->d_epos_csr, epos_csr.data(), epos_csr.size(), s, "epos")) != HF_OK) return bail(st);
         if ((st = upload(p, &p->d_epos_ls, epos_ls.data(), epos_ls.size(), s, "epos")) != HF_OK) return bail(st);
         p->d_pay = (DevPayload*)palloc(p, std::max<size_t>(sizeof(DevPayload) * (size_t)p->npay, 64), s);
@@ -421,7 +456,7 @@ static hf_status plan_set_chunk(Plan* p, int64_t chunk_elems, cudaStream_t s) {
     int64_t items = 0;
     std::vector<int32_t> chunk_task;
     std::vector<int32_t> seeds, pseeds;
-    std::vector<int2> litems;
+    std::vector<int2> litems, seg_items;
     std::vector<int32_t> item_ptr((size_t)p->levels + 1, 0);
     try {
         for (int32_t k = 0; k < p->npay; ++k) {
@@ -455,6 +490,25 @@ static hf_status plan_set_chunk(Plan* p, int64_t chunk_elems, cudaStream_t s) {
             if (k < 0) seeds.push_back(t);
             else pseeds.push_back(p->n + (int32_t)items + k);
         }
+        // team executor: each (graph, level) segment's run of items (payloads are numbered
+        // graph by graph, so a level's items are grouped by graph in batch order)
+        const size_t nseg = p->h_seg.size();
+        seg_items.assign(nseg, make_int2(0, 0));
+        std::vector<int32_t> seg_cnt(nseg, 0);
+        for (int32_t k = 0; k < p->npay; ++k) {
+            const int32_t g = (int32_t)(std::upper_bound(p->task_off.begin(), p->task_off.end(), p->pay_task[(size_t)k]) -
+                                        p->task_off.begin()) - 1;
+            seg_cnt[(size_t)(p->seg_first[(size_t)g] + p->pay_level[(size_t)k])] += p->hpay[(size_t)k].nchunks;
+        }
+        for (int32_t l = 0; l < p->levels; ++l) {
+            int32_t off = item_ptr[(size_t)l];
+            for (int32_t g = 0; g < p->ngraphs; ++g) {
+                if (l >= p->glevels[(size_t)g]) continue;
+                const size_t sidx = (size_t)(p->seg_first[(size_t)g] + l);
+                seg_items[sidx] = make_int2(off, off + seg_cnt[sidx]);
+                off += seg_cnt[sidx];
+            }
+        }
     } catch (const std::bad_alloc&) {
         return fail(HF_ENOMEM, "host allocation failed");
     }
@@ -477,13 +531,16 @@ static hf_status plan_set_chunk(Plan* p, int64_t chunk_elems, cudaStream_t s) {
         !grow((void**)&p->d_pseeds, p->cap_pseeds, 4 * pseeds.size()) ||
         !grow((void**)&p->d_pqueue, p->cap_pqueue, 4 * (size_t)p->pqcap) ||
         !grow((void**)&p->d_queue, p->cap_queue, 4 * (size_t)p->qcap) ||
-        !grow((void**)&p->d_items, p->cap_items, 8 * litems.size()))
+        !grow((void**)&p->d_items, p->cap_items, 8 * litems.size()) ||
+        !grow((void**)&p->d_seg_items, p->cap_seg_items, 8 * seg_items.size()))
         return fail(HF_ENOMEM, "device allocation failed: queue");
     cudaError_t e = cudaSuccess;
     if (!chunk_task.empty()) e = cudaMemcpyAsync(p->d_chunk_task, chunk_task.data(), 4 * chunk_task.size(), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && !seeds.empty()) e = cudaMemcpyAsync(p->d_seeds, seeds.data(), 4 * seeds.size(), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && !pseeds.empty()) e = cudaMemcpyAsync(p->d_pseeds, pseeds.data(), 4 * pseeds.size(), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && !litems.empty()) e = cudaMemcpyAsync(p->d_items, litems.data(), 8 * litems.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && !seg_items.empty())
+        e = cudaMemcpyAsync(p->d_seg_items, seg_items.data(), 8 * seg_items.size(), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && p->npay) e = cudaMemcpyAsync(p->d_pay, p->hpay.data(), sizeof(DevPayload) * (size_t)p->npay, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // host vectors die at return
     if (e != cudaSuccess) return cuda_fail(e, "piece layout upload");
@@ -591,8 +648,9 @@ hf_status plan_run(Plan* p, cudaStream_t s, const hf_run_opts& o) {
             if (st != HF_OK) return st;
         }
     }
-    if (mode != HF_MODE_LEVELSYNC && mode != HF_MODE_PERSISTENT) return fail(HF_EINVAL, "unknown mode");
-    if (mode == HF_MODE_PERSISTENT && !p->host_tasks.empty())
+    if (mode != HF_MODE_LEVELSYNC && mode != HF_MODE_PERSISTENT && mode != HF_MODE_TEAM)
+        return fail(HF_EINVAL, "unknown mode");
+    if (mode != HF_MODE_LEVELSYNC && !p->host_tasks.empty())
         return fail(HF_ENOTSUP, "host tasks need the level-synchronous executor");
     if (o.priority < HF_PRIO_FIFO || o.priority > HF_PRIO_LEARNED) return fail(HF_EINVAL, "unknown priority");
     if (o.priority == HF_PRIO_LEARNED && !p->cm) return fail(HF_ESTATE, "HF_PRIO_LEARNED needs a cost model (hf_batch_set_costmodel)");
@@ -602,7 +660,7 @@ hf_status plan_run(Plan* p, cudaStream_t s, const hf_run_opts& o) {
     // 16,384 for the persistent executor (fewer queue items); in AUTO mode the caller's piece
     // size applies to the persistent executor only
     const bool own_chunk = o.chunk_elems > 0 && !(o.mode == HF_MODE_AUTO && mode == HF_MODE_LEVELSYNC);
-    int64_t chunk = own_chunk ? o.chunk_elems : (mode == HF_MODE_LEVELSYNC ? 512 : 16384);
+    int64_t chunk = own_chunk ? o.chunk_elems : (mode == HF_MODE_PERSISTENT ? 16384 : 512);
     chunk = ((chunk + 31) / 32) * 32;
     st = plan_set_chunk(p, chunk, s);
     if (st != HF_OK) return st;
@@ -617,6 +675,52 @@ hf_status plan_run(Plan* p, cudaStream_t s, const hf_run_opts& o) {
             if (o.time_kernel) cudaEventRecord(p->kev0, s);
             e = cudaGraphLaunch(p->lexec, s);
             if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+            if (o.time_kernel) cudaEventRecord(p->kev1, s);
+        } else if (mode == HF_MODE_TEAM) {
+            if (instr || valid) return fail(HF_ENOTSUP, "instrument/validate runs need the persistent executor");
+            if ((st = plan_team_jobs(p, o, s)) != HF_OK) return st;
+            TeamArgs a;
+            std::memset(&a, 0, sizeof(a));
+            a.ls_node = p->d_ls_node;
+            a.ls_ptr = p->d_ls_ptr;
+            a.ls_in = p->d_ls_in;
+            a.key0 = p->d_key0;
+            a.key = p->d_key;
+            a.pay = p->d_pay;
+            a.items = p->d_items;
+            a.seg = p->d_seg;
+            a.seg_items = p->d_seg_items;
+            a.jobs = p->d_jobs;
+            a.njobs = p->njobs;
+            a.ncjobs = p->ncjobs;
+            a.team = p->d_team;
+            a.ctrl = p->d_ctrl;
+            a.spin_limit_ns = o.spin_limit_ns ? o.spin_limit_ns : 2000000000ull;
+            e = cudaMemsetAsync(p->d_team, 0, sizeof(int32_t) * (size_t)kTeamWords, s);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+            const int K = p->team_k;
+            int cap = team_capacity(p, K);
+            if (cap <= 0) return fail(HF_ENOTSUP, "no resident cluster of the chosen size");
+            if (K == 1 && o.ctas > 0) cap = std::min(cap, o.ctas);
+            // no more CTAs than the jobs can use: a cluster job takes K, a solo job one
+            const int64_t want = (int64_t)p->ncjobs * K + (p->njobs - p->ncjobs);
+            int grid = (int)std::max<int64_t>(std::min<int64_t>(cap, want), 1);
+            grid = ((grid + K - 1) / K) * K;
+            if (grid > cap) grid = (cap / K) * K;
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3((unsigned)grid);
+            cfg.blockDim = dim3(kTeamThreads);
+            cfg.stream = s;
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = (unsigned)K;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            cfg.attrs = at;
+            cfg.numAttrs = K > 1 ? 1 : 0;
+            if (o.time_kernel) cudaEventRecord(p->kev0, s);
+            e = p->npay ? cudaLaunchKernelEx(&cfg, k_team<true>, a) : cudaLaunchKernelEx(&cfg, k_team<false>, a);
+            if (e != cudaSuccess) return cuda_fail(e, "k_team launch");
             if (o.time_kernel) cudaEventRecord(p->kev1, s);
         } else {
             ResetArgs r;
@@ -1212,6 +1316,156 @@ hf_status plan_predict(Plan* p, int32_t priority, const hf_costmodel* cm, cudaSt
     const double warps = (double)p->num_sms * std::max(occ, 1) * kWarpsPerCta;
     *ls_ms = (float)(((double)p->levels * g_t_level_ns + lsum) / 1e6);
     *p_ms = (float)((cp + (double)p->levels * g_t_hop_ns + work / warps) / 1e6);
+    return HF_OK;
+}
+
+// Team executor: predicted time of graph g on a team of k CTAs (ns),
+//   T_g(k) = sum over levels l of  t_sync(k) + t_pass * ceil(w_l / (256 k)) + P_l / (8 k),
+// w_l the level's task count, P_l the summed predicted cost (warp-ns) of its payload tasks,
+// t_sync a CTA barrier for k = 1 and a cluster barrier otherwise.
+constexpr double kTeamPassNs = 600.0, kTeamSyncSoloNs = 150.0, kTeamSyncNs = 500.0;
+constexpr int kTeamMaxCluster = 16;  // above 8 is a non-portable cluster size
+
+static double team_time(const Plan* p, const std::vector<double>& pay_ns, int32_t g, int k) {
+    double t = 0.0;
+    const int32_t s0 = p->seg_first[(size_t)g];
+    for (int32_t l = 0; l < p->glevels[(size_t)g]; ++l) {
+        const int4& sg = p->h_seg[(size_t)(s0 + l)];
+        const int64_t w = sg.y - sg.x;
+        t += (k == 1 ? kTeamSyncSoloNs : kTeamSyncNs) + kTeamPassNs * (double)((w + 256LL * k - 1) / (256LL * k)) +
+             pay_ns[(size_t)(s0 + l)] / (8.0 * k);
+    }
+    return t;
+}
+
+// CTAs of cluster size k resident at once (k = 1: plain occupancy).
+static int team_capacity(const Plan* p, int k) {
+    const void* fn = p->npay ? (const void*)k_team<true> : (const void*)k_team<false>;
+    if (k == 1) {
+        int occ = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kTeamThreads, 0);
+        return p->num_sms * std::max(occ, 1);
+    }
+    if (k > 8) {
+        cudaFuncSetAttribute(k_team<true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        cudaFuncSetAttribute(k_team<false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)k);
+    cfg.blockDim = dim3(kTeamThreads);
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)k;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int nc = 0;
+    if (cudaOccupancyMaxActiveClusters(&nc, fn, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return nc * k;
+}
+
+// Job list: the cluster size K and the number m of cluster jobs minimise the predicted makespan
+//   M(K, m) = max( max over the m longest graphs of T_g(K),  T of the (m+1)-th longest solo,
+//                  total solo work / CTAs ),
+// over K in {1, 2, 4, 8, 16} (m at most the clusters resident at once). Jobs are in decreasing
+// predicted time. FIFO: one CTA per graph in batch order. team_size k > 0: every graph is a
+// cluster job of min(k, 16) CTAs.
+static hf_status plan_team_jobs(Plan* p, const hf_run_opts& o, cudaStream_t s) {
+    const int32_t prio = o.priority;
+    if (p->team_for[0] == prio && p->team_for[1] == o.team_size && p->team_for[2] == o.ctas &&
+        (prio != HF_PRIO_LEARNED || p->team_cm == p->cm))
+        return HF_OK;
+    const int32_t G = p->ngraphs;
+    std::vector<int32_t> order;
+    for (int32_t g = 0; g < G; ++g)
+        if (p->glevels[(size_t)g] > 0) order.push_back(g);
+    int K = 1, m = 0;
+    if (prio != HF_PRIO_FIFO) {
+        std::vector<double> pay_ns(p->h_seg.size(), 0.0);
+        if (p->npay) {
+            float* c = (float*)dev_alloc(sizeof(float) * (size_t)p->n, s);
+            float* b = (float*)dev_alloc(sizeof(float) * (size_t)p->n, s);
+            hf_status st = (!c || !b) ? fail(HF_ENOMEM, "device allocation failed: team costs")
+                                      : plan_task_costs(p, prio, p->cm, c, b, s);
+            std::vector<float> hc;
+            if (st == HF_OK) {
+                hc.resize((size_t)p->n);
+                cudaError_t e = cudaMemcpy(hc.data(), c, sizeof(float) * (size_t)p->n, cudaMemcpyDeviceToHost);
+                if (e != cudaSuccess) st = cuda_fail(e, "team cost download");
+            }
+            dev_free(c, s);
+            dev_free(b, s);
+            if (st != HF_OK) return st;
+            for (int32_t q = 0; q < p->npay; ++q) {
+                const int32_t t = p->pay_task[(size_t)q];
+                const int32_t g = (int32_t)(std::upper_bound(p->task_off.begin(), p->task_off.end(), t) -
+                                            p->task_off.begin()) - 1;
+                pay_ns[(size_t)(p->seg_first[(size_t)g] + p->pay_level[(size_t)q])] += hc[(size_t)t];
+            }
+        }
+        std::vector<double> T1((size_t)G, 0.0);
+        double work = 0.0;
+        for (int32_t g : order) {
+            T1[(size_t)g] = team_time(p, pay_ns, g, 1);
+            work += T1[(size_t)g];
+        }
+        std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return T1[(size_t)x] > T1[(size_t)y]; });
+        const int n = (int)order.size();
+        double best = 0.0;
+        for (int k : {1, 2, 4, 8, 16}) {
+            const int cap = team_capacity(p, k);
+            if (cap <= 0) continue;
+            if (o.ctas > 0 && o.ctas < cap) continue;  // a caller's CTA cap applies to solo runs only
+            const int mmax = k == 1 ? 0 : std::min(n, cap / k);
+            double pref = 0.0, solo_work = work;
+            for (int mm = 0; mm <= mmax; ++mm) {
+                if (mm > 0) {
+                    const int32_t g = order[(size_t)mm - 1];
+                    pref = std::max(pref, team_time(p, pay_ns, g, k));
+                    solo_work -= T1[(size_t)g];
+                }
+                const double next = mm < n ? T1[(size_t)order[(size_t)mm]] : 0.0;
+                const double M = std::max({pref, next, solo_work / (double)cap});
+                if ((k == 1 && mm == 0) || M < best) {
+                    best = M;
+                    K = k;
+                    m = mm;
+                }
+            }
+        }
+    }
+    if (o.team_size > 0) {
+        K = std::min(o.team_size, kTeamMaxCluster);
+        m = K > 1 ? (int)order.size() : 0;
+    }
+    std::vector<TeamJob> jobs;
+    for (int32_t g : order) jobs.push_back(TeamJob{g, 0, p->seg_first[(size_t)g], p->glevels[(size_t)g]});
+    const size_t bytes = std::max<size_t>(sizeof(TeamJob) * jobs.size(), 16);
+    if (p->cap_jobs < bytes) {
+        free_owned(p, p->d_jobs);
+        p->d_jobs = (TeamJob*)palloc(p, bytes, s);
+        p->cap_jobs = p->d_jobs ? bytes : 0;
+        if (!p->d_jobs) return fail(HF_ENOMEM, "device allocation failed: team jobs");
+    }
+    if (!p->d_team) {
+        p->d_team = (int32_t*)palloc(p, sizeof(int32_t) * (size_t)kTeamWords, s);
+        if (!p->d_team) return fail(HF_ENOMEM, "device allocation failed: team control");
+    }
+    cudaError_t e = cudaSuccess;
+    if (!jobs.empty()) e = cudaMemcpyAsync(p->d_jobs, jobs.data(), sizeof(TeamJob) * jobs.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "team job upload");
+    p->njobs = (int32_t)jobs.size();
+    p->ncjobs = m;
+    p->team_k = K;
+    p->team_for[0] = prio;
+    p->team_for[1] = o.team_size;
+    p->team_for[2] = o.ctas;
+    p->team_cm = p->cm;
     return HF_OK;
 }
 

@@ -1,0 +1,388 @@
+// team.cuh -- the team executor for batches of independent graphs (sm_103a).
+//
+// One persistent launch runs a batch. Each graph is one job, run level by level in the pull
+// form of the level-synchronous executor with a barrier between levels instead of a kernel
+// boundary. A solo job belongs to one CTA and ends each level with a CTA barrier; a cluster job
+// belongs to the CTAs of one thread-block cluster, which split each level among themselves and
+// end it with the hardware cluster barrier. Independent graphs never wait for one another, so
+// a batch costs its longest graph's chain of levels, not the sum over merged levels.
+//
+// Latency hiding. A level's critical path should be one gather of the predecessors' arrival
+// keys. Everything that does not depend on the previous level is fetched ahead:
+//   * segment descriptors (positions and in-edge range of each level) three levels ahead, in
+//     registers;
+//   * every CTA stages the task list, row starts and in-edges of the next two levels in shared
+//     memory with TMA bulk copies (three buffers, completion on mbarriers); segments too large
+//     to stage are prefetched into L2 with bulk prefetches two levels ahead;
+//   * each warp prefetches into L2 the x and y ranges of the payload pieces it will run in the
+//     next level.
+#pragma once
+
+#include "kernels.cuh"
+
+namespace hf {
+
+constexpr int kTeamThreads = 256;
+constexpr int kTeamBufs = 3;       // staged levels: the current one and two ahead
+constexpr int kTeamStageN = 384;   // tasks per staged level
+constexpr int kTeamStageE = 1280;  // in-edges per staged level
+
+struct __align__(16) TeamStage {
+    int32_t node[kTeamStageN + 8];  // copied from a 16-byte aligned start: up to 3 extra in front
+    int32_t ptr[kTeamStageN + 12];  // row starts p0..p1 (one more than node)
+    int2 in[kTeamStageE + 2];
+};
+static_assert(sizeof(TeamStage::node) % 16 == 0 && sizeof(TeamStage::ptr) % 16 == 0 &&
+                  sizeof(TeamStage::in) % 16 == 0, "bulk-copy destinations must be 16-byte multiples");
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(bar);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(s), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, unsigned bytes) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(bar);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(s), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(bar);
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(s), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// TMA bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16)
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    const unsigned b = (unsigned)__cvta_generic_to_shared(bar);
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(d),
+                 "l"(src), "r"(bytes), "r"(b)
+                 : "memory");
+}
+
+// L2 bulk prefetch of the whole 16-byte blocks inside [p, p + bytes)
+__device__ __forceinline__ void prefetch_l2_range(const void* p, int64_t bytes) {
+    uint64_t a0 = ((uint64_t)p + 15) & ~15ull;
+    const uint64_t a1 = ((uint64_t)p + (uint64_t)bytes) & ~15ull;
+    while (a1 > a0) {
+        const unsigned b = (unsigned)(a1 - a0 < 65536 ? a1 - a0 : 65536);
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a0), "r"(b) : "memory");
+        a0 += b;
+    }
+}
+
+__device__ __forceinline__ bool team_fits(const int4 sg) {
+    return sg.y > sg.x && sg.y - sg.x <= kTeamStageN && sg.w - sg.z <= kTeamStageE;
+}
+
+// Issued by one thread: stage segment sg (positions [x, y), in-edges [z, w)) into st. The
+// level-sorted arrays are allocated with slack so that rounding the ends up to 16 bytes stays
+// inside them.
+__device__ __forceinline__ void team_stage(const TeamArgs& a, TeamStage& st, unsigned long long* bar, const int4 sg) {
+    const int a0 = sg.x & ~3, a1 = (sg.y + 3) & ~3, b1 = (sg.y + 4) & ~3;
+    const int c0 = sg.z & ~1, c1 = (sg.w + 1) & ~1;
+    const unsigned bn = (unsigned)(a1 - a0) * 4u, bp = (unsigned)(b1 - a0) * 4u, bi = (unsigned)(c1 - c0) * 8u;
+    mbar_arrive_expect_tx(bar, bn + bp + bi);
+    bulk_g2s(st.node, a.ls_node + a0, bn, bar);
+    bulk_g2s(st.ptr, a.ls_ptr + a0, bp, bar);
+    if (bi) bulk_g2s(st.in, a.ls_in + c0, bi, bar);
+}
+
+__device__ __forceinline__ void team_prefetch_seg(const TeamArgs& a, const int4 sg) {
+    if (sg.y <= sg.x) return;
+    prefetch_l2_range(a.ls_node + sg.x, 4ll * (sg.y - sg.x));
+    prefetch_l2_range(a.ls_ptr + sg.x, 4ll * (sg.y - sg.x + 1));
+    prefetch_l2_range(a.ls_in + sg.z, 8ll * (sg.w - sg.z));
+}
+
+// look-ahead for one level, by thread 0 of each CTA: stage it if it fits, else (CTA 0 of the
+// team) prefetch it into L2
+__device__ __forceinline__ void team_ahead(const TeamArgs& a, int rank, TeamStage& st, unsigned long long* bar,
+                                           const int4 sg) {
+    if (team_fits(sg)) team_stage(a, st, bar, sg);
+    else if (rank == 0) team_prefetch_seg(a, sg);
+}
+
+// One payload piece, resolved: pointers already offset to the piece, cnt in elements (saxpy)
+// or bytes (copy).
+struct TeamPiece {
+    char* dst;
+    const char* src;
+    int32_t cnt;
+    uint32_t a;
+    uint32_t op;  // 0: none
+};
+
+__device__ __forceinline__ TeamPiece team_piece_desc(const TeamArgs& a, int it) {
+    const int2 w = __ldg(a.items + it);
+    const DevPayload& P = a.pay[w.x];
+    const int64_t b0 = (int64_t)w.y * P.chunk;
+    const int64_t b1 = b0 + P.chunk < P.n ? b0 + P.chunk : P.n;
+    const int64_t sc = P.op == kPayCopy ? 1 : 4;
+    TeamPiece d;
+    d.dst = (char*)P.dst + sc * b0;
+    d.src = (const char*)P.src + sc * b0;
+    d.cnt = (int32_t)(b1 > b0 ? b1 - b0 : 0);
+    d.a = P.a_bits;
+    d.op = P.op;
+    return d;
+}
+
+// Warps of a team that compute a level's arrivals: one task per thread, and the other warps
+// run the level's payload pieces at the same time, when the level has payload and the arrival
+// warps leave some spare; otherwise every warp does arrivals, then pieces (returns nwarp).
+__device__ __forceinline__ int team_arrival_warps(const int4 sg, const int2 si, int nwarp) {
+    const int na = (sg.y - sg.x + 31) >> 5;
+    return (si.y > si.x && na < nwarp) ? na : nwarp;
+}
+
+// Descriptors of the pieces this warp runs in a level (payload warps [pw0, nwarp) take items
+// si.x + (wid - pw0) + j * (nwarp - pw0); lane j holds the j-th, the first 32 only) and an L2
+// prefetch of their x and y ranges. Copies touch host memory and are not prefetched.
+__device__ __forceinline__ TeamPiece team_prefetch_items(const TeamArgs& a, const int2 si, int wid, int pw0, int nwarp,
+                                                         int lane) {
+    TeamPiece d;
+    d.op = 0;
+    const int it = si.x + (wid - pw0) + lane * (nwarp - pw0);
+    if (wid >= pw0 && it < si.y) {
+        d = team_piece_desc(a, it);
+        if (d.op != kPayCopy && d.cnt > 0) {
+            prefetch_l2_range(d.src, 4ll * d.cnt);
+            prefetch_l2_range(d.dst, 4ll * d.cnt);
+        }
+    }
+    return d;
+}
+
+__device__ __forceinline__ TeamPiece shfl_piece(const TeamPiece& d, int j) {
+    TeamPiece r;
+    r.dst = (char*)__shfl_sync(kFull, (unsigned long long)d.dst, j);
+    r.src = (const char*)__shfl_sync(kFull, (unsigned long long)d.src, j);
+    r.cnt = __shfl_sync(kFull, d.cnt, j);
+    r.a = __shfl_sync(kFull, d.a, j);
+    r.op = __shfl_sync(kFull, d.op, j);
+    return r;
+}
+
+// One piece by one warp (a 512-element FP32 piece is one round trip of 16-byte loads).
+__device__ __forceinline__ void team_run_piece(const TeamPiece& d, int lane) {
+    if (d.op == kPaySaxpyF32)
+        warp_saxpy_f32(reinterpret_cast<float*>(d.dst), reinterpret_cast<const float*>(d.src), d.cnt,
+                       __uint_as_float(d.a), lane);
+    else if (d.op == kPaySaxpyI32)
+        warp_saxpy_i32(reinterpret_cast<int32_t*>(d.dst), reinterpret_cast<const int32_t*>(d.src), d.cnt, d.a, lane);
+    else if (d.op == kPayCopy)
+        warp_copy(d.dst, d.src, d.cnt, lane);
+}
+
+// ---------------------------------------------------------------- thread-block cluster helpers
+
+__device__ __forceinline__ unsigned cluster_rank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ unsigned cluster_size() {
+    unsigned n;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(n));
+    return n;
+}
+
+// every thread of every CTA of the cluster; release/acquire at cluster scope
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// store a job into CTA `rank`'s copy of the shared variable `local`
+__device__ __forceinline__ void st_cluster_job(TeamJob* local, unsigned rank, const TeamJob j) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(local);
+    unsigned d;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(d) : "r"(s), "r"(rank));
+    asm volatile("st.shared::cluster.v4.s32 [%0], {%1, %2, %3, %4};" ::"r"(d), "r"(j.graph), "r"(j.pad_), "r"(j.seg0),
+                 "r"(j.levels)
+                 : "memory");
+}
+
+// ---------------------------------------------------------------- one level
+
+// Predecessors' keys were written by this CTA (solo job: ordinary loads, L1 may hold them) or
+// by another CTA of the cluster (loads from L2, after the cluster barrier's acquire).
+template <bool SOLO>
+__device__ __forceinline__ uint32_t team_pred_key(const TeamArgs& a, int u) {
+    if (SOLO) return a.key[u];
+    return __ldcg(a.key + u);
+}
+
+// max over in-edges [e0, e1) of key(arr[u] + d): all key loads of a batch of up to 8 in-edges
+// are issued before the first is used, so a task's gather costs one round trip
+template <bool SOLO>
+__device__ __forceinline__ uint32_t team_fold(const TeamArgs& a, const int2* in, int e0, int e1) {
+    uint32_t best = 0u;
+    for (int e = e0; e < e1; e += 8) {
+        const int cnt = e1 - e < 8 ? e1 - e : 8;
+        int2 ie[8];
+        uint32_t kk[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if (j < cnt) ie[j] = in[e + j];
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if (j < cnt) kk[j] = team_pred_key<SOLO>(a, ie[j].x);
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if (j < cnt) best = max(best, f2key(__fadd_rn(key2f(kk[j]), __int_as_float(ie[j].y))));
+    }
+    return best;
+}
+
+template <bool SOLO>
+__device__ __forceinline__ uint32_t team_task_key(const TeamArgs& a, int v, const int2* in, int e0, int e1) {
+    if (e0 == e1) return a.key0 ? __ldg(a.key0 + v) : kKeyPosZero;
+    return team_fold<SOLO>(a, in, e0, e1);
+}
+
+// ---------------------------------------------------------------- one graph
+
+// Runs job `job` on a team of k CTAs (this one is `rank`; SOLO: k = 1): level by level, staged
+// levels from shared memory, the rest from global memory (prefetched into L2), payload pieces
+// spread over the team's warps, then the team barrier (CTA barrier for a solo job, cluster
+// barrier otherwise). Returns false if a staged copy never landed (the kernel must end).
+template <bool PAY, bool SOLO>
+__device__ __forceinline__ bool team_run_graph(const TeamArgs& a, const TeamJob& job, int k, int rank,
+                                               TeamStage* st, unsigned long long* mbar, int4* ring, int2* iring,
+                                               unsigned& phase) {
+    const int t = threadIdx.x;
+    const int lane = t & 31;
+    const int nthr = k * kTeamThreads, tid = rank * kTeamThreads + t;
+    const int wid = tid >> 5, nwarp = nthr >> 5;
+    const int L = job.levels;
+    // segment descriptors and item ranges ride a ring in shared memory, written by thread 0
+    // three (items: two) levels ahead; level l uses stage buffer l % kTeamBufs
+    if (t == 0) {
+        for (int q = 0; q < 3 && q < L; ++q) ring[q] = __ldg(a.seg + job.seg0 + q);
+        if (PAY)
+            for (int q = 0; q < 2 && q < L; ++q) iring[q] = __ldg(a.seg_items + job.seg0 + q);
+        if (L > 0) team_ahead(a, rank, st[0], &mbar[0], ring[0]);
+        if (L > 1) team_ahead(a, rank, st[1], &mbar[1], ring[1]);
+    }
+    __syncthreads();
+    TeamPiece pc, pn;  // this warp's piece descriptors for the current and the next level
+    pc.op = pn.op = 0;
+    if (PAY) {
+        const int na = team_arrival_warps(ring[0], iring[0], nwarp);
+        pc = team_prefetch_items(a, iring[0], wid, na < nwarp ? na : 0, nwarp, lane);
+    }
+    for (int l = 0; l < L; ++l) {
+        const int b = l % kTeamBufs;
+        const int4 s0 = ring[l & 3];
+        if (t == 0) {
+            if (l + 3 < L) ring[(l + 3) & 3] = __ldg(a.seg + job.seg0 + l + 3);
+            if (PAY && l + 2 < L) iring[(l + 2) & 3] = __ldg(a.seg_items + job.seg0 + l + 2);
+            if (l + 2 < L) team_ahead(a, rank, st[(l + 2) % kTeamBufs], &mbar[(l + 2) % kTeamBufs], ring[(l + 2) & 3]);
+        }
+        if (PAY && l + 1 < L) {
+            const int na1 = team_arrival_warps(ring[(l + 1) & 3], iring[(l + 1) & 3], nwarp);
+            pn = team_prefetch_items(a, iring[(l + 1) & 3], wid, na1 < nwarp ? na1 : 0, nwarp, lane);
+        }
+        const int2 i0 = PAY ? iring[l & 3] : make_int2(0, 0);
+        const int na = PAY ? team_arrival_warps(s0, i0, nwarp) : nwarp;
+        const int pw0 = na < nwarp ? na : 0;  // first payload warp
+        // arrivals of level l (every CTA of a team stages the whole level and takes its share)
+        const int32_t* node = a.ls_node;
+        const int32_t* ptr = a.ls_ptr;
+        const int2* in = a.ls_in;
+        if (team_fits(s0)) {
+            uint64_t t0 = 0;
+            while (!mbar_try_wait(&mbar[b], (phase >> b) & 1u)) {
+                const uint64_t now = gtimer();
+                if (!t0) {
+                    t0 = now;
+                } else if (now - t0 > a.spin_limit_ns) {  // a bulk copy that never lands
+                    if (t == 0) atomicCAS(&a.ctrl->status, 0, (int)HF_ETIMEDOUT);
+                    return false;
+                }
+            }
+            phase ^= 1u << b;
+            const int nb = s0.x & ~3, eb = s0.z & ~1;
+            node = st[b].node - nb;  // indexed by level-sorted position / in-edge number
+            ptr = st[b].ptr - nb;
+            in = st[b].in - eb;
+        }
+        if (wid < na) {
+            for (int p = s0.x + tid; p < s0.y; p += na * 32) {
+                const int v = node[p];
+                a.key[v] = team_task_key<SOLO>(a, v, in, ptr[p], ptr[p + 1]);
+            }
+        }
+        // payload pieces of level l
+        if (PAY && wid >= pw0) {
+            int j = 0;
+            for (int it = i0.x + (wid - pw0); it < i0.y; it += nwarp - pw0, ++j)
+                team_run_piece(j < 32 ? shfl_piece(pc, j) : team_piece_desc(a, it), lane);
+        }
+        if (SOLO) __syncthreads();
+        else cluster_sync();
+        pc = pn;
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------- the kernel
+
+// Phase 1 (cluster launches with cluster jobs): CTA 0 of each cluster takes the next cluster
+// job and hands it to every CTA of its cluster through distributed shared memory; the cluster
+// runs it as one team. Phase 2: every CTA takes solo jobs until none is left.
+template <bool PAY>
+__global__ void __launch_bounds__(kTeamThreads, PAY ? 2 : 3) k_team(const TeamArgs a) {
+    __shared__ TeamStage st[kTeamBufs];
+    __shared__ __align__(8) unsigned long long mbar[kTeamBufs];
+    __shared__ __align__(16) TeamJob s_job;
+    __shared__ int4 s_ring[4];
+    __shared__ int2 s_iring[4];
+    const int t = threadIdx.x;
+    if (t == 0) {
+        for (int b = 0; b < kTeamBufs; ++b) mbar_init(&mbar[b], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    unsigned phase = 0;  // bit b: parity of buffer b's next completion
+    const int k = (int)cluster_size();
+    if (k > 1 && a.ncjobs > 0) {
+        const int rank = (int)cluster_rank();
+        cluster_sync();  // every CTA of the cluster has started before any DSMEM store
+        for (;;) {
+            if (rank == 0 && t == 0) {
+                const int j = atomicAdd(a.team + kTeamNextC, 1);
+                const TeamJob job = j < a.ncjobs ? a.jobs[j] : TeamJob{-1, 0, 0, 0};
+                for (int r = 0; r < k; ++r) st_cluster_job(&s_job, (unsigned)r, job);
+            }
+            cluster_sync();
+            const TeamJob job = s_job;
+            cluster_sync();  // all have read s_job before CTA 0 may overwrite it
+            if (job.graph < 0) break;
+            if (!team_run_graph<PAY, false>(a, job, k, rank, st, mbar, s_ring, s_iring, phase)) return;
+        }
+    }
+    for (;;) {
+        if (t == 0) {
+            const int j = a.ncjobs + atomicAdd(a.team + kTeamNext, 1);
+            s_job = j < a.njobs ? a.jobs[j] : TeamJob{-1, 0, 0, 0};
+        }
+        __syncthreads();
+        const TeamJob job = s_job;
+        __syncthreads();
+        if (job.graph < 0) break;
+        if (!team_run_graph<PAY, true>(a, job, 1, 0, st, mbar, s_ring, s_iring, phase)) return;
+    }
+}
+
+}  // namespace hf

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libhf.so")
 HF_OK, HF_EINVAL, HF_ENOMEM, HF_ECYCLE, HF_ESTATE, HF_ETIMEDOUT, HF_EQUEUE, HF_ECUDA, HF_ENOTSUP = range(9)
 HF_HOST, HF_PULL, HF_PUSH, HF_KERNEL = 0, 1, 2, 3
 HF_K_MAXPLUS, HF_K_SAXPY_F32, HF_K_SAXPY_I32 = 0, 1, 2
-HF_MODE_LEVELSYNC, HF_MODE_PERSISTENT, HF_MODE_AUTO = 0, 1, 2
+HF_MODE_LEVELSYNC, HF_MODE_PERSISTENT, HF_MODE_AUTO, HF_MODE_TEAM = 0, 1, 2, 3
 HF_PRIO_FIFO, HF_PRIO_HEURISTIC, HF_PRIO_LEARNED = 0, 1, 2
 
 STATUS_NAMES = {0: "HF_OK", 1: "HF_EINVAL", 2: "HF_ENOMEM", 3: "HF_ECYCLE", 4: "HF_ESTATE", 5: "HF_ETIMEDOUT",
@@ -64,7 +64,7 @@ class hf_run_opts(ctypes.Structure):
                 ("chunk_elems", ctypes.c_int64), ("spin_limit_ns", ctypes.c_uint64),
                 ("instrument", ctypes.c_int32), ("validate", ctypes.c_int32),
                 ("stall_task", ctypes.c_int32), ("time_kernel", ctypes.c_int32),
-                ("payload_warps", ctypes.c_int32), ("pad_", ctypes.c_int32)]
+                ("payload_warps", ctypes.c_int32), ("team_size", ctypes.c_int32)]
 
 
 class hf_graph_info_t(ctypes.Structure):

@@ -31,6 +31,10 @@ EXECUTORS = {
     "persistent_wide": dict(mode=hf.HF_MODE_PERSISTENT, ctas=148 * 8, claim=4),
     "persistent_payw2": dict(mode=hf.HF_MODE_PERSISTENT, payload_warps=2, claim=8, local_keep=8),
     "persistent_payw7": dict(mode=hf.HF_MODE_PERSISTENT, payload_warps=7, ctas=16),
+    "team": dict(mode=hf.HF_MODE_TEAM),
+    "team_heur": dict(mode=hf.HF_MODE_TEAM, priority=hf.HF_PRIO_HEURISTIC),
+    "team_k2": dict(mode=hf.HF_MODE_TEAM, team_size=2),
+    "team_k5": dict(mode=hf.HF_MODE_TEAM, team_size=5, ctas=12),
 }
 
 
@@ -65,7 +69,7 @@ def test_layered10k_bit_exact(ex):
     gd.close()
 
 
-@pytest.mark.parametrize("ex", ["levelsync", "persistent", "persistent_claim8"])
+@pytest.mark.parametrize("ex", ["levelsync", "persistent", "persistent_claim8", "team", "team_k5"])
 def test_random_graphs_100_seeds(ex):
     rng = np.random.default_rng(5)
     for seed in range(100):
@@ -98,7 +102,7 @@ def test_validate_exactly_once_and_order():
     gd.close()
 
 
-@pytest.mark.parametrize("ex", ["levelsync", "persistent", "persistent_claim8"])
+@pytest.mark.parametrize("ex", ["levelsync", "persistent", "persistent_claim8", "team_heur", "team_k5"])
 def test_circuit1m_full_size(ex):
     spec = S.config("circuit1m").graphs[0]
     ref = oracle.run_spec(spec)["arr"]
@@ -118,7 +122,8 @@ def _check_payloads(gd, ref):
 
 
 @pytest.mark.parametrize("chunk", [0, 64, 4096])
-@pytest.mark.parametrize("ex", ["levelsync", "persistent", "persistent_claim8", "persistent_payw2", "persistent_payw7"])
+@pytest.mark.parametrize("ex", ["levelsync", "persistent", "persistent_claim8", "persistent_payw2", "persistent_payw7",
+                                "team", "team_k2", "team_k5"])
 def test_mixed_small_with_payloads(ex, chunk):
     spec = S.mixed(3, n=6000, nmin=1, nmax=20000, n_copy=300)
     ref = oracle.run_spec(spec)
@@ -135,7 +140,7 @@ def test_mixed100k_full_size_sampled():
     gd = GraphOnDevice(spec)
     rng = np.random.default_rng(0)
     sample = rng.choice(spec.sx_task.size, 64, replace=False)
-    for ex in ["levelsync", "persistent"]:
+    for ex in ["levelsync", "persistent", "team_heur"]:
         gd.reset_y()
         arr = _run(gd, **EXECUTORS[ex])
         np.testing.assert_array_equal(bits(arr), bits(ref["arr"]))
@@ -150,7 +155,7 @@ def test_mixed100k_full_size_sampled():
     gd.close()
 
 
-@pytest.mark.parametrize("ex", ["levelsync", "persistent"])
+@pytest.mark.parametrize("ex", ["levelsync", "persistent", "team", "team_heur"])
 def test_batch256_full_size(ex):
     wl = S.config("batch256")
     bd = BatchOnDevice(wl)
@@ -162,7 +167,7 @@ def test_batch256_full_size(ex):
     bd.close()
 
 
-@pytest.mark.parametrize("ex", ["levelsync", "persistent", "persistent_payw2"])
+@pytest.mark.parametrize("ex", ["levelsync", "persistent", "persistent_payw2", "team", "team_heur", "team_k2"])
 def test_batch_mixed_small(ex):
     wl = S.batch(2, graphs=12, nmin=500, nmax=20000, frac_saxpy=0.1, sx_min=1, sx_max=3000)
     bd = BatchOnDevice(wl)
@@ -272,7 +277,7 @@ def test_paper_dependency_graph_order():
 
 # ------------------------------------------------------------------ edge cases
 
-@pytest.mark.parametrize("ex", ["levelsync", "persistent"])
+@pytest.mark.parametrize("ex", ["levelsync", "persistent", "team", "team_k5"])
 def test_edge_cases(ex):
     o = EXECUTORS[ex]
     # empty graph
@@ -332,7 +337,7 @@ def test_stalled_task_times_out_and_context_survives():
     gd.close()
 
 
-@pytest.mark.parametrize("ex", ["levelsync", "persistent"])
+@pytest.mark.parametrize("ex", ["levelsync", "persistent", "team_heur"])
 def test_new_timing_view_through_set_delays(ex):
     """A second timing view of the same circuit: new delays in place, arrivals as the oracle
     computes them on the new delays; a non-finite delay is reported, then recovered from."""
