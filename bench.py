@@ -284,23 +284,25 @@ def main():
         prio = hf.HF_PRIO_LEARNED
         learned = {"train_mse_log": loss, "train_s": t_tr, "held_out_error": err}
 
-    base = hf.hf_run_opts_default(priority=prio)
-    tuned_ms = None
-    if not args.no_tune:
-        best, tuned_ms = hf.hf_batch_autotune(bd.b, stream, base)
-    else:
-        best = base
-    ls_pred = pe_pred = None
-    if args.executor == "auto":
-        ls_pred, pe_pred = hf.hf_batch_predict(bd.b, prio, stream)
-    head = {k: v for k, v in hf.opts_dict(best).items() if k not in ("time_kernel", "instrument", "validate")}
+    # executor: the cost model's choice (the library's HF_MODE_AUTO rule), or forced
+    ls_pred = pe_pred = tm_pred = None
     forced = {"auto": hf.HF_MODE_AUTO, "persistent": hf.HF_MODE_PERSISTENT, "levelsync": hf.HF_MODE_LEVELSYNC,
               "team": hf.HF_MODE_TEAM}
-    head.update(mode=forced[args.executor], priority=prio)
     if args.executor == "auto":
+        ls_pred, pe_pred, tm_pred = hf.hf_batch_predict(bd.b, prio, stream)
         chosen = hf.HF_MODE_PERSISTENT if pe_pred <= ls_pred else hf.HF_MODE_LEVELSYNC
+        if tm_pred < min(ls_pred, pe_pred):
+            chosen = hf.HF_MODE_TEAM
     else:
         chosen = forced[args.executor]
+    # launch parameters: autotuned for the executor that runs
+    base = hf.hf_run_opts_default(priority=prio, mode=chosen)
+    tuned_ms = None
+    best = base
+    if not args.no_tune and chosen in (hf.HF_MODE_PERSISTENT, hf.HF_MODE_TEAM):
+        best, tuned_ms = hf.hf_batch_autotune(bd.b, stream, base)
+    head = {k: v for k, v in hf.opts_dict(best).items() if k not in ("time_kernel", "instrument", "validate")}
+    head.update(mode=forced[args.executor], priority=prio)
     bd.reset_y()
     t_setup = time.time() - t_setup
 
@@ -340,13 +342,15 @@ def main():
     compare = {}
     if not args.no_compare:
         k = max(5, args.steps // 4)
-        for name, o in (("levelsync", dict(mode=hf.HF_MODE_LEVELSYNC)),
-                        ("persistent_fifo_default", dict(mode=hf.HF_MODE_PERSISTENT, priority=hf.HF_PRIO_FIFO)),
-                        ("persistent_fifo_tuned", dict(head, mode=hf.HF_MODE_PERSISTENT, priority=hf.HF_PRIO_FIFO)),
-                        ("persistent_heuristic_tuned", dict(head, mode=hf.HF_MODE_PERSISTENT,
-                                                            priority=hf.HF_PRIO_HEURISTIC)),
-                        ("team_fifo", dict(mode=hf.HF_MODE_TEAM, priority=hf.HF_PRIO_FIFO)),
-                        ("team_heuristic", dict(mode=hf.HF_MODE_TEAM, priority=hf.HF_PRIO_HEURISTIC))):
+        arms = [("levelsync", dict(mode=hf.HF_MODE_LEVELSYNC)),
+                ("persistent_fifo", dict(mode=hf.HF_MODE_PERSISTENT, priority=hf.HF_PRIO_FIFO)),
+                ("persistent_heuristic", dict(mode=hf.HF_MODE_PERSISTENT, priority=hf.HF_PRIO_HEURISTIC)),
+                ("team_fifo", dict(mode=hf.HF_MODE_TEAM, priority=hf.HF_PRIO_FIFO)),
+                ("team_heuristic", dict(mode=hf.HF_MODE_TEAM, priority=hf.HF_PRIO_HEURISTIC))]
+        if cm is not None:
+            arms += [("persistent_learned", dict(mode=hf.HF_MODE_PERSISTENT, priority=hf.HF_PRIO_LEARNED)),
+                     ("team_learned", dict(mode=hf.HF_MODE_TEAM, priority=hf.HF_PRIO_LEARNED))]
+        for name, o in arms:
             c_ms, c_med, c_st, _ = timed(o, k, 3)
             compare[name] = {"ms_per_step": c_ms, "ms_median": c_med, "tasks_per_s": N / (c_ms / 1e3),
                              "edges_per_s": E / (c_ms / 1e3), "status": hf.hf_status_string(c_st)}
@@ -396,7 +400,8 @@ def main():
                    "chosen": {hf.HF_MODE_PERSISTENT: "persistent", hf.HF_MODE_TEAM: "team"}.get(chosen, "levelsync"),
                    "priority": {0: "fifo", 1: "heuristic", 2: "learned"}[prio],
                    "launch": {k: head[k] for k in ("ctas", "claim", "local_keep", "chunk_elems")},
-                   "autotuned_ms": tuned_ms, "predicted_ms": {"levelsync": ls_pred, "persistent": pe_pred},
+                   "autotuned_ms": tuned_ms,
+                   "predicted_ms": {"levelsync": ls_pred, "persistent": pe_pred, "team": tm_pred},
                    "l2": "inputs larger than L2 (graph %.0f MB + payload %.0f MB)" % (
                        (16 * E + 24 * N) / 1e6, 8 * wl.saxpy_elems / 1e6),
                    "setup_s": t_setup},

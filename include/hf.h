@@ -309,24 +309,31 @@ hf_status hf_batch_bottom_levels(hf_batch* b, const float* cost, float* bottom, 
 
 /* --- autotuning and executor choice ----------------------------------------------------- */
 
-/* Times trial runs of the persistent executor on this batch (coordinate descent over CTA
- * count, queue claim size, shared-memory stack depth and payload piece size; each trial the
- * median of 3 timed runs after one warm-up) and writes the fastest options to *best (mode
- * PERSISTENT, other fields from `base`, NULL = defaults) and its time to *best_ms. Results are
- * cached per size bucket (tasks, edges per task, payload share, depth), so a later call on a
- * similar batch returns without trials unless `force`. Runs the batch many times: payloads run
- * each time (saxpy updates y). Blocks. */
+/* Times trial runs on this batch and writes the fastest options to *best (other fields from
+ * `base`, NULL = defaults) and its time to *best_ms; each trial the median of 3 timed runs
+ * after one warm-up. base->mode HF_MODE_TEAM tunes the team executor (coordinate descent over
+ * the cluster size for every graph, 0 = the cost model's plan, and the payload piece size);
+ * any other mode tunes the persistent executor (CTA count, queue claim size, shared-memory
+ * stack depth, payload piece size, payload warps; mode PERSISTENT in *best). Results are
+ * cached per executor and size bucket (tasks, edges per task, payload share, depth, batch or
+ * single graph), so a later call on a similar batch returns without trials unless `force`.
+ * Runs the batch many times: payloads run each time (saxpy updates y). Blocks. */
 hf_status hf_batch_autotune(hf_batch* b, void* stream, const hf_run_opts* base, int force, hf_run_opts* best,
                             float* best_ms);
 
 /* Predicted makespans (ms) of the batch under each executor, from per-task costs of the given
- * priority source (HEURISTIC or LEARNED) and two machine constants measured once per process
- * on calibration graphs (level-synchronous time per level, persistent time per hop):
+ * priority source (HEURISTIC or LEARNED) and machine constants measured once per process on a
+ * calibration chain (level-synchronous time per level, persistent time per hop, team time per
+ * level for one CTA and for a cluster):
  *   level-sync  = levels * t_level + sum over levels of the largest task cost in the level
  *   persistent  = critical path of costs + depth * t_hop + total cost / warps
- * HF_MODE_AUTO runs the executor with the smaller prediction (LEARNED costs when a model is
+ *   team        = the team executor's planned makespan: per graph and cluster size k,
+ *                 T(k) = sum over levels of t_lvl(k) * ceil(width / 256k) + payload cost / 8k,
+ *                 the longest graphs on clusters, the rest on single CTAs (+inf with host tasks)
+ * HF_MODE_AUTO runs the executor with the smallest prediction (LEARNED costs when a model is
  * attached, else HEURISTIC). */
-hf_status hf_batch_predict(hf_batch* b, int32_t priority, void* stream, float* levelsync_ms, float* persistent_ms);
+hf_status hf_batch_predict(hf_batch* b, int32_t priority, void* stream, float* levelsync_ms, float* persistent_ms,
+                           float* team_ms);
 
 /* --- allocation-free entry point -------------------------------------------------------
  * The paper has no counterpart to this call; it exists for callers that cannot allocate

@@ -108,10 +108,10 @@ def init_params(seed=0):
 
 def heuristic_cost(F):
     """The plain heuristic task cost (ns of warp time) the learned model is judged against:
-    300 per task + 30 per out-edge + payload bytes / 25 (bytes per ns one warp moves).
+    300 per task + 30 per out-edge + payload bytes / 8 (bytes per ns one warp moves).
     Computed from the features' fan-out and payload-bytes entries."""
     F = np.asarray(F, np.float64)
-    return 300.0 + 30.0 * np.expm1(F[:, 5]) + np.expm1(F[:, 8]) / 25.0
+    return 300.0 + 30.0 * np.expm1(F[:, 5]) + np.expm1(F[:, 8]) / 8.0
 
 
 # --------------------------------------------------------------------- per-task features

@@ -630,11 +630,12 @@ hf_status hf_batch_autotune(hf_batch* b, void* stream, const hf_run_opts* base, 
     return plan_autotune(b->plan, (cudaStream_t)stream, o, force, best, best_ms);
 }
 
-hf_status hf_batch_predict(hf_batch* b, int32_t priority, void* stream, float* levelsync_ms, float* persistent_ms) {
-    if (!b || !levelsync_ms || !persistent_ms) return fail(HF_EINVAL, "NULL argument");
+hf_status hf_batch_predict(hf_batch* b, int32_t priority, void* stream, float* levelsync_ms, float* persistent_ms,
+                           float* team_ms) {
+    if (!b || !levelsync_ms || !persistent_ms || !team_ms) return fail(HF_EINVAL, "NULL argument");
     hf_status st = ensure_batch_plan(b);
     if (st != HF_OK) return st;
-    return plan_predict(b->plan, priority, b->cm, (cudaStream_t)stream, levelsync_ms, persistent_ms);
+    return plan_predict(b->plan, priority, b->cm, (cudaStream_t)stream, levelsync_ms, persistent_ms, team_ms);
 }
 
 hf_status hf_batch_bottom_levels(hf_batch* b, const float* cost, float* bottom, void* stream) {

@@ -286,7 +286,7 @@ hf_status plan_bottom_levels(Plan* p, const float* cost, float* bottom, cudaStre
 hf_status plan_autotune(Plan* p, cudaStream_t s, const hf_run_opts& base, int force, hf_run_opts* best,
                         float* best_ms);
 hf_status plan_predict(Plan* p, int32_t priority, const hf_costmodel* cm, cudaStream_t s, float* ls_ms,
-                       float* p_ms);
+                       float* p_ms, float* t_ms);
 
 // costmodel.cu
 hf_status mlp_forward(const float* params, const float* X, int64_t n, float* y, cudaStream_t s);

@@ -136,6 +136,8 @@ hf_status plan_auto_mode(Plan* p, cudaStream_t s, int* mode);
 static hf_status plan_set_chunk(Plan* p, int64_t chunk_elems, cudaStream_t s);
 static hf_status plan_team_jobs(Plan* p, const hf_run_opts& o, cudaStream_t s);
 static int team_capacity(const Plan* p, int k);
+static hf_status team_decide(Plan* p, int32_t prio, int32_t ctas_opt, cudaStream_t s, int* K_out, int* m_out,
+                             std::vector<int32_t>* order_out, double* M_out);
 hf_status plan_prepare_priority(Plan* p, int32_t priority, const hf_costmodel* cm, cudaStream_t s);
 
 void plan_set_costmodel(Plan* p, const hf_costmodel* cm) {
@@ -966,8 +968,9 @@ __global__ void k_features(int n, const int2* __restrict__ meta, const int4* __r
 
 // Plain heuristic cost (ns of warp time), the fallback the learned model is judged against:
 // a fixed cost per task, one atomic round trip per out-edge, payload bytes at the bandwidth
-// one warp sustains. Constants are first-principles estimates, not fitted.
-constexpr float kHeurTask = 300.f, kHeurEdge = 30.f, kHeurBytesPerNs = 25.f;
+// one warp sustains (one 512-element saxpy block, 6 KB, per ~0.75 us round trip). Constants
+// are first-principles estimates, not fitted.
+constexpr float kHeurTask = 300.f, kHeurEdge = 30.f, kHeurBytesPerNs = 8.f;
 
 __global__ void k_costs(int n, const float* __restrict__ X, const float* __restrict__ y, float* __restrict__ c) {
     const int stride = gridDim.x * blockDim.x;
@@ -1154,7 +1157,7 @@ static hf_status time_runs(Plan* p, cudaStream_t s, const hf_run_opts& o, int re
     return HF_OK;
 }
 
-using TuneKey = std::tuple<int, int, int, int>;
+using TuneKey = std::tuple<int, int, int, int, int>;
 static std::mutex g_tune_mu;
 static std::map<TuneKey, std::pair<hf_run_opts, float>> g_tune_cache;
 
@@ -1163,26 +1166,73 @@ static TuneKey tune_key(const Plan* p) {
     const int epn = p->n > 0 ? (int)std::lround(10.0 * (double)p->m / (double)p->n) : 0;
     const int payq = p->n > 0 ? (int)std::lround(20.0 * (double)p->npay / (double)p->n) : 0;
     const int logd = p->levels > 0 ? (int)std::floor(std::log2((double)p->levels)) : 0;
-    return TuneKey(logn, epn, payq, logd);
+    return TuneKey(logn, epn, payq, logd, p->ngraphs > 1 ? 1 : 0);
+}
+
+// Team executor: coordinate descent over the cluster size for every graph (0: the cost model's
+// plan) and the payload piece size; each trial the median of 3 timed runs.
+static hf_status autotune_team(Plan* p, cudaStream_t s, const hf_run_opts& base, hf_run_opts* best, float* best_ms) {
+    hf_run_opts cur = base;
+    cur.mode = HF_MODE_TEAM;
+    cur.instrument = cur.validate = cur.time_kernel = 0;
+    cur.stall_task = -1;
+    cur.team_size = 0;
+    if (cur.chunk_elems <= 0) cur.chunk_elems = 512;
+    float best_t = 0.f;
+    hf_status st = time_runs(p, s, cur, 3, &best_t);
+    if (st != HF_OK) return st;
+    const std::vector<int> size_v{0, 1, 2, 4, 8, 16};
+    const std::vector<int64_t> chunk_v{256, 512, 1024, 2048};
+    for (int round = 0; round < 2; ++round) {
+        for (int dim = 0; dim < 2; ++dim) {
+            if (dim == 1 && p->npay == 0) continue;
+            const size_t nv = dim == 0 ? size_v.size() : chunk_v.size();
+            for (size_t i = 0; i < nv; ++i) {
+                hf_run_opts t = cur;
+                if (dim == 0) t.team_size = size_v[i];
+                else t.chunk_elems = chunk_v[i];
+                if (t.team_size == cur.team_size && t.chunk_elems == cur.chunk_elems) continue;
+                float ms = 0.f;
+                if ((st = time_runs(p, s, t, 3, &ms)) != HF_OK) return st;
+                if (ms < best_t) {
+                    best_t = ms;
+                    cur = t;
+                }
+            }
+        }
+    }
+    *best = cur;
+    *best_ms = best_t;
+    return HF_OK;
 }
 
 hf_status plan_autotune(Plan* p, cudaStream_t s, const hf_run_opts& base, int force, hf_run_opts* best,
                         float* best_ms) {
-    const TuneKey key = tune_key(p);
+    const bool team = base.mode == HF_MODE_TEAM;
+    TuneKey key = tune_key(p);
+    std::get<4>(key) += team ? 2 : 0;
     if (!force) {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) {
             *best = base;
-            best->mode = HF_MODE_PERSISTENT;
+            best->mode = team ? HF_MODE_TEAM : HF_MODE_PERSISTENT;
             best->ctas = it->second.first.ctas;
             best->claim = it->second.first.claim;
             best->local_keep = it->second.first.local_keep;
             best->chunk_elems = it->second.first.chunk_elems;
             best->payload_warps = it->second.first.payload_warps;
+            best->team_size = it->second.first.team_size;
             *best_ms = it->second.second;
             return HF_OK;
         }
+    }
+    if (team) {
+        hf_status st = autotune_team(p, s, base, best, best_ms);
+        if (st != HF_OK) return st;
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[key] = std::make_pair(*best, *best_ms);
+        return HF_OK;
     }
     hf_run_opts cur = base;
     cur.mode = HF_MODE_PERSISTENT;
@@ -1235,11 +1285,11 @@ hf_status plan_autotune(Plan* p, cudaStream_t s, const hf_run_opts& base, int fo
 // ------------------------------------------------------------------ executor choice
 
 // Machine constants for the makespan predictions, measured once per process on a chain of
-// tasks: the level-synchronous executor's time per level and the persistent executor's time
-// per dependent hop.
+// tasks: the level-synchronous executor's time per level, the persistent executor's time per
+// dependent hop, and the team executor's time per level for a solo CTA and for a cluster.
 static std::mutex g_cal_mu;
 static bool g_cal_done = false;
-static float g_t_level_ns = 0.f, g_t_hop_ns = 0.f;
+static float g_t_level_ns = 0.f, g_t_hop_ns = 0.f, g_t_team_solo_ns = 0.f, g_t_team_cluster_ns = 0.f;
 
 static hf_status calibrate(cudaStream_t s) {
     std::lock_guard<std::mutex> lk(g_cal_mu);
@@ -1256,7 +1306,7 @@ static hf_status calibrate(cudaStream_t s) {
         std::vector<hf_graph*> one{g};
         st = plan_build(one, &p);
     }
-    float tl = 0.f, tp = 0.f;
+    float tl = 0.f, tp = 0.f, ts = 0.f, tc = 0.f;
     if (st == HF_OK) {
         hf_run_opts o;
         hf_run_opts_default(&o);
@@ -1265,21 +1315,30 @@ static hf_status calibrate(cudaStream_t s) {
         o.mode = HF_MODE_PERSISTENT;
         o.ctas = p->num_sms;
         if (st == HF_OK) st = time_runs(p, s, o, 3, &tp);
+        hf_run_opts_default(&o);
+        o.mode = HF_MODE_TEAM;
+        o.team_size = 1;
+        if (st == HF_OK) st = time_runs(p, s, o, 3, &ts);
+        o.team_size = 2;
+        if (st == HF_OK) st = time_runs(p, s, o, 3, &tc);
     }
     if (p) plan_destroy(p);
     hf_graph_destroy(g);
     if (st != HF_OK) return st;
     g_t_level_ns = 1e6f * tl / (float)n;
     g_t_hop_ns = 1e6f * tp / (float)n;
+    g_t_team_solo_ns = 1e6f * ts / (float)n;
+    g_t_team_cluster_ns = 1e6f * tc / (float)n;
     g_cal_done = true;
     return HF_OK;
 }
 
-hf_status plan_predict(Plan* p, int32_t priority, const hf_costmodel* cm, cudaStream_t s, float* ls_ms, float* p_ms) {
+hf_status plan_predict(Plan* p, int32_t priority, const hf_costmodel* cm, cudaStream_t s, float* ls_ms, float* p_ms,
+                       float* t_ms) {
     hf_status st = calibrate(s);
     if (st != HF_OK) return st;
     if (p->n == 0) {
-        *ls_ms = *p_ms = 0.f;
+        *ls_ms = *p_ms = *t_ms = 0.f;
         return HF_OK;
     }
     float* c = (float*)dev_alloc(sizeof(float) * (size_t)p->n, s);
@@ -1316,24 +1375,36 @@ hf_status plan_predict(Plan* p, int32_t priority, const hf_costmodel* cm, cudaSt
     const double warps = (double)p->num_sms * std::max(occ, 1) * kWarpsPerCta;
     *ls_ms = (float)(((double)p->levels * g_t_level_ns + lsum) / 1e6);
     *p_ms = (float)((cp + (double)p->levels * g_t_hop_ns + work / warps) / 1e6);
+    // team executor: its own plan under the same cost source (host tasks: not available)
+    *t_ms = INFINITY;
+    if (p->host_tasks.empty()) {
+        std::vector<int32_t> order;
+        int K = 1, m = 0;
+        double M = 0.0;
+        const hf_costmodel* keep = p->cm;
+        p->cm = cm;
+        st = team_decide(p, priority, 0, s, &K, &m, &order, &M);
+        p->cm = keep;
+        if (st != HF_OK) return st;
+        *t_ms = (float)(M / 1e6);
+    }
     return HF_OK;
 }
 
 // Team executor: predicted time of graph g on a team of k CTAs (ns),
-//   T_g(k) = sum over levels l of  t_sync(k) + t_pass * ceil(w_l / (256 k)) + P_l / (8 k),
+//   T_g(k) = sum over levels l of  t_lvl(k) * ceil(w_l / (256 k)) + P_l / (8 k),
 // w_l the level's task count, P_l the summed predicted cost (warp-ns) of its payload tasks,
-// t_sync a CTA barrier for k = 1 and a cluster barrier otherwise.
-constexpr double kTeamPassNs = 600.0, kTeamSyncSoloNs = 150.0, kTeamSyncNs = 500.0;
+// t_lvl the measured time of a one-task level (CTA barrier for k = 1, cluster barrier else).
 constexpr int kTeamMaxCluster = 16;  // above 8 is a non-portable cluster size
 
 static double team_time(const Plan* p, const std::vector<double>& pay_ns, int32_t g, int k) {
     double t = 0.0;
+    const double tl = k == 1 ? g_t_team_solo_ns : g_t_team_cluster_ns;
     const int32_t s0 = p->seg_first[(size_t)g];
     for (int32_t l = 0; l < p->glevels[(size_t)g]; ++l) {
         const int4& sg = p->h_seg[(size_t)(s0 + l)];
         const int64_t w = sg.y - sg.x;
-        t += (k == 1 ? kTeamSyncSoloNs : kTeamSyncNs) + kTeamPassNs * (double)((w + 256LL * k - 1) / (256LL * k)) +
-             pay_ns[(size_t)(s0 + l)] / (8.0 * k);
+        t += tl * (double)((w + 256LL * k - 1) / (256LL * k)) + pay_ns[(size_t)(s0 + l)] / (8.0 * k);
     }
     return t;
 }
@@ -1368,29 +1439,30 @@ static int team_capacity(const Plan* p, int k) {
     return nc * k;
 }
 
-// Job list: the cluster size K and the number m of cluster jobs minimise the predicted makespan
+// Team plan under a cost source: the cluster size K and the number m of cluster jobs minimise
+// the predicted makespan
 //   M(K, m) = max( max over the m longest graphs of T_g(K),  T of the (m+1)-th longest solo,
 //                  total solo work / CTAs ),
-// over K in {1, 2, 4, 8, 16} (m at most the clusters resident at once). Jobs are in decreasing
-// predicted time. FIFO: one CTA per graph in batch order. team_size k > 0: every graph is a
-// cluster job of min(k, 16) CTAs.
-static hf_status plan_team_jobs(Plan* p, const hf_run_opts& o, cudaStream_t s) {
-    const int32_t prio = o.priority;
-    if (p->team_for[0] == prio && p->team_for[1] == o.team_size && p->team_for[2] == o.ctas &&
-        (prio != HF_PRIO_LEARNED || p->team_cm == p->cm))
-        return HF_OK;
+// over K in {1, 2, 4, 8, 16} (m at most the clusters resident at once); `order` lists the
+// graphs in decreasing predicted time. FIFO: one CTA per graph in batch order, M = 0.
+static hf_status team_decide(Plan* p, int32_t prio, int32_t ctas_opt, cudaStream_t s, int* K_out, int* m_out,
+                             std::vector<int32_t>* order_out, double* M_out) {
     const int32_t G = p->ngraphs;
-    std::vector<int32_t> order;
+    std::vector<int32_t>& order = *order_out;
+    order.clear();
     for (int32_t g = 0; g < G; ++g)
         if (p->glevels[(size_t)g] > 0) order.push_back(g);
     int K = 1, m = 0;
+    double best = 0.0;
     if (prio != HF_PRIO_FIFO) {
+        hf_status st = calibrate(s);
+        if (st != HF_OK) return st;
         std::vector<double> pay_ns(p->h_seg.size(), 0.0);
         if (p->npay) {
             float* c = (float*)dev_alloc(sizeof(float) * (size_t)p->n, s);
             float* b = (float*)dev_alloc(sizeof(float) * (size_t)p->n, s);
-            hf_status st = (!c || !b) ? fail(HF_ENOMEM, "device allocation failed: team costs")
-                                      : plan_task_costs(p, prio, p->cm, c, b, s);
+            st = (!c || !b) ? fail(HF_ENOMEM, "device allocation failed: team costs")
+                            : plan_task_costs(p, prio, p->cm, c, b, s);
             std::vector<float> hc;
             if (st == HF_OK) {
                 hc.resize((size_t)p->n);
@@ -1415,11 +1487,12 @@ static hf_status plan_team_jobs(Plan* p, const hf_run_opts& o, cudaStream_t s) {
         }
         std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return T1[(size_t)x] > T1[(size_t)y]; });
         const int n = (int)order.size();
-        double best = 0.0;
+        bool have = false;
         for (int k : {1, 2, 4, 8, 16}) {
-            const int cap = team_capacity(p, k);
+            int cap = team_capacity(p, k);
             if (cap <= 0) continue;
-            if (o.ctas > 0 && o.ctas < cap) continue;  // a caller's CTA cap applies to solo runs only
+            if (k == 1 && ctas_opt > 0) cap = std::min(cap, ctas_opt);  // a caller's CTA cap (solo runs)
+            else if (k > 1 && ctas_opt > 0) continue;
             const int mmax = k == 1 ? 0 : std::min(n, cap / k);
             double pref = 0.0, solo_work = work;
             for (int mm = 0; mm <= mmax; ++mm) {
@@ -1430,7 +1503,8 @@ static hf_status plan_team_jobs(Plan* p, const hf_run_opts& o, cudaStream_t s) {
                 }
                 const double next = mm < n ? T1[(size_t)order[(size_t)mm]] : 0.0;
                 const double M = std::max({pref, next, solo_work / (double)cap});
-                if ((k == 1 && mm == 0) || M < best) {
+                if (!have || M < best) {
+                    have = true;
                     best = M;
                     K = k;
                     m = mm;
@@ -1438,6 +1512,24 @@ static hf_status plan_team_jobs(Plan* p, const hf_run_opts& o, cudaStream_t s) {
             }
         }
     }
+    *K_out = K;
+    *m_out = m;
+    *M_out = best;
+    return HF_OK;
+}
+
+// Job list for a run: team_decide's plan, or with team_size k > 0 every graph a cluster job of
+// min(k, 16) CTAs (in the plan's order).
+static hf_status plan_team_jobs(Plan* p, const hf_run_opts& o, cudaStream_t s) {
+    const int32_t prio = o.priority;
+    if (p->team_for[0] == prio && p->team_for[1] == o.team_size && p->team_for[2] == o.ctas &&
+        (prio != HF_PRIO_LEARNED || p->team_cm == p->cm))
+        return HF_OK;
+    std::vector<int32_t> order;
+    int K = 1, m = 0;
+    double M = 0.0;
+    hf_status st = team_decide(p, o.team_size > 0 ? HF_PRIO_FIFO : prio, o.ctas, s, &K, &m, &order, &M);
+    if (st != HF_OK) return st;
     if (o.team_size > 0) {
         K = std::min(o.team_size, kTeamMaxCluster);
         m = K > 1 ? (int)order.size() : 0;
@@ -1474,10 +1566,11 @@ hf_status plan_auto_mode(Plan* p, cudaStream_t s, int* mode) {
         *mode = p->auto_mode;
         return HF_OK;
     }
-    float ls = 0.f, pe = 0.f;
-    hf_status st = plan_predict(p, p->cm ? HF_PRIO_LEARNED : HF_PRIO_HEURISTIC, p->cm, s, &ls, &pe);
+    float ls = 0.f, pe = 0.f, tm = 0.f;
+    hf_status st = plan_predict(p, p->cm ? HF_PRIO_LEARNED : HF_PRIO_HEURISTIC, p->cm, s, &ls, &pe, &tm);
     if (st != HF_OK) return st;
     p->auto_mode = pe <= ls ? HF_MODE_PERSISTENT : HF_MODE_LEVELSYNC;
+    if (tm < std::min(ls, pe)) p->auto_mode = HF_MODE_TEAM;
     p->auto_cm = p->cm;
     *mode = p->auto_mode;
     return HF_OK;

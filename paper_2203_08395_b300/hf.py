@@ -137,7 +137,7 @@ def load():
         "hf_batch_bottom_levels": [vp, vp, vp, vp],
         "hf_batch_autotune": [vp, vp, P(hf_run_opts), ctypes.c_int, P(hf_run_opts), P(ctypes.c_float)],
         "hf_batch_get_stats": [vp, vp, i32],
-        "hf_batch_predict": [vp, i32, vp, P(ctypes.c_float), P(ctypes.c_float)],
+        "hf_batch_predict": [vp, i32, vp, P(ctypes.c_float), P(ctypes.c_float), P(ctypes.c_float)],
         "hf_run_csr_noalloc": [i32, i32, vp, vp, vp, vp, vp, ctypes.c_uint64, vp],
     }
     for name, args in sig.items():
@@ -475,11 +475,11 @@ def hf_batch_autotune(b, stream=None, base=None, force=False):
 
 
 def hf_batch_predict(b, priority, stream=None):
-    """Returns (predicted level-sync ms, predicted persistent ms)."""
-    ls, pe = ctypes.c_float(), ctypes.c_float()
-    _check(load().hf_batch_predict(b, priority, _stream_handle(stream), ctypes.byref(ls), ctypes.byref(pe)),
-           "hf_batch_predict")
-    return ls.value, pe.value
+    """Returns predicted (level-sync ms, persistent ms, team ms)."""
+    ls, pe, tm = ctypes.c_float(), ctypes.c_float(), ctypes.c_float()
+    _check(load().hf_batch_predict(b, priority, _stream_handle(stream), ctypes.byref(ls), ctypes.byref(pe),
+                                   ctypes.byref(tm)), "hf_batch_predict")
+    return ls.value, pe.value, tm.value
 
 
 STAT_NAMES = ["rounds", "items", "idle", "edges", "cas", "push_local", "push_global", "claims", "pops", "pieces",

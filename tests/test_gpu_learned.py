@@ -51,8 +51,8 @@ def test_autotune_choice_is_exact_and_cached():
 
 def test_auto_mode_predicts_and_runs_exactly():
     bd = BatchOnDevice(S.batch(10, graphs=12, nmin=1000, nmax=20000))
-    ls, pe = hf.hf_batch_predict(bd.b, hf.HF_PRIO_HEURISTIC)
-    assert ls > 0 and pe > 0
+    ls, pe, tm = hf.hf_batch_predict(bd.b, hf.HF_PRIO_HEURISTIC)
+    assert ls > 0 and pe > 0 and tm > 0
     bd.run(mode=hf.HF_MODE_AUTO)
     bd.sync()
     _check(bd)

@@ -101,7 +101,7 @@ def test_adam_matches_torch():
 def test_heuristic_cost_by_hand():
     F = np.zeros((2, 12))
     F[0, 5], F[0, 8] = np.log1p(3), np.log1p(1200)  # fan-out 3, 1200 payload bytes
-    np.testing.assert_allclose(mlp.heuristic_cost(F), [300 + 90 + 48, 300.0])
+    np.testing.assert_allclose(mlp.heuristic_cost(F), [300 + 90 + 150, 300.0])
 
 
 def test_features_on_paper_saxpy_graph():
