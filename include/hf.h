@@ -124,8 +124,10 @@ typedef struct {
                                applies only when the persistent executor is chosen */
     uint64_t spin_limit_ns; /* persistent: give up (HF_ETIMEDOUT) after this long without any
                                task completing; 0 = 2 s */
-    int32_t instrument;     /* bit 0: record per-task %globaltimer start/end (hf_get_task_times);
-                               bit 1: record persistent-executor counters (hf_batch_get_stats) */
+    int32_t instrument;     /* bit 0: record per-task %globaltimer start/end (hf_get_task_times;
+                               persistent executor) or per-graph start/end (team executor,
+                               hf_batch_get_graph_times); bit 1: record persistent-executor
+                               counters (hf_batch_get_stats) */
     int32_t validate;       /* record per-task start/finish tickets and execution counts */
     int32_t stall_task;     /* failure-injection hook for tests: -1 = off; else this task's
                                pending-predecessor counter starts one too high, so it never
@@ -242,6 +244,14 @@ hf_status hf_batch_kernel_ms(hf_batch* b, float* ms);
  * kept in warp stacks, items pushed to / claims on / items popped from the global queue,
  * payload pieces run. Diagnostics only. */
 hf_status hf_batch_get_stats(hf_batch* b, int64_t* out, int32_t n);
+/* Per-graph %globaltimer start and end (ns; host arrays of the batch's graph count) of the last
+ * team-executor run with instrument bit 0: when the graph's job started and when its last
+ * level ended. */
+hf_status hf_batch_get_graph_times(hf_batch* b, int64_t* start_ns, int64_t* end_ns);
+/* Kernels the last run launched (executor kernels; copies and memsets not counted): one per
+ * level for the level-synchronous executor, 2 for the persistent one (reset + executor), one
+ * per team class for the team executor. */
+hf_status hf_batch_last_launches(hf_batch* b, int32_t* n);
 /* As hf_set_delays for every graph of the batch: delay holds the graphs' edge delays
  * concatenated in batch order (sum of their edge counts). */
 hf_status hf_batch_set_delays(hf_batch* b, const float* delay, int on_device, void* stream);

@@ -683,6 +683,18 @@ hf_status hf_batch_get_stats(hf_batch* b, int64_t* out, int32_t n) {
     return plan_get_stats(b->plan, out, n);
 }
 
+hf_status hf_batch_get_graph_times(hf_batch* b, int64_t* start, int64_t* end) {
+    if (!b || !start || !end) return fail(HF_EINVAL, "NULL argument");
+    if (!b->plan) return fail(HF_ESTATE, "batch has not run");
+    return plan_get_graph_times(b->plan, start, end);
+}
+
+hf_status hf_batch_last_launches(hf_batch* b, int32_t* n) {
+    if (!b || !n) return fail(HF_EINVAL, "NULL argument");
+    if (!b->plan) return fail(HF_ESTATE, "batch has not run");
+    return plan_last_launches(b->plan, n);
+}
+
 hf_status hf_batch_kernel_ms(hf_batch* b, float* ms) {
     if (!b || !ms) return fail(HF_EINVAL, "NULL argument");
     if (!b->plan) return fail(HF_ESTATE, "batch has not run");

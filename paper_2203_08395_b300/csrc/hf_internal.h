@@ -172,6 +172,8 @@ struct TeamArgs {
     int32_t* team;           // control words (kTeam*)
     Ctrl* ctrl;              // status word (HF_ETIMEDOUT when a staged copy never lands)
     uint64_t spin_limit_ns;
+    int64_t* g_start;        // instrument: %globaltimer per graph at job start / end (else NULL)
+    int64_t* g_end;
 };
 
 // Arguments of one level kernel of the level-synchronous executor.
@@ -276,6 +278,8 @@ hf_status plan_get_times(Plan* p, int32_t gi, int64_t* a, int64_t* b);
 hf_status plan_get_stamps(Plan* p, int32_t gi, int64_t* a, int64_t* b, int32_t* c);
 hf_status plan_kernel_ms(Plan* p, float* ms);
 hf_status plan_get_stats(Plan* p, int64_t* out, int32_t n);
+hf_status plan_get_graph_times(Plan* p, int64_t* start, int64_t* end);
+hf_status plan_last_launches(Plan* p, int32_t* n);
 hf_status plan_set_delays(Plan* p, const float* delay, int on_device, cudaStream_t s);
 hf_status plan_features(Plan* p, float* X, cudaStream_t s);
 hf_status plan_task_costs(Plan* p, int32_t priority, const hf_costmodel* cm, float* cost, float* bottom,

@@ -54,9 +54,17 @@ struct Plan {
     TeamJob* d_jobs = nullptr;
     size_t cap_jobs = 0;
     int32_t njobs = 0;
-    int32_t ncjobs = 0;               // cluster jobs (the first ncjobs of the list)
-    int32_t team_k = 1;               // cluster size of the launch
-    int32_t* d_team = nullptr;        // control words (job counters)
+    struct TeamClass {
+        int32_t k;      // cluster size of the class's launch (1: single CTAs)
+        int32_t job0;   // its jobs in d_jobs
+        int32_t njobs;
+        int32_t grid;   // CTAs launched
+    };
+    std::vector<TeamClass> tclass;    // one launch per class, run concurrently
+    cudaStream_t tstream[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t tev_fork = nullptr;
+    cudaEvent_t tev_join[4] = {nullptr, nullptr, nullptr, nullptr};
+    int32_t* d_team = nullptr;        // control words (job counters), kTeamWords per class
     int32_t team_for[3] = {-1, -1, -1};  // priority, team_size, CTAs the job list was built for
     const hf_costmodel* team_cm = nullptr;
 
@@ -98,6 +106,9 @@ struct Plan {
     int64_t* d_tk_end = nullptr;
     int32_t* d_exec = nullptr;
     unsigned long long* d_stats = nullptr;  // executor counters (instrument & 2)
+    int64_t* d_gtime = nullptr;             // team executor: per-graph start, then end (instrument & 1)
+    int32_t last_launches = 0;              // executor kernels of the last run
+    bool last_gtimes = false;
     bool last_stats = false;
     bool last_instrument = false, last_validate = false;
     // level-sync CUDA graph
@@ -136,7 +147,7 @@ hf_status plan_auto_mode(Plan* p, cudaStream_t s, int* mode);
 static hf_status plan_set_chunk(Plan* p, int64_t chunk_elems, cudaStream_t s);
 static hf_status plan_team_jobs(Plan* p, const hf_run_opts& o, cudaStream_t s);
 static int team_capacity(const Plan* p, int k);
-static hf_status team_decide(Plan* p, int32_t prio, int32_t ctas_opt, cudaStream_t s, int* K_out, int* m_out,
+static hf_status team_decide(Plan* p, int32_t prio, int32_t ctas_opt, cudaStream_t s, std::vector<int>* k_out,
                              std::vector<int32_t>* order_out, double* M_out);
 hf_status plan_prepare_priority(Plan* p, int32_t priority, const hf_costmodel* cm, cudaStream_t s);
 
@@ -199,6 +210,11 @@ void plan_destroy(Plan* p) {
     if (p->done_ev) cudaEventDestroy(p->done_ev);
     if (p->kev0) cudaEventDestroy(p->kev0);
     if (p->kev1) cudaEventDestroy(p->kev1);
+    for (int i = 0; i < 4; ++i) {
+        if (p->tstream[i]) cudaStreamDestroy(p->tstream[i]);
+        if (p->tev_join[i]) cudaEventDestroy(p->tev_join[i]);
+    }
+    if (p->tev_fork) cudaEventDestroy(p->tev_fork);
     delete p;
 }
 
@@ -679,7 +695,7 @@ hf_status plan_run(Plan* p, cudaStream_t s, const hf_run_opts& o) {
             if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
             if (o.time_kernel) cudaEventRecord(p->kev1, s);
         } else if (mode == HF_MODE_TEAM) {
-            if (instr || valid) return fail(HF_ENOTSUP, "instrument/validate runs need the persistent executor");
+            if (valid) return fail(HF_ENOTSUP, "validate runs need the persistent executor");
             if ((st = plan_team_jobs(p, o, s)) != HF_OK) return st;
             TeamArgs a;
             std::memset(&a, 0, sizeof(a));
@@ -692,37 +708,55 @@ hf_status plan_run(Plan* p, cudaStream_t s, const hf_run_opts& o) {
             a.items = p->d_items;
             a.seg = p->d_seg;
             a.seg_items = p->d_seg_items;
-            a.jobs = p->d_jobs;
-            a.njobs = p->njobs;
-            a.ncjobs = p->ncjobs;
-            a.team = p->d_team;
             a.ctrl = p->d_ctrl;
             a.spin_limit_ns = o.spin_limit_ns ? o.spin_limit_ns : 2000000000ull;
-            e = cudaMemsetAsync(p->d_team, 0, sizeof(int32_t) * (size_t)kTeamWords, s);
+            if (instr) {
+                if (!p->d_gtime) {
+                    p->d_gtime = (int64_t*)palloc(p, sizeof(int64_t) * 2 * std::max<size_t>((size_t)p->ngraphs, 1), s);
+                    if (!p->d_gtime) return fail(HF_ENOMEM, "device allocation failed: graph timers");
+                }
+                a.g_start = p->d_gtime;
+                a.g_end = p->d_gtime + p->ngraphs;
+            }
+            p->last_gtimes = instr;
+            e = cudaMemsetAsync(p->d_team, 0, sizeof(int32_t) * (size_t)kTeamWords * p->tclass.size(), s);
             if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
-            const int K = p->team_k;
-            int cap = team_capacity(p, K);
-            if (cap <= 0) return fail(HF_ENOTSUP, "no resident cluster of the chosen size");
-            if (K == 1 && o.ctas > 0) cap = std::min(cap, o.ctas);
-            // no more CTAs than the jobs can use: a cluster job takes K, a solo job one
-            const int64_t want = (int64_t)p->ncjobs * K + (p->njobs - p->ncjobs);
-            int grid = (int)std::max<int64_t>(std::min<int64_t>(cap, want), 1);
-            grid = ((grid + K - 1) / K) * K;
-            if (grid > cap) grid = (cap / K) * K;
-            cudaLaunchConfig_t cfg = {};
-            cfg.gridDim = dim3((unsigned)grid);
-            cfg.blockDim = dim3(kTeamThreads);
-            cfg.stream = s;
-            cudaLaunchAttribute at[1];
-            at[0].id = cudaLaunchAttributeClusterDimension;
-            at[0].val.clusterDim.x = (unsigned)K;
-            at[0].val.clusterDim.y = 1;
-            at[0].val.clusterDim.z = 1;
-            cfg.attrs = at;
-            cfg.numAttrs = K > 1 ? 1 : 0;
             if (o.time_kernel) cudaEventRecord(p->kev0, s);
-            e = p->npay ? cudaLaunchKernelEx(&cfg, k_team<true>, a) : cudaLaunchKernelEx(&cfg, k_team<false>, a);
-            if (e != cudaSuccess) return cuda_fail(e, "k_team launch");
+            // one launch per team class, all at once: the first on the caller's stream, the
+            // others on the plan's streams forked from it and joined back
+            const size_t nc = p->tclass.size();
+            if (nc > 1) {
+                if ((e = cudaEventRecord(p->tev_fork, s)) != cudaSuccess) return cuda_fail(e, "team fork");
+                for (size_t i = 1; i < nc; ++i)
+                    if ((e = cudaStreamWaitEvent(p->tstream[i - 1], p->tev_fork, 0)) != cudaSuccess)
+                        return cuda_fail(e, "team fork");
+            }
+            for (size_t i = 0; i < nc; ++i) {
+                const Plan::TeamClass& c = p->tclass[i];
+                TeamArgs ai = a;
+                ai.jobs = p->d_jobs + c.job0;
+                ai.njobs = c.njobs;
+                ai.ncjobs = c.k > 1 ? c.njobs : 0;
+                ai.team = p->d_team + (size_t)kTeamWords * i;
+                cudaLaunchConfig_t cfg = {};
+                cfg.gridDim = dim3((unsigned)c.grid);
+                cfg.blockDim = dim3(kTeamThreads);
+                            cfg.stream = i == 0 ? s : p->tstream[i - 1];
+                cudaLaunchAttribute at[1];
+                at[0].id = cudaLaunchAttributeClusterDimension;
+                at[0].val.clusterDim.x = (unsigned)c.k;
+                at[0].val.clusterDim.y = 1;
+                at[0].val.clusterDim.z = 1;
+                cfg.attrs = at;
+                cfg.numAttrs = c.k > 1 ? 1 : 0;
+                e = p->npay ? cudaLaunchKernelEx(&cfg, k_team<true>, ai) : cudaLaunchKernelEx(&cfg, k_team<false>, ai);
+                if (e != cudaSuccess) return cuda_fail(e, "k_team launch");
+            }
+            for (size_t i = 1; i < nc; ++i) {
+                if ((e = cudaEventRecord(p->tev_join[i - 1], p->tstream[i - 1])) != cudaSuccess ||
+                    (e = cudaStreamWaitEvent(s, p->tev_join[i - 1], 0)) != cudaSuccess)
+                    return cuda_fail(e, "team join");
+            }
             if (o.time_kernel) cudaEventRecord(p->kev1, s);
         } else {
             ResetArgs r;
@@ -813,6 +847,10 @@ hf_status plan_run(Plan* p, cudaStream_t s, const hf_run_opts& o) {
     p->last_stream = s;
     p->ran = true;
     p->last_timed = o.time_kernel && p->n > 0;
+    p->last_launches = p->n == 0 ? 0
+                       : mode == HF_MODE_LEVELSYNC ? p->levels
+                       : mode == HF_MODE_PERSISTENT ? 2
+                                                     : (int32_t)p->tclass.size();
     p->last_instrument = instr && mode == HF_MODE_PERSISTENT;
     p->last_validate = valid && mode == HF_MODE_PERSISTENT;
     return HF_OK;
@@ -884,6 +922,21 @@ hf_status plan_get_stats(Plan* p, int64_t* out, int32_t n) {
     if (e == cudaSuccess) e = cudaMemcpy(h, p->d_stats, sizeof(h), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(e, "stats copy");
     for (int32_t i = 0; i < n && i < kStatCount; ++i) out[i] = (int64_t)h[i];
+    return HF_OK;
+}
+
+hf_status plan_get_graph_times(Plan* p, int64_t* start, int64_t* end) {
+    if (!p->ran || !p->last_gtimes) return fail(HF_ESTATE, "last run was not an instrumented team run");
+    const size_t g = (size_t)p->ngraphs;
+    cudaError_t e = cudaStreamSynchronize(p->last_stream);
+    if (e == cudaSuccess && g) e = cudaMemcpy(start, p->d_gtime, 8 * g, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && g) e = cudaMemcpy(end, p->d_gtime + g, 8 * g, cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? HF_OK : cuda_fail(e, "graph timer copy");
+}
+
+hf_status plan_last_launches(Plan* p, int32_t* n) {
+    if (!p->ran) return fail(HF_ESTATE, "not run");
+    *n = p->last_launches;
     return HF_OK;
 }
 
@@ -1379,11 +1432,11 @@ hf_status plan_predict(Plan* p, int32_t priority, const hf_costmodel* cm, cudaSt
     *t_ms = INFINITY;
     if (p->host_tasks.empty()) {
         std::vector<int32_t> order;
-        int K = 1, m = 0;
+        std::vector<int> k;
         double M = 0.0;
         const hf_costmodel* keep = p->cm;
         p->cm = cm;
-        st = team_decide(p, priority, 0, s, &K, &m, &order, &M);
+        st = team_decide(p, priority, 0, s, &k, &order, &M);
         p->cm = keep;
         if (st != HF_OK) return st;
         *t_ms = (float)(M / 1e6);
@@ -1439,103 +1492,138 @@ static int team_capacity(const Plan* p, int k) {
     return nc * k;
 }
 
-// Team plan under a cost source: the cluster size K and the number m of cluster jobs minimise
-// the predicted makespan
-//   M(K, m) = max( max over the m longest graphs of T_g(K),  T of the (m+1)-th longest solo,
-//                  total solo work / CTAs ),
-// over K in {1, 2, 4, 8, 16} (m at most the clusters resident at once); `order` lists the
-// graphs in decreasing predicted time. FIFO: one CTA per graph in batch order, M = 0.
-static hf_status team_decide(Plan* p, int32_t prio, int32_t ctas_opt, cudaStream_t s, int* K_out, int* m_out,
+// Team plan under a cost source: a team size k_g in {1, 2, 4, 8, 16} per graph (k > 1: a
+// thread-block cluster, resident for the whole run). Predicted makespan
+//   M = max( longest T_g(k_g),  sum of T_g(1) over single-CTA graphs / CTAs left to them ).
+// Every graph starts on one CTA; the graph with the longest predicted time doubles its team
+// while that lowers M (and the clusters fit); the first time it does not, the plan is final.
+// `order` lists the graphs in decreasing predicted time. FIFO: one CTA per graph in batch
+// order, M = 0.
+static hf_status team_decide(Plan* p, int32_t prio, int32_t ctas_opt, cudaStream_t s, std::vector<int>* k_out,
                              std::vector<int32_t>* order_out, double* M_out) {
     const int32_t G = p->ngraphs;
     std::vector<int32_t>& order = *order_out;
+    std::vector<int>& k = *k_out;
     order.clear();
+    k.assign((size_t)G, 1);
     for (int32_t g = 0; g < G; ++g)
         if (p->glevels[(size_t)g] > 0) order.push_back(g);
-    int K = 1, m = 0;
-    double best = 0.0;
-    if (prio != HF_PRIO_FIFO) {
-        hf_status st = calibrate(s);
+    *M_out = 0.0;
+    if (prio == HF_PRIO_FIFO) return HF_OK;
+    hf_status st = calibrate(s);
+    if (st != HF_OK) return st;
+    std::vector<double> pay_ns(p->h_seg.size(), 0.0);
+    if (p->npay) {
+        float* c = (float*)dev_alloc(sizeof(float) * (size_t)p->n, s);
+        float* b = (float*)dev_alloc(sizeof(float) * (size_t)p->n, s);
+        st = (!c || !b) ? fail(HF_ENOMEM, "device allocation failed: team costs")
+                        : plan_task_costs(p, prio, p->cm, c, b, s);
+        std::vector<float> hc;
+        if (st == HF_OK) {
+            hc.resize((size_t)p->n);
+            cudaError_t e = cudaMemcpy(hc.data(), c, sizeof(float) * (size_t)p->n, cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) st = cuda_fail(e, "team cost download");
+        }
+        dev_free(c, s);
+        dev_free(b, s);
         if (st != HF_OK) return st;
-        std::vector<double> pay_ns(p->h_seg.size(), 0.0);
-        if (p->npay) {
-            float* c = (float*)dev_alloc(sizeof(float) * (size_t)p->n, s);
-            float* b = (float*)dev_alloc(sizeof(float) * (size_t)p->n, s);
-            st = (!c || !b) ? fail(HF_ENOMEM, "device allocation failed: team costs")
-                            : plan_task_costs(p, prio, p->cm, c, b, s);
-            std::vector<float> hc;
-            if (st == HF_OK) {
-                hc.resize((size_t)p->n);
-                cudaError_t e = cudaMemcpy(hc.data(), c, sizeof(float) * (size_t)p->n, cudaMemcpyDeviceToHost);
-                if (e != cudaSuccess) st = cuda_fail(e, "team cost download");
-            }
-            dev_free(c, s);
-            dev_free(b, s);
-            if (st != HF_OK) return st;
-            for (int32_t q = 0; q < p->npay; ++q) {
-                const int32_t t = p->pay_task[(size_t)q];
-                const int32_t g = (int32_t)(std::upper_bound(p->task_off.begin(), p->task_off.end(), t) -
-                                            p->task_off.begin()) - 1;
-                pay_ns[(size_t)(p->seg_first[(size_t)g] + p->pay_level[(size_t)q])] += hc[(size_t)t];
-            }
-        }
-        std::vector<double> T1((size_t)G, 0.0);
-        double work = 0.0;
-        for (int32_t g : order) {
-            T1[(size_t)g] = team_time(p, pay_ns, g, 1);
-            work += T1[(size_t)g];
-        }
-        std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return T1[(size_t)x] > T1[(size_t)y]; });
-        const int n = (int)order.size();
-        bool have = false;
-        for (int k : {1, 2, 4, 8, 16}) {
-            int cap = team_capacity(p, k);
-            if (cap <= 0) continue;
-            if (k == 1 && ctas_opt > 0) cap = std::min(cap, ctas_opt);  // a caller's CTA cap (solo runs)
-            else if (k > 1 && ctas_opt > 0) continue;
-            const int mmax = k == 1 ? 0 : std::min(n, cap / k);
-            double pref = 0.0, solo_work = work;
-            for (int mm = 0; mm <= mmax; ++mm) {
-                if (mm > 0) {
-                    const int32_t g = order[(size_t)mm - 1];
-                    pref = std::max(pref, team_time(p, pay_ns, g, k));
-                    solo_work -= T1[(size_t)g];
-                }
-                const double next = mm < n ? T1[(size_t)order[(size_t)mm]] : 0.0;
-                const double M = std::max({pref, next, solo_work / (double)cap});
-                if (!have || M < best) {
-                    have = true;
-                    best = M;
-                    K = k;
-                    m = mm;
-                }
-            }
+        for (int32_t q = 0; q < p->npay; ++q) {
+            const int32_t t = p->pay_task[(size_t)q];
+            const int32_t g = (int32_t)(std::upper_bound(p->task_off.begin(), p->task_off.end(), t) -
+                                        p->task_off.begin()) - 1;
+            pay_ns[(size_t)(p->seg_first[(size_t)g] + p->pay_level[(size_t)q])] += hc[(size_t)t];
         }
     }
-    *K_out = K;
-    *m_out = m;
-    *M_out = best;
+    std::vector<double> T((size_t)G, 0.0);
+    double work = 0.0;
+    for (int32_t g : order) {
+        T[(size_t)g] = team_time(p, pay_ns, g, 1);
+        work += T[(size_t)g];
+    }
+    int cap1 = team_capacity(p, 1);
+    if (ctas_opt > 0) cap1 = std::min(cap1, ctas_opt);
+    int capk[17] = {0};
+    for (int kk = 2; kk <= kTeamMaxCluster; kk *= 2) capk[kk] = ctas_opt > 0 ? 0 : team_capacity(p, kk);
+    // predicted makespan: the longest team, or the single-CTA graphs' total over the CTAs left
+    // to them (they queue when there are more of them than CTAs)
+    int cl_ctas = 0, inclass[17] = {0};
+    double solo_sum = work;
+    int nsolo = (int)order.size();
+    auto makespan = [&](double tmax, double ssum, int c1, int ns) {
+        return std::max(tmax, ns > 0 ? ssum / (double)std::max(c1, 1) : 0.0);
+    };
+    using Item = std::pair<double, int32_t>;
+    std::priority_queue<Item> heap;
+    for (int32_t g : order) heap.push({T[(size_t)g], g});
+    while (!heap.empty()) {
+        const Item top = heap.top();
+        const int32_t g = top.second;
+        const int k0 = k[(size_t)g], k1 = 2 * k0;
+        if (k1 > kTeamMaxCluster || (inclass[k1] + 1) * k1 > capk[k1]) break;
+        const int cl1 = cl_ctas + k1 - (k0 > 1 ? k0 : 0);
+        const int ns1 = nsolo - (k0 == 1 ? 1 : 0);
+        if (cl1 > cap1 - (ns1 > 0 ? 1 : 0)) break;
+        const double t1 = team_time(p, pay_ns, g, k1);
+        heap.pop();
+        const double next = heap.empty() ? 0.0 : heap.top().first;
+        const double ss1 = solo_sum - (k0 == 1 ? T[(size_t)g] : 0.0);
+        const double m0 = makespan(top.first, solo_sum, cap1 - cl_ctas, nsolo);
+        const double m1 = makespan(std::max(next, t1), ss1, cap1 - cl1, ns1);
+        if (!(m1 < m0)) {  // doubling the longest graph's team does not shorten the makespan
+            heap.push(top);
+            break;
+        }
+        if (k0 > 1) inclass[k0] -= 1;
+        inclass[k1] += 1;
+        k[(size_t)g] = k1;
+        T[(size_t)g] = t1;
+        cl_ctas = cl1;
+        nsolo = ns1;
+        solo_sum = ss1;
+        heap.push({t1, g});
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return T[(size_t)x] > T[(size_t)y]; });
+    *M_out = makespan(order.empty() ? 0.0 : T[(size_t)order[0]], solo_sum, cap1 - cl_ctas, nsolo);
     return HF_OK;
 }
 
-// Job list for a run: team_decide's plan, or with team_size k > 0 every graph a cluster job of
-// min(k, 16) CTAs (in the plan's order).
+// Job lists for a run: one class per team size, each class one concurrent launch with every
+// one of its graphs resident (k > 1: cluster jobs, one per cluster; k = 1: solo jobs, queued
+// when there are more than CTAs). team_size k > 0: every graph in one class of min(k, 16).
 static hf_status plan_team_jobs(Plan* p, const hf_run_opts& o, cudaStream_t s) {
     const int32_t prio = o.priority;
     if (p->team_for[0] == prio && p->team_for[1] == o.team_size && p->team_for[2] == o.ctas &&
         (prio != HF_PRIO_LEARNED || p->team_cm == p->cm))
         return HF_OK;
     std::vector<int32_t> order;
-    int K = 1, m = 0;
+    std::vector<int> k;
     double M = 0.0;
-    hf_status st = team_decide(p, o.team_size > 0 ? HF_PRIO_FIFO : prio, o.ctas, s, &K, &m, &order, &M);
+    hf_status st = team_decide(p, o.team_size > 0 ? HF_PRIO_FIFO : prio, o.ctas, s, &k, &order, &M);
     if (st != HF_OK) return st;
-    if (o.team_size > 0) {
-        K = std::min(o.team_size, kTeamMaxCluster);
-        m = K > 1 ? (int)order.size() : 0;
-    }
+    if (o.team_size > 0)
+        for (auto& x : k) x = std::min(o.team_size, kTeamMaxCluster);
     std::vector<TeamJob> jobs;
-    for (int32_t g : order) jobs.push_back(TeamJob{g, 0, p->seg_first[(size_t)g], p->glevels[(size_t)g]});
+    p->tclass.clear();
+    int cap1 = team_capacity(p, 1);
+    if (o.ctas > 0) cap1 = std::min(cap1, o.ctas);
+    int used = 0;
+    for (int kk = kTeamMaxCluster; kk >= 1; --kk) {
+        Plan::TeamClass c{kk, (int32_t)jobs.size(), 0, 0};
+        for (int32_t g : order)
+            if (k[(size_t)g] == kk) jobs.push_back(TeamJob{g, 0, p->seg_first[(size_t)g], p->glevels[(size_t)g]});
+        c.njobs = (int32_t)jobs.size() - c.job0;
+        if (c.njobs == 0) continue;
+        if (kk > 1) {
+            const int capk = team_capacity(p, kk);
+            if (capk < kk) return fail(HF_ENOTSUP, "no resident cluster of " + std::to_string(kk) + " CTAs");
+            c.grid = std::min(c.njobs * kk, (capk / kk) * kk);
+        } else {
+            c.grid = std::max(1, std::min(c.njobs, std::max(cap1 - used, 1)));
+        }
+        used += c.grid;
+        p->tclass.push_back(c);
+    }
+    if (p->tclass.size() > 5) return fail(HF_ENOTSUP, "too many team classes");
     const size_t bytes = std::max<size_t>(sizeof(TeamJob) * jobs.size(), 16);
     if (p->cap_jobs < bytes) {
         free_owned(p, p->d_jobs);
@@ -1544,16 +1632,22 @@ static hf_status plan_team_jobs(Plan* p, const hf_run_opts& o, cudaStream_t s) {
         if (!p->d_jobs) return fail(HF_ENOMEM, "device allocation failed: team jobs");
     }
     if (!p->d_team) {
-        p->d_team = (int32_t*)palloc(p, sizeof(int32_t) * (size_t)kTeamWords, s);
+        p->d_team = (int32_t*)palloc(p, sizeof(int32_t) * (size_t)kTeamWords * 5, s);
         if (!p->d_team) return fail(HF_ENOMEM, "device allocation failed: team control");
+    }
+    if (!p->tev_fork) {
+        cudaError_t e = cudaEventCreateWithFlags(&p->tev_fork, cudaEventDisableTiming);
+        for (int i = 0; i < 4 && e == cudaSuccess; ++i) {
+            e = cudaStreamCreateWithFlags(&p->tstream[i], cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->tev_join[i], cudaEventDisableTiming);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "team streams");
     }
     cudaError_t e = cudaSuccess;
     if (!jobs.empty()) e = cudaMemcpyAsync(p->d_jobs, jobs.data(), sizeof(TeamJob) * jobs.size(), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "team job upload");
     p->njobs = (int32_t)jobs.size();
-    p->ncjobs = m;
-    p->team_k = K;
     p->team_for[0] = prio;
     p->team_for[1] = o.team_size;
     p->team_for[2] = o.ctas;

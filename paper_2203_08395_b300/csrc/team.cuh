@@ -25,7 +25,8 @@ namespace hf {
 constexpr int kTeamThreads = 256;
 constexpr int kTeamBufs = 3;       // staged levels: the current one and two ahead
 constexpr int kTeamStageN = 384;   // tasks per staged level
-constexpr int kTeamStageE = 1280;  // in-edges per staged level
+constexpr int kTeamStageE = 1024;  // in-edges per staged level
+constexpr int kTeamSlots = 16;     // payload piece descriptors kept per warp and level
 
 struct __align__(16) TeamStage {
     int32_t node[kTeamStageN + 8];  // copied from a 16-byte aligned start: up to 3 extra in front
@@ -112,7 +113,7 @@ __device__ __forceinline__ void team_ahead(const TeamArgs& a, int rank, TeamStag
 
 // One payload piece, resolved: pointers already offset to the piece, cnt in elements (saxpy)
 // or bytes (copy).
-struct TeamPiece {
+struct __align__(16) TeamPiece {
     char* dst;
     const char* src;
     int32_t cnt;
@@ -144,10 +145,11 @@ __device__ __forceinline__ int team_arrival_warps(const int4 sg, const int2 si, 
 }
 
 // Descriptors of the pieces this warp runs in a level (payload warps [pw0, nwarp) take items
-// si.x + (wid - pw0) + j * (nwarp - pw0); lane j holds the j-th, the first 32 only) and an L2
-// prefetch of their x and y ranges. Copies touch host memory and are not prefetched.
-__device__ __forceinline__ TeamPiece team_prefetch_items(const TeamArgs& a, const int2 si, int wid, int pw0, int nwarp,
-                                                         int lane) {
+// si.x + (wid - pw0) + j * (nwarp - pw0); lane j writes the j-th, the first 32 only, into the
+// warp's shared-memory slots) and an L2 prefetch of their x and y ranges. Copies touch host
+// memory and are not prefetched.
+__device__ __forceinline__ void team_prefetch_items(const TeamArgs& a, const int2 si, int wid, int pw0, int nwarp,
+                                                    int lane, TeamPiece* slots) {
     TeamPiece d;
     d.op = 0;
     const int it = si.x + (wid - pw0) + lane * (nwarp - pw0);
@@ -158,17 +160,7 @@ __device__ __forceinline__ TeamPiece team_prefetch_items(const TeamArgs& a, cons
             prefetch_l2_range(d.dst, 4ll * d.cnt);
         }
     }
-    return d;
-}
-
-__device__ __forceinline__ TeamPiece shfl_piece(const TeamPiece& d, int j) {
-    TeamPiece r;
-    r.dst = (char*)__shfl_sync(kFull, (unsigned long long)d.dst, j);
-    r.src = (const char*)__shfl_sync(kFull, (unsigned long long)d.src, j);
-    r.cnt = __shfl_sync(kFull, d.cnt, j);
-    r.a = __shfl_sync(kFull, d.a, j);
-    r.op = __shfl_sync(kFull, d.op, j);
-    return r;
+    if (lane < kTeamSlots) slots[lane] = d;
 }
 
 // One piece by one warp (a 512-element FP32 piece is one round trip of 16-byte loads).
@@ -258,7 +250,7 @@ __device__ __forceinline__ uint32_t team_task_key(const TeamArgs& a, int v, cons
 template <bool PAY, bool SOLO>
 __device__ __forceinline__ bool team_run_graph(const TeamArgs& a, const TeamJob& job, int k, int rank,
                                                TeamStage* st, unsigned long long* mbar, int4* ring, int2* iring,
-                                               unsigned& phase) {
+                                               TeamPiece* pslots, unsigned& phase) {
     const int t = threadIdx.x;
     const int lane = t & 31;
     const int nthr = k * kTeamThreads, tid = rank * kTeamThreads + t;
@@ -274,11 +266,12 @@ __device__ __forceinline__ bool team_run_graph(const TeamArgs& a, const TeamJob&
         if (L > 1) team_ahead(a, rank, st[1], &mbar[1], ring[1]);
     }
     __syncthreads();
-    TeamPiece pc, pn;  // this warp's piece descriptors for the current and the next level
-    pc.op = pn.op = 0;
+    if (a.g_start && rank == 0 && t == 0) a.g_start[job.graph] = (int64_t)gtimer();
+    // this warp's piece descriptors: slots[(l & 1)][warp][j] for level l
+    TeamPiece* const myslots = pslots + (t >> 5) * kTeamSlots;
     if (PAY) {
         const int na = team_arrival_warps(ring[0], iring[0], nwarp);
-        pc = team_prefetch_items(a, iring[0], wid, na < nwarp ? na : 0, nwarp, lane);
+        team_prefetch_items(a, iring[0], wid, na < nwarp ? na : 0, nwarp, lane, myslots);
     }
     for (int l = 0; l < L; ++l) {
         const int b = l % kTeamBufs;
@@ -290,7 +283,8 @@ __device__ __forceinline__ bool team_run_graph(const TeamArgs& a, const TeamJob&
         }
         if (PAY && l + 1 < L) {
             const int na1 = team_arrival_warps(ring[(l + 1) & 3], iring[(l + 1) & 3], nwarp);
-            pn = team_prefetch_items(a, iring[(l + 1) & 3], wid, na1 < nwarp ? na1 : 0, nwarp, lane);
+            team_prefetch_items(a, iring[(l + 1) & 3], wid, na1 < nwarp ? na1 : 0, nwarp, lane,
+                                myslots + ((l + 1) & 1) * (kTeamThreads / 32) * kTeamSlots);
         }
         const int2 i0 = PAY ? iring[l & 3] : make_int2(0, 0);
         const int na = PAY ? team_arrival_warps(s0, i0, nwarp) : nwarp;
@@ -324,14 +318,16 @@ __device__ __forceinline__ bool team_run_graph(const TeamArgs& a, const TeamJob&
         }
         // payload pieces of level l
         if (PAY && wid >= pw0) {
+            __syncwarp();
+            const TeamPiece* cur = myslots + (l & 1) * (kTeamThreads / 32) * kTeamSlots;
             int j = 0;
             for (int it = i0.x + (wid - pw0); it < i0.y; it += nwarp - pw0, ++j)
-                team_run_piece(j < 32 ? shfl_piece(pc, j) : team_piece_desc(a, it), lane);
+                team_run_piece(j < kTeamSlots ? cur[j] : team_piece_desc(a, it), lane);
         }
         if (SOLO) __syncthreads();
         else cluster_sync();
-        pc = pn;
     }
+    if (a.g_end && rank == 0 && t == 0) a.g_end[job.graph] = (int64_t)gtimer();
     return true;
 }
 
@@ -347,6 +343,7 @@ __global__ void __launch_bounds__(kTeamThreads, PAY ? 2 : 3) k_team(const TeamAr
     __shared__ __align__(16) TeamJob s_job;
     __shared__ int4 s_ring[4];
     __shared__ int2 s_iring[4];
+    __shared__ TeamPiece s_piece[2][kTeamSlots * (kTeamThreads / 32)];  // piece descriptors, by level parity
     const int t = threadIdx.x;
     if (t == 0) {
         for (int b = 0; b < kTeamBufs; ++b) mbar_init(&mbar[b], 1);
@@ -369,7 +366,7 @@ __global__ void __launch_bounds__(kTeamThreads, PAY ? 2 : 3) k_team(const TeamAr
             const TeamJob job = s_job;
             cluster_sync();  // all have read s_job before CTA 0 may overwrite it
             if (job.graph < 0) break;
-            if (!team_run_graph<PAY, false>(a, job, k, rank, st, mbar, s_ring, s_iring, phase)) return;
+            if (!team_run_graph<PAY, false>(a, job, k, rank, st, mbar, s_ring, s_iring, &s_piece[0][0], phase)) return;
         }
     }
     for (;;) {
@@ -381,7 +378,7 @@ __global__ void __launch_bounds__(kTeamThreads, PAY ? 2 : 3) k_team(const TeamAr
         const TeamJob job = s_job;
         __syncthreads();
         if (job.graph < 0) break;
-        if (!team_run_graph<PAY, true>(a, job, 1, 0, st, mbar, s_ring, s_iring, phase)) return;
+        if (!team_run_graph<PAY, true>(a, job, 1, 0, st, mbar, s_ring, s_iring, &s_piece[0][0], phase)) return;
     }
 }
 

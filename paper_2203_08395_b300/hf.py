@@ -139,6 +139,8 @@ def load():
         "hf_batch_get_stats": [vp, vp, i32],
         "hf_batch_predict": [vp, i32, vp, P(ctypes.c_float), P(ctypes.c_float), P(ctypes.c_float)],
         "hf_run_csr_noalloc": [i32, i32, vp, vp, vp, vp, vp, ctypes.c_uint64, vp],
+        "hf_batch_get_graph_times": [vp, vp, vp],
+        "hf_batch_last_launches": [vp, P(i32)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -480,6 +482,19 @@ def hf_batch_predict(b, priority, stream=None):
     _check(load().hf_batch_predict(b, priority, _stream_handle(stream), ctypes.byref(ls), ctypes.byref(pe),
                                    ctypes.byref(tm)), "hf_batch_predict")
     return ls.value, pe.value, tm.value
+
+
+def hf_batch_get_graph_times(b, ngraphs):
+    """Per-graph (start, end) %globaltimer ns of the last instrumented team run."""
+    s0, s1 = np.empty(ngraphs, np.int64), np.empty(ngraphs, np.int64)
+    _check(load().hf_batch_get_graph_times(b, s0.ctypes.data, s1.ctypes.data), "hf_batch_get_graph_times")
+    return s0, s1
+
+
+def hf_batch_last_launches(b):
+    n = ctypes.c_int32()
+    _check(load().hf_batch_last_launches(b, ctypes.byref(n)), "hf_batch_last_launches")
+    return n.value
 
 
 STAT_NAMES = ["rounds", "items", "idle", "edges", "cas", "push_local", "push_global", "claims", "pops", "pieces",

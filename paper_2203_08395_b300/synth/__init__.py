@@ -395,7 +395,8 @@ def paper_dependency_example():
 # ------------------------------------------------------------------ named configurations
 
 def config(name: str, seed: int = 0) -> Workload:
-    """The five evaluation configurations (see the project design notes for the recipe)."""
+    """The five evaluation configurations (see the project design notes for the recipe), and
+    batch32 / batch32_mixed: the batch recipe with 32 graphs, a small case for profiling."""
     if name == "layered10k":
         return Workload("layered10k", [layered(seed, 10_000, 40, 1, 4)])
     if name == "circuit1m":
@@ -406,6 +407,10 @@ def config(name: str, seed: int = 0) -> Workload:
         return batch(seed, name="batch256")
     if name == "batch256_mixed":
         return batch(seed, frac_saxpy=0.10, name="batch256_mixed")
+    if name == "batch32":
+        return batch(seed, graphs=32, name="batch32")
+    if name == "batch32_mixed":
+        return batch(seed, graphs=32, frac_saxpy=0.10, name="batch32_mixed")
     raise KeyError(name)
 
 
