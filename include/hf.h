@@ -139,6 +139,12 @@ typedef struct {
     int32_t team_size;      /* team: thread-block cluster size for every graph, 1..16 (above 16:
                                16); 0 = cluster size and clustered graphs chosen from predicted
                                costs (one CTA per graph under HF_PRIO_FIFO) */
+    int32_t team_scale;     /* team planner: factor on the predicted payload cost, standing for
+                               the slowdown of memory traffic when every graph streams at once;
+                               larger values give payload-heavy graphs larger teams; 0 = 4 (a
+                               512-element piece: ~0.75 us for a warp alone, ~3 us when every SM
+                               streams, measured on B300) */
+    int32_t pad2_;
 } hf_run_opts;
 
 void hf_run_opts_default(hf_run_opts* opts);

@@ -65,7 +65,7 @@ struct Plan {
     cudaEvent_t tev_fork = nullptr;
     cudaEvent_t tev_join[4] = {nullptr, nullptr, nullptr, nullptr};
     int32_t* d_team = nullptr;        // control words (job counters), kTeamWords per class
-    int32_t team_for[3] = {-1, -1, -1};  // priority, team_size, CTAs the job list was built for
+    int32_t team_for[4] = {-1, -1, -1, -1};  // priority, team_size, CTAs, scale the jobs were built for
     const hf_costmodel* team_cm = nullptr;
 
     // device buffers
@@ -146,9 +146,12 @@ hf_status plan_auto_mode(Plan* p, cudaStream_t s, int* mode);
 
 static hf_status plan_set_chunk(Plan* p, int64_t chunk_elems, cudaStream_t s);
 static hf_status plan_team_jobs(Plan* p, const hf_run_opts& o, cudaStream_t s);
+// default payload-cost scale: a 512-element piece takes ~0.75 us for a warp alone and ~3 us when
+// every SM streams (measured on this B300), so concurrent graphs see about 4x the unloaded cost
+constexpr int kTeamScaleDefault = 4;
 static int team_capacity(const Plan* p, int k);
-static hf_status team_decide(Plan* p, int32_t prio, int32_t ctas_opt, cudaStream_t s, std::vector<int>* k_out,
-                             std::vector<int32_t>* order_out, double* M_out);
+static hf_status team_decide(Plan* p, int32_t prio, int32_t ctas_opt, double scale, cudaStream_t s,
+                             std::vector<int>* k_out, std::vector<int32_t>* order_out, double* M_out);
 hf_status plan_prepare_priority(Plan* p, int32_t priority, const hf_costmodel* cm, cudaStream_t s);
 
 void plan_set_costmodel(Plan* p, const hf_costmodel* cm) {
@@ -1222,29 +1225,35 @@ static TuneKey tune_key(const Plan* p) {
     return TuneKey(logn, epn, payq, logd, p->ngraphs > 1 ? 1 : 0);
 }
 
-// Team executor: coordinate descent over the cluster size for every graph (0: the cost model's
-// plan) and the payload piece size; each trial the median of 3 timed runs.
+// Team executor: coordinate descent over the planner's payload-cost scale (contention), the
+// cluster size for every graph (0: the cost model's plan) and the payload piece size; each
+// trial the median of 3 timed runs.
 static hf_status autotune_team(Plan* p, cudaStream_t s, const hf_run_opts& base, hf_run_opts* best, float* best_ms) {
     hf_run_opts cur = base;
     cur.mode = HF_MODE_TEAM;
     cur.instrument = cur.validate = cur.time_kernel = 0;
     cur.stall_task = -1;
     cur.team_size = 0;
+    cur.team_scale = kTeamScaleDefault;
     if (cur.chunk_elems <= 0) cur.chunk_elems = 512;
     float best_t = 0.f;
     hf_status st = time_runs(p, s, cur, 3, &best_t);
     if (st != HF_OK) return st;
     const std::vector<int> size_v{0, 1, 2, 4, 8, 16};
     const std::vector<int64_t> chunk_v{256, 512, 1024, 2048};
+    const std::vector<int> scale_v{1, 2, 4, 8, 16};
     for (int round = 0; round < 2; ++round) {
-        for (int dim = 0; dim < 2; ++dim) {
-            if (dim == 1 && p->npay == 0) continue;
-            const size_t nv = dim == 0 ? size_v.size() : chunk_v.size();
+        for (int dim = 0; dim < 3; ++dim) {  // planner scale, then cluster size, then piece size
+            if (dim != 1 && p->npay == 0) continue;
+            if (dim == 0 && (cur.team_size != 0 || cur.priority == HF_PRIO_FIFO)) continue;
+            const size_t nv = dim == 0 ? scale_v.size() : dim == 1 ? size_v.size() : chunk_v.size();
             for (size_t i = 0; i < nv; ++i) {
                 hf_run_opts t = cur;
-                if (dim == 0) t.team_size = size_v[i];
+                if (dim == 0) t.team_scale = scale_v[i];
+                else if (dim == 1) t.team_size = size_v[i];
                 else t.chunk_elems = chunk_v[i];
-                if (t.team_size == cur.team_size && t.chunk_elems == cur.chunk_elems) continue;
+                if (t.team_size == cur.team_size && t.chunk_elems == cur.chunk_elems && t.team_scale == cur.team_scale)
+                    continue;
                 float ms = 0.f;
                 if ((st = time_runs(p, s, t, 3, &ms)) != HF_OK) return st;
                 if (ms < best_t) {
@@ -1276,6 +1285,7 @@ hf_status plan_autotune(Plan* p, cudaStream_t s, const hf_run_opts& base, int fo
             best->chunk_elems = it->second.first.chunk_elems;
             best->payload_warps = it->second.first.payload_warps;
             best->team_size = it->second.first.team_size;
+            best->team_scale = it->second.first.team_scale;
             *best_ms = it->second.second;
             return HF_OK;
         }
@@ -1436,7 +1446,7 @@ hf_status plan_predict(Plan* p, int32_t priority, const hf_costmodel* cm, cudaSt
         double M = 0.0;
         const hf_costmodel* keep = p->cm;
         p->cm = cm;
-        st = team_decide(p, priority, 0, s, &k, &order, &M);
+        st = team_decide(p, priority, 0, (double)kTeamScaleDefault, s, &k, &order, &M);
         p->cm = keep;
         if (st != HF_OK) return st;
         *t_ms = (float)(M / 1e6);
@@ -1450,14 +1460,14 @@ hf_status plan_predict(Plan* p, int32_t priority, const hf_costmodel* cm, cudaSt
 // t_lvl the measured time of a one-task level (CTA barrier for k = 1, cluster barrier else).
 constexpr int kTeamMaxCluster = 16;  // above 8 is a non-portable cluster size
 
-static double team_time(const Plan* p, const std::vector<double>& pay_ns, int32_t g, int k) {
+static double team_time(const Plan* p, const std::vector<double>& pay_ns, int32_t g, int k, double scale = 1.0) {
     double t = 0.0;
     const double tl = k == 1 ? g_t_team_solo_ns : g_t_team_cluster_ns;
     const int32_t s0 = p->seg_first[(size_t)g];
     for (int32_t l = 0; l < p->glevels[(size_t)g]; ++l) {
         const int4& sg = p->h_seg[(size_t)(s0 + l)];
         const int64_t w = sg.y - sg.x;
-        t += tl * (double)((w + 256LL * k - 1) / (256LL * k)) + pay_ns[(size_t)(s0 + l)] / (8.0 * k);
+        t += tl * (double)((w + 256LL * k - 1) / (256LL * k)) + scale * pay_ns[(size_t)(s0 + l)] / (8.0 * k);
     }
     return t;
 }
@@ -1497,10 +1507,12 @@ static int team_capacity(const Plan* p, int k) {
 //   M = max( longest T_g(k_g),  sum of T_g(1) over single-CTA graphs / CTAs left to them ).
 // Every graph starts on one CTA; the graph with the longest predicted time doubles its team
 // while that lowers M (and the clusters fit); the first time it does not, the plan is final.
-// `order` lists the graphs in decreasing predicted time. FIFO: one CTA per graph in batch
-// order, M = 0.
-static hf_status team_decide(Plan* p, int32_t prio, int32_t ctas_opt, cudaStream_t s, std::vector<int>* k_out,
-                             std::vector<int32_t>* order_out, double* M_out) {
+// `order` lists the graphs in decreasing predicted time. Planning multiplies the payload costs
+// by `scale` (the slowdown of memory traffic when all graphs stream together); *M_out is the
+// plan's makespan in unscaled costs, comparable with the other executors' predictions. FIFO:
+// one CTA per graph in batch order, M = 0.
+static hf_status team_decide(Plan* p, int32_t prio, int32_t ctas_opt, double scale, cudaStream_t s,
+                             std::vector<int>* k_out, std::vector<int32_t>* order_out, double* M_out) {
     const int32_t G = p->ngraphs;
     std::vector<int32_t>& order = *order_out;
     std::vector<int>& k = *k_out;
@@ -1537,7 +1549,7 @@ static hf_status team_decide(Plan* p, int32_t prio, int32_t ctas_opt, cudaStream
     std::vector<double> T((size_t)G, 0.0);
     double work = 0.0;
     for (int32_t g : order) {
-        T[(size_t)g] = team_time(p, pay_ns, g, 1);
+        T[(size_t)g] = team_time(p, pay_ns, g, 1, scale);
         work += T[(size_t)g];
     }
     int cap1 = team_capacity(p, 1);
@@ -1563,7 +1575,7 @@ static hf_status team_decide(Plan* p, int32_t prio, int32_t ctas_opt, cudaStream
         const int cl1 = cl_ctas + k1 - (k0 > 1 ? k0 : 0);
         const int ns1 = nsolo - (k0 == 1 ? 1 : 0);
         if (cl1 > cap1 - (ns1 > 0 ? 1 : 0)) break;
-        const double t1 = team_time(p, pay_ns, g, k1);
+        const double t1 = team_time(p, pay_ns, g, k1, scale);
         heap.pop();
         const double next = heap.empty() ? 0.0 : heap.top().first;
         const double ss1 = solo_sum - (k0 == 1 ? T[(size_t)g] : 0.0);
@@ -1583,7 +1595,14 @@ static hf_status team_decide(Plan* p, int32_t prio, int32_t ctas_opt, cudaStream
         heap.push({t1, g});
     }
     std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return T[(size_t)x] > T[(size_t)y]; });
-    *M_out = makespan(order.empty() ? 0.0 : T[(size_t)order[0]], solo_sum, cap1 - cl_ctas, nsolo);
+    // the plan's makespan in unscaled costs (the units of the other executors' predictions)
+    double tmax = 0.0, ssum = 0.0;
+    for (int32_t g : order) {
+        const double t = team_time(p, pay_ns, g, k[(size_t)g]);
+        tmax = std::max(tmax, t);
+        if (k[(size_t)g] == 1) ssum += t;
+    }
+    *M_out = makespan(tmax, ssum, cap1 - cl_ctas, nsolo);
     return HF_OK;
 }
 
@@ -1592,13 +1611,14 @@ static hf_status team_decide(Plan* p, int32_t prio, int32_t ctas_opt, cudaStream
 // when there are more than CTAs). team_size k > 0: every graph in one class of min(k, 16).
 static hf_status plan_team_jobs(Plan* p, const hf_run_opts& o, cudaStream_t s) {
     const int32_t prio = o.priority;
+    const int32_t scale = o.team_scale > 0 ? o.team_scale : kTeamScaleDefault;
     if (p->team_for[0] == prio && p->team_for[1] == o.team_size && p->team_for[2] == o.ctas &&
-        (prio != HF_PRIO_LEARNED || p->team_cm == p->cm))
+        p->team_for[3] == scale && (prio != HF_PRIO_LEARNED || p->team_cm == p->cm))
         return HF_OK;
     std::vector<int32_t> order;
     std::vector<int> k;
     double M = 0.0;
-    hf_status st = team_decide(p, o.team_size > 0 ? HF_PRIO_FIFO : prio, o.ctas, s, &k, &order, &M);
+    hf_status st = team_decide(p, o.team_size > 0 ? HF_PRIO_FIFO : prio, o.ctas, (double)scale, s, &k, &order, &M);
     if (st != HF_OK) return st;
     if (o.team_size > 0)
         for (auto& x : k) x = std::min(o.team_size, kTeamMaxCluster);
@@ -1651,6 +1671,7 @@ static hf_status plan_team_jobs(Plan* p, const hf_run_opts& o, cudaStream_t s) {
     p->team_for[0] = prio;
     p->team_for[1] = o.team_size;
     p->team_for[2] = o.ctas;
+    p->team_for[3] = scale;
     p->team_cm = p->cm;
     return HF_OK;
 }

@@ -164,9 +164,51 @@ __device__ __forceinline__ void team_prefetch_items(const TeamArgs& a, const int
 }
 
 // One piece by one warp (a 512-element FP32 piece is one round trip of 16-byte loads).
+// FP32 saxpy piece with 32-bit indexing (a piece is at most a few thousand elements); same
+// access pattern as warp_saxpy_f32
+__device__ __forceinline__ void team_saxpy_f32(float* __restrict__ y, const float* __restrict__ x, int cnt, float a,
+                                               int lane) {
+    if ((((uintptr_t)y ^ (uintptr_t)x) & 15) != 0) {
+        for (int i = lane; i < cnt; i += 32) y[i] = __fmaf_rn(a, __ldcg(x + i), __ldcg(y + i));
+        return;
+    }
+    int head = (int)(((16 - ((uintptr_t)y & 15)) & 15) >> 2);
+    if (head > cnt) head = cnt;
+    const int nv = (cnt - head) >> 2, tail0 = head + 4 * nv;
+    // lanes [0, head) take the unaligned leading elements, the next cnt - tail0 lanes the
+    // trailing ones (at most 3 + 3)
+    const bool scalar = lane < head + (cnt - tail0);
+    const int li = lane < head ? lane : tail0 + (lane - head);
+    float sx = 0.f, sy = 0.f;
+    if (scalar) {
+        sx = __ldcg(x + li);
+        sy = __ldcg(y + li);
+    }
+    float4* __restrict__ y4 = reinterpret_cast<float4*>(y + head);
+    const float4* __restrict__ x4 = reinterpret_cast<const float4*>(x + head);
+    for (int k = lane; k - lane < nv; k += 128) {
+        float4 xv[4], yv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = k + 32 * u < nv ? k + 32 * u : nv - 1;
+            xv[u] = __ldcs(x4 + i);
+            yv[u] = __ldcs(y4 + i);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            yv[u].x = __fmaf_rn(a, xv[u].x, yv[u].x);
+            yv[u].y = __fmaf_rn(a, xv[u].y, yv[u].y);
+            yv[u].z = __fmaf_rn(a, xv[u].z, yv[u].z);
+            yv[u].w = __fmaf_rn(a, xv[u].w, yv[u].w);
+            if (k + 32 * u < nv) __stcs(y4 + k + 32 * u, yv[u]);
+        }
+    }
+    if (scalar) y[li] = __fmaf_rn(a, sx, sy);
+}
+
 __device__ __forceinline__ void team_run_piece(const TeamPiece& d, int lane) {
     if (d.op == kPaySaxpyF32)
-        warp_saxpy_f32(reinterpret_cast<float*>(d.dst), reinterpret_cast<const float*>(d.src), d.cnt,
+        team_saxpy_f32(reinterpret_cast<float*>(d.dst), reinterpret_cast<const float*>(d.src), d.cnt,
                        __uint_as_float(d.a), lane);
     else if (d.op == kPaySaxpyI32)
         warp_saxpy_i32(reinterpret_cast<int32_t*>(d.dst), reinterpret_cast<const int32_t*>(d.src), d.cnt, d.a, lane);
@@ -220,17 +262,15 @@ __device__ __forceinline__ uint32_t team_fold(const TeamArgs& a, const int2* in,
     uint32_t best = 0u;
     for (int e = e0; e < e1; e += 8) {
         const int cnt = e1 - e < 8 ? e1 - e : 8;
-        int2 ie[8];
         uint32_t kk[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j)
-            if (j < cnt) ie[j] = in[e + j];
+            if (j < cnt) kk[j] = team_pred_key<SOLO>(a, in[e + j].x);
+        // the delays are read again once the keys are in (fewer live registers)
+        const volatile int* dl = reinterpret_cast<const volatile int*>(in + e) + 1;
 #pragma unroll
         for (int j = 0; j < 8; ++j)
-            if (j < cnt) kk[j] = team_pred_key<SOLO>(a, ie[j].x);
-#pragma unroll
-        for (int j = 0; j < 8; ++j)
-            if (j < cnt) best = max(best, f2key(__fadd_rn(key2f(kk[j]), __int_as_float(ie[j].y))));
+            if (j < cnt) best = max(best, f2key(__fadd_rn(key2f(kk[j]), __int_as_float(dl[2 * j]))));
     }
     return best;
 }
@@ -337,7 +377,7 @@ __device__ __forceinline__ bool team_run_graph(const TeamArgs& a, const TeamJob&
 // job and hands it to every CTA of its cluster through distributed shared memory; the cluster
 // runs it as one team. Phase 2: every CTA takes solo jobs until none is left.
 template <bool PAY>
-__global__ void __launch_bounds__(kTeamThreads, PAY ? 2 : 3) k_team(const TeamArgs a) {
+__global__ void __launch_bounds__(kTeamThreads, 3) k_team(const TeamArgs a) {
     __shared__ TeamStage st[kTeamBufs];
     __shared__ __align__(8) unsigned long long mbar[kTeamBufs];
     __shared__ __align__(16) TeamJob s_job;

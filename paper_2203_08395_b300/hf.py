@@ -64,7 +64,8 @@ class hf_run_opts(ctypes.Structure):
                 ("chunk_elems", ctypes.c_int64), ("spin_limit_ns", ctypes.c_uint64),
                 ("instrument", ctypes.c_int32), ("validate", ctypes.c_int32),
                 ("stall_task", ctypes.c_int32), ("time_kernel", ctypes.c_int32),
-                ("payload_warps", ctypes.c_int32), ("team_size", ctypes.c_int32)]
+                ("payload_warps", ctypes.c_int32), ("team_size", ctypes.c_int32),
+                ("team_scale", ctypes.c_int32), ("pad2_", ctypes.c_int32)]
 
 
 class hf_graph_info_t(ctypes.Structure):

@@ -254,6 +254,35 @@ def test_paper_saxpy_graph_persistent_without_host_tasks():
     hf.hf_graph_destroy(g)
 
 
+@pytest.mark.parametrize("ex", ["levelsync", "persistent", "team", "team_k2"])
+def test_saxpy_unaligned_and_ragged(ex):
+    """Saxpy tasks on device pointers at every 4-byte offset of x and y (shared and different
+    16-byte alignment) and every length 0..40 plus longer ragged ones, chained on the same y
+    (each task after the previous one on its buffer), against the oracle's saxpy."""
+    rng = np.random.default_rng(11)
+    cases = [(ox, oy, n) for ox in range(4) for oy in range(4) for n in (0, 1, 2, 3, 5, 7, 13, 31, 40, 517, 1029)]
+    xs = [torch.from_numpy(rng.uniform(-1, 1, n + 8).astype(np.float32)).cuda() for _, _, n in cases]
+    ys = [torch.from_numpy(rng.uniform(-1, 1, n + 8).astype(np.float32)).cuda() for _, _, n in cases]
+    y0 = [y.cpu().numpy().copy() for y in ys]
+    g = hf.hf_graph_create()
+    ids = []
+    for c, (ox, oy, n) in enumerate(cases):
+        p = hf.hf_saxpy_payload(op=hf.HF_K_SAXPY_F32, a_f=float(1.5 + c % 3), n=n, x_pull=-1, y_pull=-1,
+                                x_dev=xs[c].data_ptr() + 4 * ox, y_dev=ys[c].data_ptr() + 4 * oy)
+        ids.append((hf.hf_add_task(g, hf.HF_KERNEL, p), hf.hf_add_task(g, hf.HF_KERNEL, p)))
+        hf.hf_precede(g, ids[-1][0], ids[-1][1])  # the second saxpy on the same y runs after the first
+    hf.hf_run(g, None, hf.hf_run_opts_default(chunk_elems=256, **EXECUTORS[ex]))
+    hf.hf_sync_status(g)
+    for c, (ox, oy, n) in enumerate(cases):
+        a = np.float32(1.5 + c % 3)
+        x = xs[c].cpu().numpy()[ox:ox + n]
+        want = y0[c].copy()
+        want[oy:oy + n] = oracle.saxpy_f32(a, x, oracle.saxpy_f32(a, x, want[oy:oy + n]))
+        np.testing.assert_array_equal(ys[c].cpu().numpy().view(np.uint32), want.view(np.uint32),
+                                      err_msg="case %s" % (cases[c],))
+    hf.hf_graph_destroy(g)
+
+
 def test_paper_dependency_graph_order():
     from golden_io import load
 
