@@ -192,6 +192,36 @@ def cpu_oracle_rate(wl, budget_s=15.0):
     return tasks / spent, edges / spent, desc
 
 
+def max_over_ranks(x, device="cpu"):
+    """The largest value over the ranks of the process group (a job's step ends with its slowest
+    rank); the value itself without a process group."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x, device="cpu"):
+    """The sum over the ranks of the process group (units every rank processed)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def job_rate(units_all_ranks, ms_max):
+    """Whole-job throughput: units all ranks processed over the max-over-ranks step time."""
+    return units_all_ranks / (ms_max / 1e3)
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -334,11 +364,11 @@ def main():
         bd.run(stream, time_kernel=1, **head)
         kms.append(hf.hf_batch_kernel_ms(bd.b))
     kernel_ms = float(np.mean(kms))
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * N / (ms / 1e3)
+    # weak scaling: every rank runs its own batch (its own seed); the job processed all of them
+    ms = max_over_ranks(ms, "cuda")
+    N_all = sum_over_ranks(N, "cuda")
+    E_all = sum_over_ranks(E, "cuda")
+    value = job_rate(N_all, ms)
 
     compare = {}
     if not args.no_compare:
@@ -370,8 +400,8 @@ def main():
             bd.run(stream, **head)
             hf.hf_batch_get_arrivals(bd.b, -1, N, out=arr_host.numpy())
         st = bd.sync(check=False)
-        dt = (time.perf_counter() - t0) / steps
-        e2e = {"value": world * N / dt, "unit": "tasks/s", "h2d_bytes_per_step": 4 * E,
+        dt = max_over_ranks((time.perf_counter() - t0) / steps, "cuda")
+        e2e = {"value": job_rate(N_all, 1e3 * dt), "unit": "tasks/s", "h2d_bytes_per_step": 4 * E,
                "d2h_bytes_per_step": 4 * N + 12, "ms_per_step": 1e3 * dt, "status": hf.hf_status_string(st)}
 
     cpu = None
@@ -398,7 +428,7 @@ def main():
         "metric": "DAG tasks/s", "value": value, "unit": "tasks/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "ms_per_step_median": ms_med, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "edges_per_s": world * E / (ms / 1e3),
+        "edges_per_s": job_rate(E_all, ms),
         "config": {"workload": args.workload, "tasks": N, "edges": E, "graphs": len(wl.graphs),
                    "saxpy_elems": wl.saxpy_elems, "executor": args.executor,
                    "chosen": {hf.HF_MODE_PERSISTENT: "persistent", hf.HF_MODE_TEAM: "team"}.get(chosen, "levelsync"),
