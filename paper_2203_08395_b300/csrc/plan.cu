@@ -1428,8 +1428,12 @@ hf_status plan_predict(Plan* p, int32_t priority, const hf_costmodel* cm, cudaSt
     for (int32_t v = 0; v < p->n; ++v) {
         cp = std::max(cp, (double)hb[(size_t)v]);
         work += hc[(size_t)v];
-        double& m = lmax[(size_t)p->h_level[(size_t)v]];
-        m = std::max(m, (double)hc[(size_t)v]);
+        // a level-synchronous level costs t_level plus its slowest payload task (a max-plus task
+        // is one gather, part of t_level)
+        if (p->h_cat[(size_t)v] != 0) {
+            double& m = lmax[(size_t)p->h_level[(size_t)v]];
+            m = std::max(m, (double)hc[(size_t)v]);
+        }
     }
     double lsum = 0.0;
     for (double x : lmax) lsum += x;
@@ -1467,7 +1471,10 @@ static double team_time(const Plan* p, const std::vector<double>& pay_ns, int32_
     for (int32_t l = 0; l < p->glevels[(size_t)g]; ++l) {
         const int4& sg = p->h_seg[(size_t)(s0 + l)];
         const int64_t w = sg.y - sg.x;
-        t += tl * (double)((w + 256LL * k - 1) / (256LL * k)) + scale * pay_ns[(size_t)(s0 + l)] / (8.0 * k);
+        // a level too large to stage reads its task list, row starts and in-edges from memory:
+        // three dependent round trips instead of one
+        const double stage = (w <= kTeamStageN && sg.w - sg.z <= kTeamStageE) ? 1.0 : 2.5;
+        t += stage * tl * (double)((w + 256LL * k - 1) / (256LL * k)) + scale * pay_ns[(size_t)(s0 + l)] / (8.0 * k);
     }
     return t;
 }
