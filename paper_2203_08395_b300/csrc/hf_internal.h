@@ -169,6 +169,8 @@ struct TeamArgs {
     const TeamJob* jobs;     // cluster jobs first, then solo jobs
     int32_t njobs;
     int32_t ncjobs;
+    int32_t stage_n;         // stage buffer capacity: tasks and in-edges of a level
+    int32_t stage_e;
     int32_t* team;           // control words (kTeam*)
     Ctrl* ctrl;              // status word (HF_ETIMEDOUT when a staged copy never lands)
     uint64_t spin_limit_ns;

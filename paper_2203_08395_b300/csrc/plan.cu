@@ -65,6 +65,7 @@ struct Plan {
     cudaEvent_t tev_fork = nullptr;
     cudaEvent_t tev_join[4] = {nullptr, nullptr, nullptr, nullptr};
     int32_t* d_team = nullptr;        // control words (job counters), kTeamWords per class
+    int32_t stage_n = 4, stage_e = 2;  // stage buffer capacities (tasks, in-edges per level)
     int32_t team_for[4] = {-1, -1, -1, -1};  // priority, team_size, CTAs, scale the jobs were built for
     const hf_costmodel* team_cm = nullptr;
 
@@ -150,6 +151,8 @@ static hf_status plan_team_jobs(Plan* p, const hf_run_opts& o, cudaStream_t s);
 // every SM streams (measured on this B300), so concurrent graphs see about 4x the unloaded cost
 constexpr int kTeamScaleDefault = 4;
 static int team_capacity(const Plan* p, int k);
+static size_t team_smem(const Plan* p);
+static void team_smem_attr(const Plan* p);
 static hf_status team_decide(Plan* p, int32_t prio, int32_t ctas_opt, double scale, cudaStream_t s,
                              std::vector<int>* k_out, std::vector<int32_t>* order_out, double* M_out);
 hf_status plan_prepare_priority(Plan* p, int32_t priority, const hf_costmodel* cm, cudaStream_t s);
@@ -450,6 +453,12 @@ hf_status plan_build(const std::vector<hf_graph*>& graphs, Plan** out) {
         if ((st = upload(p, &p->d_ls_ptr, ls_ptr.data(), ls_ptr.size(), s, "ls_ptr", 64)) != HF_OK) return bail(st);
         if ((st = upload(p, &p->d_ls_in, ls_in.data(), ls_in.size(), s, "ls_in", 64)) != HF_OK) return bail(st);
         if ((st = upload(p, &p->d_seg, p->h_seg.data(), p->h_seg.size(), s, "seg")) != HF_OK) return bail(st);
+        // team stage buffers cover the widest level, up to 1,024 tasks and 2,048 in-edges (about
+        // 25 KB per buffer); larger levels go through L2 instead
+        for (const int4& sg : p->h_seg) {
+            p->stage_n = std::max(p->stage_n, std::min(((sg.y - sg.x + 3) / 4) * 4, 1024));
+            p->stage_e = std::max(p->stage_e, std::min(((sg.w - sg.z + 1) / 2) * 2, 2048));
+        }
         if ((st = upload(p, &p->d_epos_csr, epos_csr.data(), epos_csr.size(), s, "epos")) != HF_OK) return bail(st);
         if ((st = upload(p, &p->d_epos_ls, epos_ls.data(), epos_ls.size(), s, "epos")) != HF_OK) return bail(st);
         p->d_pay = (DevPayload*)palloc(p, std::max<size_t>(sizeof(DevPayload) * (size_t)p->npay, 64), s);
@@ -713,6 +722,9 @@ hf_status plan_run(Plan* p, cudaStream_t s, const hf_run_opts& o) {
             a.seg_items = p->d_seg_items;
             a.ctrl = p->d_ctrl;
             a.spin_limit_ns = o.spin_limit_ns ? o.spin_limit_ns : 2000000000ull;
+            a.stage_n = p->stage_n;
+            a.stage_e = p->stage_e;
+            team_smem_attr(p);
             if (instr) {
                 if (!p->d_gtime) {
                     p->d_gtime = (int64_t*)palloc(p, sizeof(int64_t) * 2 * std::max<size_t>((size_t)p->ngraphs, 1), s);
@@ -744,7 +756,8 @@ hf_status plan_run(Plan* p, cudaStream_t s, const hf_run_opts& o) {
                 cudaLaunchConfig_t cfg = {};
                 cfg.gridDim = dim3((unsigned)c.grid);
                 cfg.blockDim = dim3(kTeamThreads);
-                            cfg.stream = i == 0 ? s : p->tstream[i - 1];
+                cfg.dynamicSmemBytes = team_smem(p);
+                cfg.stream = i == 0 ? s : p->tstream[i - 1];
                 cudaLaunchAttribute at[1];
                 at[0].id = cudaLaunchAttributeClusterDimension;
                 at[0].val.clusterDim.x = (unsigned)c.k;
@@ -1473,18 +1486,33 @@ static double team_time(const Plan* p, const std::vector<double>& pay_ns, int32_
         const int64_t w = sg.y - sg.x;
         // a level too large to stage reads its task list, row starts and in-edges from memory:
         // three dependent round trips instead of one
-        const double stage = (w <= kTeamStageN && sg.w - sg.z <= kTeamStageE) ? 1.0 : 2.5;
+        const double stage = (w <= p->stage_n && sg.w - sg.z <= p->stage_e) ? 1.0 : 2.5;
         t += stage * tl * (double)((w + 256LL * k - 1) / (256LL * k)) + scale * pay_ns[(size_t)(s0 + l)] / (8.0 * k);
     }
     return t;
 }
 
 // CTAs of cluster size k resident at once (k = 1: plain occupancy).
+static size_t team_smem(const Plan* p) { return kTeamBufs * team_stage_bytes(p->stage_n, p->stage_e); }
+
+static void team_smem_attr(const Plan* p) {
+    static std::mutex mu;
+    static size_t set_to = 0;
+    std::lock_guard<std::mutex> lk(mu);
+    const size_t need = team_smem(p);
+    if (need > set_to) {
+        cudaFuncSetAttribute(k_team<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
+        cudaFuncSetAttribute(k_team<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
+        set_to = need;
+    }
+}
+
 static int team_capacity(const Plan* p, int k) {
     const void* fn = p->npay ? (const void*)k_team<true> : (const void*)k_team<false>;
+    team_smem_attr(p);
     if (k == 1) {
         int occ = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kTeamThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kTeamThreads, team_smem(p));
         return p->num_sms * std::max(occ, 1);
     }
     if (k > 8) {
@@ -1494,6 +1522,7 @@ static int team_capacity(const Plan* p, int k) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)k);
     cfg.blockDim = dim3(kTeamThreads);
+    cfg.dynamicSmemBytes = team_smem(p);
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
     at[0].val.clusterDim.x = (unsigned)k;

@@ -24,18 +24,30 @@ namespace hf {
 
 constexpr int kTeamThreads = 256;
 constexpr int kTeamBufs = 3;       // staged levels: the current one and two ahead
-constexpr int kTeamStageN = 384;   // tasks per staged level
-constexpr int kTeamStageE = 1024;  // in-edges per staged level
+// Stage buffers live in dynamic shared memory, sized per plan (TeamArgs::stage_n tasks and
+// stage_e in-edges per level, multiples of 4 and 2): node[stage_n + 8] (copied from a 16-byte
+// aligned start, up to 3 extra entries in front), ptr[stage_n + 12] (one more row start),
+// in[stage_e + 2].
+__host__ __device__ constexpr size_t team_stage_bytes(int stage_n, int stage_e) {
+    return (size_t)(stage_n + 8) * 4 + (size_t)(stage_n + 12) * 4 + (size_t)(stage_e + 2) * 8;
+}
 constexpr int kTeamSlots = 16;     // payload piece descriptors kept per warp and level
 
-struct __align__(16) TeamStage {
-    int32_t node[kTeamStageN + 8];  // copied from a 16-byte aligned start: up to 3 extra in front
-    int32_t ptr[kTeamStageN + 12];  // row starts p0..p1 (one more than node)
-    int2 in[kTeamStageE + 2];
+// One stage buffer carved out of dynamic shared memory.
+struct TeamStage {
+    int32_t* node;
+    int32_t* ptr;
+    int2* in;
 };
-static_assert(sizeof(TeamStage::node) % 16 == 0 && sizeof(TeamStage::ptr) % 16 == 0 &&
-                  sizeof(TeamStage::in) % 16 == 0, "bulk-copy destinations must be 16-byte multiples");
 
+__device__ __forceinline__ TeamStage team_stage_view(unsigned char* base, int b, int stage_n, int stage_e) {
+    unsigned char* p = base + (size_t)b * team_stage_bytes(stage_n, stage_e);
+    TeamStage st;
+    st.node = reinterpret_cast<int32_t*>(p);
+    st.ptr = st.node + stage_n + 8;
+    st.in = reinterpret_cast<int2*>(st.ptr + stage_n + 12);
+    return st;
+}
 __device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(bar);
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(s), "r"(count) : "memory");
@@ -79,14 +91,14 @@ __device__ __forceinline__ void prefetch_l2_range(const void* p, int64_t bytes) 
     }
 }
 
-__device__ __forceinline__ bool team_fits(const int4 sg) {
-    return sg.y > sg.x && sg.y - sg.x <= kTeamStageN && sg.w - sg.z <= kTeamStageE;
+__device__ __forceinline__ bool team_fits(const TeamArgs& a, const int4 sg) {
+    return sg.y > sg.x && sg.y - sg.x <= a.stage_n && sg.w - sg.z <= a.stage_e;
 }
 
 // Issued by one thread: stage segment sg (positions [x, y), in-edges [z, w)) into st. The
 // level-sorted arrays are allocated with slack so that rounding the ends up to 16 bytes stays
 // inside them.
-__device__ __forceinline__ void team_stage(const TeamArgs& a, TeamStage& st, unsigned long long* bar, const int4 sg) {
+__device__ __forceinline__ void team_stage(const TeamArgs& a, const TeamStage& st, unsigned long long* bar, const int4 sg) {
     const int a0 = sg.x & ~3, a1 = (sg.y + 3) & ~3, b1 = (sg.y + 4) & ~3;
     const int c0 = sg.z & ~1, c1 = (sg.w + 1) & ~1;
     const unsigned bn = (unsigned)(a1 - a0) * 4u, bp = (unsigned)(b1 - a0) * 4u, bi = (unsigned)(c1 - c0) * 8u;
@@ -105,10 +117,24 @@ __device__ __forceinline__ void team_prefetch_seg(const TeamArgs& a, const int4 
 
 // look-ahead for one level, by thread 0 of each CTA: stage it if it fits, else (CTA 0 of the
 // team) prefetch it into L2
-__device__ __forceinline__ void team_ahead(const TeamArgs& a, int rank, TeamStage& st, unsigned long long* bar,
-                                           const int4 sg) {
-    if (team_fits(sg)) team_stage(a, st, bar, sg);
+__device__ __forceinline__ void team_ahead_body(const TeamArgs& a, int rank, const TeamStage& st,
+                                                unsigned long long* bar, const int4 sg) {
+    if (team_fits(a, sg)) team_stage(a, st, bar, sg);
     else if (rank == 0) team_prefetch_seg(a, sg);
+}
+
+// the payload kernel calls it out of line: its address arithmetic would otherwise push the
+// level loop's registers past the three-CTAs-per-SM budget
+__device__ __noinline__ void team_ahead_call(const TeamArgs& a, int rank, const TeamStage& st, unsigned long long* bar,
+                                             const int4 sg) {
+    team_ahead_body(a, rank, st, bar, sg);
+}
+
+template <bool PAY>
+__device__ __forceinline__ void team_ahead(const TeamArgs& a, int rank, const TeamStage& st, unsigned long long* bar,
+                                           const int4 sg) {
+    if (PAY) team_ahead_call(a, rank, st, bar, sg);
+    else team_ahead_body(a, rank, st, bar, sg);
 }
 
 // One payload piece, resolved: pointers already offset to the piece, cnt in elements (saxpy)
@@ -289,7 +315,7 @@ __device__ __forceinline__ uint32_t team_task_key(const TeamArgs& a, int v, cons
 // barrier otherwise). Returns false if a staged copy never landed (the kernel must end).
 template <bool PAY, bool SOLO>
 __device__ __forceinline__ bool team_run_graph(const TeamArgs& a, const TeamJob& job, int k, int rank,
-                                               TeamStage* st, unsigned long long* mbar, int4* ring, int2* iring,
+                                               const TeamStage* sview, unsigned long long* mbar, int4* ring, int2* iring,
                                                TeamPiece* pslots, unsigned& phase) {
     const int t = threadIdx.x;
     const int lane = t & 31;
@@ -302,8 +328,8 @@ __device__ __forceinline__ bool team_run_graph(const TeamArgs& a, const TeamJob&
         for (int q = 0; q < 3 && q < L; ++q) ring[q] = __ldg(a.seg + job.seg0 + q);
         if (PAY)
             for (int q = 0; q < 2 && q < L; ++q) iring[q] = __ldg(a.seg_items + job.seg0 + q);
-        if (L > 0) team_ahead(a, rank, st[0], &mbar[0], ring[0]);
-        if (L > 1) team_ahead(a, rank, st[1], &mbar[1], ring[1]);
+        if (L > 0) team_ahead<PAY>(a, rank, sview[0], &mbar[0], ring[0]);
+        if (L > 1) team_ahead<PAY>(a, rank, sview[1], &mbar[1], ring[1]);
     }
     __syncthreads();
     if (a.g_start && rank == 0 && t == 0) a.g_start[job.graph] = (int64_t)gtimer();
@@ -319,7 +345,9 @@ __device__ __forceinline__ bool team_run_graph(const TeamArgs& a, const TeamJob&
         if (t == 0) {
             if (l + 3 < L) ring[(l + 3) & 3] = __ldg(a.seg + job.seg0 + l + 3);
             if (PAY && l + 2 < L) iring[(l + 2) & 3] = __ldg(a.seg_items + job.seg0 + l + 2);
-            if (l + 2 < L) team_ahead(a, rank, st[(l + 2) % kTeamBufs], &mbar[(l + 2) % kTeamBufs], ring[(l + 2) & 3]);
+            if (l + 2 < L)
+                team_ahead<PAY>(a, rank, sview[(l + 2) % kTeamBufs],
+                           &mbar[(l + 2) % kTeamBufs], ring[(l + 2) & 3]);
         }
         if (PAY && l + 1 < L) {
             const int na1 = team_arrival_warps(ring[(l + 1) & 3], iring[(l + 1) & 3], nwarp);
@@ -333,7 +361,7 @@ __device__ __forceinline__ bool team_run_graph(const TeamArgs& a, const TeamJob&
         const int32_t* node = a.ls_node;
         const int32_t* ptr = a.ls_ptr;
         const int2* in = a.ls_in;
-        if (team_fits(s0)) {
+        if (team_fits(a, s0)) {
             uint64_t t0 = 0;
             while (!mbar_try_wait(&mbar[b], (phase >> b) & 1u)) {
                 const uint64_t now = gtimer();
@@ -346,9 +374,10 @@ __device__ __forceinline__ bool team_run_graph(const TeamArgs& a, const TeamJob&
             }
             phase ^= 1u << b;
             const int nb = s0.x & ~3, eb = s0.z & ~1;
-            node = st[b].node - nb;  // indexed by level-sorted position / in-edge number
-            ptr = st[b].ptr - nb;
-            in = st[b].in - eb;
+            const TeamStage sv = sview[b];
+            node = sv.node - nb;  // indexed by level-sorted position / in-edge number
+            ptr = sv.ptr - nb;
+            in = sv.in - eb;
         }
         if (wid < na) {
             for (int p = s0.x + tid; p < s0.y; p += na * 32) {
@@ -378,7 +407,8 @@ __device__ __forceinline__ bool team_run_graph(const TeamArgs& a, const TeamJob&
 // runs it as one team. Phase 2: every CTA takes solo jobs until none is left.
 template <bool PAY>
 __global__ void __launch_bounds__(kTeamThreads, 3) k_team(const TeamArgs a) {
-    __shared__ TeamStage st[kTeamBufs];
+    extern __shared__ __align__(16) unsigned char s_stage[];  // kTeamBufs stage buffers
+    __shared__ TeamStage s_view[kTeamBufs];
     __shared__ __align__(8) unsigned long long mbar[kTeamBufs];
     __shared__ __align__(16) TeamJob s_job;
     __shared__ int4 s_ring[4];
@@ -386,7 +416,10 @@ __global__ void __launch_bounds__(kTeamThreads, 3) k_team(const TeamArgs a) {
     __shared__ TeamPiece s_piece[2][kTeamSlots * (kTeamThreads / 32)];  // piece descriptors, by level parity
     const int t = threadIdx.x;
     if (t == 0) {
-        for (int b = 0; b < kTeamBufs; ++b) mbar_init(&mbar[b], 1);
+        for (int b = 0; b < kTeamBufs; ++b) {
+            mbar_init(&mbar[b], 1);
+            s_view[b] = team_stage_view(s_stage, b, a.stage_n, a.stage_e);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
@@ -406,7 +439,7 @@ __global__ void __launch_bounds__(kTeamThreads, 3) k_team(const TeamArgs a) {
             const TeamJob job = s_job;
             cluster_sync();  // all have read s_job before CTA 0 may overwrite it
             if (job.graph < 0) break;
-            if (!team_run_graph<PAY, false>(a, job, k, rank, st, mbar, s_ring, s_iring, &s_piece[0][0], phase)) return;
+            if (!team_run_graph<PAY, false>(a, job, k, rank, s_view, mbar, s_ring, s_iring, &s_piece[0][0], phase)) return;
         }
     }
     for (;;) {
@@ -418,7 +451,7 @@ __global__ void __launch_bounds__(kTeamThreads, 3) k_team(const TeamArgs a) {
         const TeamJob job = s_job;
         __syncthreads();
         if (job.graph < 0) break;
-        if (!team_run_graph<PAY, true>(a, job, 1, 0, st, mbar, s_ring, s_iring, &s_piece[0][0], phase)) return;
+        if (!team_run_graph<PAY, true>(a, job, 1, 0, s_view, mbar, s_ring, s_iring, &s_piece[0][0], phase)) return;
     }
 }
 
