@@ -222,6 +222,17 @@ def job_rate(units_all_ranks, ms_max):
     return units_all_ranks / (ms_max / 1e3)
 
 
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -408,7 +419,8 @@ def main():
     if rank == 0 and not args.no_cpu:
         rate, erate, desc = cpu_oracle_rate(wl)
         cpu = {"value": rate, "unit": "tasks/s", "cores": 1, "kind": "oracle", "sample": desc,
-               "edges_per_s": erate, "host_nproc": os.cpu_count()}
+               "edges_per_s": erate, "host_nproc": os.cpu_count(), "host_cpu": cpu_model(),
+               "note": "the oracle is sequential: 1 of %d host cores" % os.cpu_count()}
 
     peak, peak_kind = peaks()
     b_alg = algorithmic_bytes(wl)
@@ -424,6 +436,19 @@ def main():
             "ms_per_launch": kernel_ms / k_launches, "peak_source": peak_kind + " (MEASURED_PEAKS hbm_gbs)"}
     if chosen == hf.HF_MODE_TEAM:
         roof["per"] = "step: %d concurrent team-class launches, bytes and time summed over them" % launches
+    if roof["traffic"] is not None:  # ncu DRAM bytes over the CUDA-event time of the same unit
+        roof["dram_gbs"] = roof["traffic"] / (kernel_ms / k_launches / 1e3) / 1e9
+    # dependency-latency bound beside the bandwidth bound: the deepest graph's chain of levels at
+    # the per-level (per-hop) times measured on the calibration chain
+    t_lvl, t_hop, t_solo, t_cl = hf.hf_calibration(stream)
+    depth = max(g.levels for g in wl.graphs)
+    roof["critical_path"] = {"levels": depth, "ns_per_level": {"levelsync": t_lvl, "persistent_hop": t_hop,
+                                                                "team_cta": t_solo, "team_cluster": t_cl},
+                             "bound_ms": {"levelsync": depth * t_lvl / 1e6, "persistent": depth * t_hop / 1e6,
+                                          "team": depth * t_solo / 1e6}}
+    copy_bytes = sum(4 * int(g.sx_n[j]) for g in wl.graphs for j in list(g.pl_saxpy) + list(g.ps_saxpy))
+    if copy_bytes:
+        roof["host_link"] = {"bytes_per_step": copy_bytes, "gbs": copy_bytes / (ms / 1e3) / 1e9}
     line = {
         "metric": "DAG tasks/s", "value": value, "unit": "tasks/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "ms_per_step_median": ms_med, "higher_is_better": True,

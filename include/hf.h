@@ -174,6 +174,11 @@ hf_status hf_precede_w(hf_graph* g, hf_task a, hf_task b, float delay);
  * no edge is added. */
 hf_status hf_precede_bulk(hf_graph* g, int64_t m, const int32_t* src, const int32_t* dst, const float* delay);
 
+/* Writes the graph in Graphviz DOT to the file at `path` (Section III-A's graph dump): one node
+ * per task labelled "<id> <kind> ..." (maxplus arr0=..., saxpy n=..., pull/push <bytes> B,
+ * host), one edge per dependency labelled with its delay. Host only; any time. */
+hf_status hf_dump(const hf_graph* g, const char* path);
+
 /* Host-side preparation: successor (CSR) and level-sorted predecessor lists, in-degrees,
  * topological levels, cycle check. Optional: hf_run finalizes a changed graph itself. */
 hf_status hf_finalize(hf_graph* g);
@@ -198,6 +203,15 @@ hf_status hf_get_levels(const hf_graph* g, int32_t* level_out);
  * defaults. Device-side failures are reported by hf_sync_status. Re-running a graph re-runs
  * every payload (saxpy updates y again). */
 hf_status hf_run(hf_graph* g, void* stream, const hf_run_opts* opts);
+
+/* Section III-B's run_n and run_until. hf_run_n enqueues n runs back to back on `stream` (the
+ * plan is reused; payloads apply n times) and returns at once; hf_sync_status then reports the
+ * first failure of the n runs. hf_run_until runs, waits and calls pred(ctx) on the calling
+ * thread after each run until it returns nonzero or max_runs runs have completed (*runs_out:
+ * runs done); a failed run ends the loop with its status. Batch forms below. */
+hf_status hf_run_n(hf_graph* g, void* stream, const hf_run_opts* opts, int32_t n);
+hf_status hf_run_until(hf_graph* g, void* stream, const hf_run_opts* opts, int32_t (*pred)(void* ctx), void* ctx,
+                       int32_t max_runs, int32_t* runs_out);
 
 /* Waits for the graph's last run and returns its device status (HF_OK, HF_ETIMEDOUT, ...). */
 hf_status hf_sync_status(hf_graph* g);
@@ -239,6 +253,9 @@ hf_status hf_batch_destroy(hf_batch* b);
 hf_status hf_batch_add(hf_batch* b, hf_graph* g, int32_t* index_out);
 hf_status hf_batch_run(hf_batch* b, void* stream, const hf_run_opts* opts);
 hf_status hf_batch_sync_status(hf_batch* b);
+hf_status hf_batch_run_n(hf_batch* b, void* stream, const hf_run_opts* opts, int32_t n);
+hf_status hf_batch_run_until(hf_batch* b, void* stream, const hf_run_opts* opts, int32_t (*pred)(void* ctx),
+                             void* ctx, int32_t max_runs, int32_t* runs_out);
 /* Arrivals of graph `index` (its n floats), as hf_get_arrivals; index -1: every graph's
  * arrivals concatenated in batch order (sum of their task counts) in one copy. */
 hf_status hf_batch_get_arrivals(hf_batch* b, int32_t index, float* out, int on_device);
@@ -351,6 +368,11 @@ hf_status hf_batch_autotune(hf_batch* b, void* stream, const hf_run_opts* base, 
  * attached, else HEURISTIC). */
 hf_status hf_batch_predict(hf_batch* b, int32_t priority, void* stream, float* levelsync_ms, float* persistent_ms,
                            float* team_ms);
+/* The machine constants behind the predictions (ns), measured on the calibration chain on first
+ * use in this process (2,048 tasks, one per level, on the current device): level-synchronous time
+ * per level, persistent time per dependent hop, team time per level on one CTA and on a
+ * cluster. out[4]. Blocks the first time. */
+hf_status hf_calibration(void* stream, float* out);
 
 /* --- allocation-free entry point -------------------------------------------------------
  * The paper has no counterpart to this call; it exists for callers that cannot allocate

@@ -3,6 +3,7 @@
 // predecessor lists, in-degrees, topological levels, cycle check), batches, the allocator hook
 // and error reporting. Execution lives in plan.cu.
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -462,6 +463,39 @@ hf_status hf_get_levels(const hf_graph* g, int32_t* level_out) {
     return HF_OK;
 }
 
+// Graphviz text of the graph: one node per task labelled with its id and kind (saxpy: size;
+// copies: bytes; max-plus: source arrival when it has one), one edge per dependency labelled
+// with its delay (%.9g round-trips binary32).
+hf_status hf_dump(const hf_graph* g, const char* path) {
+    if (!g || !path) return fail(HF_EINVAL, "NULL argument");
+    FILE* f = std::fopen(path, "w");
+    if (!f) return fail(HF_EINVAL, std::string("cannot open ") + path);
+    std::fprintf(f, "digraph hf {\n  node [shape=box];\n");
+    for (size_t v = 0; v < g->kind.size(); ++v) {
+        const int k = g->kind[v];
+        const int32_t pi = g->pay[v];
+        const hf::PayloadRec* r = pi >= 0 ? &g->payloads[(size_t)pi] : nullptr;
+        char label[96];
+        if (k == HF_KERNEL && r && r->op != HF_K_MAXPLUS)
+            std::snprintf(label, sizeof label, "%zu saxpy%s n=%lld", v, r->op == HF_K_SAXPY_I32 ? "_i32" : "",
+                          (long long)r->n);
+        else if (k == HF_KERNEL)
+            std::snprintf(label, sizeof label, "%zu maxplus arr0=%.9g", v, g->arr0.empty() ? 0.0 : (double)g->arr0[v]);
+        else if (k == HF_PULL && r)
+            std::snprintf(label, sizeof label, "%zu pull %zu B", v, r->bytes);
+        else if (k == HF_PUSH && r)
+            std::snprintf(label, sizeof label, "%zu push %zu B", v, r->bytes);
+        else
+            std::snprintf(label, sizeof label, "%zu host", v);
+        std::fprintf(f, "  t%zu [label=\"%s\"];\n", v, label);
+    }
+    for (size_t e = 0; e < g->esrc.size(); ++e)
+        std::fprintf(f, "  t%d -> t%d [label=\"%.9g\"];\n", g->esrc[e], g->edst[e], (double)g->edly[e]);
+    std::fprintf(f, "}\n");
+    const bool ok = std::fclose(f) == 0;
+    return ok ? HF_OK : fail(HF_EINVAL, std::string("write failed: ") + path);
+}
+
 static hf_status ensure_plan(hf_graph* g) {
     if (g->dirty) {
         if (g->in_batches > 0) return fail(HF_ESTATE, "graph belongs to a batch");
@@ -486,6 +520,38 @@ hf_status hf_run(hf_graph* g, void* stream, const hf_run_opts* opts) {
     if (opts) o = *opts;
     else hf_run_opts_default(&o);
     return plan_run(g->plan, (cudaStream_t)stream, o);
+}
+
+hf_status hf_run_n(hf_graph* g, void* stream, const hf_run_opts* opts, int32_t n) {
+    if (!g) return fail(HF_EINVAL, "graph is NULL");
+    if (n < 0) return fail(HF_EINVAL, "n < 0");
+    for (int32_t i = 0; i < n; ++i) {
+        hf_status st = i == 0 ? hf_run(g, stream, opts) : HF_OK;
+        if (i > 0) {
+            hf_run_opts o;
+            if (opts) o = *opts;
+            else hf_run_opts_default(&o);
+            st = plan_run(g->plan, (cudaStream_t)stream, o, true);
+        }
+        if (st != HF_OK) return st;
+    }
+    return HF_OK;
+}
+
+hf_status hf_run_until(hf_graph* g, void* stream, const hf_run_opts* opts, int32_t (*pred)(void* ctx), void* ctx,
+                       int32_t max_runs, int32_t* runs_out) {
+    if (!g || !pred) return fail(HF_EINVAL, "NULL argument");
+    if (max_runs < 0) return fail(HF_EINVAL, "max_runs < 0");
+    int32_t runs = 0;
+    hf_status st = HF_OK;
+    while (runs < max_runs) {
+        if ((st = hf_run(g, stream, opts)) != HF_OK) break;
+        if ((st = hf_sync_status(g)) != HF_OK) break;
+        ++runs;
+        if (pred(ctx)) break;
+    }
+    if (runs_out) *runs_out = runs;
+    return st;
 }
 
 hf_status hf_sync_status(hf_graph* g) {
@@ -638,6 +704,11 @@ hf_status hf_batch_predict(hf_batch* b, int32_t priority, void* stream, float* l
     return plan_predict(b->plan, priority, b->cm, (cudaStream_t)stream, levelsync_ms, persistent_ms, team_ms);
 }
 
+hf_status hf_calibration(void* stream, float* out) {
+    if (!out) return fail(HF_EINVAL, "NULL argument");
+    return plan_calibration((cudaStream_t)stream, out);
+}
+
 hf_status hf_batch_bottom_levels(hf_batch* b, const float* cost, float* bottom, void* stream) {
     if (!b) return fail(HF_EINVAL, "batch is NULL");
     hf_status st = ensure_batch_plan(b);
@@ -655,6 +726,40 @@ hf_status hf_batch_run(hf_batch* b, void* stream, const hf_run_opts* opts) {
     if (opts) o = *opts;
     else hf_run_opts_default(&o);
     return plan_run(b->plan, (cudaStream_t)stream, o);
+}
+
+hf_status hf_batch_run_n(hf_batch* b, void* stream, const hf_run_opts* opts, int32_t n) {
+    if (!b) return fail(HF_EINVAL, "batch is NULL");
+    if (n < 0) return fail(HF_EINVAL, "n < 0");
+    for (int32_t i = 0; i < n; ++i) {
+        hf_status st = HF_OK;
+        if (i == 0) {
+            st = hf_batch_run(b, stream, opts);
+        } else {
+            hf_run_opts o;
+            if (opts) o = *opts;
+            else hf_run_opts_default(&o);
+            st = plan_run(b->plan, (cudaStream_t)stream, o, true);
+        }
+        if (st != HF_OK) return st;
+    }
+    return HF_OK;
+}
+
+hf_status hf_batch_run_until(hf_batch* b, void* stream, const hf_run_opts* opts, int32_t (*pred)(void* ctx),
+                             void* ctx, int32_t max_runs, int32_t* runs_out) {
+    if (!b || !pred) return fail(HF_EINVAL, "NULL argument");
+    if (max_runs < 0) return fail(HF_EINVAL, "max_runs < 0");
+    int32_t runs = 0;
+    hf_status st = HF_OK;
+    while (runs < max_runs) {
+        if ((st = hf_batch_run(b, stream, opts)) != HF_OK) break;
+        if ((st = hf_batch_sync_status(b)) != HF_OK) break;
+        ++runs;
+        if (pred(ctx)) break;
+    }
+    if (runs_out) *runs_out = runs;
+    return st;
 }
 
 hf_status hf_batch_sync_status(hf_batch* b) {

@@ -121,6 +121,7 @@ struct ResetArgs {
     int32_t n_seed;
     int32_t n_pay;
     int32_t stall_task;  // test hook: this task's counter starts one too high (-1: none)
+    int32_t keep_status; // leave ctrl->status as the previous run left it
     int32_t n_pseed;     // payload seed items
     int32_t pqcap;
     int32_t split;       // payload seeds go to the payload queue (else to the main queue)
@@ -272,7 +273,9 @@ void dev_free(void* p, cudaStream_t s);
 // plan.cu
 hf_status plan_build(const std::vector<hf_graph*>& graphs, Plan** out);
 void plan_destroy(Plan* p);
-hf_status plan_run(Plan* p, cudaStream_t s, const hf_run_opts& o);
+// keep_status: a later run of a sequence (hf_run_n) keeps the device status word of the runs
+// before it, so the sequence reports its first failure
+hf_status plan_run(Plan* p, cudaStream_t s, const hf_run_opts& o, bool keep_status = false);
 hf_status plan_sync(Plan* p);
 hf_status plan_busy(Plan* p);  // HF_ESTATE while a run is in flight
 hf_status plan_get_arrivals(Plan* p, int32_t gi, float* out, int on_device);
@@ -291,6 +294,7 @@ void plan_set_costmodel(Plan* p, const hf_costmodel* cm);
 hf_status plan_bottom_levels(Plan* p, const float* cost, float* bottom, cudaStream_t s);
 hf_status plan_autotune(Plan* p, cudaStream_t s, const hf_run_opts& base, int force, hf_run_opts* best,
                         float* best_ms);
+hf_status plan_calibration(cudaStream_t s, float* out);
 hf_status plan_predict(Plan* p, int32_t priority, const hf_costmodel* cm, cudaStream_t s, float* ls_ms,
                        float* p_ms, float* t_ms);
 

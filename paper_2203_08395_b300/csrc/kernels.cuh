@@ -356,7 +356,7 @@ __global__ void k_reset(const ResetArgs a) {
         a.ctrl->phead = 0;
         a.ctrl->ptail = a.split ? a.n_pseed : 0;
         a.ctrl->done = 0;
-        a.ctrl->status = 0;
+        if (!a.keep_status) a.ctrl->status = 0;
         a.ctrl->abort = 0;
         a.ctrl->ticket = 0;
     }

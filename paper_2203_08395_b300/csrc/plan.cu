@@ -668,7 +668,7 @@ hf_status plan_busy(Plan* p) {
     return HF_OK;
 }
 
-hf_status plan_run(Plan* p, cudaStream_t s, const hf_run_opts& o) {
+hf_status plan_run(Plan* p, cudaStream_t s, const hf_run_opts& o, bool keep_status) {
     int mode = o.mode;
     if (mode == HF_MODE_AUTO) {
         if (!p->host_tasks.empty()) {
@@ -696,7 +696,7 @@ hf_status plan_run(Plan* p, cudaStream_t s, const hf_run_opts& o) {
     if (st != HF_OK) return st;
     const bool instr = (o.instrument & 1) != 0, valid = o.validate != 0;
     if ((st = ensure_instr(p, instr, valid, s)) != HF_OK) return st;
-    cudaError_t e = cudaMemsetAsync(&p->d_ctrl->status, 0, sizeof(int32_t), s);
+    cudaError_t e = keep_status ? cudaSuccess : cudaMemsetAsync(&p->d_ctrl->status, 0, sizeof(int32_t), s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
     if (p->n > 0) {
         if (mode == HF_MODE_LEVELSYNC) {
@@ -800,6 +800,7 @@ hf_status plan_run(Plan* p, cudaStream_t s, const hf_run_opts& o) {
             r.tk_end = valid ? p->d_tk_end : nullptr;
             r.exec_count = valid ? p->d_exec : nullptr;
             r.stall_task = (o.stall_task >= 0 && o.stall_task < p->n) ? o.stall_task : -1;
+            r.keep_status = keep_status ? 1 : 0;
             const int64_t work = std::max<int64_t>(p->n, p->qcap);
             const int rgrid = (int)std::min<int64_t>((work + 255) / 256, (int64_t)p->num_sms * 16);
             k_reset<<<std::max(rgrid, 1), 256, 0, s>>>(r);
@@ -1406,6 +1407,16 @@ static hf_status calibrate(cudaStream_t s) {
     g_t_team_solo_ns = 1e6f * ts / (float)n;
     g_t_team_cluster_ns = 1e6f * tc / (float)n;
     g_cal_done = true;
+    return HF_OK;
+}
+
+hf_status plan_calibration(cudaStream_t s, float* out) {
+    hf_status st = calibrate(s);
+    if (st != HF_OK) return st;
+    out[0] = g_t_level_ns;
+    out[1] = g_t_hop_ns;
+    out[2] = g_t_team_solo_ns;
+    out[3] = g_t_team_cluster_ns;
     return HF_OK;
 }
 

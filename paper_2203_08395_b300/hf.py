@@ -74,6 +74,7 @@ class hf_graph_info_t(ctypes.Structure):
                 ("finalized", ctypes.c_int32), ("pad_", ctypes.c_int32)]
 
 
+PRED_FN = ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.c_void_p)
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
 
@@ -142,6 +143,12 @@ def load():
         "hf_run_csr_noalloc": [i32, i32, vp, vp, vp, vp, vp, ctypes.c_uint64, vp],
         "hf_batch_get_graph_times": [vp, vp, vp],
         "hf_batch_last_launches": [vp, P(i32)],
+        "hf_calibration": [vp, vp],
+        "hf_dump": [vp, ctypes.c_char_p],
+        "hf_run_n": [vp, vp, P(hf_run_opts), i32],
+        "hf_batch_run_n": [vp, vp, P(hf_run_opts), i32],
+        "hf_run_until": [vp, vp, P(hf_run_opts), PRED_FN, vp, i32, P(i32)],
+        "hf_batch_run_until": [vp, vp, P(hf_run_opts), PRED_FN, vp, i32, P(i32)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -496,6 +503,45 @@ def hf_batch_last_launches(b):
     n = ctypes.c_int32()
     _check(load().hf_batch_last_launches(b, ctypes.byref(n)), "hf_batch_last_launches")
     return n.value
+
+
+def hf_calibration(stream=None):
+    """(level-sync ns/level, persistent ns/hop, team ns/level on one CTA, on a cluster)."""
+    out = np.zeros(4, np.float32)
+    _check(load().hf_calibration(_stream_handle(stream), out.ctypes.data), "hf_calibration")
+    return tuple(float(x) for x in out)
+
+
+def hf_dump(g, path):
+    _check(load().hf_dump(g, os.fsencode(path)), "hf_dump")
+
+
+def hf_run_n(g, n, stream=None, opts=None):
+    o = opts if opts is not None else hf_run_opts_default()
+    _check(load().hf_run_n(g, _stream_handle(stream), ctypes.byref(o), n), "hf_run_n")
+
+
+def hf_batch_run_n(b, n, stream=None, opts=None):
+    o = opts if opts is not None else hf_run_opts_default()
+    _check(load().hf_batch_run_n(b, _stream_handle(stream), ctypes.byref(o), n), "hf_batch_run_n")
+
+
+def _run_until(fn, obj, pred, max_runs, stream, opts, where):
+    o = opts if opts is not None else hf_run_opts_default()
+    cb = PRED_FN(lambda ctx: 1 if pred() else 0)
+    runs = ctypes.c_int32()
+    _check(fn(obj, _stream_handle(stream), ctypes.byref(o), cb, None, max_runs, ctypes.byref(runs)), where)
+    return runs.value
+
+
+def hf_run_until(g, pred, max_runs, stream=None, opts=None):
+    """Runs until pred() (a Python callable, called after each completed run) is true or
+    max_runs runs completed; returns the number of runs."""
+    return _run_until(load().hf_run_until, g, pred, max_runs, stream, opts, "hf_run_until")
+
+
+def hf_batch_run_until(b, pred, max_runs, stream=None, opts=None):
+    return _run_until(load().hf_batch_run_until, b, pred, max_runs, stream, opts, "hf_batch_run_until")
 
 
 STAT_NAMES = ["rounds", "items", "idle", "edges", "cas", "push_local", "push_global", "claims", "pops", "pieces",
