@@ -179,6 +179,14 @@ hf_status hf_precede_bulk(hf_graph* g, int64_t m, const int32_t* src, const int3
  * host), one edge per dependency labelled with its delay. Host only; any time. */
 hf_status hf_dump(const hf_graph* g, const char* path);
 
+/* Device placement (Section III-C, Algorithm 1): kernel tasks are grouped with the pull tasks
+ * whose buffers they use, and push tasks with the pull they read (union-find), so that a group
+ * never spans devices; the groups are packed onto ndev devices by decreasing cost, each onto the
+ * least-loaded device. cost: host float[n] per-task costs, or NULL for the heuristic
+ * 300 ns + 30 ns per out-edge + payload bytes / 8 bytes per ns. dev_out: host int32[n], the
+ * device of each task, -1 for host tasks. Host only. */
+hf_status hf_place(const hf_graph* g, int32_t ndev, const float* cost, int32_t* dev_out);
+
 /* Host-side preparation: successor (CSR) and level-sorted predecessor lists, in-degrees,
  * topological levels, cycle check. Optional: hf_run finalizes a changed graph itself. */
 hf_status hf_finalize(hf_graph* g);
@@ -254,6 +262,11 @@ hf_status hf_batch_add(hf_batch* b, hf_graph* g, int32_t* index_out);
 hf_status hf_batch_run(hf_batch* b, void* stream, const hf_run_opts* opts);
 hf_status hf_batch_sync_status(hf_batch* b);
 hf_status hf_batch_run_n(hf_batch* b, void* stream, const hf_run_opts* opts, int32_t n);
+/* Sharding of a batch over ndev devices (one process per GPU, each running its own share):
+ * graphs packed by decreasing heuristic cost (the sum of hf_place's per-task heuristic), each onto
+ * the least-loaded device. dev_of_graph: host int32[graphs]; load_out: host double[ndev] or NULL.
+ * Host only. */
+hf_status hf_batch_partition(const hf_batch* b, int32_t ndev, int32_t* dev_of_graph, double* load_out);
 hf_status hf_batch_run_until(hf_batch* b, void* stream, const hf_run_opts* opts, int32_t (*pred)(void* ctx),
                              void* ctx, int32_t max_runs, int32_t* runs_out);
 /* Arrivals of graph `index` (its n floats), as hf_get_arrivals; index -1: every graph's

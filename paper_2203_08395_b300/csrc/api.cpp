@@ -2,6 +2,7 @@
 // kinds, explicit edges, acyclic graphs), host-side finalization (successor CSR, level-sorted
 // predecessor lists, in-degrees, topological levels, cycle check), batches, the allocator hook
 // and error reporting. Execution lives in plan.cu.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -496,6 +497,96 @@ hf_status hf_dump(const hf_graph* g, const char* path) {
     return ok ? HF_OK : fail(HF_EINVAL, std::string("write failed: ") + path);
 }
 
+// ----------------------------------------------------------------------- device placement
+
+// Heuristic task cost on the host (the same formula as the device's heuristic cost model):
+// 300 ns + 30 ns per out-edge + payload bytes at 8 bytes/ns (saxpy 12 bytes per element,
+// copies their bytes twice).
+static double host_heuristic_cost(const hf_graph* g, int32_t v, int32_t fanout) {
+    double bytes = 0.0;
+    const int32_t pi = g->pay[(size_t)v];
+    if (pi >= 0) {
+        const hf::PayloadRec& r = g->payloads[(size_t)pi];
+        if (r.kind == HF_KERNEL && r.op != HF_K_MAXPLUS) bytes = 12.0 * (double)r.n;
+        else if (r.kind == HF_PULL || r.kind == HF_PUSH) bytes = 2.0 * (double)r.bytes;
+    }
+    return 300.0 + 30.0 * fanout + bytes / 8.0;
+}
+
+static int32_t uf_find(std::vector<int32_t>& up, int32_t x) {
+    while (up[(size_t)x] != x) {
+        up[(size_t)x] = up[(size_t)up[(size_t)x]];
+        x = up[(size_t)x];
+    }
+    return x;
+}
+
+// Greedy longest-processing-time packing: items in decreasing cost (ties: lower index first),
+// each onto the least-loaded device (ties: lower device).
+static void lpt_pack(const std::vector<double>& cost, int32_t ndev, std::vector<int32_t>* dev, std::vector<double>* load) {
+    std::vector<int32_t> order(cost.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (int32_t)i;
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return cost[(size_t)a] > cost[(size_t)b]; });
+    load->assign((size_t)ndev, 0.0);
+    dev->assign(cost.size(), 0);
+    for (int32_t i : order) {
+        int32_t best = 0;
+        for (int32_t d = 1; d < ndev; ++d)
+            if ((*load)[(size_t)d] < (*load)[(size_t)best]) best = d;
+        (*dev)[(size_t)i] = best;
+        (*load)[(size_t)best] += cost[(size_t)i];
+    }
+}
+
+hf_status hf_place(const hf_graph* g, int32_t ndev, const float* cost, int32_t* dev_out) {
+    if (!g || !dev_out) return fail(HF_EINVAL, "NULL argument");
+    if (ndev < 1) return fail(HF_EINVAL, "ndev < 1");
+    const int32_t n = (int32_t)g->kind.size();
+    try {
+        // groups: a kernel task with the pulls it reads or writes, a push with the pull it reads
+        std::vector<int32_t> up((size_t)n);
+        for (int32_t v = 0; v < n; ++v) up[(size_t)v] = v;
+        auto unite = [&](int32_t a, int32_t b) {
+            a = uf_find(up, a);
+            b = uf_find(up, b);
+            if (a != b) up[(size_t)std::max(a, b)] = std::min(a, b);
+        };
+        std::vector<int32_t> fanout((size_t)n, 0);
+        for (int32_t u : g->esrc) fanout[(size_t)u] += 1;
+        for (int32_t v = 0; v < n; ++v) {
+            const int32_t pi = g->pay[(size_t)v];
+            if (pi < 0) continue;
+            const hf::PayloadRec& r = g->payloads[(size_t)pi];
+            if (r.kind == HF_KERNEL && r.op != HF_K_MAXPLUS) {
+                if (r.x_pull >= 0) unite(v, r.x_pull);
+                if (r.y_pull >= 0) unite(v, r.y_pull);
+            } else if (r.kind == HF_PUSH && r.src_pull >= 0) {
+                unite(v, r.src_pull);
+            }
+        }
+        // group costs, then LPT over the groups (host tasks stay on the CPU: -1)
+        std::vector<int32_t> gid((size_t)n, -1), root_gid((size_t)n, -1);
+        std::vector<double> gcost;
+        for (int32_t v = 0; v < n; ++v) {
+            if (g->kind[(size_t)v] == HF_HOST) continue;
+            const int32_t r = uf_find(up, v);
+            if (root_gid[(size_t)r] < 0) {
+                root_gid[(size_t)r] = (int32_t)gcost.size();
+                gcost.push_back(0.0);
+            }
+            gid[(size_t)v] = root_gid[(size_t)r];
+            gcost[(size_t)gid[(size_t)v]] += cost ? (double)cost[v] : host_heuristic_cost(g, v, fanout[(size_t)v]);
+        }
+        std::vector<int32_t> gdev;
+        std::vector<double> load;
+        lpt_pack(gcost, ndev, &gdev, &load);
+        for (int32_t v = 0; v < n; ++v) dev_out[v] = gid[(size_t)v] < 0 ? -1 : gdev[(size_t)gid[(size_t)v]];
+    } catch (const std::bad_alloc&) {
+        return fail(HF_ENOMEM, "host allocation failed");
+    }
+    return HF_OK;
+}
+
 static hf_status ensure_plan(hf_graph* g) {
     if (g->dirty) {
         if (g->in_batches > 0) return fail(HF_ESTATE, "graph belongs to a batch");
@@ -760,6 +851,29 @@ hf_status hf_batch_run_until(hf_batch* b, void* stream, const hf_run_opts* opts,
     }
     if (runs_out) *runs_out = runs;
     return st;
+}
+
+hf_status hf_batch_partition(const hf_batch* b, int32_t ndev, int32_t* dev_of_graph, double* load_out) {
+    if (!b || !dev_of_graph) return fail(HF_EINVAL, "NULL argument");
+    if (ndev < 1) return fail(HF_EINVAL, "ndev < 1");
+    try {
+        std::vector<double> cost(b->graphs.size(), 0.0);
+        for (size_t i = 0; i < b->graphs.size(); ++i) {
+            const hf_graph* g = b->graphs[i];
+            std::vector<int32_t> fanout(g->kind.size(), 0);
+            for (int32_t u : g->esrc) fanout[(size_t)u] += 1;
+            for (int32_t v = 0; v < (int32_t)g->kind.size(); ++v) cost[i] += host_heuristic_cost(g, v, fanout[(size_t)v]);
+        }
+        std::vector<int32_t> dev;
+        std::vector<double> load;
+        lpt_pack(cost, ndev, &dev, &load);
+        for (size_t i = 0; i < dev.size(); ++i) dev_of_graph[i] = dev[i];
+        if (load_out)
+            for (int32_t d = 0; d < ndev; ++d) load_out[d] = load[(size_t)d];
+    } catch (const std::bad_alloc&) {
+        return fail(HF_ENOMEM, "host allocation failed");
+    }
+    return HF_OK;
 }
 
 hf_status hf_batch_sync_status(hf_batch* b) {

@@ -145,6 +145,8 @@ def load():
         "hf_batch_last_launches": [vp, P(i32)],
         "hf_calibration": [vp, vp],
         "hf_dump": [vp, ctypes.c_char_p],
+        "hf_place": [vp, i32, vp, vp],
+        "hf_batch_partition": [vp, i32, vp, vp],
         "hf_run_n": [vp, vp, P(hf_run_opts), i32],
         "hf_batch_run_n": [vp, vp, P(hf_run_opts), i32],
         "hf_run_until": [vp, vp, P(hf_run_opts), PRED_FN, vp, i32, P(i32)],
@@ -510,6 +512,22 @@ def hf_calibration(stream=None):
     out = np.zeros(4, np.float32)
     _check(load().hf_calibration(_stream_handle(stream), out.ctypes.data), "hf_calibration")
     return tuple(float(x) for x in out)
+
+
+def hf_place(g, n_tasks, ndev, cost=None):
+    """Device of each task (int32 array; -1 for host tasks)."""
+    out = np.empty(n_tasks, np.int32)
+    c = None if cost is None else np.ascontiguousarray(cost, np.float32)
+    _check(load().hf_place(g, ndev, None if c is None else c.ctypes.data, out.ctypes.data), "hf_place")
+    return out
+
+
+def hf_batch_partition(b, n_graphs, ndev):
+    """(device of each graph, load of each device)."""
+    dev = np.empty(n_graphs, np.int32)
+    loads = np.empty(ndev, np.float64)
+    _check(load().hf_batch_partition(b, ndev, dev.ctypes.data, loads.ctypes.data), "hf_batch_partition")
+    return dev, loads
 
 
 def hf_dump(g, path):
