@@ -93,8 +93,11 @@ typedef struct { const void* host_ptr; size_t bytes; } hf_pull_payload;
  * buffer (Section III-A "Push Task") or, when src_pull == -1, from device pointer src_dev. */
 typedef struct { hf_task src_pull; int32_t pad_; const void* src_dev; void* host_ptr; size_t bytes; } hf_push_payload;
 
-/* kind HF_HOST: fn(arg) runs on a CPU thread (Section III-A "Host Task"). Supported by the
- * level-synchronous executor only (it becomes a host node of the CUDA graph). */
+/* kind HF_HOST: fn(arg) runs on a CPU thread (Section III-A "Host Task"). The level-synchronous
+ * executor makes it a host node of its CUDA graph; the team executor posts it, once its level's
+ * device work is done, to a mailbox in mapped page-locked memory where a proxy thread of the
+ * library runs it and raises its done flag, which the device waits for (bounded by
+ * spin_limit_ns) before the next level. The persistent executor returns HF_ENOTSUP. */
 typedef struct { void (*fn)(void* arg); void* arg; } hf_host_payload;
 
 /* --- run options ---------------------------------------------------------------------- */

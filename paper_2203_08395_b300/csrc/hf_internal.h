@@ -177,6 +177,11 @@ struct TeamArgs {
     uint64_t spin_limit_ns;
     int64_t* g_start;        // instrument: %globaltimer per graph at job start / end (else NULL)
     int64_t* g_end;
+    const int2* seg_host;    // host tasks: (graph, level) segment -> range in host_order (NULL: none)
+    const int32_t* host_order;
+    int32_t* post;           // mapped host memory: the i-th posted host task
+    const int32_t* hdone;    // mapped host memory: host task k has run
+    int32_t* post_ctr;       // device counter of posts
 };
 
 // Arguments of one level kernel of the level-synchronous executor.

@@ -9,7 +9,10 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <atomic>
+#include <chrono>
 #include <mutex>
+#include <thread>
 #include <queue>
 #include <string>
 #include <tuple>
@@ -25,6 +28,7 @@ struct HostTask {
     int32_t level;
     void (*fn)(void*);
     void* arg;
+    int32_t graph;  // batch index of its graph
 };
 
 struct Plan {
@@ -66,6 +70,15 @@ struct Plan {
     cudaEvent_t tev_join[4] = {nullptr, nullptr, nullptr, nullptr};
     int32_t* d_team = nullptr;        // control words (job counters), kTeamWords per class
     int32_t stage_n = 4, stage_e = 2;  // stage buffer capacities (tasks, in-edges per level)
+    // team executor's host tasks: a mailbox in mapped page-locked memory and a proxy thread
+    int2* d_seg_host = nullptr;       // (graph, level) segment -> host-task range in host_order
+    int32_t* d_host_order = nullptr;  // host-task indices grouped by segment
+    int32_t* h_post = nullptr;        // mapped: the i-th posted host task (-1: not yet)
+    int32_t* h_hdone = nullptr;       // mapped: 1 once host task k has run
+    int32_t* d_post = nullptr;        // device views of the two
+    int32_t* d_hdone = nullptr;
+    int32_t* d_post_ctr = nullptr;    // posts so far (device counter)
+    std::thread proxy;                // runs the host tasks of the current run
     int32_t team_for[4] = {-1, -1, -1, -1};  // priority, team_size, CTAs, scale the jobs were built for
     const hf_costmodel* team_cm = nullptr;
 
@@ -209,6 +222,9 @@ static uint32_t host_f2key(float f) {
 void plan_destroy(Plan* p) {
     if (!p) return;
     if (p->ran && p->done_ev) cudaEventSynchronize(p->done_ev);
+    if (p->proxy.joinable()) p->proxy.join();
+    if (p->h_post) cudaFreeHost(p->h_post);
+    if (p->h_hdone) cudaFreeHost(p->h_hdone);
     if (p->lexec) cudaGraphExecDestroy(p->lexec);
     if (p->lgraph) cudaGraphDestroy(p->lgraph);
     for (void* d : p->owned) dev_free(d, nullptr);
@@ -378,7 +394,7 @@ hf_status plan_build(const std::vector<hf_graph*>& graphs, Plan** out) {
                 if (k < 0) continue;
                 const PayloadRec& r = g->payloads[(size_t)k];
                 if (r.kind == HF_HOST) {
-                    p->host_tasks.push_back(HostTask{g->fin.level[(size_t)v], r.fn, r.arg});
+                    p->host_tasks.push_back(HostTask{g->fin.level[(size_t)v], r.fn, r.arg, i});
                     continue;
                 }
                 DevPayload d;
@@ -668,6 +684,72 @@ hf_status plan_busy(Plan* p) {
     return HF_OK;
 }
 
+// Team executor, host tasks: per-segment lists of host-task indices on the device and the
+// mailbox in mapped page-locked memory (built once); before every run the previous run must be
+// over (its kernel may still wait on a done flag) and the mailbox is cleared.
+static hf_status team_host_setup(Plan* p, cudaStream_t s) {
+    const size_t nh = p->host_tasks.size();
+    if (!p->h_post) {
+        std::vector<int2> seg_host(p->h_seg.size(), make_int2(0, 0));
+        std::vector<int32_t> order(nh);
+        std::vector<int32_t> cnt(p->h_seg.size() + 1, 0);
+        for (size_t k = 0; k < nh; ++k) {
+            const HostTask& h = p->host_tasks[k];
+            cnt[(size_t)(p->seg_first[(size_t)h.graph] + h.level) + 1] += 1;
+        }
+        for (size_t q = 0; q < p->h_seg.size(); ++q) cnt[q + 1] += cnt[q];
+        std::vector<int32_t> fill(cnt.begin(), cnt.end() - 1);
+        for (size_t k = 0; k < nh; ++k) {
+            const HostTask& h = p->host_tasks[k];
+            const size_t q = (size_t)(p->seg_first[(size_t)h.graph] + h.level);
+            order[(size_t)fill[q]++] = (int32_t)k;
+        }
+        for (size_t q = 0; q < p->h_seg.size(); ++q) seg_host[q] = make_int2(cnt[q], cnt[q + 1]);
+        hf_status st;
+        if ((st = upload(p, &p->d_seg_host, seg_host.data(), seg_host.size(), s, "host segments")) != HF_OK) return st;
+        if ((st = upload(p, &p->d_host_order, order.data(), order.size(), s, "host order")) != HF_OK) return st;
+        p->d_post_ctr = (int32_t*)palloc(p, 16, s);
+        if (!p->d_post_ctr) return fail(HF_ENOMEM, "device allocation failed: host mailbox");
+        cudaError_t e = cudaHostAlloc((void**)&p->h_post, sizeof(int32_t) * nh, cudaHostAllocMapped);
+        if (e == cudaSuccess) e = cudaHostAlloc((void**)&p->h_hdone, sizeof(int32_t) * nh, cudaHostAllocMapped);
+        if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&p->d_post, p->h_post, 0);
+        if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&p->d_hdone, p->h_hdone, 0);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(e, "host mailbox");
+    }
+    if (p->ran) {
+        cudaError_t e = cudaEventSynchronize(p->done_ev);
+        if (e != cudaSuccess) return cuda_fail(e, "previous run");
+    }
+    if (p->proxy.joinable()) p->proxy.join();
+    for (size_t k = 0; k < nh; ++k) {
+        __atomic_store_n(&p->h_post[k], -1, __ATOMIC_RELAXED);
+        __atomic_store_n(&p->h_hdone[k], 0, __ATOMIC_RELAXED);
+    }
+    std::atomic_thread_fence(std::memory_order_seq_cst);
+    return HF_OK;
+}
+
+// Host proxy of a team run: runs the host tasks in the order the device posts them and raises
+// each one's done flag. Gives up after limit_ns without a new post (the run ended early).
+static void team_host_proxy(Plan* p, uint64_t limit_ns) {
+    const size_t nh = p->host_tasks.size();
+    auto last = std::chrono::steady_clock::now();
+    for (size_t i = 0; i < nh; ++i) {
+        int32_t k;
+        while ((k = __atomic_load_n(&p->h_post[i], __ATOMIC_ACQUIRE)) < 0) {
+            if ((uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now() - last)
+                    .count() > limit_ns)
+                return;
+            std::this_thread::yield();
+        }
+        const HostTask& h = p->host_tasks[(size_t)k];
+        if (h.fn) h.fn(h.arg);
+        __atomic_store_n(&p->h_hdone[k], 1, __ATOMIC_RELEASE);
+        last = std::chrono::steady_clock::now();
+    }
+}
+
 hf_status plan_run(Plan* p, cudaStream_t s, const hf_run_opts& o, bool keep_status) {
     int mode = o.mode;
     if (mode == HF_MODE_AUTO) {
@@ -680,8 +762,8 @@ hf_status plan_run(Plan* p, cudaStream_t s, const hf_run_opts& o, bool keep_stat
     }
     if (mode != HF_MODE_LEVELSYNC && mode != HF_MODE_PERSISTENT && mode != HF_MODE_TEAM)
         return fail(HF_EINVAL, "unknown mode");
-    if (mode != HF_MODE_LEVELSYNC && !p->host_tasks.empty())
-        return fail(HF_ENOTSUP, "host tasks need the level-synchronous executor");
+    if (mode == HF_MODE_PERSISTENT && !p->host_tasks.empty())
+        return fail(HF_ENOTSUP, "host tasks need the level-synchronous or the team executor");
     if (o.priority < HF_PRIO_FIFO || o.priority > HF_PRIO_LEARNED) return fail(HF_EINVAL, "unknown priority");
     if (o.priority == HF_PRIO_LEARNED && !p->cm) return fail(HF_ESTATE, "HF_PRIO_LEARNED needs a cost model (hf_batch_set_costmodel)");
     hf_status st = HF_OK;
@@ -725,6 +807,16 @@ hf_status plan_run(Plan* p, cudaStream_t s, const hf_run_opts& o, bool keep_stat
             a.stage_n = p->stage_n;
             a.stage_e = p->stage_e;
             team_smem_attr(p);
+            if (!p->host_tasks.empty()) {
+                if ((st = team_host_setup(p, s)) != HF_OK) return st;
+                a.seg_host = p->d_seg_host;
+                a.host_order = p->d_host_order;
+                a.post = p->d_post;
+                a.hdone = p->d_hdone;
+                a.post_ctr = p->d_post_ctr;
+                e = cudaMemsetAsync(p->d_post_ctr, 0, sizeof(int32_t), s);
+                if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+            }
             if (instr) {
                 if (!p->d_gtime) {
                     p->d_gtime = (int64_t*)palloc(p, sizeof(int64_t) * 2 * std::max<size_t>((size_t)p->ngraphs, 1), s);
@@ -774,6 +866,10 @@ hf_status plan_run(Plan* p, cudaStream_t s, const hf_run_opts& o, bool keep_stat
                     return cuda_fail(e, "team join");
             }
             if (o.time_kernel) cudaEventRecord(p->kev1, s);
+            if (!p->host_tasks.empty()) {
+                const uint64_t limit = o.spin_limit_ns ? o.spin_limit_ns : 2000000000ull;
+                p->proxy = std::thread(team_host_proxy, p, limit);
+            }
         } else {
             ResetArgs r;
             r.n_tasks = p->n;
@@ -876,6 +972,7 @@ hf_status plan_run(Plan* p, cudaStream_t s, const hf_run_opts& o, bool keep_stat
 hf_status plan_sync(Plan* p) {
     if (!p->ran) return fail(HF_ESTATE, "not run");
     cudaError_t e = cudaEventSynchronize(p->done_ev);
+    if (p->proxy.joinable()) p->proxy.join();
     if (e != cudaSuccess) return cuda_fail(e, "run");
     const int32_t s = p->h_status[0];
     if (p->h_status[2]) return fail(HF_EINVAL, "a delay given to hf_set_delays is not finite");

@@ -242,6 +242,41 @@ __device__ __forceinline__ void team_run_piece(const TeamPiece& d, int lane) {
         warp_copy(d.dst, d.src, d.cnt, lane);
 }
 
+// ---------------------------------------------------------------- host tasks
+
+__device__ __forceinline__ void st_release_sys(int32_t* p, int v) {
+    asm volatile("st.release.sys.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ int ld_acquire_sys(const int32_t* p) {
+    int v;
+    asm volatile("ld.acquire.sys.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// The host tasks of one level (thread 0 of the team's first CTA, after the level's device work):
+// post each to the mailbox in mapped host memory, where the host proxy thread runs it, and
+// wait until all of them have run (bounded: HF_ETIMEDOUT after spin_limit_ns). The system-scope
+// fence makes the graph's earlier device writes (push copies into host memory) visible to the
+// callbacks; the acquire of each done flag orders the callbacks' writes before later levels.
+__device__ __noinline__ void team_host_tasks(const TeamArgs& a, int seg) {
+    const int2 hr = __ldg(a.seg_host + seg);
+    if (hr.y <= hr.x) return;
+    __threadfence_system();
+    for (int h = hr.x; h < hr.y; ++h) st_release_sys(a.post + atomicAdd(a.post_ctr, 1), __ldg(a.host_order + h));
+    for (int h = hr.x; h < hr.y; ++h) {
+        const int k = __ldg(a.host_order + h);
+        const uint64_t t0 = gtimer();
+        while (ld_acquire_sys(a.hdone + k) == 0) {
+            if (gtimer() - t0 > a.spin_limit_ns) {
+                atomicCAS(&a.ctrl->status, 0, (int)HF_ETIMEDOUT);
+                return;
+            }
+            __nanosleep(200);
+        }
+    }
+}
+
 // ---------------------------------------------------------------- thread-block cluster helpers
 
 __device__ __forceinline__ unsigned cluster_rank() {
@@ -393,6 +428,7 @@ __device__ __forceinline__ bool team_run_graph(const TeamArgs& a, const TeamJob&
             for (int it = i0.x + (wid - pw0); it < i0.y; it += nwarp - pw0, ++j)
                 team_run_piece(j < kTeamSlots ? cur[j] : team_piece_desc(a, it), lane);
         }
+        if (a.seg_host && rank == 0 && t == 0) team_host_tasks(a, job.seg0 + l);
         if (SOLO) __syncthreads();
         else cluster_sync();
     }

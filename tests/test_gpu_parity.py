@@ -221,15 +221,62 @@ def test_paper_saxpy_graph_through_c_abi():
             ids[nm] = hf.hf_add_task(g, hf.HF_PUSH, p)
     for a, b in gold["edges"]:
         hf.hf_precede(g, ids[a], ids[b])
-    hf.hf_run(g, None, hf.hf_run_opts_default(mode=hf.HF_MODE_LEVELSYNC))
-    hf.hf_sync_status(g)
-    assert sorted(calls) == ["x", "y"]
-    assert bool((y == P["expect_y"]).all()) and bool((x == P["expect_x"]).all())
+    for opts in (dict(mode=hf.HF_MODE_LEVELSYNC), dict(mode=hf.HF_MODE_TEAM), dict(mode=hf.HF_MODE_TEAM, team_size=2)):
+        x.zero_()
+        y.zero_()
+        calls.clear()
+        hf.hf_run(g, None, hf.hf_run_opts_default(**opts))
+        hf.hf_sync_status(g)
+        assert sorted(calls) == ["x", "y"], opts
+        assert bool((y == P["expect_y"]).all()) and bool((x == P["expect_x"]).all()), opts
     # host tasks are not supported by the persistent executor (reported, not silently run)
     with pytest.raises(hf.HfError) as ei:
         hf.hf_run(g, None, hf.hf_run_opts_default(mode=hf.HF_MODE_PERSISTENT))
     assert ei.value.status == hf.HF_ENOTSUP
     hf.hf_graph_destroy(g)
+
+
+@pytest.mark.parametrize("opts", [dict(mode=hf.HF_MODE_TEAM), dict(mode=hf.HF_MODE_TEAM, team_size=4),
+                                  dict(mode=hf.HF_MODE_TEAM, priority=hf.HF_PRIO_HEURISTIC)])
+def test_team_host_tasks_in_a_batch(opts):
+    """Host tasks inside a batch run by the team executor: each runs exactly once, after its
+    predecessors and before its successors (callbacks record the order), and every arrival is
+    the oracle's (a host task propagates arrivals like a max-plus task)."""
+    rng = np.random.default_rng(21)
+    order = []
+    keep = []
+    b = hf.hf_batch_create()
+    graphs, specs = [], []
+    for gi in range(4):
+        n, _, src, dst, dly = S.layered_dag(100 + gi, 3000 + 500 * gi, 12, 1, 3)
+        host_ids = set(int(v) for v in rng.choice(n, 6, replace=False))
+        g = hf.hf_graph_create()
+        for v in range(n):
+            if v in host_ids:
+                f = hf.HOST_FN(lambda arg, gi=gi, v=v: order.append((gi, v)))
+                keep.append(f)
+                hf.hf_add_task(g, hf.HF_HOST, hf.hf_host_payload(fn=f, arg=None))
+            else:
+                hf.hf_add_task(g, hf.HF_KERNEL, None)
+        hf.hf_precede_bulk(g, src, dst, dly)
+        hf.hf_batch_add(b, g)
+        graphs.append((g, n, src, dst, host_ids))
+        specs.append(S.GraphSpec(name="h%d" % gi, n=n, src=src, dst=dst, delay=dly, kind=np.zeros(n, np.uint8)))
+    for rep in range(2):
+        order.clear()
+        hf.hf_batch_run(b, None, hf.hf_run_opts_default(**opts))
+        hf.hf_batch_sync_status(b)
+        assert sorted(order) == sorted((gi, v) for gi, (_, _, _, _, hs) in enumerate(graphs) for v in hs)
+        pos = {t: i for i, t in enumerate(order)}
+        for gi, (g, n, src, dst, hs) in enumerate(graphs):
+            for u, v in zip(src, dst):  # host-to-host dependencies (direct edges) run in order
+                if int(u) in hs and int(v) in hs:
+                    assert pos[(gi, int(u))] < pos[(gi, int(v))]
+            np.testing.assert_array_equal(bits(hf.hf_batch_get_arrivals(b, gi, n)),
+                                          bits(oracle.run_spec(specs[gi])["arr"]))
+    hf.hf_batch_destroy(b)
+    for g, *_ in graphs:
+        hf.hf_graph_destroy(g)
 
 
 def test_paper_saxpy_graph_persistent_without_host_tasks():
