@@ -14,8 +14,8 @@
 //   * every CTA stages the task list, row starts and in-edges of the next two levels in shared
 //     memory with TMA bulk copies (three buffers, completion on mbarriers); segments too large
 //     to stage are prefetched into L2 with bulk prefetches two levels ahead;
-//   * each warp prefetches into L2 the x and y ranges of the payload pieces it will run in the
-//     next level.
+//   * each warp resolves the descriptors of the payload pieces it will run in the next level,
+//     and in cluster jobs prefetches their x and y ranges into L2.
 #pragma once
 
 #include "kernels.cuh"
@@ -171,9 +171,12 @@ __device__ __forceinline__ int team_arrival_warps(const int4 sg, const int2 si, 
 }
 
 // Descriptors of the pieces this warp runs in a level (payload warps [pw0, nwarp) take items
-// si.x + (wid - pw0) + j * (nwarp - pw0); lane j writes the j-th, the first 32 only, into the
-// warp's shared-memory slots) and an L2 prefetch of their x and y ranges. Copies touch host
-// memory and are not prefetched.
+// si.x + (wid - pw0) + j * (nwarp - pw0); lane j writes the j-th, the first 16 only, into the
+// warp's shared-memory slots) and, with PF, an L2 prefetch of their x and y ranges. Cluster jobs
+// prefetch (their warps run one or two pieces per level, so the level waits on latency); single
+// CTAs do not (measured: their prefetches only add to the memory traffic every graph competes
+// for). Copies touch host memory and are not prefetched.
+template <bool PF>
 __device__ __forceinline__ void team_prefetch_items(const TeamArgs& a, const int2 si, int wid, int pw0, int nwarp,
                                                     int lane, TeamPiece* slots) {
     TeamPiece d;
@@ -181,7 +184,7 @@ __device__ __forceinline__ void team_prefetch_items(const TeamArgs& a, const int
     const int it = si.x + (wid - pw0) + lane * (nwarp - pw0);
     if (wid >= pw0 && it < si.y) {
         d = team_piece_desc(a, it);
-        if (d.op != kPayCopy && d.cnt > 0) {
+        if (PF && d.op != kPayCopy && d.cnt > 0) {
             prefetch_l2_range(d.src, 4ll * d.cnt);
             prefetch_l2_range(d.dst, 4ll * d.cnt);
         }
@@ -372,7 +375,7 @@ __device__ __forceinline__ bool team_run_graph(const TeamArgs& a, const TeamJob&
     TeamPiece* const myslots = pslots + (t >> 5) * kTeamSlots;
     if (PAY) {
         const int na = team_arrival_warps(ring[0], iring[0], nwarp);
-        team_prefetch_items(a, iring[0], wid, na < nwarp ? na : 0, nwarp, lane, myslots);
+        team_prefetch_items<!SOLO>(a, iring[0], wid, na < nwarp ? na : 0, nwarp, lane, myslots);
     }
     for (int l = 0; l < L; ++l) {
         const int b = l % kTeamBufs;
@@ -386,7 +389,7 @@ __device__ __forceinline__ bool team_run_graph(const TeamArgs& a, const TeamJob&
         }
         if (PAY && l + 1 < L) {
             const int na1 = team_arrival_warps(ring[(l + 1) & 3], iring[(l + 1) & 3], nwarp);
-            team_prefetch_items(a, iring[(l + 1) & 3], wid, na1 < nwarp ? na1 : 0, nwarp, lane,
+            team_prefetch_items<!SOLO>(a, iring[(l + 1) & 3], wid, na1 < nwarp ? na1 : 0, nwarp, lane,
                                 myslots + ((l + 1) & 1) * (kTeamThreads / 32) * kTeamSlots);
         }
         const int2 i0 = PAY ? iring[l & 3] : make_int2(0, 0);
