@@ -374,7 +374,8 @@ hf_status hf_batch_autotune(hf_batch* b, void* stream, const hf_run_opts* base, 
  * priority source (HEURISTIC or LEARNED) and machine constants measured once per process on a
  * calibration chain (level-synchronous time per level, persistent time per hop, team time per
  * level for one CTA and for a cluster):
- *   level-sync  = levels * t_level + sum over levels of the largest payload-task cost in it
+ *   level-sync  = levels * t_level (x 2.5 when the level data exceed half the L2) + sum over
+ *                 levels of the largest payload-task cost in it
  *   persistent  = critical path of costs + depth * t_hop + total cost / warps
  *   team        = the team executor's planned makespan: per graph and cluster size k,
  *                 T(k) = sum over levels of t_lvl(k) * ceil(width / 256k) + payload cost / 8k

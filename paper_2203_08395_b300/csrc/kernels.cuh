@@ -237,6 +237,10 @@ __device__ __forceinline__ void run_piece(const DevPayload& P, int piece, int la
 // task; the remaining blocks do payload pieces, one warp per piece.
 template <bool PAY>
 __global__ void __launch_bounds__(256) k_level(const LevelArgs a) {
+    // programmatic dependent launch: the next level's kernel may be scheduled now; this one
+    // reads the previous level's results only after griddepcontrol.wait, so it can load its
+    // own task list and in-edges while the previous level finishes
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     if ((int)blockIdx.x < a.nb_mp) {
         const int p = a.p0 + (int)blockIdx.x * 256 + (int)threadIdx.x;
         if (p >= a.p1) return;
@@ -256,6 +260,7 @@ __global__ void __launch_bounds__(256) k_level(const LevelArgs a) {
 #pragma unroll
                 for (int j = 0; j < 8; ++j)
                     if (j < cnt) ie[j] = __ldg(a.ls_in + e + j);
+                if (e == e0) asm volatile("griddepcontrol.wait;" ::: "memory");
 #pragma unroll
                 for (int j = 0; j < 8; ++j)
                     if (j < cnt) kk[j] = __ldcg(a.key + ie[j].x);
@@ -267,6 +272,7 @@ __global__ void __launch_bounds__(256) k_level(const LevelArgs a) {
         a.key[v] = best;
         return;
     }
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     if (PAY) {
         const int lane = threadIdx.x & 31;
         const int wg = ((int)blockIdx.x - a.nb_mp) * 8 + ((int)threadIdx.x >> 5);

@@ -625,6 +625,7 @@ static hf_status build_level_graph(Plan* p) {
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphCreate");
     p->largs.assign((size_t)p->levels, LevelArgs());
     std::vector<cudaGraphNode_t> prev, cur;
+    bool prev_kernel_only = false;  // the previous level is one kernel node (no host node)
     std::vector<std::vector<const HostTask*>> host_at((size_t)p->levels);
     for (const HostTask& h : p->host_tasks) host_at[(size_t)h.level].push_back(&h);
     const bool pay = p->npay > 0;
@@ -647,15 +648,22 @@ static hf_status build_level_graph(Plan* p) {
         const int nb_pay = items ? std::min((items + 7) / 8, p->num_sms * 8) : 0;
         const int grid = a.nb_mp + nb_pay;
         if (grid > 0) {
-            cudaKernelNodeParams kp = {};
-            kp.func = pay ? (void*)k_level<true> : (void*)k_level<false>;
-            kp.gridDim = dim3((unsigned)grid);
-            kp.blockDim = dim3(256);
+            // a level after a level of one kernel node depends on it programmatically: it launches
+            // while that kernel runs and waits inside (griddepcontrol.wait) for its results
+            cudaGraphNodeParams np = {};
+            np.type = cudaGraphNodeTypeKernel;
+            np.kernel.func = pay ? (void*)k_level<true> : (void*)k_level<false>;
+            np.kernel.gridDim = dim3((unsigned)grid);
+            np.kernel.blockDim = dim3(256);
             void* args[1] = {&a};
-            kp.kernelParams = args;
+            np.kernel.kernelParams = args;
+            cudaGraphEdgeData ed = {};
+            ed.from_port = cudaGraphKernelNodePortProgrammatic;
+            ed.type = cudaGraphDependencyTypeProgrammatic;
+            const bool pdl = prev_kernel_only && prev.size() == 1;
             cudaGraphNode_t node;
-            e = cudaGraphAddKernelNode(&node, p->lgraph, prev.data(), prev.size(), &kp);
-            if (e != cudaSuccess) return cuda_fail(e, "cudaGraphAddKernelNode");
+            e = cudaGraphAddNode(&node, p->lgraph, prev.data(), pdl ? &ed : nullptr, prev.size(), &np);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaGraphAddNode (level kernel)");
             cur.push_back(node);
         }
         for (const HostTask* h : host_at[(size_t)l]) {
@@ -667,7 +675,10 @@ static hf_status build_level_graph(Plan* p) {
             if (e != cudaSuccess) return cuda_fail(e, "cudaGraphAddHostNode");
             cur.push_back(node);
         }
-        if (!cur.empty()) prev.swap(cur);
+        if (!cur.empty()) {
+            prev_kernel_only = grid > 0 && host_at[(size_t)l].empty();
+            prev.swap(cur);
+        }
     }
     e = cudaGraphInstantiate(&p->lexec, p->lgraph, 0);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
@@ -1561,7 +1572,15 @@ hf_status plan_predict(Plan* p, int32_t priority, const hf_costmodel* cm, cudaSt
     int occ = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_persist<false>, kWarpsPerCta * 32, 0);
     const double warps = (double)p->num_sms * std::max(occ, 1) * kWarpsPerCta;
-    *ls_ms = (float)(((double)p->levels * g_t_level_ns + lsum) / 1e6);
+    // the calibration chain's levels come from L2; when the level-sorted arrays exceed half the
+    // L2, every level's task list and in-edges come from DRAM first: three dependent DRAM round
+    // trips per level instead of L2 ones (x2.5)
+    int l2 = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
+    const double ls_bytes = 8.0 * (double)p->m + 8.0 * (double)p->n;
+    const double dram = ls_bytes > 0.5 * (double)l2 ? 2.5 : 1.0;
+    *ls_ms = (float)(((double)p->levels * dram * g_t_level_ns + lsum) / 1e6);
     *p_ms = (float)((cp + (double)p->levels * g_t_hop_ns + work / warps) / 1e6);
     // team executor: its own plan under the same cost source (host tasks: not available)
     *t_ms = INFINITY;
