@@ -248,8 +248,9 @@ hf_status hf_kernel_ms(hf_graph* g, float* ms);
  * circuit): delay[e] is the new delay of the e-th edge in the order edges were added
  * (hf_precede*), m floats, all finite (checked on the device: a non-finite delay is stored
  * anyway and makes every later hf_sync_status return HF_EINVAL until delays are set again).
- * on_device != 0: `delay` is a device pointer; else host
- * memory (page-locked for an asynchronous copy). Enqueued on `stream`; later runs on any
+ * on_device != 0: `delay` is a device pointer; else host memory: page-locked memory is read by
+ * the device directly (leave it unchanged until `stream` has passed this point), other host
+ * memory through a staging copy. Enqueued on `stream`; later runs on any
  * stream see the new delays once that stream has reached this point. The graph's own edge
  * list keeps the delays it was built with (they return if the plan is ever rebuilt, e.g.
  * after a mutation). Finalizes and uploads the graph first if needed. */

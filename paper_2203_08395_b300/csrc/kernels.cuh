@@ -813,7 +813,7 @@ __global__ void k_set_delays(const float* __restrict__ delay, const int32_t* __r
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     bool nonfinite = false;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
-        const int b = __float_as_int(__ldg(delay + i));
+        const int b = __float_as_int(__ldcs(delay + i));  // device or page-locked host memory, read once
         nonfinite |= (b & 0x7f800000) == 0x7f800000;
         reinterpret_cast<int*>(erec)[4 * (int64_t)__ldg(pos_csr + i) + 1] = b;
         reinterpret_cast<int*>(ls_in)[2 * (int64_t)__ldg(pos_ls + i) + 1] = b;

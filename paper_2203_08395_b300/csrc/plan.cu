@@ -1076,7 +1076,12 @@ hf_status plan_set_delays(Plan* p, const float* delay, int on_device, cudaStream
     if (p->m == 0) return HF_OK;
     if (!delay) return fail(HF_EINVAL, "delay is NULL");
     const float* src = delay;
-    if (!on_device) {
+    // page-locked host memory: the scatter kernel reads it over the host link directly (one
+    // pass, no staging copy); other host memory goes through a staging copy
+    const float* mapped = on_device ? nullptr : (const float*)host_dev_ptr(delay);
+    if (mapped) {
+        src = mapped;
+    } else if (!on_device) {
         if (!p->d_dly_stage) {
             p->d_dly_stage = (float*)palloc(p, 4 * (size_t)p->m, s);
             if (!p->d_dly_stage) return fail(HF_ENOMEM, "device allocation failed: delay staging");
