@@ -151,6 +151,18 @@ struct TeamJob {
     int32_t levels;  // levels of the graph
 };
 
+// One payload piece resolved for the team executor (built on the host per piece size, staged in
+// shared memory with its level): pointers already offset to the piece, cnt in elements (saxpy)
+// or bytes (copy), op 0 = none. 32 bytes.
+struct alignas(16) TeamPiece {
+    char* dst;
+    const char* src;
+    int32_t cnt;
+    uint32_t a;
+    uint32_t op;
+    int32_t pad_;
+};
+
 // Team-executor control words (zeroed before every run): solo-job counter, cluster-job counter.
 constexpr int kTeamNext = 0;
 constexpr int kTeamNextC = 32;
@@ -172,6 +184,9 @@ struct TeamArgs {
     int32_t ncjobs;
     int32_t stage_n;         // stage buffer capacity: tasks and in-edges of a level
     int32_t stage_e;
+    int32_t stage_p;         // ... and payload piece descriptors (0: none staged)
+    int32_t pad2_;
+    const TeamPiece* pdesc;  // piece descriptors, in item order
     int32_t* team;           // control words (kTeam*)
     Ctrl* ctrl;              // status word (HF_ETIMEDOUT when a staged copy never lands)
     uint64_t spin_limit_ns;

@@ -70,6 +70,9 @@ struct Plan {
     cudaEvent_t tev_join[4] = {nullptr, nullptr, nullptr, nullptr};
     int32_t* d_team = nullptr;        // control words (job counters), kTeamWords per class
     int32_t stage_n = 4, stage_e = 2;  // stage buffer capacities (tasks, in-edges per level)
+    int32_t stage_p = 0;               // ... piece descriptors per level (per piece size)
+    TeamPiece* d_pdesc = nullptr;      // piece descriptors in item order (per piece size)
+    size_t cap_pdesc = 0;
     // team executor's host tasks: a mailbox in mapped page-locked memory and a proxy thread
     int2* d_seg_host = nullptr;       // (graph, level) segment -> host-task range in host_order
     int32_t* d_host_order = nullptr;  // host-task indices grouped by segment
@@ -503,6 +506,8 @@ static hf_status plan_set_chunk(Plan* p, int64_t chunk_elems, cudaStream_t s) {
     std::vector<int32_t> chunk_task;
     std::vector<int32_t> seeds, pseeds;
     std::vector<int2> litems, seg_items;
+    std::vector<TeamPiece> pdesc;  // team executor: litems resolved
+    int32_t stage_p = 0;
     std::vector<int32_t> item_ptr((size_t)p->levels + 1, 0);
     try {
         for (int32_t k = 0; k < p->npay; ++k) {
@@ -553,7 +558,23 @@ static hf_status plan_set_chunk(Plan* p, int64_t chunk_elems, cudaStream_t s) {
                 const size_t sidx = (size_t)(p->seg_first[(size_t)g] + l);
                 seg_items[sidx] = make_int2(off, off + seg_cnt[sidx]);
                 off += seg_cnt[sidx];
+                // stage buffers hold a level's descriptors up to 256 of them (8 KB)
+                stage_p = std::max(stage_p, std::min(seg_cnt[sidx], 256));
             }
+        }
+        pdesc.resize(litems.size());
+        for (size_t q = 0; q < litems.size(); ++q) {
+            const DevPayload& d = p->hpay[(size_t)litems[q].x];
+            const int64_t b0 = (int64_t)litems[q].y * d.chunk;
+            const int64_t b1 = std::min(b0 + d.chunk, d.n);
+            const int64_t sc = d.op == kPayCopy ? 1 : 4;
+            TeamPiece& t = pdesc[q];
+            t.dst = (char*)d.dst + sc * b0;
+            t.src = (const char*)d.src + sc * b0;
+            t.cnt = (int32_t)std::max<int64_t>(b1 - b0, 0);
+            t.a = d.a_bits;
+            t.op = d.op;
+            t.pad_ = 0;
         }
     } catch (const std::bad_alloc&) {
         return fail(HF_ENOMEM, "host allocation failed");
@@ -564,6 +585,7 @@ static hf_status plan_set_chunk(Plan* p, int64_t chunk_elems, cudaStream_t s) {
     p->npseed = (int32_t)pseeds.size();
     p->pqcap = p->npay + (int32_t)items;
     p->item_ptr = item_ptr;
+    p->stage_p = stage_p;
     auto grow = [&](void** ptr, size_t& cap, size_t bytes) -> bool {
         bytes = std::max<size_t>(bytes, 16);
         if (cap >= bytes) return true;
@@ -578,7 +600,8 @@ static hf_status plan_set_chunk(Plan* p, int64_t chunk_elems, cudaStream_t s) {
         !grow((void**)&p->d_pqueue, p->cap_pqueue, 4 * (size_t)p->pqcap) ||
         !grow((void**)&p->d_queue, p->cap_queue, 4 * (size_t)p->qcap) ||
         !grow((void**)&p->d_items, p->cap_items, 8 * litems.size()) ||
-        !grow((void**)&p->d_seg_items, p->cap_seg_items, 8 * seg_items.size()))
+        !grow((void**)&p->d_seg_items, p->cap_seg_items, 8 * seg_items.size()) ||
+        !grow((void**)&p->d_pdesc, p->cap_pdesc, sizeof(TeamPiece) * pdesc.size()))
         return fail(HF_ENOMEM, "device allocation failed: queue");
     cudaError_t e = cudaSuccess;
     if (!chunk_task.empty()) e = cudaMemcpyAsync(p->d_chunk_task, chunk_task.data(), 4 * chunk_task.size(), cudaMemcpyHostToDevice, s);
@@ -587,6 +610,8 @@ static hf_status plan_set_chunk(Plan* p, int64_t chunk_elems, cudaStream_t s) {
     if (e == cudaSuccess && !litems.empty()) e = cudaMemcpyAsync(p->d_items, litems.data(), 8 * litems.size(), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && !seg_items.empty())
         e = cudaMemcpyAsync(p->d_seg_items, seg_items.data(), 8 * seg_items.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && !pdesc.empty())
+        e = cudaMemcpyAsync(p->d_pdesc, pdesc.data(), sizeof(TeamPiece) * pdesc.size(), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && p->npay) e = cudaMemcpyAsync(p->d_pay, p->hpay.data(), sizeof(DevPayload) * (size_t)p->npay, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // host vectors die at return
     if (e != cudaSuccess) return cuda_fail(e, "piece layout upload");
@@ -817,6 +842,8 @@ hf_status plan_run(Plan* p, cudaStream_t s, const hf_run_opts& o, bool keep_stat
             a.spin_limit_ns = o.spin_limit_ns ? o.spin_limit_ns : 2000000000ull;
             a.stage_n = p->stage_n;
             a.stage_e = p->stage_e;
+            a.stage_p = p->npay ? p->stage_p : 0;
+            a.pdesc = p->d_pdesc;
             team_smem_attr(p);
             if (!p->host_tasks.empty()) {
                 if ((st = team_host_setup(p, s)) != HF_OK) return st;
@@ -1625,7 +1652,7 @@ static double team_time(const Plan* p, const std::vector<double>& pay_ns, int32_
 }
 
 // CTAs of cluster size k resident at once (k = 1: plain occupancy).
-static size_t team_smem(const Plan* p) { return kTeamBufs * team_stage_bytes(p->stage_n, p->stage_e); }
+static size_t team_smem(const Plan* p) { return kTeamBufs * team_stage_bytes(p->stage_n, p->stage_e, p->stage_p); }
 
 static void team_smem_attr(const Plan* p) {
     static std::mutex mu;

@@ -24,28 +24,30 @@ namespace hf {
 
 constexpr int kTeamThreads = 256;
 constexpr int kTeamBufs = 3;       // staged levels: the current one and two ahead
-// Stage buffers live in dynamic shared memory, sized per plan (TeamArgs::stage_n tasks and
-// stage_e in-edges per level, multiples of 4 and 2): node[stage_n + 8] (copied from a 16-byte
-// aligned start, up to 3 extra entries in front), ptr[stage_n + 12] (one more row start),
-// in[stage_e + 2].
-__host__ __device__ constexpr size_t team_stage_bytes(int stage_n, int stage_e) {
-    return (size_t)(stage_n + 8) * 4 + (size_t)(stage_n + 12) * 4 + (size_t)(stage_e + 2) * 8;
+// Stage buffers live in dynamic shared memory, sized per plan (TeamArgs::stage_n tasks,
+// stage_e in-edges and stage_p piece descriptors per level; stage_n a multiple of 4, stage_e of
+// 2): node[stage_n + 8] (copied from a 16-byte aligned start, up to 3 extra entries in front),
+// ptr[stage_n + 12] (one more row start), in[stage_e + 2], pdesc[stage_p].
+__host__ __device__ constexpr size_t team_stage_bytes(int stage_n, int stage_e, int stage_p) {
+    return (size_t)(stage_n + 8) * 4 + (size_t)(stage_n + 12) * 4 + (size_t)(stage_e + 2) * 8 +
+           (size_t)stage_p * sizeof(TeamPiece);
 }
-constexpr int kTeamSlots = 16;     // payload piece descriptors kept per warp and level
 
 // One stage buffer carved out of dynamic shared memory.
 struct TeamStage {
     int32_t* node;
     int32_t* ptr;
     int2* in;
+    TeamPiece* pdesc;
 };
 
-__device__ __forceinline__ TeamStage team_stage_view(unsigned char* base, int b, int stage_n, int stage_e) {
-    unsigned char* p = base + (size_t)b * team_stage_bytes(stage_n, stage_e);
+__device__ __forceinline__ TeamStage team_stage_view(unsigned char* base, int b, int stage_n, int stage_e, int stage_p) {
+    unsigned char* p = base + (size_t)b * team_stage_bytes(stage_n, stage_e, stage_p);
     TeamStage st;
     st.node = reinterpret_cast<int32_t*>(p);
     st.ptr = st.node + stage_n + 8;
     st.in = reinterpret_cast<int2*>(st.ptr + stage_n + 12);
+    st.pdesc = reinterpret_cast<TeamPiece*>(st.in + stage_e + 2);
     return st;
 }
 __device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
@@ -95,17 +97,24 @@ __device__ __forceinline__ bool team_fits(const TeamArgs& a, const int4 sg) {
     return sg.y > sg.x && sg.y - sg.x <= a.stage_n && sg.w - sg.z <= a.stage_e;
 }
 
-// Issued by one thread: stage segment sg (positions [x, y), in-edges [z, w)) into st. The
-// level-sorted arrays are allocated with slack so that rounding the ends up to 16 bytes stays
-// inside them.
-__device__ __forceinline__ void team_stage(const TeamArgs& a, const TeamStage& st, unsigned long long* bar, const int4 sg) {
+// Issued by one thread: stage segment sg (positions [x, y), in-edges [z, w)) into st, and the
+// level's piece descriptors si = [i0, i1) when they fit. The level-sorted arrays are allocated
+// with slack so that rounding the ends up to 16 bytes stays inside them.
+__device__ __forceinline__ bool team_desc_fits(const TeamArgs& a, const int2 si) {
+    return si.y > si.x && si.y - si.x <= a.stage_p;
+}
+
+__device__ __forceinline__ void team_stage(const TeamArgs& a, const TeamStage& st, unsigned long long* bar, const int4 sg,
+                                           const int2 si) {
     const int a0 = sg.x & ~3, a1 = (sg.y + 3) & ~3, b1 = (sg.y + 4) & ~3;
     const int c0 = sg.z & ~1, c1 = (sg.w + 1) & ~1;
     const unsigned bn = (unsigned)(a1 - a0) * 4u, bp = (unsigned)(b1 - a0) * 4u, bi = (unsigned)(c1 - c0) * 8u;
-    mbar_arrive_expect_tx(bar, bn + bp + bi);
+    const unsigned bd = team_desc_fits(a, si) ? (unsigned)(si.y - si.x) * (unsigned)sizeof(TeamPiece) : 0u;
+    mbar_arrive_expect_tx(bar, bn + bp + bi + bd);
     bulk_g2s(st.node, a.ls_node + a0, bn, bar);
     bulk_g2s(st.ptr, a.ls_ptr + a0, bp, bar);
     if (bi) bulk_g2s(st.in, a.ls_in + c0, bi, bar);
+    if (bd) bulk_g2s(st.pdesc, a.pdesc + si.x, bd, bar);
 }
 
 __device__ __forceinline__ void team_prefetch_seg(const TeamArgs& a, const int4 sg) {
@@ -118,48 +127,23 @@ __device__ __forceinline__ void team_prefetch_seg(const TeamArgs& a, const int4 
 // look-ahead for one level, by thread 0 of each CTA: stage it if it fits, else (CTA 0 of the
 // team) prefetch it into L2
 __device__ __forceinline__ void team_ahead_body(const TeamArgs& a, int rank, const TeamStage& st,
-                                                unsigned long long* bar, const int4 sg) {
-    if (team_fits(a, sg)) team_stage(a, st, bar, sg);
+                                                unsigned long long* bar, const int4 sg, const int2 si) {
+    if (team_fits(a, sg)) team_stage(a, st, bar, sg, si);
     else if (rank == 0) team_prefetch_seg(a, sg);
 }
 
 // the payload kernel calls it out of line: its address arithmetic would otherwise push the
 // level loop's registers past the three-CTAs-per-SM budget
 __device__ __noinline__ void team_ahead_call(const TeamArgs& a, int rank, const TeamStage& st, unsigned long long* bar,
-                                             const int4 sg) {
-    team_ahead_body(a, rank, st, bar, sg);
+                                             const int4 sg, const int2 si) {
+    team_ahead_body(a, rank, st, bar, sg, si);
 }
 
 template <bool PAY>
 __device__ __forceinline__ void team_ahead(const TeamArgs& a, int rank, const TeamStage& st, unsigned long long* bar,
-                                           const int4 sg) {
-    if (PAY) team_ahead_call(a, rank, st, bar, sg);
-    else team_ahead_body(a, rank, st, bar, sg);
-}
-
-// One payload piece, resolved: pointers already offset to the piece, cnt in elements (saxpy)
-// or bytes (copy).
-struct __align__(16) TeamPiece {
-    char* dst;
-    const char* src;
-    int32_t cnt;
-    uint32_t a;
-    uint32_t op;  // 0: none
-};
-
-__device__ __forceinline__ TeamPiece team_piece_desc(const TeamArgs& a, int it) {
-    const int2 w = __ldg(a.items + it);
-    const DevPayload& P = a.pay[w.x];
-    const int64_t b0 = (int64_t)w.y * P.chunk;
-    const int64_t b1 = b0 + P.chunk < P.n ? b0 + P.chunk : P.n;
-    const int64_t sc = P.op == kPayCopy ? 1 : 4;
-    TeamPiece d;
-    d.dst = (char*)P.dst + sc * b0;
-    d.src = (const char*)P.src + sc * b0;
-    d.cnt = (int32_t)(b1 > b0 ? b1 - b0 : 0);
-    d.a = P.a_bits;
-    d.op = P.op;
-    return d;
+                                           const int4 sg, const int2 si) {
+    if (PAY) team_ahead_call(a, rank, st, bar, sg, si);
+    else team_ahead_body(a, rank, st, bar, sg, si);
 }
 
 // Warps of a team that compute a level's arrivals: one task per thread, and the other warps
@@ -170,26 +154,16 @@ __device__ __forceinline__ int team_arrival_warps(const int4 sg, const int2 si, 
     return (si.y > si.x && na < nwarp) ? na : nwarp;
 }
 
-// Descriptors of the pieces this warp runs in a level (payload warps [pw0, nwarp) take items
-// si.x + (wid - pw0) + j * (nwarp - pw0); lane j writes the j-th, the first 16 only, into the
-// warp's shared-memory slots) and, with PF, an L2 prefetch of their x and y ranges. Cluster jobs
-// prefetch (their warps run one or two pieces per level, so the level waits on latency); single
-// CTAs do not (measured: their prefetches only add to the memory traffic every graph competes
-// for). Copies touch host memory and are not prefetched.
-template <bool PF>
-__device__ __forceinline__ void team_prefetch_items(const TeamArgs& a, const int2 si, int wid, int pw0, int nwarp,
-                                                    int lane, TeamPiece* slots) {
-    TeamPiece d;
-    d.op = 0;
-    const int it = si.x + (wid - pw0) + lane * (nwarp - pw0);
-    if (wid >= pw0 && it < si.y) {
-        d = team_piece_desc(a, it);
-        if (PF && d.op != kPayCopy && d.cnt > 0) {
-            prefetch_l2_range(d.src, 4ll * d.cnt);
-            prefetch_l2_range(d.dst, 4ll * d.cnt);
-        }
+// L2 prefetch of the x and y ranges of the pieces payload warp w (of nw) runs in a level
+// (items si.x + w + j * nw; lane j takes the j-th), from staged descriptors. Copies touch host
+// memory and are skipped.
+__device__ __forceinline__ void team_prefetch_pieces(const TeamPiece* dsc, const int2 si, int w, int nw, int lane) {
+    for (int it = si.x + w + lane * nw; it < si.y; it += 32 * nw) {
+        const TeamPiece d = dsc[it];
+        if (d.op == kPayCopy || d.cnt <= 0) continue;
+        prefetch_l2_range(d.src, 4ll * d.cnt);
+        prefetch_l2_range(d.dst, 4ll * d.cnt);
     }
-    if (lane < kTeamSlots) slots[lane] = d;
 }
 
 // One piece by one warp (a 512-element FP32 piece is one round trip of 16-byte loads).
@@ -348,58 +322,54 @@ __device__ __forceinline__ uint32_t team_task_key(const TeamArgs& a, int v, cons
 // ---------------------------------------------------------------- one graph
 
 // Runs job `job` on a team of k CTAs (this one is `rank`; SOLO: k = 1): level by level, staged
-// levels from shared memory, the rest from global memory (prefetched into L2), payload pieces
-// spread over the team's warps, then the team barrier (CTA barrier for a solo job, cluster
-// barrier otherwise). Returns false if a staged copy never landed (the kernel must end).
+// levels (task list, in-edges, piece descriptors) from shared memory, the rest from global
+// memory (prefetched into L2), payload pieces spread over the team's warps, then the team
+// barrier (CTA barrier for a solo job, cluster barrier otherwise). Returns false if a staged
+// copy never landed (the kernel must end).
 template <bool PAY, bool SOLO>
 __device__ __forceinline__ bool team_run_graph(const TeamArgs& a, const TeamJob& job, int k, int rank,
                                                const TeamStage* sview, unsigned long long* mbar, int4* ring, int2* iring,
-                                               TeamPiece* pslots, unsigned& phase) {
+                                               unsigned& phase) {
     const int t = threadIdx.x;
     const int lane = t & 31;
     const int nthr = k * kTeamThreads, tid = rank * kTeamThreads + t;
     const int wid = tid >> 5, nwarp = nthr >> 5;
     const int L = job.levels;
+    const int2 z2 = make_int2(0, 0);
     // segment descriptors and item ranges ride a ring in shared memory, written by thread 0
-    // three (items: two) levels ahead; level l uses stage buffer l % kTeamBufs
+    // three levels ahead; level l uses stage buffer l % kTeamBufs, staged two levels ahead
     if (t == 0) {
-        for (int q = 0; q < 3 && q < L; ++q) ring[q] = __ldg(a.seg + job.seg0 + q);
-        if (PAY)
-            for (int q = 0; q < 2 && q < L; ++q) iring[q] = __ldg(a.seg_items + job.seg0 + q);
-        if (L > 0) team_ahead<PAY>(a, rank, sview[0], &mbar[0], ring[0]);
-        if (L > 1) team_ahead<PAY>(a, rank, sview[1], &mbar[1], ring[1]);
+        for (int q = 0; q < 3 && q < L; ++q) {
+            ring[q] = __ldg(a.seg + job.seg0 + q);
+            iring[q] = PAY ? __ldg(a.seg_items + job.seg0 + q) : z2;
+        }
+        if (L > 0) team_ahead<PAY>(a, rank, sview[0], &mbar[0], ring[0], iring[0]);
+        if (L > 1) team_ahead<PAY>(a, rank, sview[1], &mbar[1], ring[1], iring[1]);
     }
     __syncthreads();
     if (a.g_start && rank == 0 && t == 0) a.g_start[job.graph] = (int64_t)gtimer();
-    // this warp's piece descriptors: slots[(l & 1)][warp][j] for level l
-    TeamPiece* const myslots = pslots + (t >> 5) * kTeamSlots;
-    if (PAY) {
-        const int na = team_arrival_warps(ring[0], iring[0], nwarp);
-        team_prefetch_items<!SOLO>(a, iring[0], wid, na < nwarp ? na : 0, nwarp, lane, myslots);
-    }
     for (int l = 0; l < L; ++l) {
         const int b = l % kTeamBufs;
         const int4 s0 = ring[l & 3];
+        const int2 i0 = PAY ? iring[l & 3] : z2;
         if (t == 0) {
-            if (l + 3 < L) ring[(l + 3) & 3] = __ldg(a.seg + job.seg0 + l + 3);
-            if (PAY && l + 2 < L) iring[(l + 2) & 3] = __ldg(a.seg_items + job.seg0 + l + 2);
+            if (l + 3 < L) {
+                ring[(l + 3) & 3] = __ldg(a.seg + job.seg0 + l + 3);
+                if (PAY) iring[(l + 3) & 3] = __ldg(a.seg_items + job.seg0 + l + 3);
+            }
             if (l + 2 < L)
-                team_ahead<PAY>(a, rank, sview[(l + 2) % kTeamBufs],
-                           &mbar[(l + 2) % kTeamBufs], ring[(l + 2) & 3]);
+                team_ahead<PAY>(a, rank, sview[(l + 2) % kTeamBufs], &mbar[(l + 2) % kTeamBufs], ring[(l + 2) & 3],
+                                iring[(l + 2) & 3]);
         }
-        if (PAY && l + 1 < L) {
-            const int na1 = team_arrival_warps(ring[(l + 1) & 3], iring[(l + 1) & 3], nwarp);
-            team_prefetch_items<!SOLO>(a, iring[(l + 1) & 3], wid, na1 < nwarp ? na1 : 0, nwarp, lane,
-                                myslots + ((l + 1) & 1) * (kTeamThreads / 32) * kTeamSlots);
-        }
-        const int2 i0 = PAY ? iring[l & 3] : make_int2(0, 0);
         const int na = PAY ? team_arrival_warps(s0, i0, nwarp) : nwarp;
         const int pw0 = na < nwarp ? na : 0;  // first payload warp
         // arrivals of level l (every CTA of a team stages the whole level and takes its share)
         const int32_t* node = a.ls_node;
         const int32_t* ptr = a.ls_ptr;
         const int2* in = a.ls_in;
-        if (team_fits(a, s0)) {
+        const TeamPiece* dsc = PAY ? a.pdesc : nullptr;
+        const bool staged = team_fits(a, s0);
+        if (staged) {
             uint64_t t0 = 0;
             while (!mbar_try_wait(&mbar[b], (phase >> b) & 1u)) {
                 const uint64_t now = gtimer();
@@ -413,9 +383,10 @@ __device__ __forceinline__ bool team_run_graph(const TeamArgs& a, const TeamJob&
             phase ^= 1u << b;
             const int nb = s0.x & ~3, eb = s0.z & ~1;
             const TeamStage sv = sview[b];
-            node = sv.node - nb;  // indexed by level-sorted position / in-edge number
+            node = sv.node - nb;  // indexed by level-sorted position / in-edge number / item
             ptr = sv.ptr - nb;
             in = sv.in - eb;
+            if (PAY && team_desc_fits(a, i0)) dsc = sv.pdesc - i0.x;
         }
         if (wid < na) {
             for (int p = s0.x + tid; p < s0.y; p += na * 32) {
@@ -423,13 +394,20 @@ __device__ __forceinline__ bool team_run_graph(const TeamArgs& a, const TeamJob&
                 a.key[v] = team_task_key<SOLO>(a, v, in, ptr[p], ptr[p + 1]);
             }
         }
-        // payload pieces of level l
+        // payload pieces of level l; in cluster jobs each payload warp first warms L2 with the
+        // pieces it will run in the next level, when that level's staged descriptors have landed
         if (PAY && wid >= pw0) {
-            __syncwarp();
-            const TeamPiece* cur = myslots + (l & 1) * (kTeamThreads / 32) * kTeamSlots;
-            int j = 0;
-            for (int it = i0.x + (wid - pw0); it < i0.y; it += nwarp - pw0, ++j)
-                team_run_piece(j < kTeamSlots ? cur[j] : team_piece_desc(a, it), lane);
+            if (!SOLO && l + 1 < L) {
+                const int b1 = (l + 1) % kTeamBufs;
+                const int2 i1 = iring[(l + 1) & 3];
+                const int4 s1 = ring[(l + 1) & 3];
+                const int na1 = team_arrival_warps(s1, i1, nwarp);
+                const int q0 = na1 < nwarp ? na1 : 0;
+                if (wid >= q0 && team_fits(a, s1) && team_desc_fits(a, i1) &&
+                    mbar_try_wait(&mbar[b1], (phase >> b1) & 1u))
+                    team_prefetch_pieces(sview[b1].pdesc - i1.x, i1, wid - q0, nwarp - q0, lane);
+            }
+            for (int it = i0.x + (wid - pw0); it < i0.y; it += nwarp - pw0) team_run_piece(dsc[it], lane);
         }
         if (a.seg_host && rank == 0 && t == 0) team_host_tasks(a, job.seg0 + l);
         if (SOLO) __syncthreads();
@@ -452,12 +430,11 @@ __global__ void __launch_bounds__(kTeamThreads, 3) k_team(const TeamArgs a) {
     __shared__ __align__(16) TeamJob s_job;
     __shared__ int4 s_ring[4];
     __shared__ int2 s_iring[4];
-    __shared__ TeamPiece s_piece[2][kTeamSlots * (kTeamThreads / 32)];  // piece descriptors, by level parity
     const int t = threadIdx.x;
     if (t == 0) {
         for (int b = 0; b < kTeamBufs; ++b) {
             mbar_init(&mbar[b], 1);
-            s_view[b] = team_stage_view(s_stage, b, a.stage_n, a.stage_e);
+            s_view[b] = team_stage_view(s_stage, b, a.stage_n, a.stage_e, a.stage_p);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -478,7 +455,7 @@ __global__ void __launch_bounds__(kTeamThreads, 3) k_team(const TeamArgs a) {
             const TeamJob job = s_job;
             cluster_sync();  // all have read s_job before CTA 0 may overwrite it
             if (job.graph < 0) break;
-            if (!team_run_graph<PAY, false>(a, job, k, rank, s_view, mbar, s_ring, s_iring, &s_piece[0][0], phase)) return;
+            if (!team_run_graph<PAY, false>(a, job, k, rank, s_view, mbar, s_ring, s_iring, phase)) return;
         }
     }
     for (;;) {
@@ -490,7 +467,7 @@ __global__ void __launch_bounds__(kTeamThreads, 3) k_team(const TeamArgs a) {
         const TeamJob job = s_job;
         __syncthreads();
         if (job.graph < 0) break;
-        if (!team_run_graph<PAY, true>(a, job, 1, 0, s_view, mbar, s_ring, s_iring, &s_piece[0][0], phase)) return;
+        if (!team_run_graph<PAY, true>(a, job, 1, 0, s_view, mbar, s_ring, s_iring, phase)) return;
     }
 }
 
