@@ -9,13 +9,15 @@
 //
 // Latency hiding. A level's critical path should be one gather of the predecessors' arrival
 // keys. Everything that does not depend on the previous level is fetched ahead:
-//   * segment descriptors (positions and in-edge range of each level) three levels ahead, in
-//     registers;
-//   * every CTA stages the task list, row starts and in-edges of the next two levels in shared
-//     memory with TMA bulk copies (three buffers, completion on mbarriers); segments too large
-//     to stage are prefetched into L2 with bulk prefetches two levels ahead;
-//   * each warp resolves the descriptors of the payload pieces it will run in the next level,
-//     and in cluster jobs prefetches their x and y ranges into L2.
+//   * segment descriptors (positions, in-edge and payload-piece ranges of each level) three
+//     levels ahead, by asynchronous copies into a ring in shared memory;
+//   * every CTA stages the task list, row starts, in-edges and payload-piece descriptors of the
+//     next two levels in shared memory with TMA bulk copies (three buffers, completion on
+//     mbarriers); segments too large to stage are prefetched into L2 two levels ahead;
+//   * in cluster jobs, each CTA prefetches the x and y ranges of its next-level pieces into L2.
+// Balance. Each CTA of a team takes a contiguous slice of every level's tasks (one per thread)
+// and of its payload pieces; the CTA's warps claim pieces one at a time from a shared counter,
+// warps without arrivals at once, the others when their arrivals are done.
 #pragma once
 
 #include "kernels.cuh"
@@ -74,6 +76,12 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned 
 }
 
 // TMA bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16)
+// asynchronous 8-byte global -> shared copy (completion: cp_async_wait_all by the issuer)
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem) : "memory");
+}
+
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
     const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
     const unsigned b = (unsigned)__cvta_generic_to_shared(bar);
@@ -93,18 +101,31 @@ __device__ __forceinline__ void prefetch_l2_range(const void* p, int64_t bytes) 
     }
 }
 
-__device__ __forceinline__ bool team_fits(const TeamArgs& a, const int4 sg) {
+// The staging sources and capacities, copied from TeamArgs into shared memory at kernel start:
+// the look-ahead reads them there (kernel parameters read through a reference in an out-of-line
+// call cost several hundred ns per dependent load).
+struct TeamSrc {
+    const int32_t* ls_node;
+    const int32_t* ls_ptr;
+    const int2* ls_in;
+    const TeamPiece* pdesc;
+    int32_t stage_n, stage_e, stage_p, pad_;
+};
+
+template <class S>
+__device__ __forceinline__ bool team_fits(const S& a, const int4 sg) {
     return sg.y > sg.x && sg.y - sg.x <= a.stage_n && sg.w - sg.z <= a.stage_e;
 }
 
 // Issued by one thread: stage segment sg (positions [x, y), in-edges [z, w)) into st, and the
 // level's piece descriptors si = [i0, i1) when they fit. The level-sorted arrays are allocated
 // with slack so that rounding the ends up to 16 bytes stays inside them.
-__device__ __forceinline__ bool team_desc_fits(const TeamArgs& a, const int2 si) {
+template <class S>
+__device__ __forceinline__ bool team_desc_fits(const S& a, const int2 si) {
     return si.y > si.x && si.y - si.x <= a.stage_p;
 }
 
-__device__ __forceinline__ void team_stage(const TeamArgs& a, const TeamStage& st, unsigned long long* bar, const int4 sg,
+__device__ __forceinline__ void team_stage(const TeamSrc& a, const TeamStage& st, unsigned long long* bar, const int4 sg,
                                            const int2 si) {
     const int a0 = sg.x & ~3, a1 = (sg.y + 3) & ~3, b1 = (sg.y + 4) & ~3;
     const int c0 = sg.z & ~1, c1 = (sg.w + 1) & ~1;
@@ -117,7 +138,7 @@ __device__ __forceinline__ void team_stage(const TeamArgs& a, const TeamStage& s
     if (bd) bulk_g2s(st.pdesc, a.pdesc + si.x, bd, bar);
 }
 
-__device__ __forceinline__ void team_prefetch_seg(const TeamArgs& a, const int4 sg) {
+__device__ __forceinline__ void team_prefetch_seg(const TeamSrc& a, const int4 sg) {
     if (sg.y <= sg.x) return;
     prefetch_l2_range(a.ls_node + sg.x, 4ll * (sg.y - sg.x));
     prefetch_l2_range(a.ls_ptr + sg.x, 4ll * (sg.y - sg.x + 1));
@@ -125,40 +146,23 @@ __device__ __forceinline__ void team_prefetch_seg(const TeamArgs& a, const int4 
 }
 
 // look-ahead for one level, by thread 0 of each CTA: stage it if it fits, else (CTA 0 of the
-// team) prefetch it into L2
-__device__ __forceinline__ void team_ahead_body(const TeamArgs& a, int rank, const TeamStage& st,
-                                                unsigned long long* bar, const int4 sg, const int2 si) {
+// team) prefetch it into L2. Inline: the sources come from shared memory, so the address
+// arithmetic stays within the three-CTAs-per-SM register budget.
+__device__ __forceinline__ void team_ahead(const TeamSrc& a, int rank, const TeamStage& st, unsigned long long* bar,
+                                           const int4 sg, const int2 si) {
     if (team_fits(a, sg)) team_stage(a, st, bar, sg, si);
     else if (rank == 0) team_prefetch_seg(a, sg);
 }
 
-// the payload kernel calls it out of line: its address arithmetic would otherwise push the
-// level loop's registers past the three-CTAs-per-SM budget
-__device__ __noinline__ void team_ahead_call(const TeamArgs& a, int rank, const TeamStage& st, unsigned long long* bar,
-                                             const int4 sg, const int2 si) {
-    team_ahead_body(a, rank, st, bar, sg, si);
+// The slice [x0 + n * r / k, x0 + n * (r + 1) / k) of a range of n that CTA r of a team of k takes.
+__device__ __forceinline__ int team_slice(int x0, int n, int r, int k) {
+    return x0 + (int)(((int64_t)n * r) / k);
 }
 
-template <bool PAY>
-__device__ __forceinline__ void team_ahead(const TeamArgs& a, int rank, const TeamStage& st, unsigned long long* bar,
-                                           const int4 sg, const int2 si) {
-    if (PAY) team_ahead_call(a, rank, st, bar, sg, si);
-    else team_ahead_body(a, rank, st, bar, sg, si);
-}
-
-// Warps of a team that compute a level's arrivals: one task per thread, and the other warps
-// run the level's payload pieces at the same time, when the level has payload and the arrival
-// warps leave some spare; otherwise every warp does arrivals, then pieces (returns nwarp).
-__device__ __forceinline__ int team_arrival_warps(const int4 sg, const int2 si, int nwarp) {
-    const int na = (sg.y - sg.x + 31) >> 5;
-    return (si.y > si.x && na < nwarp) ? na : nwarp;
-}
-
-// L2 prefetch of the x and y ranges of the pieces payload warp w (of nw) runs in a level
-// (items si.x + w + j * nw; lane j takes the j-th), from staged descriptors. Copies touch host
-// memory and are skipped.
-__device__ __forceinline__ void team_prefetch_pieces(const TeamPiece* dsc, const int2 si, int w, int nw, int lane) {
-    for (int it = si.x + w + lane * nw; it < si.y; it += 32 * nw) {
+// L2 prefetch of the x and y ranges of pieces [i0, i1) (one warp, lanes strided), from staged
+// descriptors. Copies touch host memory and are skipped.
+__device__ __forceinline__ void team_prefetch_pieces(const TeamPiece* dsc, int i0, int i1, int lane) {
+    for (int it = i0 + lane; it < i1; it += 32) {
         const TeamPiece d = dsc[it];
         if (d.op == kPayCopy || d.cnt <= 0) continue;
         prefetch_l2_range(d.src, 4ll * d.cnt);
@@ -328,23 +332,24 @@ __device__ __forceinline__ uint32_t team_task_key(const TeamArgs& a, int v, cons
 // copy never landed (the kernel must end).
 template <bool PAY, bool SOLO>
 __device__ __forceinline__ bool team_run_graph(const TeamArgs& a, const TeamJob& job, int k, int rank,
-                                               const TeamStage* sview, unsigned long long* mbar, int4* ring, int2* iring,
-                                               unsigned& phase) {
+                                               const TeamSrc& src, const TeamStage* sview, unsigned long long* mbar,
+                                               int4* ring, int2* iring, int* pcnt, unsigned& phase) {
     const int t = threadIdx.x;
     const int lane = t & 31;
-    const int nthr = k * kTeamThreads, tid = rank * kTeamThreads + t;
-    const int wid = tid >> 5, nwarp = nthr >> 5;
     const int L = job.levels;
     const int2 z2 = make_int2(0, 0);
-    // segment descriptors and item ranges ride a ring in shared memory, written by thread 0
-    // three levels ahead; level l uses stage buffer l % kTeamBufs, staged two levels ahead
+    // segment descriptors and item ranges ride a ring in shared memory, fetched by thread 0
+    // three levels ahead (asynchronous copies, completed before the level's barrier, so that
+    // their latency stays off the level's path); level l uses stage buffer l % kTeamBufs,
+    // staged two levels ahead
     if (t == 0) {
+        pcnt[0] = pcnt[1] = 0;
         for (int q = 0; q < 3 && q < L; ++q) {
             ring[q] = __ldg(a.seg + job.seg0 + q);
             iring[q] = PAY ? __ldg(a.seg_items + job.seg0 + q) : z2;
         }
-        if (L > 0) team_ahead<PAY>(a, rank, sview[0], &mbar[0], ring[0], iring[0]);
-        if (L > 1) team_ahead<PAY>(a, rank, sview[1], &mbar[1], ring[1], iring[1]);
+        if (L > 0) team_ahead(src, rank, sview[0], &mbar[0], ring[0], iring[0]);
+        if (L > 1) team_ahead(src, rank, sview[1], &mbar[1], ring[1], iring[1]);
     }
     __syncthreads();
     if (a.g_start && rank == 0 && t == 0) a.g_start[job.graph] = (int64_t)gtimer();
@@ -353,16 +358,16 @@ __device__ __forceinline__ bool team_run_graph(const TeamArgs& a, const TeamJob&
         const int4 s0 = ring[l & 3];
         const int2 i0 = PAY ? iring[l & 3] : z2;
         if (t == 0) {
-            if (l + 3 < L) {
-                ring[(l + 3) & 3] = __ldg(a.seg + job.seg0 + l + 3);
-                if (PAY) iring[(l + 3) & 3] = __ldg(a.seg_items + job.seg0 + l + 3);
-            }
             if (l + 2 < L)
-                team_ahead<PAY>(a, rank, sview[(l + 2) % kTeamBufs], &mbar[(l + 2) % kTeamBufs], ring[(l + 2) & 3],
+                team_ahead(src, rank, sview[(l + 2) % kTeamBufs], &mbar[(l + 2) % kTeamBufs], ring[(l + 2) & 3],
                                 iring[(l + 2) & 3]);
+            if (l + 3 < L) {
+                cp_async16(&ring[(l + 3) & 3], a.seg + job.seg0 + l + 3);
+                if (PAY) cp_async8(&iring[(l + 3) & 3], a.seg_items + job.seg0 + l + 3);
+                cp_async_commit();
+            }
         }
-        const int na = PAY ? team_arrival_warps(s0, i0, nwarp) : nwarp;
-        const int pw0 = na < nwarp ? na : 0;  // first payload warp
+        if (PAY && t == 0) pcnt[(l + 1) & 1] = 0;  // the next level's piece counter (free since the barrier)
         // arrivals of level l (every CTA of a team stages the whole level and takes its share)
         const int32_t* node = a.ls_node;
         const int32_t* ptr = a.ls_ptr;
@@ -377,6 +382,7 @@ __device__ __forceinline__ bool team_run_graph(const TeamArgs& a, const TeamJob&
                     t0 = now;
                 } else if (now - t0 > a.spin_limit_ns) {  // a bulk copy that never lands
                     if (t == 0) atomicCAS(&a.ctrl->status, 0, (int)HF_ETIMEDOUT);
+                    cp_async_wait_all();
                     return false;
                 }
             }
@@ -388,28 +394,38 @@ __device__ __forceinline__ bool team_run_graph(const TeamArgs& a, const TeamJob&
             in = sv.in - eb;
             if (PAY && team_desc_fits(a, i0)) dsc = sv.pdesc - i0.x;
         }
-        if (wid < na) {
-            for (int p = s0.x + tid; p < s0.y; p += na * 32) {
+        // this CTA's slice of the level's tasks: one per thread
+        {
+            const int p1 = team_slice(s0.x, s0.y - s0.x, rank + 1, k);
+            for (int p = team_slice(s0.x, s0.y - s0.x, rank, k) + t; p < p1; p += kTeamThreads) {
                 const int v = node[p];
                 a.key[v] = team_task_key<SOLO>(a, v, in, ptr[p], ptr[p + 1]);
             }
         }
-        // payload pieces of level l; in cluster jobs each payload warp first warms L2 with the
-        // pieces it will run in the next level, when that level's staged descriptors have landed
-        if (PAY && wid >= pw0) {
-            if (!SOLO && l + 1 < L) {
+        // this CTA's slice of the level's payload pieces: each warp takes the next piece from a
+        // shared counter, the warps without arrivals at once, the others after them. In cluster
+        // jobs the last warp first warms L2 with the CTA's pieces of the next level, when that
+        // level's staged descriptors have landed.
+        if (PAY) {
+            if (!SOLO && t >= kTeamThreads - 32 && l + 1 < L) {
                 const int b1 = (l + 1) % kTeamBufs;
                 const int2 i1 = iring[(l + 1) & 3];
-                const int4 s1 = ring[(l + 1) & 3];
-                const int na1 = team_arrival_warps(s1, i1, nwarp);
-                const int q0 = na1 < nwarp ? na1 : 0;
-                if (wid >= q0 && team_fits(a, s1) && team_desc_fits(a, i1) &&
+                if (team_fits(a, ring[(l + 1) & 3]) && team_desc_fits(a, i1) &&
                     mbar_try_wait(&mbar[b1], (phase >> b1) & 1u))
-                    team_prefetch_pieces(sview[b1].pdesc - i1.x, i1, wid - q0, nwarp - q0, lane);
+                    team_prefetch_pieces(sview[b1].pdesc - i1.x, team_slice(i1.x, i1.y - i1.x, rank, k),
+                                         team_slice(i1.x, i1.y - i1.x, rank + 1, k), lane);
             }
-            for (int it = i0.x + (wid - pw0); it < i0.y; it += nwarp - pw0) team_run_piece(dsc[it], lane);
+            const int q0 = team_slice(i0.x, i0.y - i0.x, rank, k), q1 = team_slice(i0.x, i0.y - i0.x, rank + 1, k);
+            for (;;) {
+                int it = 0;
+                if (lane == 0) it = q0 + atomicAdd(&pcnt[l & 1], 1);
+                it = __shfl_sync(0xffffffffu, it, 0);
+                if (it >= q1) break;
+                team_run_piece(dsc[it], lane);
+            }
         }
         if (a.seg_host && rank == 0 && t == 0) team_host_tasks(a, job.seg0 + l);
+        if (t == 0) cp_async_wait_all();  // ring entry l + 3
         if (SOLO) __syncthreads();
         else cluster_sync();
     }
@@ -426,12 +442,15 @@ template <bool PAY>
 __global__ void __launch_bounds__(kTeamThreads, 3) k_team(const TeamArgs a) {
     extern __shared__ __align__(16) unsigned char s_stage[];  // kTeamBufs stage buffers
     __shared__ TeamStage s_view[kTeamBufs];
+    __shared__ TeamSrc s_src;
     __shared__ __align__(8) unsigned long long mbar[kTeamBufs];
     __shared__ __align__(16) TeamJob s_job;
     __shared__ int4 s_ring[4];
     __shared__ int2 s_iring[4];
+    __shared__ int s_pcnt[2];  // payload piece counters, alternating by level
     const int t = threadIdx.x;
     if (t == 0) {
+        s_src = TeamSrc{a.ls_node, a.ls_ptr, a.ls_in, a.pdesc, a.stage_n, a.stage_e, a.stage_p, 0};
         for (int b = 0; b < kTeamBufs; ++b) {
             mbar_init(&mbar[b], 1);
             s_view[b] = team_stage_view(s_stage, b, a.stage_n, a.stage_e, a.stage_p);
@@ -455,7 +474,7 @@ __global__ void __launch_bounds__(kTeamThreads, 3) k_team(const TeamArgs a) {
             const TeamJob job = s_job;
             cluster_sync();  // all have read s_job before CTA 0 may overwrite it
             if (job.graph < 0) break;
-            if (!team_run_graph<PAY, false>(a, job, k, rank, s_view, mbar, s_ring, s_iring, phase)) return;
+            if (!team_run_graph<PAY, false>(a, job, k, rank, s_src, s_view, mbar, s_ring, s_iring, s_pcnt, phase)) return;
         }
     }
     for (;;) {
@@ -467,7 +486,7 @@ __global__ void __launch_bounds__(kTeamThreads, 3) k_team(const TeamArgs a) {
         const TeamJob job = s_job;
         __syncthreads();
         if (job.graph < 0) break;
-        if (!team_run_graph<PAY, true>(a, job, 1, 0, s_view, mbar, s_ring, s_iring, phase)) return;
+        if (!team_run_graph<PAY, true>(a, job, 1, 0, s_src, s_view, mbar, s_ring, s_iring, s_pcnt, phase)) return;
     }
 }
 
