@@ -26,6 +26,9 @@ namespace hf {
 
 constexpr int kTeamThreads = 256;
 constexpr int kTeamBufs = 3;       // staged levels: the current one and two ahead
+// The thread that runs a CTA's look-ahead (segment ring, stage copies): lane 0 of the last warp,
+// which takes arrivals only when the CTA's slice of a level exceeds 224 tasks.
+constexpr int kTeamLead = kTeamThreads - 32;
 // Stage buffers live in dynamic shared memory, sized per plan (TeamArgs::stage_n tasks,
 // stage_e in-edges and stage_p piece descriptors per level; stage_n a multiple of 4, stage_e of
 // 2): node[stage_n + 8] (copied from a 16-byte aligned start, up to 3 extra entries in front),
@@ -338,11 +341,11 @@ __device__ __forceinline__ bool team_run_graph(const TeamArgs& a, const TeamJob&
     const int lane = t & 31;
     const int L = job.levels;
     const int2 z2 = make_int2(0, 0);
-    // segment descriptors and item ranges ride a ring in shared memory, fetched by thread 0
-    // three levels ahead (asynchronous copies, completed before the level's barrier, so that
-    // their latency stays off the level's path); level l uses stage buffer l % kTeamBufs,
+    // segment descriptors and item ranges ride a ring in shared memory, fetched by the lead
+    // thread three levels ahead (asynchronous copies, completed before the level's barrier, so
+    // that their latency stays off the level's path); level l uses stage buffer l % kTeamBufs,
     // staged two levels ahead
-    if (t == 0) {
+    if (t == kTeamLead) {
         pcnt[0] = pcnt[1] = 0;
         for (int q = 0; q < 3 && q < L; ++q) {
             ring[q] = __ldg(a.seg + job.seg0 + q);
@@ -357,7 +360,7 @@ __device__ __forceinline__ bool team_run_graph(const TeamArgs& a, const TeamJob&
         const int b = l % kTeamBufs;
         const int4 s0 = ring[l & 3];
         const int2 i0 = PAY ? iring[l & 3] : z2;
-        if (t == 0) {
+        if (t == kTeamLead) {
             if (l + 2 < L)
                 team_ahead(src, rank, sview[(l + 2) % kTeamBufs], &mbar[(l + 2) % kTeamBufs], ring[(l + 2) & 3],
                                 iring[(l + 2) & 3]);
@@ -367,7 +370,7 @@ __device__ __forceinline__ bool team_run_graph(const TeamArgs& a, const TeamJob&
                 cp_async_commit();
             }
         }
-        if (PAY && t == 0) pcnt[(l + 1) & 1] = 0;  // the next level's piece counter (free since the barrier)
+        if (PAY && t == kTeamLead) pcnt[(l + 1) & 1] = 0;  // the next level's piece counter (free since the barrier)
         // arrivals of level l (every CTA of a team stages the whole level and takes its share)
         const int32_t* node = a.ls_node;
         const int32_t* ptr = a.ls_ptr;
@@ -425,7 +428,7 @@ __device__ __forceinline__ bool team_run_graph(const TeamArgs& a, const TeamJob&
             }
         }
         if (a.seg_host && rank == 0 && t == 0) team_host_tasks(a, job.seg0 + l);
-        if (t == 0) cp_async_wait_all();  // ring entry l + 3
+        if (t == kTeamLead) cp_async_wait_all();  // ring entry l + 3
         if (SOLO) __syncthreads();
         else cluster_sync();
     }
