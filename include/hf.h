@@ -292,6 +292,10 @@ hf_status hf_batch_get_graph_times(hf_batch* b, int64_t* start_ns, int64_t* end_
  * level for the level-synchronous executor, 2 for the persistent one (reset + executor), one
  * per team class for the team executor. */
 hf_status hf_batch_last_launches(hf_batch* b, int32_t* n);
+/* Team size (CTAs) each graph of the batch ran on in the last team-executor run, into a host
+ * array of the batch's graph count: 1 for a single-CTA job, 2, 4, 8 or 16 for a thread-block
+ * cluster, 0 for a graph without tasks. HF_ESTATE before the first team-executor run. */
+hf_status hf_batch_team_plan(hf_batch* b, int32_t* team_size);
 /* As hf_set_delays for every graph of the batch: delay holds the graphs' edge delays
  * concatenated in batch order (sum of their edge counts). */
 hf_status hf_batch_set_delays(hf_batch* b, const float* delay, int on_device, void* stream);

@@ -914,6 +914,12 @@ hf_status hf_batch_last_launches(hf_batch* b, int32_t* n) {
     return plan_last_launches(b->plan, n);
 }
 
+hf_status hf_batch_team_plan(hf_batch* b, int32_t* team_size) {
+    if (!b || !team_size) return fail(HF_EINVAL, "NULL argument");
+    if (!b->plan) return fail(HF_ESTATE, "batch has not run");
+    return plan_team_plan(b->plan, team_size);
+}
+
 hf_status hf_batch_kernel_ms(hf_batch* b, float* ms) {
     if (!b || !ms) return fail(HF_EINVAL, "NULL argument");
     if (!b->plan) return fail(HF_ESTATE, "batch has not run");

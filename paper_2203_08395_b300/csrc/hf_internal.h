@@ -305,6 +305,7 @@ hf_status plan_kernel_ms(Plan* p, float* ms);
 hf_status plan_get_stats(Plan* p, int64_t* out, int32_t n);
 hf_status plan_get_graph_times(Plan* p, int64_t* start, int64_t* end);
 hf_status plan_last_launches(Plan* p, int32_t* n);
+hf_status plan_team_plan(Plan* p, int32_t* team_size);
 hf_status plan_set_delays(Plan* p, const float* delay, int on_device, cudaStream_t s);
 hf_status plan_features(Plan* p, float* X, cudaStream_t s);
 hf_status plan_task_costs(Plan* p, int32_t priority, const hf_costmodel* cm, float* cost, float* bottom,

@@ -52,6 +52,7 @@ struct Plan {
     std::vector<int4> h_seg;          // (graph, level) segment -> {p0, p1, e0, e1}
     std::vector<int32_t> seg_first;   // graph -> first segment (ngraphs + 1)
     std::vector<int32_t> glevels;     // graph -> levels
+    std::vector<int32_t> team_k;      // graph -> team size of the current team plan (0: no levels)
     int4* d_seg = nullptr;
     int2* d_seg_items = nullptr;      // segment -> payload items {i0, i1} (per piece size)
     size_t cap_seg_items = 0;
@@ -1092,6 +1093,12 @@ hf_status plan_last_launches(Plan* p, int32_t* n) {
     return HF_OK;
 }
 
+hf_status plan_team_plan(Plan* p, int32_t* team_size) {
+    if (p->team_k.size() != (size_t)p->ngraphs) return fail(HF_ESTATE, "no team-executor run yet");
+    std::memcpy(team_size, p->team_k.data(), sizeof(int32_t) * p->team_k.size());
+    return HF_OK;
+}
+
 hf_status plan_kernel_ms(Plan* p, float* ms) {
     if (!p->ran || !p->last_timed) return fail(HF_ESTATE, "last run was not a time_kernel run");
     cudaError_t e = cudaEventSynchronize(p->kev1);
@@ -1817,6 +1824,8 @@ static hf_status plan_team_jobs(Plan* p, const hf_run_opts& o, cudaStream_t s) {
     if (st != HF_OK) return st;
     if (o.team_size > 0)
         for (auto& x : k) x = std::min(o.team_size, kTeamMaxCluster);
+    p->team_k.assign((size_t)p->ngraphs, 0);
+    for (int32_t g : order) p->team_k[(size_t)g] = k[(size_t)g];
     std::vector<TeamJob> jobs;
     p->tclass.clear();
     int cap1 = team_capacity(p, 1);

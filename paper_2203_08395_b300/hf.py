@@ -143,6 +143,7 @@ def load():
         "hf_run_csr_noalloc": [i32, i32, vp, vp, vp, vp, vp, ctypes.c_uint64, vp],
         "hf_batch_get_graph_times": [vp, vp, vp],
         "hf_batch_last_launches": [vp, P(i32)],
+        "hf_batch_team_plan": [vp, vp],
         "hf_calibration": [vp, vp],
         "hf_dump": [vp, ctypes.c_char_p],
         "hf_place": [vp, i32, vp, vp],
@@ -505,6 +506,13 @@ def hf_batch_last_launches(b):
     n = ctypes.c_int32()
     _check(load().hf_batch_last_launches(b, ctypes.byref(n)), "hf_batch_last_launches")
     return n.value
+
+
+def hf_batch_team_plan(b, ngraphs):
+    """Team size each graph ran on in the last team-executor run (int32 array)."""
+    k = np.zeros(ngraphs, np.int32)
+    _check(load().hf_batch_team_plan(b, k.ctypes.data), "hf_batch_team_plan")
+    return k
 
 
 def hf_calibration(stream=None):

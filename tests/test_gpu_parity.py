@@ -180,6 +180,28 @@ def test_batch_mixed_small(ex):
     bd.close()
 
 
+def test_team_plan_reports_team_sizes():
+    wl = S.batch(3, graphs=16, nmin=500, nmax=60000, frac_saxpy=0.1)
+    bd = BatchOnDevice(wl)
+    G = len(wl.graphs)
+    with pytest.raises(hf.HfError):
+        hf.hf_batch_team_plan(bd.b, G)  # no run yet
+    bd.run(mode=hf.HF_MODE_LEVELSYNC)
+    bd.sync()
+    with pytest.raises(hf.HfError):
+        hf.hf_batch_team_plan(bd.b, G)  # no team-executor run yet
+    bd.run(mode=hf.HF_MODE_TEAM, team_size=4)
+    bd.sync()
+    assert (hf.hf_batch_team_plan(bd.b, G) == 4).all()
+    bd.run(mode=hf.HF_MODE_TEAM, priority=hf.HF_PRIO_HEURISTIC)
+    bd.sync()
+    k = hf.hf_batch_team_plan(bd.b, G)
+    assert set(k.tolist()) <= {1, 2, 4, 8, 16}
+    for i, spec in enumerate(wl.graphs):
+        np.testing.assert_array_equal(bits(bd.arrivals(i)), bits(oracle.run_spec(spec)["arr"]))
+    bd.close()
+
+
 # ------------------------------------------------------------------ the paper's examples
 
 def test_paper_saxpy_graph_through_c_abi():
