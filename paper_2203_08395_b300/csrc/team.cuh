@@ -292,25 +292,42 @@ __device__ __forceinline__ void st_cluster_job(TeamJob* local, unsigned rank, co
 
 // ---------------------------------------------------------------- one level
 
+// Arrival keys are loaded and stored with an L2 evict-last policy: a predecessor may sit
+// anywhere earlier in its graph, and the keys should stay in L2 while the payload pieces stream
+// through it with evict-first hints.
+__device__ __forceinline__ uint64_t l2_keep_policy() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
 // Predecessors' keys were written by this CTA (solo job: ordinary loads, L1 may hold them) or
 // by another CTA of the cluster (loads from L2, after the cluster barrier's acquire).
 template <bool SOLO>
-__device__ __forceinline__ uint32_t team_pred_key(const TeamArgs& a, int u) {
-    if (SOLO) return a.key[u];
-    return __ldcg(a.key + u);
+__device__ __forceinline__ uint32_t team_pred_key(const TeamArgs& a, int u, uint64_t pol) {
+    uint32_t v;
+    if (SOLO)
+        asm volatile("ld.global.ca.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(a.key + u), "l"(pol) : "memory");
+    else
+        asm volatile("ld.global.cg.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(a.key + u), "l"(pol) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void team_store_key(uint32_t* p, uint32_t v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.u32 [%0], %1, %2;" ::"l"(p), "r"(v), "l"(pol) : "memory");
 }
 
 // max over in-edges [e0, e1) of key(arr[u] + d): all key loads of a batch of up to 8 in-edges
 // are issued before the first is used, so a task's gather costs one round trip
 template <bool SOLO>
-__device__ __forceinline__ uint32_t team_fold(const TeamArgs& a, const int2* in, int e0, int e1) {
+__device__ __forceinline__ uint32_t team_fold(const TeamArgs& a, const int2* in, int e0, int e1, uint64_t pol) {
     uint32_t best = 0u;
     for (int e = e0; e < e1; e += 8) {
         const int cnt = e1 - e < 8 ? e1 - e : 8;
         uint32_t kk[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j)
-            if (j < cnt) kk[j] = team_pred_key<SOLO>(a, in[e + j].x);
+            if (j < cnt) kk[j] = team_pred_key<SOLO>(a, in[e + j].x, pol);
         // the delays are read again once the keys are in (fewer live registers)
         const volatile int* dl = reinterpret_cast<const volatile int*>(in + e) + 1;
 #pragma unroll
@@ -321,9 +338,10 @@ __device__ __forceinline__ uint32_t team_fold(const TeamArgs& a, const int2* in,
 }
 
 template <bool SOLO>
-__device__ __forceinline__ uint32_t team_task_key(const TeamArgs& a, int v, const int2* in, int e0, int e1) {
+__device__ __forceinline__ uint32_t team_task_key(const TeamArgs& a, int v, const int2* in, int e0, int e1,
+                                                  uint64_t pol) {
     if (e0 == e1) return a.key0 ? __ldg(a.key0 + v) : kKeyPosZero;
-    return team_fold<SOLO>(a, in, e0, e1);
+    return team_fold<SOLO>(a, in, e0, e1, pol);
 }
 
 // ---------------------------------------------------------------- one graph
@@ -400,9 +418,10 @@ __device__ __forceinline__ bool team_run_graph(const TeamArgs& a, const TeamJob&
         // this CTA's slice of the level's tasks: one per thread
         {
             const int p1 = team_slice(s0.x, s0.y - s0.x, rank + 1, k);
+            const uint64_t pol = l2_keep_policy();
             for (int p = team_slice(s0.x, s0.y - s0.x, rank, k) + t; p < p1; p += kTeamThreads) {
                 const int v = node[p];
-                a.key[v] = team_task_key<SOLO>(a, v, in, ptr[p], ptr[p + 1]);
+                team_store_key(a.key + v, team_task_key<SOLO>(a, v, in, ptr[p], ptr[p + 1], pol), pol);
             }
         }
         // this CTA's slice of the level's payload pieces: each warp takes the next piece from a
