@@ -403,13 +403,16 @@ def main():
         delays = torch.cat([torch.from_numpy(g.delay) for g in wl.graphs]).pin_memory()
         arr_host = torch.empty(N, dtype=torch.float32, pin_memory=True)
         steps = max(3, args.steps // 4)
+        # the public call a user makes per timing view: delays in from page-locked host memory,
+        # run, every arrival out to page-locked host memory (non-blocking; the device orders
+        # consecutive steps; synchronised once at the end of the timed region)
         for i in range(steps + 2):
             if i == 2:
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
-            hf.hf_batch_set_delays(bd.b, delays, on_device=False, stream=stream)
-            bd.run(stream, **head)
-            hf.hf_batch_get_arrivals(bd.b, -1, N, out=arr_host.numpy())
+            bd.run_host(delays, arr_host, stream, **head)
+            if i < 2:
+                bd.sync()
         st = bd.sync(check=False)
         dt = max_over_ranks((time.perf_counter() - t0) / steps, "cuda")
         e2e = {"value": job_rate(N_all, 1e3 * dt), "unit": "tasks/s", "h2d_bytes_per_step": 4 * E,

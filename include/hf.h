@@ -214,6 +214,19 @@ hf_status hf_get_levels(const hf_graph* g, int32_t* level_out);
  * defaults. Device-side failures are reported by hf_sync_status. Re-running a graph re-runs
  * every payload (saxpy updates y again). */
 hf_status hf_run(hf_graph* g, void* stream, const hf_run_opts* opts);
+/* One execution on new edge delays read from host memory, with every arrival copied back to
+ * host memory: the same result as hf_set_delays(delay, host) + hf_run + hf_get_arrivals, but
+ * non-blocking like hf_run. The paper has no counterpart; it serves callers that stream timing
+ * views through the graph. delay: m floats in insertion order (as hf_set_delays), or NULL to
+ * keep the current delays; arr_out: n floats, or NULL. Both must be page-locked host memory
+ * (cudaHostAlloc / cudaHostRegister), else HF_EINVAL and nothing is enqueued. The device reads
+ * delay directly (no staging copy) on `stream` before the run; leave it unchanged until the
+ * run has ended. The arrivals are converted on `stream` after the run and copied to arr_out on
+ * a stream of the library's own, so that `stream` goes on at once with the caller's next work
+ * (the next view's delays and run overlap this copy): arr_out is complete when hf_sync_status
+ * for this run returns (a synchronisation of `stream` alone does not cover the copy).
+ * Non-finite delays: as hf_set_delays. */
+hf_status hf_run_host(hf_graph* g, void* stream, const hf_run_opts* opts, const float* delay, float* arr_out);
 
 /* Section III-B's run_n and run_until. hf_run_n enqueues n runs back to back on `stream` (the
  * plan is reused; payloads apply n times) and returns at once; hf_sync_status then reports the
@@ -264,6 +277,11 @@ hf_status hf_batch_destroy(hf_batch* b);
  * be mutated while it belongs to a batch (HF_ESTATE); destroy the batch first. */
 hf_status hf_batch_add(hf_batch* b, hf_graph* g, int32_t* index_out);
 hf_status hf_batch_run(hf_batch* b, void* stream, const hf_run_opts* opts);
+/* As hf_run_host for a batch: delay holds every graph's edge delays concatenated in batch order
+ * (as hf_batch_set_delays), arr_out receives every graph's arrivals concatenated in batch order
+ * (as hf_batch_get_arrivals with index -1); arr_out is complete when hf_batch_sync_status for
+ * this run returns. */
+hf_status hf_batch_run_host(hf_batch* b, void* stream, const hf_run_opts* opts, const float* delay, float* arr_out);
 hf_status hf_batch_sync_status(hf_batch* b);
 hf_status hf_batch_run_n(hf_batch* b, void* stream, const hf_run_opts* opts, int32_t n);
 /* Sharding of a batch over ndev devices (one process per GPU, each running its own share):

@@ -613,6 +613,21 @@ hf_status hf_run(hf_graph* g, void* stream, const hf_run_opts* opts) {
     return plan_run(g->plan, (cudaStream_t)stream, o);
 }
 
+hf_status hf_run_host(hf_graph* g, void* stream, const hf_run_opts* opts, const float* delay, float* arr_out) {
+    if (!g) return fail(HF_EINVAL, "graph is NULL");
+    if (g->dirty && g->plan) {
+        if (plan_busy(g->plan) != HF_OK) return fail(HF_ESTATE, "a run of this graph is in flight");
+        plan_destroy(g->plan);
+        g->plan = nullptr;
+    }
+    hf_status st = ensure_plan(g);
+    if (st != HF_OK) return st;
+    hf_run_opts o;
+    if (opts) o = *opts;
+    else hf_run_opts_default(&o);
+    return plan_run_host(g->plan, (cudaStream_t)stream, o, delay, arr_out);
+}
+
 hf_status hf_run_n(hf_graph* g, void* stream, const hf_run_opts* opts, int32_t n) {
     if (!g) return fail(HF_EINVAL, "graph is NULL");
     if (n < 0) return fail(HF_EINVAL, "n < 0");
@@ -817,6 +832,16 @@ hf_status hf_batch_run(hf_batch* b, void* stream, const hf_run_opts* opts) {
     if (opts) o = *opts;
     else hf_run_opts_default(&o);
     return plan_run(b->plan, (cudaStream_t)stream, o);
+}
+
+hf_status hf_batch_run_host(hf_batch* b, void* stream, const hf_run_opts* opts, const float* delay, float* arr_out) {
+    if (!b) return fail(HF_EINVAL, "batch is NULL");
+    hf_status st = ensure_batch_plan(b);
+    if (st != HF_OK) return st;
+    hf_run_opts o;
+    if (opts) o = *opts;
+    else hf_run_opts_default(&o);
+    return plan_run_host(b->plan, (cudaStream_t)stream, o, delay, arr_out);
 }
 
 hf_status hf_batch_run_n(hf_batch* b, void* stream, const hf_run_opts* opts, int32_t n) {

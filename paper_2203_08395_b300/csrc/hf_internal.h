@@ -295,7 +295,11 @@ hf_status plan_build(const std::vector<hf_graph*>& graphs, Plan** out);
 void plan_destroy(Plan* p);
 // keep_status: a later run of a sequence (hf_run_n) keeps the device status word of the runs
 // before it, so the sequence reports its first failure
-hf_status plan_run(Plan* p, cudaStream_t s, const hf_run_opts& o, bool keep_status = false);
+// io_dly (device-accessible view of page-locked host memory, or NULL): the run first takes its
+// edge delays from it; io_arr (page-locked host memory, or NULL): every arrival is copied there
+// after the run, on the plan's copy stream (see hf_batch_run_host).
+hf_status plan_run(Plan* p, cudaStream_t s, const hf_run_opts& o, bool keep_status = false,
+                   const float* io_dly = nullptr, float* io_arr = nullptr);
 hf_status plan_sync(Plan* p);
 hf_status plan_busy(Plan* p);  // HF_ESTATE while a run is in flight
 hf_status plan_get_arrivals(Plan* p, int32_t gi, float* out, int on_device);
@@ -307,6 +311,7 @@ hf_status plan_get_graph_times(Plan* p, int64_t* start, int64_t* end);
 hf_status plan_last_launches(Plan* p, int32_t* n);
 hf_status plan_team_plan(Plan* p, int32_t* team_size);
 hf_status plan_set_delays(Plan* p, const float* delay, int on_device, cudaStream_t s);
+hf_status plan_run_host(Plan* p, cudaStream_t s, const hf_run_opts& o, const float* delay, float* arr_out);
 hf_status plan_features(Plan* p, float* X, cudaStream_t s);
 hf_status plan_task_costs(Plan* p, int32_t priority, const hf_costmodel* cm, float* cost, float* bottom,
                           cudaStream_t s);

@@ -151,6 +151,11 @@ struct Plan {
     int32_t* d_level = nullptr;
     uint8_t* d_cat = nullptr;
     int32_t* d_toff = nullptr;
+    // host-buffer runs (hf_run_host): the arrivals go to the host from d_arr on a stream of the
+    // plan's own, overlapping the caller's next work; d_arr is reused only after that copy
+    cudaStream_t cstream = nullptr;
+    cudaEvent_t ev_conv = nullptr, ev_d2h = nullptr;
+    bool d2h_pending = false;
     float4* d_gstat = nullptr;
     float* d_prio = nullptr;       // bottom-level weight per task under seed_prio
     int32_t seed_prio = HF_PRIO_FIFO;  // priority the seed order was built for
@@ -226,6 +231,7 @@ static uint32_t host_f2key(float f) {
 void plan_destroy(Plan* p) {
     if (!p) return;
     if (p->ran && p->done_ev) cudaEventSynchronize(p->done_ev);
+    if (p->d2h_pending) cudaEventSynchronize(p->ev_d2h);
     if (p->proxy.joinable()) p->proxy.join();
     if (p->h_post) cudaFreeHost(p->h_post);
     if (p->h_hdone) cudaFreeHost(p->h_hdone);
@@ -241,6 +247,9 @@ void plan_destroy(Plan* p) {
         if (p->tev_join[i]) cudaEventDestroy(p->tev_join[i]);
     }
     if (p->tev_fork) cudaEventDestroy(p->tev_fork);
+    if (p->cstream) cudaStreamDestroy(p->cstream);
+    if (p->ev_conv) cudaEventDestroy(p->ev_conv);
+    if (p->ev_d2h) cudaEventDestroy(p->ev_d2h);
     delete p;
 }
 
@@ -714,6 +723,7 @@ static hf_status build_level_graph(Plan* p) {
 hf_status plan_busy(Plan* p) {
     if (!p || !p->ran) return HF_OK;
     cudaError_t e = cudaEventQuery(p->done_ev);
+    if (e == cudaSuccess && p->d2h_pending) e = cudaEventQuery(p->ev_d2h);
     if (e == cudaErrorNotReady) {
         cudaGetLastError();
         return HF_ESTATE;
@@ -787,7 +797,34 @@ static void team_host_proxy(Plan* p, uint64_t limit_ns) {
     }
 }
 
-hf_status plan_run(Plan* p, cudaStream_t s, const hf_run_opts& o, bool keep_status) {
+// Arrivals of the run just enqueued on s to page-locked host memory: converted into d_arr on s,
+// copied out on the plan's copy stream, so that s goes on with the caller's next work (a new
+// delay upload, the next run) while the copy runs. The next use of d_arr waits for the copy.
+static hf_status arrivals_to_host(Plan* p, cudaStream_t s, float* host) {
+    cudaError_t e = cudaSuccess;
+    if (!p->cstream) {
+        e = cudaStreamCreateWithFlags(&p->cstream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_conv, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_d2h, cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(e, "copy stream");
+    }
+    if (!p->d_arr) {
+        p->d_arr = (float*)palloc(p, std::max<size_t>(4 * (size_t)p->n, 16), s);
+        if (!p->d_arr) return fail(HF_ENOMEM, "device allocation failed");
+    }
+    if (p->d2h_pending && (e = cudaStreamWaitEvent(s, p->ev_d2h, 0)) != cudaSuccess) return cuda_fail(e, "arrival copy");
+    const int grid = (int)std::min<int64_t>(((int64_t)p->n + 255) / 256, (int64_t)p->num_sms * 16);
+    k_keys_to_f32<<<grid, 256, 0, s>>>(p->d_key, p->d_arr, p->n);
+    if ((e = cudaEventRecord(p->ev_conv, s)) != cudaSuccess || (e = cudaStreamWaitEvent(p->cstream, p->ev_conv, 0)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(host, p->d_arr, 4 * (size_t)p->n, cudaMemcpyDeviceToHost, p->cstream)) != cudaSuccess ||
+        (e = cudaEventRecord(p->ev_d2h, p->cstream)) != cudaSuccess)
+        return cuda_fail(e, "arrival copy");
+    p->d2h_pending = true;
+    return HF_OK;
+}
+
+hf_status plan_run(Plan* p, cudaStream_t s, const hf_run_opts& o, bool keep_status, const float* io_dly,
+                   float* io_arr) {
     int mode = o.mode;
     if (mode == HF_MODE_AUTO) {
         if (!p->host_tasks.empty()) {
@@ -815,6 +852,8 @@ hf_status plan_run(Plan* p, cudaStream_t s, const hf_run_opts& o, bool keep_stat
     if (st != HF_OK) return st;
     const bool instr = (o.instrument & 1) != 0, valid = o.validate != 0;
     if ((st = ensure_instr(p, instr, valid, s)) != HF_OK) return st;
+    // host buffers: new delays scattered from page-locked host memory before the run
+    if (io_dly && (st = plan_set_delays(p, io_dly, 1, s)) != HF_OK) return st;
     cudaError_t e = keep_status ? cudaSuccess : cudaMemsetAsync(&p->d_ctrl->status, 0, sizeof(int32_t), s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
     if (p->n > 0) {
@@ -989,6 +1028,7 @@ hf_status plan_run(Plan* p, cudaStream_t s, const hf_run_opts& o, bool keep_stat
             else k_persist<false><<<ctas, kWarpsPerCta * 32, 0, s>>>(a);
             if (o.time_kernel) cudaEventRecord(p->kev1, s);
         }
+        if (io_arr && (st = arrivals_to_host(p, s, io_arr)) != HF_OK) return st;
         e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
     }
@@ -1008,9 +1048,18 @@ hf_status plan_run(Plan* p, cudaStream_t s, const hf_run_opts& o, bool keep_stat
     return HF_OK;
 }
 
+hf_status plan_run_host(Plan* p, cudaStream_t s, const hf_run_opts& o, const float* delay, float* arr_out) {
+    const float* dv = nullptr;
+    if (delay && p->m > 0 && !(dv = (const float*)host_dev_ptr(delay)))
+        return fail(HF_EINVAL, "delay is not page-locked host memory");
+    if (arr_out && p->n > 0 && !host_dev_ptr(arr_out)) return fail(HF_EINVAL, "arr_out is not page-locked host memory");
+    return plan_run(p, s, o, false, dv, p->n > 0 ? arr_out : nullptr);
+}
+
 hf_status plan_sync(Plan* p) {
     if (!p->ran) return fail(HF_ESTATE, "not run");
     cudaError_t e = cudaEventSynchronize(p->done_ev);
+    if (e == cudaSuccess && p->d2h_pending) e = cudaEventSynchronize(p->ev_d2h);  // arrivals to the host
     if (p->proxy.joinable()) p->proxy.join();
     if (e != cudaSuccess) return cuda_fail(e, "run");
     const int32_t s = p->h_status[0];
@@ -1037,6 +1086,7 @@ hf_status plan_get_arrivals(Plan* p, int32_t gi, float* out, int on_device) {
         p->d_arr = (float*)palloc(p, std::max<size_t>(4 * (size_t)p->n, 16), s);
         if (!p->d_arr) return fail(HF_ENOMEM, "device allocation failed");
     }
+    if (p->d2h_pending) cudaStreamWaitEvent(s, p->ev_d2h, 0);
     k_keys_to_f32<<<grid, 256, 0, s>>>(p->d_key + off, p->d_arr + off, cnt);
     cudaError_t e = cudaMemcpyAsync(out, p->d_arr + off, 4 * (size_t)cnt, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

@@ -104,6 +104,7 @@ def load():
         "hf_graph_info": [vp, P(hf_graph_info_t)],
         "hf_get_levels": [vp, vp],
         "hf_run": [vp, vp, P(hf_run_opts)],
+        "hf_run_host": [vp, vp, P(hf_run_opts), vp, vp],
         "hf_sync_status": [vp],
         "hf_get_arrivals": [vp, vp, ctypes.c_int],
         "hf_get_stamps": [vp, vp, vp, vp],
@@ -112,6 +113,7 @@ def load():
         "hf_batch_destroy": [vp],
         "hf_batch_add": [vp, vp, P(i32)],
         "hf_batch_run": [vp, vp, P(hf_run_opts)],
+        "hf_batch_run_host": [vp, vp, P(hf_run_opts), vp, vp],
         "hf_batch_sync_status": [vp],
         "hf_batch_get_arrivals": [vp, i32, vp, ctypes.c_int],
         "hf_batch_get_task_times": [vp, i32, vp, vp],
@@ -292,6 +294,13 @@ def hf_run(g, stream=None, opts=None):
     _check(load().hf_run(g, _stream_handle(stream), ctypes.byref(o)), "hf_run")
 
 
+def hf_run_host(g, delay, arr_out, stream=None, opts=None):
+    """hf_run on new delays from page-locked host memory, arrivals written to page-locked host
+    memory (float32 tensors or arrays; None for either to skip it). Non-blocking."""
+    o = opts if opts is not None else hf_run_opts_default()
+    _check(load().hf_run_host(g, _stream_handle(stream), ctypes.byref(o), _ptr(delay), _ptr(arr_out)), "hf_run_host")
+
+
 def hf_sync_status(g, check=True):
     s = load().hf_sync_status(g)
     if check:
@@ -340,6 +349,14 @@ def hf_batch_add(b, g):
 def hf_batch_run(b, stream=None, opts=None):
     o = opts if opts is not None else hf_run_opts_default()
     _check(load().hf_batch_run(b, _stream_handle(stream), ctypes.byref(o)), "hf_batch_run")
+
+
+def hf_batch_run_host(b, delay, arr_out, stream=None, opts=None):
+    """hf_batch_run on new delays from page-locked host memory (batch edge order), every arrival
+    written to page-locked host memory (batch task order). Non-blocking."""
+    o = opts if opts is not None else hf_run_opts_default()
+    _check(load().hf_batch_run_host(b, _stream_handle(stream), ctypes.byref(o), _ptr(delay), _ptr(arr_out)),
+           "hf_batch_run_host")
 
 
 def hf_batch_sync_status(b, check=True):

@@ -158,6 +158,9 @@ class GraphOnDevice:
     def run(self, stream=None, **opts):
         hf.hf_run(self.g, stream, hf.hf_run_opts_default(**opts))
 
+    def run_host(self, delay, arr_out, stream=None, **opts):
+        hf.hf_run_host(self.g, delay, arr_out, stream, hf.hf_run_opts_default(**opts))
+
     def sync(self, check=True):
         return hf.hf_sync_status(self.g, check)
 
@@ -196,6 +199,9 @@ class BatchOnDevice:
 
     def run(self, stream=None, **opts):
         hf.hf_batch_run(self.b, stream, hf.hf_run_opts_default(**opts))
+
+    def run_host(self, delay, arr_out, stream=None, **opts):
+        hf.hf_batch_run_host(self.b, delay, arr_out, stream, hf.hf_run_opts_default(**opts))
 
     def sync(self, check=True):
         return hf.hf_batch_sync_status(self.b, check)

@@ -465,6 +465,59 @@ def test_new_timing_view_through_set_delays(ex):
     bd.close()
 
 
+@pytest.mark.parametrize("ex", ["levelsync", "persistent", "team", "team_heur", "team_k2"])
+def test_run_host_streams_timing_views(ex):
+    """hf_batch_run_host: delays in from page-locked memory and arrivals out to it, in one call,
+    for several timing views in a row (each the oracle's arrivals on its delays); payloads run as
+    in hf_batch_run; NULL delays keep the current ones; unpinned buffers are rejected."""
+    wl = S.batch(6, graphs=10, nmin=500, nmax=30000, frac_saxpy=0.1, sx_min=1, sx_max=3000)
+    bd = BatchOnDevice(wl)
+    N = wl.n_tasks
+    views = [[S.uniform_f32(91 + v, i, g.m, -0.5, 2.0) for i, g in enumerate(wl.graphs)] for v in range(3)]
+    outs = [torch.empty(N, dtype=torch.float32).pin_memory() for _ in views]
+    for v, new in enumerate(views):
+        dl = torch.from_numpy(np.concatenate(new)).pin_memory()
+        bd.run_host(dl, outs[v], chunk_elems=256, **EXECUTORS[ex])
+        bd.sync()
+        ref = np.concatenate([oracle.kahn(g.n, g.src, g.dst, new[i])[0] for i, g in enumerate(wl.graphs)])
+        np.testing.assert_array_equal(bits(outs[v].numpy()), bits(ref), err_msg="view %d" % v)
+    # the device keeps the last view: a plain run and a run_host without delays agree with it
+    bd.run(chunk_elems=256, **EXECUTORS[ex])
+    bd.sync()
+    np.testing.assert_array_equal(bits(hf.hf_batch_get_arrivals(bd.b, -1, N)), bits(outs[-1].numpy()))
+    again = torch.empty(N, dtype=torch.float32).pin_memory()
+    bd.run_host(None, again, **EXECUTORS[ex])
+    bd.sync()
+    np.testing.assert_array_equal(bits(again.numpy()), bits(outs[-1].numpy()))
+    with pytest.raises(hf.HfError):
+        bd.run_host(np.zeros(wl.n_edges, np.float32), again, **EXECUTORS[ex])  # not page-locked
+    with pytest.raises(hf.HfError):
+        bd.run_host(None, np.zeros(N, np.float32), **EXECUTORS[ex])
+    bd.close()
+
+
+def test_run_host_payloads_and_bad_delay():
+    """Payload results through hf_batch_run_host equal the oracle's; a non-finite delay is
+    reported by the next synchronisation, as with hf_batch_set_delays."""
+    wl = S.batch(7, graphs=8, nmin=500, nmax=20000, frac_saxpy=0.1, sx_min=1, sx_max=3000)
+    bd = BatchOnDevice(wl)
+    N = wl.n_tasks
+    dl = torch.from_numpy(np.concatenate([g.delay for g in wl.graphs])).pin_memory()
+    out = torch.empty(N, dtype=torch.float32).pin_memory()
+    bd.run_host(dl, out, mode=hf.HF_MODE_TEAM, priority=hf.HF_PRIO_HEURISTIC)
+    bd.sync()
+    for i, spec in enumerate(wl.graphs):
+        ref = oracle.run_spec(spec)
+        _check_payloads(bd.graphs[i], ref)
+    ref = np.concatenate([oracle.run_spec(g)["arr"] for g in wl.graphs])
+    np.testing.assert_array_equal(bits(out.numpy()), bits(ref))
+    bad = dl.clone().pin_memory()
+    bad[777] = float("inf")
+    bd.run_host(bad, out, mode=hf.HF_MODE_TEAM)
+    assert bd.sync(check=False) == hf.HF_EINVAL
+    bd.close()
+
+
 def test_unpinned_pull_buffer_rejected():
     g = hf.hf_graph_create()
     buf = np.zeros(16, np.float32)  # pageable host memory
