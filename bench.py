@@ -39,7 +39,10 @@ sys.path.insert(0, ROOT)
 DEFAULT_WORKLOAD = "batch256_mixed"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
-KERNEL_SRC = [os.path.join(ROOT, "paper_2203_08395_b300", "csrc", f) for f in ("kernels.cuh", "team.cuh")]
+# the device sources each kernel is built from (k_level, k_persist: kernels.cuh; k_team: both)
+KERNEL_SRC = {k: [os.path.join(ROOT, "paper_2203_08395_b300", "csrc", f) for f in fs]
+              for k, fs in (("k_level", ("kernels.cuh",)), ("k_persist", ("kernels.cuh",)),
+                            ("k_team", ("kernels.cuh", "team.cuh")))}
 
 
 def parse():
@@ -68,9 +71,10 @@ def peaks():
         return 6400.0, "fallback"
 
 
-def kernel_sha():
+def kernel_sha(kernel):
+    """sha256 over the device sources `kernel` is built from."""
     h = hashlib.sha256()
-    for f in KERNEL_SRC:
+    for f in KERNEL_SRC[kernel]:
         h.update(open(f, "rb").read())
     return h.hexdigest()
 
@@ -81,7 +85,7 @@ def traffic_for(kernel, workload):
         with open(TRAFFIC_FILE) as f:
             t = json.load(f)
         e = t.get(kernel + "/" + workload)
-        if e and e.get("kernels_sha256") == kernel_sha():
+        if e and e.get("kernels_sha256") == kernel_sha(kernel):
             return float(e["dram_bytes_per_launch"])
     except Exception:
         pass
