@@ -295,9 +295,9 @@ hf_status plan_build(const std::vector<hf_graph*>& graphs, Plan** out);
 void plan_destroy(Plan* p);
 // keep_status: a later run of a sequence (hf_run_n) keeps the device status word of the runs
 // before it, so the sequence reports its first failure
-// io_dly (device-accessible view of page-locked host memory, or NULL): the run first takes its
-// edge delays from it; io_arr (page-locked host memory, or NULL): every arrival is copied there
-// after the run, on the plan's copy stream (see hf_batch_run_host).
+// io_dly (page-locked host memory, or NULL): the run first takes its edge delays from it (copied
+// on the plan's input stream); io_arr (page-locked host memory, or NULL): every arrival is copied
+// there after the run, on the plan's output stream (see hf_batch_run_host).
 hf_status plan_run(Plan* p, cudaStream_t s, const hf_run_opts& o, bool keep_status = false,
                    const float* io_dly = nullptr, float* io_arr = nullptr);
 hf_status plan_sync(Plan* p);

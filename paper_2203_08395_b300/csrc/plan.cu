@@ -152,10 +152,15 @@ struct Plan {
     uint8_t* d_cat = nullptr;
     int32_t* d_toff = nullptr;
     // host-buffer runs (hf_run_host): the arrivals go to the host from d_arr on a stream of the
-    // plan's own, overlapping the caller's next work; d_arr is reused only after that copy
-    cudaStream_t cstream = nullptr;
-    cudaEvent_t ev_conv = nullptr, ev_d2h = nullptr;
-    bool d2h_pending = false;
+    // plan's own, overlapping the caller's next work; d_arr is reused only after that copy.
+    // New delays come in by copy engine on another plan stream into d_hstage (waiting only until
+    // the previous view's gather has read it), then a gather puts them in ls_in.
+    cudaStream_t cstream = nullptr, istream = nullptr;
+    cudaEvent_t ev_conv = nullptr, ev_d2h = nullptr, ev_h2d = nullptr, ev_gather = nullptr;
+    bool d2h_pending = false, gather_pending = false;
+    float* d_hstage = nullptr;      // host-buffer delays on the device (m)
+    int32_t* d_ls_edge = nullptr;   // in-edge position -> edge in insertion order (m)
+    bool erec_stale = false;        // erec's delays older than ls_in's (refreshed before a persistent run)
     float4* d_gstat = nullptr;
     float* d_prio = nullptr;       // bottom-level weight per task under seed_prio
     int32_t seed_prio = HF_PRIO_FIFO;  // priority the seed order was built for
@@ -232,6 +237,7 @@ void plan_destroy(Plan* p) {
     if (!p) return;
     if (p->ran && p->done_ev) cudaEventSynchronize(p->done_ev);
     if (p->d2h_pending) cudaEventSynchronize(p->ev_d2h);
+    if (p->gather_pending) cudaEventSynchronize(p->ev_h2d);
     if (p->proxy.joinable()) p->proxy.join();
     if (p->h_post) cudaFreeHost(p->h_post);
     if (p->h_hdone) cudaFreeHost(p->h_hdone);
@@ -248,8 +254,11 @@ void plan_destroy(Plan* p) {
     }
     if (p->tev_fork) cudaEventDestroy(p->tev_fork);
     if (p->cstream) cudaStreamDestroy(p->cstream);
+    if (p->istream) cudaStreamDestroy(p->istream);
     if (p->ev_conv) cudaEventDestroy(p->ev_conv);
     if (p->ev_d2h) cudaEventDestroy(p->ev_d2h);
+    if (p->ev_h2d) cudaEventDestroy(p->ev_h2d);
+    if (p->ev_gather) cudaEventDestroy(p->ev_gather);
     delete p;
 }
 
@@ -797,6 +806,78 @@ static void team_host_proxy(Plan* p, uint64_t limit_ns) {
     }
 }
 
+// New delays for the level-sorted in-edges only, as a gather: in-edge j takes delay[edge[j]]
+// (edge[j]: its edge in insertion order), so the writes are sequential; non-finite flagged as in
+// k_set_delays.
+__global__ void k_gather_delays(const float* __restrict__ delay, const int32_t* __restrict__ edge, int2* ls_in,
+                                int64_t m, int32_t* bad) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    bool nonfinite = false;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += stride) {
+        const int b = __float_as_int(__ldg(delay + __ldg(edge + j)));
+        nonfinite |= (b & 0x7f800000) == 0x7f800000;
+        reinterpret_cast<int*>(ls_in)[2 * j + 1] = b;
+    }
+    if (__any_sync(0xffffffffu, nonfinite) && (threadIdx.x & 31) == 0) atomicExch(bad, 1);
+}
+
+// The successor edge records' delays brought up to date from the level-sorted in-edges.
+__global__ void k_erec_delays(const int32_t* __restrict__ pos_csr, const int32_t* __restrict__ pos_ls, int4* erec,
+                              const int2* __restrict__ ls_in, int64_t m) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride)
+        reinterpret_cast<int*>(erec)[4 * (int64_t)__ldg(pos_csr + i) + 1] =
+            reinterpret_cast<const int*>(ls_in)[2 * (int64_t)__ldg(pos_ls + i) + 1];
+}
+
+// edge[pos_ls[e]] = e: the inverse of the edge -> in-edge position map.
+__global__ void k_invert_pos(const int32_t* __restrict__ pos_ls, int32_t* __restrict__ edge, int64_t m) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) edge[__ldg(pos_ls + i)] = (int32_t)i;
+}
+
+// New delays for the run about to be enqueued on s, from page-locked host memory: copied by
+// the copy engine on the plan's input stream, which waits only until the previous view's
+// gather has read the staging buffer (so the copy overlaps the previous run), then gathered on s
+// into the level-sorted in-edges (the persistent executor: scattered into both layouts).
+static hf_status delays_from_host(Plan* p, cudaStream_t s, const float* host, int mode) {
+    cudaError_t e = cudaSuccess;
+    if (!p->istream) {
+        e = cudaStreamCreateWithFlags(&p->istream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_h2d, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_gather, cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(e, "delay upload stream");
+    }
+    const int grid = (int)std::min<int64_t>((p->m + 255) / 256, (int64_t)p->num_sms * 16);
+    if (!p->d_hstage) {
+        p->d_hstage = (float*)palloc(p, 4 * (size_t)p->m, s);
+        p->d_ls_edge = (int32_t*)palloc(p, 4 * (size_t)p->m, s);
+        if (!p->d_hstage || !p->d_ls_edge) return fail(HF_ENOMEM, "device allocation failed: delay staging");
+        k_invert_pos<<<grid, 256, 0, s>>>(p->d_epos_ls, p->d_ls_edge, p->m);
+        // the first upload must not overtake the allocations on s
+        if ((e = cudaEventRecord(p->ev_gather, s)) != cudaSuccess) return cuda_fail(e, "delay upload");
+        p->gather_pending = true;
+    }
+    if (p->ran && p->last_stream != s && (e = cudaStreamWaitEvent(s, p->done_ev, 0)) != cudaSuccess)
+        return cuda_fail(e, "delay upload");
+    if ((p->gather_pending && (e = cudaStreamWaitEvent(p->istream, p->ev_gather, 0)) != cudaSuccess) ||
+        (e = cudaMemcpyAsync(p->d_hstage, host, 4 * (size_t)p->m, cudaMemcpyHostToDevice, p->istream)) != cudaSuccess ||
+        (e = cudaEventRecord(p->ev_h2d, p->istream)) != cudaSuccess || (e = cudaStreamWaitEvent(s, p->ev_h2d, 0)) != cudaSuccess ||
+        (e = cudaMemsetAsync(&p->d_ctrl->bad_input, 0, sizeof(int32_t), s)) != cudaSuccess)
+        return cuda_fail(e, "delay upload");
+    if (mode == HF_MODE_PERSISTENT) {
+        k_set_delays<<<grid, 256, 0, s>>>(p->d_hstage, p->d_epos_csr, p->d_epos_ls, p->d_erec, p->d_ls_in, p->m,
+                                          &p->d_ctrl->bad_input);
+        p->erec_stale = false;
+    } else {
+        k_gather_delays<<<grid, 256, 0, s>>>(p->d_hstage, p->d_ls_edge, p->d_ls_in, p->m, &p->d_ctrl->bad_input);
+        p->erec_stale = true;
+    }
+    if ((e = cudaEventRecord(p->ev_gather, s)) != cudaSuccess) return cuda_fail(e, "delay upload");
+    p->gather_pending = true;
+    return HF_OK;
+}
+
 // Arrivals of the run just enqueued on s to page-locked host memory: converted into d_arr on s,
 // copied out on the plan's copy stream, so that s goes on with the caller's next work (a new
 // delay upload, the next run) while the copy runs. The next use of d_arr waits for the copy.
@@ -852,8 +933,13 @@ hf_status plan_run(Plan* p, cudaStream_t s, const hf_run_opts& o, bool keep_stat
     if (st != HF_OK) return st;
     const bool instr = (o.instrument & 1) != 0, valid = o.validate != 0;
     if ((st = ensure_instr(p, instr, valid, s)) != HF_OK) return st;
-    // host buffers: new delays scattered from page-locked host memory before the run
-    if (io_dly && (st = plan_set_delays(p, io_dly, 1, s)) != HF_OK) return st;
+    // host buffers: new delays from page-locked host memory before the run
+    if (io_dly && p->m > 0 && (st = delays_from_host(p, s, io_dly, mode)) != HF_OK) return st;
+    if (mode == HF_MODE_PERSISTENT && p->erec_stale && p->m > 0) {
+        const int grid = (int)std::min<int64_t>((p->m + 255) / 256, (int64_t)p->num_sms * 16);
+        k_erec_delays<<<grid, 256, 0, s>>>(p->d_epos_csr, p->d_epos_ls, p->d_erec, p->d_ls_in, p->m);
+        p->erec_stale = false;
+    }
     cudaError_t e = keep_status ? cudaSuccess : cudaMemsetAsync(&p->d_ctrl->status, 0, sizeof(int32_t), s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
     if (p->n > 0) {
@@ -1049,11 +1135,9 @@ hf_status plan_run(Plan* p, cudaStream_t s, const hf_run_opts& o, bool keep_stat
 }
 
 hf_status plan_run_host(Plan* p, cudaStream_t s, const hf_run_opts& o, const float* delay, float* arr_out) {
-    const float* dv = nullptr;
-    if (delay && p->m > 0 && !(dv = (const float*)host_dev_ptr(delay)))
-        return fail(HF_EINVAL, "delay is not page-locked host memory");
+    if (delay && p->m > 0 && !host_dev_ptr(delay)) return fail(HF_EINVAL, "delay is not page-locked host memory");
     if (arr_out && p->n > 0 && !host_dev_ptr(arr_out)) return fail(HF_EINVAL, "arr_out is not page-locked host memory");
-    return plan_run(p, s, o, false, dv, p->n > 0 ? arr_out : nullptr);
+    return plan_run(p, s, o, false, p->m > 0 ? delay : nullptr, p->n > 0 ? arr_out : nullptr);
 }
 
 hf_status plan_sync(Plan* p) {
@@ -1179,6 +1263,7 @@ hf_status plan_set_delays(Plan* p, const float* delay, int on_device, cudaStream
     if (e0 != cudaSuccess) return cuda_fail(e0, "cudaMemsetAsync");
     k_set_delays<<<grid, 256, 0, s>>>(src, p->d_epos_csr, p->d_epos_ls, p->d_erec, p->d_ls_in, p->m,
                                       &p->d_ctrl->bad_input);
+    p->erec_stale = false;
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? HF_OK : cuda_fail(e, "delay scatter");
 }

@@ -489,6 +489,12 @@ def test_run_host_streams_timing_views(ex):
     bd.run_host(None, again, **EXECUTORS[ex])
     bd.sync()
     np.testing.assert_array_equal(bits(again.numpy()), bits(outs[-1].numpy()))
+    # the other executors see the last view too (the level-sorted in-edges and the persistent
+    # executor's edge records both follow it)
+    for other in ("persistent", "levelsync", "team"):
+        bd.run(chunk_elems=256, **EXECUTORS[other])
+        bd.sync()
+        np.testing.assert_array_equal(bits(hf.hf_batch_get_arrivals(bd.b, -1, N)), bits(outs[-1].numpy()), err_msg=other)
     with pytest.raises(hf.HfError):
         bd.run_host(np.zeros(wl.n_edges, np.float32), again, **EXECUTORS[ex])  # not page-locked
     with pytest.raises(hf.HfError):
