@@ -78,13 +78,13 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned 
     return ok != 0;
 }
 
-// TMA bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16)
 // asynchronous 8-byte global -> shared copy (completion: cp_async_wait_all by the issuer)
 __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem) : "memory");
 }
 
+// TMA bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16)
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
     const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
     const unsigned b = (unsigned)__cvta_generic_to_shared(bar);
@@ -104,9 +104,8 @@ __device__ __forceinline__ void prefetch_l2_range(const void* p, int64_t bytes) 
     }
 }
 
-// The staging sources and capacities, copied from TeamArgs into shared memory at kernel start:
-// the look-ahead reads them there (kernel parameters read through a reference in an out-of-line
-// call cost several hundred ns per dependent load).
+// The staging sources and capacities, copied from TeamArgs into shared memory at kernel start,
+// where the look-ahead reads them.
 struct TeamSrc {
     const int32_t* ls_node;
     const int32_t* ls_ptr;
@@ -120,14 +119,14 @@ __device__ __forceinline__ bool team_fits(const S& a, const int4 sg) {
     return sg.y > sg.x && sg.y - sg.x <= a.stage_n && sg.w - sg.z <= a.stage_e;
 }
 
-// Issued by one thread: stage segment sg (positions [x, y), in-edges [z, w)) into st, and the
-// level's piece descriptors si = [i0, i1) when they fit. The level-sorted arrays are allocated
-// with slack so that rounding the ends up to 16 bytes stays inside them.
 template <class S>
 __device__ __forceinline__ bool team_desc_fits(const S& a, const int2 si) {
     return si.y > si.x && si.y - si.x <= a.stage_p;
 }
 
+// Issued by one thread: stage segment sg (positions [x, y), in-edges [z, w)) into st, and the
+// level's piece descriptors si = [i0, i1) when they fit. The level-sorted arrays are allocated
+// with slack so that rounding the ends up to 16 bytes stays inside them.
 __device__ __forceinline__ void team_stage(const TeamSrc& a, const TeamStage& st, unsigned long long* bar, const int4 sg,
                                            const int2 si) {
     const int a0 = sg.x & ~3, a1 = (sg.y + 3) & ~3, b1 = (sg.y + 4) & ~3;
@@ -148,8 +147,8 @@ __device__ __forceinline__ void team_prefetch_seg(const TeamSrc& a, const int4 s
     prefetch_l2_range(a.ls_in + sg.z, 8ll * (sg.w - sg.z));
 }
 
-// look-ahead for one level, by thread 0 of each CTA: stage it if it fits, else (CTA 0 of the
-// team) prefetch it into L2. Inline: the sources come from shared memory, so the address
+// look-ahead for one level, by the lead thread of each CTA: stage it if it fits, else (CTA 0 of
+// the team) prefetch it into L2. Inline: the sources come from shared memory, so the address
 // arithmetic stays within the three-CTAs-per-SM register budget.
 __device__ __forceinline__ void team_ahead(const TeamSrc& a, int rank, const TeamStage& st, unsigned long long* bar,
                                            const int4 sg, const int2 si) {
@@ -173,9 +172,9 @@ __device__ __forceinline__ void team_prefetch_pieces(const TeamPiece* dsc, int i
     }
 }
 
-// One piece by one warp (a 512-element FP32 piece is one round trip of 16-byte loads).
-// FP32 saxpy piece with 32-bit indexing (a piece is at most a few thousand elements); same
-// access pattern as warp_saxpy_f32
+// One FP32 saxpy piece by one warp, with 32-bit indexing (a piece is at most a few thousand
+// elements): a 512-element piece is one round trip of 16-byte loads, the ragged head and tail
+// loaded alongside; same access pattern as warp_saxpy_f32.
 __device__ __forceinline__ void team_saxpy_f32(float* __restrict__ y, const float* __restrict__ x, int cnt, float a,
                                                int lane) {
     if ((((uintptr_t)y ^ (uintptr_t)x) & 15) != 0) {
@@ -389,7 +388,7 @@ __device__ __forceinline__ bool team_run_graph(const TeamArgs& a, const TeamJob&
             }
         }
         if (PAY && t == kTeamLead) pcnt[(l + 1) & 1] = 0;  // the next level's piece counter (free since the barrier)
-        // arrivals of level l (every CTA of a team stages the whole level and takes its share)
+        // level l's task list, row starts and in-edges (every CTA of a team stages the whole level)
         const int32_t* node = a.ls_node;
         const int32_t* ptr = a.ls_ptr;
         const int2* in = a.ls_in;
@@ -429,7 +428,7 @@ __device__ __forceinline__ bool team_run_graph(const TeamArgs& a, const TeamJob&
         // jobs the last warp first warms L2 with the CTA's pieces of the next level, when that
         // level's staged descriptors have landed.
         if (PAY) {
-            if (!SOLO && t >= kTeamThreads - 32 && l + 1 < L) {
+            if (!SOLO && (t >> 5) == (kTeamLead >> 5) && l + 1 < L) {
                 const int b1 = (l + 1) % kTeamBufs;
                 const int2 i1 = iring[(l + 1) & 3];
                 if (team_fits(a, ring[(l + 1) & 3]) && team_desc_fits(a, i1) &&
