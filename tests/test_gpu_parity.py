@@ -410,6 +410,42 @@ def test_edge_cases(ex):
         gd.close()
 
 
+@pytest.mark.parametrize("ex", ["levelsync", "persistent", "team", "auto"])
+def test_run_host_edge_cases(ex):
+    """hf_run_host / hf_batch_run_host on degenerate inputs: an empty graph, a graph without
+    edges (NULL and non-NULL delays), a single task, and a batch mixing them with a chain."""
+    o = dict(mode=hf.HF_MODE_AUTO) if ex == "auto" else EXECUTORS[ex]
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).pin_memory()
+    g = hf.hf_graph_create()  # empty: nothing to copy either way
+    hf.hf_run_host(g, None, None, None, hf.hf_run_opts_default(**o))
+    hf.hf_sync_status(g)
+    hf.hf_graph_destroy(g)
+    g = hf.hf_graph_create()  # one task, no edges
+    hf.hf_add_task(g, hf.HF_KERNEL, hf.hf_maxplus_payload(op=hf.HF_K_MAXPLUS, arr0=2.25))
+    out = pin(np.zeros(1))
+    hf.hf_run_host(g, pin(np.zeros(0)), out, None, hf.hf_run_opts_default(**o))
+    hf.hf_sync_status(g)
+    assert out[0].item() == 2.25
+    hf.hf_graph_destroy(g)
+    specs = [S.GraphSpec(name="lone", n=4, src=np.zeros(0, np.int32), dst=np.zeros(0, np.int32),
+                         delay=np.zeros(0, np.float32), kind=np.zeros(4, np.uint8)),
+             S.GraphSpec(name="chain", n=300, src=np.arange(299, dtype=np.int32), dst=np.arange(1, 300, dtype=np.int32),
+                         delay=S.uniform_f32(12, 0, 299, -1.0, 1.0), kind=np.zeros(300, np.uint8)),
+             S.GraphSpec(name="one", n=1, src=np.zeros(0, np.int32), dst=np.zeros(0, np.int32),
+                         delay=np.zeros(0, np.float32), kind=np.zeros(1, np.uint8))]
+    wl = S.Workload("edge_batch", specs)
+    bd = BatchOnDevice(wl)
+    new = S.uniform_f32(13, 0, 299, 0.0, 2.0)
+    out = pin(np.zeros(wl.n_tasks))
+    bd.run_host(pin(new), out, **o)
+    bd.sync()
+    ref = np.concatenate([oracle.kahn(4, specs[0].src, specs[0].dst, specs[0].delay)[0],
+                          oracle.kahn(300, specs[1].src, specs[1].dst, new)[0],
+                          oracle.kahn(1, specs[2].src, specs[2].dst, specs[2].delay)[0]])
+    np.testing.assert_array_equal(bits(out.numpy()), bits(ref))
+    bd.close()
+
+
 def test_arrivals_on_device():
     spec = S.layered(7, 5000, 20, 1, 4)
     gd = GraphOnDevice(spec)
