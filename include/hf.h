@@ -52,7 +52,7 @@ typedef enum {
     HF_ETIMEDOUT = 5,  /* the persistent executor saw no progress for spin_limit_ns and gave up */
     HF_EQUEUE = 6,     /* a device queue overflowed (internal error; never expected) */
     HF_ECUDA = 7,      /* a CUDA runtime call failed; hf_last_error() has its message */
-    HF_ENOTSUP = 8     /* valid request this build does not support (e.g. host tasks, persistent mode) */
+    HF_ENOTSUP = 8     /* valid request this build does not support (e.g. a validate run of the team executor) */
 } hf_status;
 
 /* The paper's four task kinds (Section I; Section III-A). */
@@ -94,10 +94,13 @@ typedef struct { const void* host_ptr; size_t bytes; } hf_pull_payload;
 typedef struct { hf_task src_pull; int32_t pad_; const void* src_dev; void* host_ptr; size_t bytes; } hf_push_payload;
 
 /* kind HF_HOST: fn(arg) runs on a CPU thread (Section III-A "Host Task"). The level-synchronous
- * executor makes it a host node of its CUDA graph; the team executor posts it, once its level's
- * device work is done, to a mailbox in mapped page-locked memory where a proxy thread of the
- * library runs it and raises its done flag, which the device waits for (bounded by
- * spin_limit_ns) before the next level. The persistent executor returns HF_ENOTSUP. */
+ * executor makes it a host node of its CUDA graph. The team and persistent executors post it to
+ * a mailbox in mapped page-locked memory, where a proxy thread of the library runs the posted
+ * tasks in posting order and raises each one's done flag; the device waits for the flag
+ * (bounded by spin_limit_ns: HF_ETIMEDOUT) before the task's successors run. The team executor
+ * posts a level's host tasks once the level's device work is done; the persistent executor
+ * posts a host task when it becomes ready, and only the warp that took it waits. Callbacks must
+ * not wait for the run itself. */
 typedef struct { void (*fn)(void* arg); void* arg; } hf_host_payload;
 
 /* --- run options ---------------------------------------------------------------------- */

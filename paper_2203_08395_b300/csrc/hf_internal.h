@@ -21,7 +21,10 @@ namespace hf {
 constexpr uint32_t kKeyNegInf = 0x007FFFFFu;  // key(-inf)
 constexpr uint32_t kKeyPosZero = 0x80000000u;  // key(+0)
 
-enum PayOp : uint32_t { kPaySaxpyF32 = 1, kPaySaxpyI32 = 2, kPayCopy = 3 };
+// kPayHost: a host task (a_bits: its index in the plan's host-task list). The persistent
+// executor's warp posts it to the host proxy and waits for it; the level-synchronous and team
+// executors run host tasks their own way and skip the piece.
+enum PayOp : uint32_t { kPaySaxpyF32 = 1, kPaySaxpyI32 = 2, kPayCopy = 3, kPayHost = 4 };
 
 // One device payload record (saxpy or copy), 64 bytes. It also carries its task's id and row so
 // that a warp holding only the payload index has everything it needs after one load.
@@ -89,6 +92,9 @@ struct PersistArgs {
     int64_t* tk_end;
     int32_t* exec_count;
     unsigned long long* stats;  // instrument & 2: executor counters (kStat*), else NULL
+    int32_t* post;              // host tasks: mapped mailbox (the i-th posted host task), else NULL
+    const int32_t* hdone;       // mapped: host task k has run
+    int32_t* post_ctr;          // device counter of posts
 };
 
 // Executor counters recorded by runs with instrument & 2 (hf_get_stats).

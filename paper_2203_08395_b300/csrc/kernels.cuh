@@ -225,9 +225,40 @@ __device__ __forceinline__ void run_piece(const DevPayload& P, int piece, int la
         warp_saxpy_f32((float*)P.dst + b0, (const float*)P.src + b0, b1 - b0, __uint_as_float(P.a_bits), lane);
     } else if (P.op == kPaySaxpyI32) {
         warp_saxpy_i32((int32_t*)P.dst + b0, (const int32_t*)P.src + b0, b1 - b0, P.a_bits, lane);
-    } else {
+    } else if (P.op == kPayCopy) {
         warp_copy((char*)P.dst + b0, (const char*)P.src + b0, b1 - b0, lane);
     }
+}
+
+__device__ __forceinline__ void st_release_sys(int32_t* p, int v) {
+    asm volatile("st.release.sys.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ int ld_acquire_sys(const int32_t* p) {
+    int v;
+    asm volatile("ld.acquire.sys.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Host task k through the mapped mailbox (one thread): the system-scope fence makes what this
+// thread observed of upstream device work (push copies into host memory included) visible to
+// the callback; the post is a release, the done flag an acquire that orders the callback's
+// writes before the successors this warp releases. Bounded: after limit_ns the status becomes
+// HF_ETIMEDOUT and `abort` (if given) is raised. Returns false on timeout.
+__device__ __noinline__ bool host_task_roundtrip(int32_t* post, int32_t* post_ctr, const int32_t* hdone, int k,
+                                                 uint64_t limit_ns, int32_t* status, int32_t* abort) {
+    __threadfence_system();
+    st_release_sys(post + atomicAdd(post_ctr, 1), k);
+    const uint64_t t0 = gtimer();
+    while (ld_acquire_sys(hdone + k) == 0) {
+        if (gtimer() - t0 > limit_ns) {
+            atomicCAS(status, 0, (int)HF_ETIMEDOUT);
+            if (abort) atomicExch(abort, 1);
+            return false;
+        }
+        __nanosleep(200);
+    }
+    return true;
 }
 
 // ------------------------------------------------------------------ level-synchronous kernel
@@ -747,7 +778,14 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 2) k_persist(const PersistA
                     work &= work - 1;
                     const int pp = __shfl_sync(kFull, p, src);
                     const int pc = __shfl_sync(kFull, piece, src);
-                    run_piece(a.pay[pp], pc, lane);
+                    if (a.pay[pp].op == kPayHost) {  // a host task: this warp waits for the proxy
+                        if (lane == 0 && a.post)
+                            host_task_roundtrip(a.post, a.post_ctr, a.hdone, (int)a.pay[pp].a_bits, a.spin_limit_ns,
+                                                &a.ctrl->status, &a.ctrl->abort);
+                        __syncwarp();
+                    } else {
+                        run_piece(a.pay[pp], pc, lane);
+                    }
                 }
                 fence_acq_rel();  // release: every lane's payload writes before any release below
                 __syncwarp();

@@ -415,10 +415,6 @@ hf_status plan_build(const std::vector<hf_graph*>& graphs, Plan** out) {
                 const int32_t k = g->pay[(size_t)v];
                 if (k < 0) continue;
                 const PayloadRec& r = g->payloads[(size_t)k];
-                if (r.kind == HF_HOST) {
-                    p->host_tasks.push_back(HostTask{g->fin.level[(size_t)v], r.fn, r.arg, i});
-                    continue;
-                }
                 DevPayload d;
                 std::memset(&d, 0, sizeof(d));
                 d.nchunks = 1;
@@ -426,7 +422,12 @@ hf_status plan_build(const std::vector<hf_graph*>& graphs, Plan** out) {
                 d.task = toff + v;
                 d.row = row_ptr[(size_t)toff + v];
                 d.deg = row_ptr[(size_t)toff + v + 1] - row_ptr[(size_t)toff + v];
-                if (r.kind == HF_KERNEL) {
+                if (r.kind == HF_HOST) {  // the persistent executor's handle on it (one piece)
+                    d.op = kPayHost;
+                    d.n = 1;
+                    d.a_bits = (uint32_t)p->host_tasks.size();
+                    p->host_tasks.push_back(HostTask{g->fin.level[(size_t)v], r.fn, r.arg, i});
+                } else if (r.kind == HF_KERNEL) {
                     d.op = r.op == HF_K_SAXPY_I32 ? kPaySaxpyI32 : kPaySaxpyF32;
                     d.n = r.n;
                     if (r.op == HF_K_SAXPY_I32) std::memcpy(&d.a_bits, &r.a_i, 4);
@@ -917,8 +918,6 @@ hf_status plan_run(Plan* p, cudaStream_t s, const hf_run_opts& o, bool keep_stat
     }
     if (mode != HF_MODE_LEVELSYNC && mode != HF_MODE_PERSISTENT && mode != HF_MODE_TEAM)
         return fail(HF_EINVAL, "unknown mode");
-    if (mode == HF_MODE_PERSISTENT && !p->host_tasks.empty())
-        return fail(HF_ENOTSUP, "host tasks need the level-synchronous or the team executor");
     if (o.priority < HF_PRIO_FIFO || o.priority > HF_PRIO_LEARNED) return fail(HF_EINVAL, "unknown priority");
     if (o.priority == HF_PRIO_LEARNED && !p->cm) return fail(HF_ESTATE, "HF_PRIO_LEARNED needs a cost model (hf_batch_set_costmodel)");
     hf_status st = HF_OK;
@@ -1101,6 +1100,14 @@ hf_status plan_run(Plan* p, cudaStream_t s, const hf_run_opts& o, bool keep_stat
                 a.stats = p->d_stats;
             }
             p->last_stats = a.stats != nullptr;
+            if (!p->host_tasks.empty()) {  // host tasks: the team executor's mailbox and proxy thread
+                if ((st = team_host_setup(p, s)) != HF_OK) return st;
+                a.post = p->d_post;
+                a.hdone = p->d_hdone;
+                a.post_ctr = p->d_post_ctr;
+                e = cudaMemsetAsync(p->d_post_ctr, 0, sizeof(int32_t), s);
+                if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+            }
             int ctas = o.ctas;
             if (ctas <= 0) {  // two CTAs (16 warps) per SM, capped by occupancy: more idle warps
                               // only add polling traffic (the autotuner searches around this)
@@ -1113,6 +1120,10 @@ hf_status plan_run(Plan* p, cudaStream_t s, const hf_run_opts& o, bool keep_stat
             if (p->npay) k_persist<true><<<ctas, kWarpsPerCta * 32, 0, s>>>(a);
             else k_persist<false><<<ctas, kWarpsPerCta * 32, 0, s>>>(a);
             if (o.time_kernel) cudaEventRecord(p->kev1, s);
+            if (!p->host_tasks.empty()) {
+                const uint64_t limit = o.spin_limit_ns ? o.spin_limit_ns : 2000000000ull;
+                p->proxy = std::thread(team_host_proxy, p, limit);
+            }
         }
         if (io_arr && (st = arrivals_to_host(p, s, io_arr)) != HF_OK) return st;
         e = cudaGetLastError();
@@ -1290,7 +1301,7 @@ __global__ void k_features(int n, const int2* __restrict__ meta, const int4* __r
         const int lev = level[v];
         double bytes = 0.0;
         const int p = pidx ? pidx[v] : -1;
-        if (p >= 0) bytes = pay[p].op == kPayCopy ? (double)pay[p].n : 12.0 * (double)pay[p].n;
+        if (p >= 0) bytes = pay[p].op == kPayCopy ? (double)pay[p].n : pay[p].op == kPayHost ? 0.0 : 12.0 * (double)pay[p].n;
         float msf = 0.f;
         if (mt.y > 0) {
             int64_t sum = 0;

@@ -162,11 +162,11 @@ __device__ __forceinline__ int team_slice(int x0, int n, int r, int k) {
 }
 
 // L2 prefetch of the x and y ranges of pieces [i0, i1) (one warp, lanes strided), from staged
-// descriptors. Copies touch host memory and are skipped.
+// descriptors; saxpy pieces only (copies touch host memory, host tasks no memory).
 __device__ __forceinline__ void team_prefetch_pieces(const TeamPiece* dsc, int i0, int i1, int lane) {
     for (int it = i0 + lane; it < i1; it += 32) {
         const TeamPiece d = dsc[it];
-        if (d.op == kPayCopy || d.cnt <= 0) continue;
+        if ((d.op != kPaySaxpyF32 && d.op != kPaySaxpyI32) || d.cnt <= 0) continue;
         prefetch_l2_range(d.src, 4ll * d.cnt);
         prefetch_l2_range(d.dst, 4ll * d.cnt);
     }
@@ -226,16 +226,6 @@ __device__ __forceinline__ void team_run_piece(const TeamPiece& d, int lane) {
 }
 
 // ---------------------------------------------------------------- host tasks
-
-__device__ __forceinline__ void st_release_sys(int32_t* p, int v) {
-    asm volatile("st.release.sys.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-__device__ __forceinline__ int ld_acquire_sys(const int32_t* p) {
-    int v;
-    asm volatile("ld.acquire.sys.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
 
 // The host tasks of one level (thread 0 of the team's first CTA, after the level's device work):
 // post each to the mailbox in mapped host memory, where the host proxy thread runs it, and

@@ -243,7 +243,8 @@ def test_paper_saxpy_graph_through_c_abi():
             ids[nm] = hf.hf_add_task(g, hf.HF_PUSH, p)
     for a, b in gold["edges"]:
         hf.hf_precede(g, ids[a], ids[b])
-    for opts in (dict(mode=hf.HF_MODE_LEVELSYNC), dict(mode=hf.HF_MODE_TEAM), dict(mode=hf.HF_MODE_TEAM, team_size=2)):
+    for opts in (dict(mode=hf.HF_MODE_LEVELSYNC), dict(mode=hf.HF_MODE_TEAM), dict(mode=hf.HF_MODE_TEAM, team_size=2),
+                 dict(mode=hf.HF_MODE_PERSISTENT), dict(mode=hf.HF_MODE_PERSISTENT, validate=1, chunk_elems=4096)):
         x.zero_()
         y.zero_()
         calls.clear()
@@ -251,19 +252,22 @@ def test_paper_saxpy_graph_through_c_abi():
         hf.hf_sync_status(g)
         assert sorted(calls) == ["x", "y"], opts
         assert bool((y == P["expect_y"]).all()) and bool((x == P["expect_x"]).all()), opts
-    # host tasks are not supported by the persistent executor (reported, not silently run)
-    with pytest.raises(hf.HfError) as ei:
-        hf.hf_run(g, None, hf.hf_run_opts_default(mode=hf.HF_MODE_PERSISTENT))
-    assert ei.value.status == hf.HF_ENOTSUP
+        if opts.get("validate"):  # every task once, every edge in order (host tasks included)
+            s0, s1, c = hf.hf_get_stamps(g, len(gold["tasks"]))
+            assert np.all(c == 1)
+            for a, b in gold["edges"]:
+                assert s1[ids[a]] < s0[ids[b]], (a, b)
     hf.hf_graph_destroy(g)
 
 
 @pytest.mark.parametrize("opts", [dict(mode=hf.HF_MODE_TEAM), dict(mode=hf.HF_MODE_TEAM, team_size=4),
-                                  dict(mode=hf.HF_MODE_TEAM, priority=hf.HF_PRIO_HEURISTIC)])
-def test_team_host_tasks_in_a_batch(opts):
-    """Host tasks inside a batch run by the team executor: each runs exactly once, after its
-    predecessors and before its successors (callbacks record the order), and every arrival is
-    the oracle's (a host task propagates arrivals like a max-plus task)."""
+                                  dict(mode=hf.HF_MODE_TEAM, priority=hf.HF_PRIO_HEURISTIC),
+                                  dict(mode=hf.HF_MODE_PERSISTENT), dict(mode=hf.HF_MODE_PERSISTENT, ctas=4),
+                                  dict(mode=hf.HF_MODE_PERSISTENT, priority=hf.HF_PRIO_HEURISTIC, payload_warps=2)])
+def test_host_tasks_in_a_batch(opts):
+    """Host tasks inside a batch run by the team or the persistent executor: each runs exactly
+    once, after its predecessors and before its successors (callbacks record the order), and
+    every arrival is the oracle's (a host task propagates arrivals like a max-plus task)."""
     rng = np.random.default_rng(21)
     order = []
     keep = []
