@@ -119,9 +119,10 @@ __device__ __forceinline__ bool team_fits(const S& a, const int4 sg) {
     return sg.y > sg.x && sg.y - sg.x <= a.stage_n && sg.w - sg.z <= a.stage_e;
 }
 
+// (64-bit difference: a range never overflows into a "fitting" one)
 template <class S>
 __device__ __forceinline__ bool team_desc_fits(const S& a, const int2 si) {
-    return si.y > si.x && si.y - si.x <= a.stage_p;
+    return si.x >= 0 && si.y > si.x && (int64_t)si.y - (int64_t)si.x <= (int64_t)a.stage_p;
 }
 
 // Issued by one thread: stage segment sg (positions [x, y), in-edges [z, w)) into st, and the
@@ -161,8 +162,9 @@ __device__ __forceinline__ int team_slice(int x0, int n, int r, int k) {
     return x0 + (int)(((int64_t)n * r) / k);
 }
 
-// L2 prefetch of the x and y ranges of pieces [i0, i1) (one warp, lanes strided), from staged
-// descriptors; saxpy pieces only (copies touch host memory, host tasks no memory).
+// L2 prefetch of the x and y ranges of staged pieces [i0, i1) (indices into the stage buffer's
+// descriptors; one warp, lanes strided); saxpy pieces only (copies touch host memory, host
+// tasks no memory).
 __device__ __forceinline__ void team_prefetch_pieces(const TeamPiece* dsc, int i0, int i1, int lane) {
     for (int it = i0 + lane; it < i1; it += 32) {
         const TeamPiece d = dsc[it];
@@ -358,8 +360,8 @@ __device__ __forceinline__ bool team_run_graph(const TeamArgs& a, const TeamJob&
             ring[q] = __ldg(a.seg + job.seg0 + q);
             iring[q] = PAY ? __ldg(a.seg_items + job.seg0 + q) : z2;
         }
-        if (L > 0) team_ahead(src, rank, sview[0], &mbar[0], ring[0], iring[0]);
-        if (L > 1) team_ahead(src, rank, sview[1], &mbar[1], ring[1], iring[1]);
+        if (L > 0) team_ahead(src, rank, sview[0], &mbar[0], ring[0], PAY ? iring[0] : z2);
+        if (L > 1) team_ahead(src, rank, sview[1], &mbar[1], ring[1], PAY ? iring[1] : z2);
     }
     __syncthreads();
     if (a.g_start && rank == 0 && t == 0) a.g_start[job.graph] = (int64_t)gtimer();
@@ -370,7 +372,7 @@ __device__ __forceinline__ bool team_run_graph(const TeamArgs& a, const TeamJob&
         if (t == kTeamLead) {
             if (l + 2 < L)
                 team_ahead(src, rank, sview[(l + 2) % kTeamBufs], &mbar[(l + 2) % kTeamBufs], ring[(l + 2) & 3],
-                                iring[(l + 2) & 3]);
+                           PAY ? iring[(l + 2) & 3] : z2);  // the item ring is filled only with payloads
             if (l + 3 < L) {
                 cp_async16(&ring[(l + 3) & 3], a.seg + job.seg0 + l + 3);
                 if (PAY) cp_async8(&iring[(l + 3) & 3], a.seg_items + job.seg0 + l + 3);
@@ -378,11 +380,14 @@ __device__ __forceinline__ bool team_run_graph(const TeamArgs& a, const TeamJob&
             }
         }
         if (PAY && t == kTeamLead) pcnt[(l + 1) & 1] = 0;  // the next level's piece counter (free since the barrier)
-        // level l's task list, row starts and in-edges (every CTA of a team stages the whole level)
+        // level l's task list, row starts and in-edges (every CTA of a team stages the whole level):
+        // from the stage buffer, which holds them from position nb, in-edge eb and item ib on
+        // (indices are rebased; a pointer is never moved outside its buffer), else from memory
         const int32_t* node = a.ls_node;
         const int32_t* ptr = a.ls_ptr;
         const int2* in = a.ls_in;
         const TeamPiece* dsc = PAY ? a.pdesc : nullptr;
+        int nb = 0, eb = 0, ib = 0;
         const bool staged = team_fits(a, s0);
         if (staged) {
             uint64_t t0 = 0;
@@ -397,20 +402,25 @@ __device__ __forceinline__ bool team_run_graph(const TeamArgs& a, const TeamJob&
                 }
             }
             phase ^= 1u << b;
-            const int nb = s0.x & ~3, eb = s0.z & ~1;
+            nb = s0.x & ~3;
+            eb = s0.z & ~1;
             const TeamStage sv = sview[b];
-            node = sv.node - nb;  // indexed by level-sorted position / in-edge number / item
-            ptr = sv.ptr - nb;
-            in = sv.in - eb;
-            if (PAY && team_desc_fits(a, i0)) dsc = sv.pdesc - i0.x;
+            node = sv.node;
+            ptr = sv.ptr;
+            in = sv.in;
+            if (PAY && team_desc_fits(a, i0)) {
+                dsc = sv.pdesc;
+                ib = i0.x;
+            }
         }
         // this CTA's slice of the level's tasks: one per thread
         {
             const int p1 = team_slice(s0.x, s0.y - s0.x, rank + 1, k);
             const uint64_t pol = l2_keep_policy();
             for (int p = team_slice(s0.x, s0.y - s0.x, rank, k) + t; p < p1; p += kTeamThreads) {
-                const int v = node[p];
-                team_store_key(a.key + v, team_task_key<SOLO>(a, v, in, ptr[p], ptr[p + 1], pol), pol);
+                const int v = node[p - nb];
+                team_store_key(a.key + v,
+                               team_task_key<SOLO>(a, v, in, ptr[p - nb] - eb, ptr[p + 1 - nb] - eb, pol), pol);
             }
         }
         // this CTA's slice of the level's payload pieces: each warp takes the next piece from a
@@ -423,8 +433,8 @@ __device__ __forceinline__ bool team_run_graph(const TeamArgs& a, const TeamJob&
                 const int2 i1 = iring[(l + 1) & 3];
                 if (team_fits(a, ring[(l + 1) & 3]) && team_desc_fits(a, i1) &&
                     mbar_try_wait(&mbar[b1], (phase >> b1) & 1u))
-                    team_prefetch_pieces(sview[b1].pdesc - i1.x, team_slice(i1.x, i1.y - i1.x, rank, k),
-                                         team_slice(i1.x, i1.y - i1.x, rank + 1, k), lane);
+                    team_prefetch_pieces(sview[b1].pdesc, team_slice(i1.x, i1.y - i1.x, rank, k) - i1.x,
+                                         team_slice(i1.x, i1.y - i1.x, rank + 1, k) - i1.x, lane);
             }
             const int q0 = team_slice(i0.x, i0.y - i0.x, rank, k), q1 = team_slice(i0.x, i0.y - i0.x, rank + 1, k);
             for (;;) {
@@ -432,7 +442,7 @@ __device__ __forceinline__ bool team_run_graph(const TeamArgs& a, const TeamJob&
                 if (lane == 0) it = q0 + atomicAdd(&pcnt[l & 1], 1);
                 it = __shfl_sync(0xffffffffu, it, 0);
                 if (it >= q1) break;
-                team_run_piece(dsc[it], lane);
+                team_run_piece(dsc[it - ib], lane);
             }
         }
         if (a.seg_host && rank == 0 && t == 0) team_host_tasks(a, job.seg0 + l);
