@@ -133,6 +133,16 @@ struct Plan {
     cudaGraph_t lgraph = nullptr;
     cudaGraphExec_t lexec = nullptr;
     std::vector<LevelArgs> largs;
+    // host-buffer runs: a second level-sorted in-edge buffer (and its level graph); the next
+    // view's delays are gathered into it while a run reads d_ls_in, then the two swap
+    int2* d_ls_in_alt = nullptr;
+    cudaGraph_t lgraph_alt = nullptr;
+    cudaGraphExec_t lexec_alt = nullptr;
+    std::vector<LevelArgs> largs_alt;
+    int lsb = 0;                      // which of the two buffers d_ls_in is (0: the original)
+    cudaEvent_t ev_buf[2] = {nullptr, nullptr};  // after the last run that read buffer b
+    bool buf_used[2] = {false, false};
+    int32_t* d_bad2 = nullptr;        // per buffer: a gathered delay was not finite
     // runtime
     int num_sms = 0;
     cudaStream_t last_stream = nullptr;
@@ -241,8 +251,13 @@ void plan_destroy(Plan* p) {
     if (p->proxy.joinable()) p->proxy.join();
     if (p->h_post) cudaFreeHost(p->h_post);
     if (p->h_hdone) cudaFreeHost(p->h_hdone);
+    if (p->istream) cudaStreamSynchronize(p->istream);
     if (p->lexec) cudaGraphExecDestroy(p->lexec);
     if (p->lgraph) cudaGraphDestroy(p->lgraph);
+    if (p->lexec_alt) cudaGraphExecDestroy(p->lexec_alt);
+    if (p->lgraph_alt) cudaGraphDestroy(p->lgraph_alt);
+    for (int i = 0; i < 2; ++i)
+        if (p->ev_buf[i]) cudaEventDestroy(p->ev_buf[i]);
     for (void* d : p->owned) dev_free(d, nullptr);
     if (p->h_status) cudaFreeHost(p->h_status);
     if (p->done_ev) cudaEventDestroy(p->done_ev);
@@ -635,14 +650,16 @@ static hf_status plan_set_chunk(Plan* p, int64_t chunk_elems, cudaStream_t s) {
     if (e == cudaSuccess && p->npay) e = cudaMemcpyAsync(p->d_pay, p->hpay.data(), sizeof(DevPayload) * (size_t)p->npay, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // host vectors die at return
     if (e != cudaSuccess) return cuda_fail(e, "piece layout upload");
-    if (p->lexec) {
-        cudaGraphExecDestroy(p->lexec);
-        p->lexec = nullptr;
-    }
-    if (p->lgraph) {
-        cudaGraphDestroy(p->lgraph);
-        p->lgraph = nullptr;
-    }
+    for (cudaGraphExec_t* x : {&p->lexec, &p->lexec_alt})
+        if (*x) {
+            cudaGraphExecDestroy(*x);
+            *x = nullptr;
+        }
+    for (cudaGraph_t* x : {&p->lgraph, &p->lgraph_alt})
+        if (*x) {
+            cudaGraphDestroy(*x);
+            *x = nullptr;
+        }
     p->chunk_elems = chunk_elems;
     return HF_OK;
 }
@@ -837,6 +854,52 @@ __global__ void k_invert_pos(const int32_t* __restrict__ pos_ls, int32_t* __rest
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) edge[__ldg(pos_ls + i)] = (int32_t)i;
 }
 
+// New delays for the level-synchronous or team run about to be enqueued on s: copied by the
+// copy engine and gathered, both on the plan's input stream, into the in-edge buffer the run
+// before it did not use (waiting only for the last run that read that buffer), so that both
+// overlap that run; s waits for the gather, then the buffers (and level graphs) swap.
+static hf_status delays_double_buffered(Plan* p, cudaStream_t s, const float* host) {
+    cudaError_t e = cudaSuccess;
+    const int grid = (int)std::min<int64_t>((p->m + 255) / 256, (int64_t)p->num_sms * 16);
+    if (!p->d_ls_in_alt) {
+        p->d_hstage = p->d_hstage ? p->d_hstage : (float*)palloc(p, 4 * (size_t)p->m, s);
+        p->d_ls_edge = p->d_ls_edge ? p->d_ls_edge : (int32_t*)palloc(p, 4 * (size_t)p->m, s);
+        p->d_ls_in_alt = (int2*)palloc(p, 8 * (size_t)p->m + 64, s);
+        p->d_bad2 = (int32_t*)palloc(p, 16, s);
+        if (!p->d_hstage || !p->d_ls_edge || !p->d_ls_in_alt || !p->d_bad2)
+            return fail(HF_ENOMEM, "device allocation failed: delay buffers");
+        k_invert_pos<<<grid, 256, 0, s>>>(p->d_epos_ls, p->d_ls_edge, p->m);
+        // the second buffer starts as a copy (predecessor ids and delays)
+        if ((e = cudaMemcpyAsync(p->d_ls_in_alt, p->d_ls_in, 8 * (size_t)p->m, cudaMemcpyDeviceToDevice, s)) != cudaSuccess ||
+            (e = cudaEventRecord(p->ev_gather, s)) != cudaSuccess ||  // nothing on istream overtakes this
+            (e = cudaStreamWaitEvent(p->istream, p->ev_gather, 0)) != cudaSuccess)
+            return cuda_fail(e, "delay buffers");
+    }
+    if (p->ran && p->last_stream != s && (e = cudaStreamWaitEvent(s, p->done_ev, 0)) != cudaSuccess)
+        return cuda_fail(e, "delay upload");
+    const int nb = 1 - p->lsb;        // the buffer the coming run reads
+    int2* other = p->d_ls_in_alt;     // (d_ls_in_alt always names the buffer that is not d_ls_in)
+    // the staging buffer is free once the last gather or scatter has read it
+    if ((p->gather_pending && (e = cudaStreamWaitEvent(p->istream, p->ev_gather, 0)) != cudaSuccess) ||
+        (e = cudaMemcpyAsync(p->d_hstage, host, 4 * (size_t)p->m, cudaMemcpyHostToDevice, p->istream)) != cudaSuccess ||
+        (p->buf_used[nb] && (e = cudaStreamWaitEvent(p->istream, p->ev_buf[nb], 0)) != cudaSuccess) ||
+        (e = cudaMemsetAsync(p->d_bad2 + nb, 0, sizeof(int32_t), p->istream)) != cudaSuccess)
+        return cuda_fail(e, "delay upload");
+    k_gather_delays<<<grid, 256, 0, p->istream>>>(p->d_hstage, p->d_ls_edge, other, p->m, p->d_bad2 + nb);
+    if ((e = cudaGetLastError()) != cudaSuccess || (e = cudaEventRecord(p->ev_gather, p->istream)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(s, p->ev_gather, 0)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(&p->d_ctrl->bad_input, p->d_bad2 + nb, sizeof(int32_t), cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+        return cuda_fail(e, "delay gather");
+    std::swap(p->d_ls_in, p->d_ls_in_alt);
+    std::swap(p->lgraph, p->lgraph_alt);
+    std::swap(p->lexec, p->lexec_alt);
+    std::swap(p->largs, p->largs_alt);
+    p->lsb = nb;
+    p->erec_stale = true;
+    p->gather_pending = true;
+    return HF_OK;
+}
+
 // New delays for the run about to be enqueued on s, from page-locked host memory: copied by
 // the copy engine on the plan's input stream, which waits only until the previous view's
 // gather has read the staging buffer (so the copy overlaps the previous run), then gathered on s
@@ -847,8 +910,10 @@ static hf_status delays_from_host(Plan* p, cudaStream_t s, const float* host, in
         e = cudaStreamCreateWithFlags(&p->istream, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_h2d, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_gather, cudaEventDisableTiming);
+        for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&p->ev_buf[i], cudaEventDisableTiming);
         if (e != cudaSuccess) return cuda_fail(e, "delay upload stream");
     }
+    if (mode != HF_MODE_PERSISTENT) return delays_double_buffered(p, s, host);
     const int grid = (int)std::min<int64_t>((p->m + 255) / 256, (int64_t)p->num_sms * 16);
     if (!p->d_hstage) {
         p->d_hstage = (float*)palloc(p, 4 * (size_t)p->m, s);
@@ -1128,6 +1193,11 @@ hf_status plan_run(Plan* p, cudaStream_t s, const hf_run_opts& o, bool keep_stat
         if (io_arr && (st = arrivals_to_host(p, s, io_arr)) != HF_OK) return st;
         e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+    }
+    if (p->ev_buf[p->lsb] && p->n > 0) {  // host-buffer runs: this run's in-edge buffer is read until here
+        e = cudaEventRecord(p->ev_buf[p->lsb], s);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+        p->buf_used[p->lsb] = true;
     }
     e = cudaMemcpyAsync(p->h_status, &p->d_ctrl->status, 3 * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) return cuda_fail(e, "status copy");
