@@ -391,6 +391,7 @@ def main():
         arms = [("levelsync", dict(mode=hf.HF_MODE_LEVELSYNC)),
                 ("persistent_fifo", dict(mode=hf.HF_MODE_PERSISTENT, priority=hf.HF_PRIO_FIFO)),
                 ("persistent_heuristic", dict(mode=hf.HF_MODE_PERSISTENT, priority=hf.HF_PRIO_HEURISTIC)),
+                ("persistent_steal", dict(mode=hf.HF_MODE_PERSISTENT, priority=hf.HF_PRIO_FIFO, steal_ring=1024)),
                 ("team_fifo", dict(mode=hf.HF_MODE_TEAM, priority=hf.HF_PRIO_FIFO)),
                 ("team_heuristic", dict(mode=hf.HF_MODE_TEAM, priority=hf.HF_PRIO_HEURISTIC))]
         if cm is not None:
@@ -465,7 +466,7 @@ def main():
                    "saxpy_elems": wl.saxpy_elems, "executor": args.executor,
                    "chosen": {hf.HF_MODE_PERSISTENT: "persistent", hf.HF_MODE_TEAM: "team"}.get(chosen, "levelsync"),
                    "priority": {0: "fifo", 1: "heuristic", 2: "learned"}[prio],
-                   "launch": {k: head[k] for k in ("ctas", "claim", "local_keep", "chunk_elems")},
+                   "launch": {k: head[k] for k in ("ctas", "claim", "local_keep", "chunk_elems", "payload_warps", "steal_ring")},
                    "autotuned_ms": tuned_ms,
                    "predicted_ms": {"levelsync": ls_pred, "persistent": pe_pred, "team": tm_pred},
                    "l2": "inputs larger than L2 (graph %.0f MB + payload %.0f MB)" % (

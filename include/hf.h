@@ -119,7 +119,8 @@ typedef enum { HF_PRIO_FIFO = 0, HF_PRIO_HEURISTIC = 1, HF_PRIO_LEARNED = 2 } hf
 typedef struct {
     int32_t mode;           /* hf_mode */
     int32_t priority;       /* hf_priority (persistent executor) */
-    int32_t ctas;           /* persistent: CTAs launched; 0 = two per SM (within occupancy) */
+    int32_t ctas;           /* persistent: CTAs launched; 0 = two per SM (within occupancy), one
+                               per SM with work stealing */
     int32_t warps_per_cta;  /* persistent: fixed at 8 in this build (the field is ignored) */
     int32_t claim;          /* persistent: most queue slots a warp claims at once (it claims its
                                fair share of the backlog), 1..32; default 8 */
@@ -150,7 +151,12 @@ typedef struct {
                                larger values give payload-heavy graphs larger teams; 0 = 4 (a
                                512-element piece: ~0.75 us for a warp alone, ~3 us when every SM
                                streams, measured on B300) */
-    int32_t pad2_;
+    int32_t steal_ring;     /* persistent: 0 = one global ready queue; > 0 = work stealing
+                               (Section III-C): every CTA owns a ring of this many slots (rounded
+                               up to a power of two, 64..16384) that its warps push ready tasks
+                               and payload pieces to and take from first; a warp with nothing in
+                               its ring or the global queue (sources, ring overflow) steals half
+                               of the published front of a random other CTA's ring */
 } hf_run_opts;
 
 void hf_run_opts_default(hf_run_opts* opts);
@@ -303,7 +309,9 @@ hf_status hf_batch_kernel_ms(hf_batch* b, float* ms);
 /* Counters of the last persistent run with instrument bit 1 (host int64 out[n], n <= 16): warp
  * rounds with work, items processed, idle polls, successor releases, CAS attempts, ready tasks
  * kept in warp stacks, items pushed to / claims on / items popped from the global queue,
- * payload pieces run. Diagnostics only. */
+ * payload pieces run, SM cycles in rounds with work (4 counters: rounds, releases, CAS
+ * sections, pushes), and with work stealing the items pushed to CTA rings and the items stolen
+ * from another CTA's ring. Diagnostics only. */
 hf_status hf_batch_get_stats(hf_batch* b, int64_t* out, int32_t n);
 /* Per-graph %globaltimer start and end (ns; host arrays of the batch's graph count) of the last
  * team-executor run with instrument bit 0: when the graph's job started and when its last
@@ -389,7 +397,8 @@ hf_status hf_batch_bottom_levels(hf_batch* b, const float* cost, float* bottom, 
  * after one warm-up. base->mode HF_MODE_TEAM tunes the team executor (coordinate descent over
  * the cluster size for every graph, 0 = the cost model's plan, and the payload piece size);
  * any other mode tunes the persistent executor (CTA count, queue claim size, shared-memory
- * stack depth, payload piece size, payload warps; mode PERSISTENT in *best). Results are
+ * stack depth, payload piece size, payload warps, global queue or work stealing; mode
+ * PERSISTENT in *best). Results are
  * cached per executor and size bucket (tasks, edges per task, payload share, depth, batch or
  * single graph), so a later call on a similar batch returns without trials unless `force`.
  * Runs the batch many times: payloads run each time (saxpy updates y). Blocks. */

@@ -77,7 +77,7 @@ struct PersistArgs {
     const DevPayload* pay;
     const int32_t* chunk_pay;   // piece item -> payload index
     int32_t npieces;            // piece items (queue items n .. n+npieces-1; payload starts follow)
-    int32_t pad2_;
+    int32_t ring_mask;          // work stealing: slots per CTA ring - 1 (a power of two minus one)
     unsigned long long* state;  // n_tasks {key << 32 | pending predecessors}
     uint32_t* key;              // n_tasks final arrival keys (output)
     int32_t* queue;             // qcap ready-queue slots (-1 = empty)
@@ -95,6 +95,11 @@ struct PersistArgs {
     int32_t* post;              // host tasks: mapped mailbox (the i-th posted host task), else NULL
     const int32_t* hdone;       // mapped: host task k has run
     int32_t* post_ctr;          // device counter of posts
+    // work stealing (NULL: the global queue alone): CTA c owns ring[c * (ring_mask + 1) ...],
+    // cells {position + 1 << 32 | item} (0: never written), and ring_head[c * 32], the next
+    // position to take; positions count from 0 in every run
+    unsigned long long* ring;
+    int32_t* ring_head;
 };
 
 // Executor counters recorded by runs with instrument & 2 (hf_get_stats).
@@ -113,6 +118,8 @@ enum StatIdx {
     kStatCycRelease,     // ... of which releasing successors (pushes included)
     kStatCycCas,         // ... of which the compare-and-swap sections
     kStatCycPush,        // ... of which pushing ready tasks
+    kStatRingPush,       // work stealing: items pushed to the CTA's own ring
+    kStatSteals,         // work stealing: items taken from another CTA's ring
     kStatCount = 16
 };
 
@@ -146,6 +153,10 @@ struct ResetArgs {
     int64_t* tk_start;
     int64_t* tk_end;
     int32_t* exec_count;
+    unsigned long long* ring;  // work stealing: ring cells cleared (ring_cells of them), else NULL
+    int64_t ring_cells;
+    int32_t* ring_head;        // ring_heads counters cleared
+    int32_t ring_heads;
 };
 
 // Team executor: a job is one graph, run by one CTA (solo job) or by the CTAs of one thread-block

@@ -5,7 +5,9 @@
 //     thread pulls the arrival of one task from its level-sorted in-edges;
 //   * persistent: one launch; every warp loops popping ready tasks (shared-memory stack
 //     first, then pre-claimed global queue slots), runs their payload pieces, and releases
-//     successors through atomic in-degree counters, pushing the ones that become ready.
+//     successors through atomic in-degree counters, pushing the ones that become ready. In
+//     the work-stealing variant each CTA also owns a ring of ready tasks that its warps fill
+//     and take from first, and idle warps steal from other CTAs' rings.
 // Arrivals are kept as order-preserving uint32 keys so that the max over predecessors is
 // an unsigned integer max (an atomicMax in the persistent executor).
 #pragma once
@@ -387,6 +389,10 @@ __global__ void k_reset(const ResetArgs a) {
             a.pqueue[i] = v;
         }
     for (int64_t i = tid; i < a.n_pay; i += stride) a.chunks_left[i] = a.pay[i].nchunks;
+    if (a.ring) {  // work stealing: empty rings, positions from 0
+        for (int64_t i = tid; i < a.ring_cells; i += stride) a.ring[i] = 0ull;
+        for (int64_t i = tid; i < a.ring_heads; i += stride) a.ring_head[i] = 0;
+    }
     if (tid == 0) {
         a.ctrl->head = 0;
         a.ctrl->tail = (int32_t)nmain;
@@ -402,7 +408,7 @@ __global__ void k_reset(const ResetArgs a) {
 // Per-warp executor counters (reported when PersistArgs::stats is set); `cas` is per lane.
 struct WStats {
     uint32_t rounds = 0, items = 0, idle = 0, edges = 0, cas = 0, local = 0, global = 0, claims = 0, pops = 0,
-             pieces = 0;
+             pieces = 0, ring = 0, steals = 0;
     unsigned long long cyc_round = 0, cyc_release = 0, cyc_cas = 0, cyc_push = 0;
     bool on = false;  // cycle counts are taken only when counters are recorded
 };
@@ -443,15 +449,121 @@ __device__ __forceinline__ void push_items(const PersistArgs& a, int32_t* slots,
     __syncwarp();
 }
 
+// ---- work stealing (Section III-C): per-CTA rings beside the global queue
+// The warps of a CTA push the ready tasks that do not stay in their stacks (and the pieces of
+// payloads they expand) to the CTA's own ring. A warp takes from its own ring first, then from
+// the global queue (sources and ring overflow), and when both are empty steals from the ring of
+// a randomly chosen other CTA. A ring is a bounded FIFO with one producer side and many
+// consumers: its fill position lives in the owner's shared memory (only the owner's warps
+// push), its take position in global memory (owner and thieves take with a compare-and-swap),
+// and every cell carries the position it was written for, so a taker sees exactly which cells
+// at the front are published and a cell left from an earlier lap never passes for a new one.
+
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// As push_items, to this CTA's ring: the leading items that fit go to the ring (a slot is free
+// once the take position has passed the cell's previous lap), the rest to the global queue.
+// rt[0]: the ring's fill position; rt[1]: a lower bound of its take position (shared memory).
+__device__ __forceinline__ void ring_push(const PersistArgs& a, int* rt, int cnt, int first_item, bool multi,
+                                          int lane, WStats& ws) {
+    if (__ballot_sync(kFull, cnt > 0) == 0) return;
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const int total = __shfl_sync(kFull, incl, 31);
+    const int excl = incl - cnt;
+    const int cap = a.ring_mask + 1;
+    int base = 0, fit = 0;
+    if (lane == 0) {
+        const int32_t* hp = a.ring_head + (size_t)blockIdx.x * 32;
+        for (int tries = 0; tries < 64; ++tries) {  // contended only by this CTA's warps
+            const int t = *(volatile int*)&rt[0];
+            int h = *(volatile int*)&rt[1];
+            if (t + total - h > cap) {  // the cached take position may be behind: reload it
+                h = max(h, ld_relaxed(hp));
+                atomicMax(&rt[1], h);
+            }
+            fit = min(total, max(h + cap - t, 0));
+            if (fit == 0) break;
+            if (atomicCAS(&rt[0], t, t + fit) == t) {
+                base = t;
+                break;
+            }
+            fit = 0;
+        }
+    }
+    base = __shfl_sync(kFull, base, 0);
+    fit = __shfl_sync(kFull, fit, 0);
+    const int mine = min(cnt, max(fit - excl, 0));  // this lane's items that go to the ring
+    if (fit > 0) {
+        ws.ring += (uint32_t)fit;
+        fence_acq_rel();  // release: the ready tasks' state (and inputs) before their cells
+        unsigned long long* cells = a.ring + (size_t)blockIdx.x * cap;
+        for (int k = 0; k < mine; ++k) {
+            const int pos = base + excl + k;
+            st_relaxed_u64(cells + (pos & a.ring_mask),
+                           ((unsigned long long)(uint32_t)(pos + 1) << 32) | (uint32_t)(first_item + (multi ? k : 0)));
+        }
+    }
+    push_items(a, a.queue, a.qcap, &a.ctrl->tail, cnt - mine, first_item + (multi ? mine : 0), multi, lane, ws);
+}
+
+// Takes up to `most` (<= 32) published items from the front of CTA c's ring into lanes
+// 0..k-1 (`item`) and returns k: the published run at the front (half of it when stealing),
+// 0 when the front is not published or another warp took it first. h: the take position the
+// front is read at (the CAS fails if it moved); own: it came from this CTA's shared hint.
+__device__ __forceinline__ int ring_take_at(const PersistArgs& a, int c, int h, int most, bool half, int* rt,
+                                            int lane, int& item) {
+    int32_t* hp = a.ring_head + (size_t)c * 32;
+    unsigned long long cell = 0;
+    if (lane < most) cell = ld_relaxed_u64(a.ring + (size_t)c * (a.ring_mask + 1) + ((h + lane) & a.ring_mask));
+    const unsigned pub = __ballot_sync(kFull, lane < most && (uint32_t)(cell >> 32) == (uint32_t)(h + lane + 1));
+    int k = pub == kFull ? 32 : __ffs(~pub) - 1;
+    if (half) k = (k + 1) >> 1;
+    if (k == 0) return 0;
+    int prev = 0;
+    if (lane == 0) {
+        prev = atomicCAS(hp, h, h + k);
+        if (rt) atomicMax(&rt[1], prev == h ? h + k : prev);  // the owner's hint follows the head
+    }
+    if (__shfl_sync(kFull, prev, 0) != h) return 0;
+    if (lane < k) item = (int)(uint32_t)cell;
+    fence_acq_rel();  // acquire: what the pusher released with the cells
+    return k;
+}
+
+// This CTA's own ring: empty when the shared fill position has not passed the shared hint of
+// the take position (thieves only move the head further), so an idle check costs no global
+// access; otherwise the front is read at the hint.
+__device__ __forceinline__ int ring_take_own(const PersistArgs& a, int* rt, int most, int lane, int& item) {
+    const int t = *(volatile int*)&rt[0];
+    const int h = *(volatile int*)&rt[1];
+    if (t <= h) return 0;
+    return ring_take_at(a, (int)blockIdx.x, h, min(most, t - h), false, rt, lane, item);
+}
+
+// Another CTA's ring: its head first, then half of its published front.
+__device__ __forceinline__ int ring_steal(const PersistArgs& a, int c, int most, int lane, int& item) {
+    int h = 0;
+    if (lane == 0) h = ld_relaxed(a.ring_head + (size_t)c * 32);
+    h = __shfl_sync(kFull, h, 0);
+    return ring_take_at(a, c, h, most, true, nullptr, lane, item);
+}
+
 // Pushes this warp's ready tasks (lane: r.x >= 0 with r = {task, key, first out-edge (payload
 // index for payload tasks), out-degree | payload flag << 31}). Tasks go to the warp's stack
 // while it has room (up to local_keep) -- plain tasks with their first kStage out-edges staged
 // in shared memory for the next round -- except payload tasks in warp-specialised runs, which
-// go to the payload queue; the rest go to the main queue. nstk / nedg: the stack buffer filled
-// this round and its staging area.
+// go to the payload queue; the rest go to the main queue (with work stealing: to the CTA's ring,
+// rt). nstk / nedg: the stack buffer filled this round and its staging area.
 template <bool PAY>
 __device__ __forceinline__ void push_ready(const PersistArgs& a, int4 r, int pr, int4* nstk, int4* nedg, int& top,
-                                           int lane, WStats& ws) {
+                                           int* rt, int lane, WStats& ws) {
     const long long c_push = clk(ws);
     const int v = r.x;
     const bool haspay = PAY && v >= 0 && r.w < 0;
@@ -484,7 +596,8 @@ __device__ __forceinline__ void push_ready(const PersistArgs& a, int4 r, int pr,
     top += min(__popc(sm), max(room, 0));
     ws.local += (uint32_t)min(__popc(sm), max(room, 0));
     const int item = haspay ? a.n_tasks + a.npieces + r.z : v;
-    push_items(a, a.queue, a.qcap, &a.ctrl->tail, (go_global && !topay) ? 1 : 0, item, false, lane, ws);
+    if (a.ring) ring_push(a, rt, (go_global && !topay) ? 1 : 0, item, false, lane, ws);
+    else push_items(a, a.queue, a.qcap, &a.ctrl->tail, (go_global && !topay) ? 1 : 0, item, false, lane, ws);
     if (PAY && a.pay_warps > 0) push_items(a, a.pqueue, a.pqcap, &a.ctrl->ptail, topay ? 1 : 0, item, false, lane, ws);
     if (ws.on) ws.cyc_push += (unsigned long long)(clk(ws) - c_push);
 }
@@ -532,7 +645,7 @@ __device__ __forceinline__ bool release_succ(const PersistArgs& a, int v, uint32
 // cedg[lane * kStage ...]; nstk / nedg receive the tasks that become ready.
 template <bool PAY>
 __device__ __forceinline__ void release_all(const PersistArgs& a, int fin, uint32_t kt, int rs, int deg, bool staged,
-                                            const int4* cedg, int4* nstk, int4* nedg, int& top, int lane,
+                                            const int4* cedg, int4* nstk, int4* nedg, int& top, int* rt, int lane,
                                             WStats& ws) {
     const long long c_rel = clk(ws);
     if (fin < 0) deg = 0;
@@ -584,7 +697,7 @@ __device__ __forceinline__ void release_all(const PersistArgs& a, int fin, uint3
         }
         const bool any_ready = __ballot_sync(kFull, r.x >= 0) != 0;
         if (ws.on) ws.cyc_cas += (unsigned long long)(clk(ws) - c_cas);
-        if (any_ready) push_ready<PAY>(a, r, pr, nstk, nedg, top, lane, ws);
+        if (any_ready) push_ready<PAY>(a, r, pr, nstk, nedg, top, rt, lane, ws);
     }
     if (ws.on) ws.cyc_release += (unsigned long long)(clk(ws) - c_rel);
 }
@@ -593,8 +706,14 @@ template <bool PAY>
 __global__ void __launch_bounds__(kWarpsPerCta * 32, 2) k_persist(const PersistArgs a) {
     __shared__ int4 s_stack[kWarpsPerCta][2][kStackCap];
     __shared__ int4 s_edges[kWarpsPerCta][2][kStackCap * kStage];
+    __shared__ int s_ring[2];  // work stealing: this CTA's ring fill position, a lower bound of its take position
     const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {
+        s_ring[0] = 0;
+        s_ring[1] = 0;
+    }
+    __syncthreads();
     int pb = 0;  // buffer holding the stacked tasks; a round pops all of it and fills the other
     int top = 0;
     int qbase = 0;
@@ -613,6 +732,9 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 2) k_persist(const PersistA
     int32_t* const qtail = payw ? &a.ctrl->ptail : &a.ctrl->tail;
     const int nwarps = (int)gridDim.x * (PAY && a.pay_warps > 0 ? (payw ? a.pay_warps : kWarpsPerCta - a.pay_warps)
                                                                   : kWarpsPerCta);
+    // work stealing: main-queue warps take from rings (payload warps keep the payload queue)
+    const bool steal = a.ring != nullptr && !payw;
+    uint32_t rng = ((uint32_t)blockIdx.x * kWarpsPerCta + (uint32_t)wid) * 2654435761u + 0x9e3779b9u;  // victims
     uint32_t ndone = 0;  // completions not yet added to ctrl->done (warp-uniform)
     uint32_t iter = 0;
     WStats ws;
@@ -633,15 +755,25 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 2) k_persist(const PersistA
             pb ^= 1;
             __syncwarp();
         } else {
-            if (pend == 0) {
-                // claim a fair share of the published backlog (at least 1, at most `claim`)
+            int took = 0;  // items taken from a ring (lanes 0..took-1)
+            if (pend == 0 && steal) took = ring_take_own(a, s_ring, a.claim, lane, item);
+            if (pend == 0 && took == 0) {
+                // claim a fair share of the published backlog (at least 1, at most `claim`); with
+                // work stealing only slots the tail covers, since the global queue then holds just
+                // sources and ring overflow, and a slot past the tail may never be filled
                 int b = qcap, k = 0;
                 if (lane == 0) {
                     const int h = ld_relaxed(qhead);
+                    const int t = ld_relaxed(qtail);
                     if (h < qcap) {
-                        const int t = ld_relaxed(qtail);
                         k = max(1, min((t - h) / nwarps, a.claim));
-                        b = atomicAdd(qhead, k);
+                        if (!steal) {
+                            b = atomicAdd(qhead, k);
+                        } else {
+                            k = t > h ? min(k, t - h) : 0;
+                            if (k > 0 && atomicCAS(qhead, h, h + k) == h) b = h;
+                            else k = 0;
+                        }
                         ws.claims++;
                     }
                 }
@@ -650,6 +782,15 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 2) k_persist(const PersistA
                 qbase = b;
                 k = min(k, qcap - b);
                 pend = k <= 0 ? 0u : (k >= 32 ? kFull : ((1u << k) - 1u));
+                if (steal && pend == 0 && gridDim.x > 1) {  // both empty: try a random victim
+                    rng ^= rng << 13;
+                    rng ^= rng >> 17;
+                    rng ^= rng << 5;
+                    int c = (int)(rng % (gridDim.x - 1u));
+                    if (c >= (int)blockIdx.x) ++c;
+                    took = ring_steal(a, c, a.claim, lane, item);
+                    ws.steals += (uint32_t)took;
+                }
             }
             if (pend & (1u << lane)) {
                 const int v = ld_relaxed(qslots + qbase + lane);
@@ -755,7 +896,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 2) k_persist(const PersistA
         }
         if (__ballot_sync(kFull, fin >= 0))
             release_all<PAY>(a, fin, kt, rs, deg, staged, s_edges[wid][cb], s_stack[wid][pb], s_edges[wid][pb], top,
-                             lane, ws);
+                             s_ring, lane, ws);
         if (a.t_end && fin >= 0) a.t_end[fin] = (int64_t)gtimer();
         ndone += (uint32_t)__popc(__ballot_sync(kFull, fin >= 0));
 
@@ -770,7 +911,8 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 2) k_persist(const PersistA
                     nc = a.pay[p].nchunks;
                     cf = a.pay[p].chunk_first;
                 }
-                push_items(a, qslots, qcap, qtail, (expand && nc > 1) ? nc - 1 : 0, n_tasks + cf + 1, true, lane, ws);
+                if (steal) ring_push(a, s_ring, (expand && nc > 1) ? nc - 1 : 0, n_tasks + cf + 1, true, lane, ws);
+                else push_items(a, qslots, qcap, qtail, (expand && nc > 1) ? nc - 1 : 0, n_tasks + cf + 1, true, lane, ws);
                 ws.pieces += (uint32_t)__popc(work);
                 fence_acq_rel();  // acquire: inputs written by upstream payload tasks
                 while (work) {
@@ -806,7 +948,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 2) k_persist(const PersistA
                 }
                 if (__ballot_sync(kFull, fin2 >= 0))
                     release_all<PAY>(a, fin2, kt, rs, deg, false, s_edges[wid][cb], s_stack[wid][pb],
-                                     s_edges[wid][pb], top, lane, ws);
+                                     s_edges[wid][pb], top, s_ring, lane, ws);
                 if (a.t_end && fin2 >= 0) a.t_end[fin2] = (int64_t)gtimer();
                 ndone += (uint32_t)__popc(__ballot_sync(kFull, fin2 >= 0));
             }
@@ -838,6 +980,8 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 2) k_persist(const PersistA
             atomicAdd(a.stats + kStatCycRelease, ws.cyc_release);
             atomicAdd(a.stats + kStatCycCas, ws.cyc_cas);
             atomicAdd(a.stats + kStatCycPush, ws.cyc_push);
+            atomicAdd(a.stats + kStatRingPush, (unsigned long long)ws.ring);
+            atomicAdd(a.stats + kStatSteals, (unsigned long long)ws.steals);
         }
     }
 }

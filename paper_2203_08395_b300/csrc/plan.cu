@@ -124,6 +124,9 @@ struct Plan {
     int64_t* d_tk_end = nullptr;
     int32_t* d_exec = nullptr;
     unsigned long long* d_stats = nullptr;  // executor counters (instrument & 2)
+    unsigned long long* d_ring = nullptr;   // work stealing: per-CTA rings of ready tasks
+    int32_t* d_ring_head = nullptr;         // their take positions (one 128-byte line per CTA)
+    size_t cap_ring = 0, cap_ring_head = 0;
     int64_t* d_gtime = nullptr;             // team executor: per-graph start, then end (instrument & 1)
     int32_t last_launches = 0;              // executor kernels of the last run
     bool last_gtimes = false;
@@ -1125,7 +1128,43 @@ hf_status plan_run(Plan* p, cudaStream_t s, const hf_run_opts& o, bool keep_stat
             r.exec_count = valid ? p->d_exec : nullptr;
             r.stall_task = (o.stall_task >= 0 && o.stall_task < p->n) ? o.stall_task : -1;
             r.keep_status = keep_status ? 1 : 0;
-            const int64_t work = std::max<int64_t>(p->n, p->qcap);
+            int ctas = o.ctas;
+            if (ctas <= 0) {  // two CTAs (16 warps) per SM, capped by occupancy: more idle warps
+                              // only add polling traffic (the autotuner searches around this); with
+                              // work stealing one per SM, as idle warps probe other CTAs' rings
+                int occ = 0;
+                if (p->npay) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_persist<true>, kWarpsPerCta * 32, 0);
+                else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_persist<false>, kWarpsPerCta * 32, 0);
+                ctas = p->num_sms * std::min(std::max(occ, 1), o.steal_ring > 0 ? 1 : 2);
+            }
+            // work stealing: a ring of ring_slots cells per CTA (a power of two, 64..16384)
+            int32_t ring_slots = 0;
+            r.ring = nullptr;
+            r.ring_cells = 0;
+            r.ring_head = nullptr;
+            r.ring_heads = 0;
+            if (o.steal_ring > 0) {
+                ring_slots = 64;
+                while (ring_slots < o.steal_ring && ring_slots < 16384) ring_slots *= 2;
+                const size_t cells = (size_t)ctas * (size_t)ring_slots;
+                const size_t heads = (size_t)ctas * 32;
+                if (p->cap_ring < 8 * cells) {
+                    free_owned(p, p->d_ring);
+                    p->d_ring = (unsigned long long*)palloc(p, 8 * cells, s);
+                    p->cap_ring = p->d_ring ? 8 * cells : 0;
+                }
+                if (p->cap_ring_head < 4 * heads) {
+                    free_owned(p, p->d_ring_head);
+                    p->d_ring_head = (int32_t*)palloc(p, 4 * heads, s);
+                    p->cap_ring_head = p->d_ring_head ? 4 * heads : 0;
+                }
+                if (!p->d_ring || !p->d_ring_head) return fail(HF_ENOMEM, "device allocation failed: steal rings");
+                r.ring = p->d_ring;
+                r.ring_cells = (int64_t)cells;
+                r.ring_head = p->d_ring_head;
+                r.ring_heads = (int32_t)heads;
+            }
+            const int64_t work = std::max<int64_t>(std::max<int64_t>(p->n, p->qcap), r.ring_cells);
             const int rgrid = (int)std::min<int64_t>((work + 255) / 256, (int64_t)p->num_sms * 16);
             k_reset<<<std::max(rgrid, 1), 256, 0, s>>>(r);
             PersistArgs a;
@@ -1154,6 +1193,9 @@ hf_status plan_run(Plan* p, cudaStream_t s, const hf_run_opts& o, bool keep_stat
             a.tk_start = r.tk_start;
             a.tk_end = r.tk_end;
             a.exec_count = r.exec_count;
+            a.ring = r.ring;
+            a.ring_head = r.ring_head;
+            a.ring_mask = ring_slots > 0 ? ring_slots - 1 : 0;
             a.stats = nullptr;
             if (o.instrument & 2) {
                 if (!p->d_stats) {
@@ -1172,14 +1214,6 @@ hf_status plan_run(Plan* p, cudaStream_t s, const hf_run_opts& o, bool keep_stat
                 a.post_ctr = p->d_post_ctr;
                 e = cudaMemsetAsync(p->d_post_ctr, 0, sizeof(int32_t), s);
                 if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
-            }
-            int ctas = o.ctas;
-            if (ctas <= 0) {  // two CTAs (16 warps) per SM, capped by occupancy: more idle warps
-                              // only add polling traffic (the autotuner searches around this)
-                int occ = 0;
-                if (p->npay) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_persist<true>, kWarpsPerCta * 32, 0);
-                else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_persist<false>, kWarpsPerCta * 32, 0);
-                ctas = p->num_sms * std::min(std::max(occ, 1), 2);
             }
             if (o.time_kernel) cudaEventRecord(p->kev0, s);
             if (p->npay) k_persist<true><<<ctas, kWarpsPerCta * 32, 0, s>>>(a);
@@ -1663,6 +1697,7 @@ hf_status plan_autotune(Plan* p, cudaStream_t s, const hf_run_opts& base, int fo
             best->payload_warps = it->second.first.payload_warps;
             best->team_size = it->second.first.team_size;
             best->team_scale = it->second.first.team_scale;
+            best->steal_ring = it->second.first.steal_ring;
             *best_ms = it->second.second;
             return HF_OK;
         }
@@ -1691,20 +1726,23 @@ hf_status plan_autotune(Plan* p, cudaStream_t s, const hf_run_opts& base, int fo
     const std::vector<int> keep_v{4, 8, 12, 16};
     const std::vector<int64_t> chunk_v{1024, 4096, 16384};
     const std::vector<int> payw_v{0, 1, 2, 4};
+    const std::vector<int> ring_v{0, 1024};  // global queue alone, or work stealing
     for (int round = 0; round < 2; ++round) {
-        for (int dim = 0; dim < 5; ++dim) {
-            if (dim >= 3 && p->npay == 0) continue;
+        for (int dim = 0; dim < 6; ++dim) {
+            if ((dim == 3 || dim == 4) && p->npay == 0) continue;
             const size_t nv = dim == 0 ? ctas_v.size() : dim == 1 ? claim_v.size() : dim == 2 ? keep_v.size()
-                              : dim == 3 ? chunk_v.size() : payw_v.size();
+                              : dim == 3 ? chunk_v.size() : dim == 4 ? payw_v.size() : ring_v.size();
             for (size_t i = 0; i < nv; ++i) {
                 hf_run_opts t = cur;
                 if (dim == 0) t.ctas = ctas_v[i];
                 else if (dim == 1) t.claim = claim_v[i];
                 else if (dim == 2) t.local_keep = keep_v[i];
                 else if (dim == 3) t.chunk_elems = chunk_v[i];
-                else t.payload_warps = payw_v[i];
+                else if (dim == 4) t.payload_warps = payw_v[i];
+                else t.steal_ring = ring_v[i];
                 if (t.ctas == cur.ctas && t.claim == cur.claim && t.local_keep == cur.local_keep &&
-                    t.chunk_elems == cur.chunk_elems && t.payload_warps == cur.payload_warps)
+                    t.chunk_elems == cur.chunk_elems && t.payload_warps == cur.payload_warps &&
+                    t.steal_ring == cur.steal_ring)
                     continue;
                 float ms = 0.f;
                 if ((st = time_runs(p, s, t, 3, &ms)) != HF_OK) return st;

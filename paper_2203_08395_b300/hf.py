@@ -65,7 +65,7 @@ class hf_run_opts(ctypes.Structure):
                 ("instrument", ctypes.c_int32), ("validate", ctypes.c_int32),
                 ("stall_task", ctypes.c_int32), ("time_kernel", ctypes.c_int32),
                 ("payload_warps", ctypes.c_int32), ("team_size", ctypes.c_int32),
-                ("team_scale", ctypes.c_int32), ("pad2_", ctypes.c_int32)]
+                ("team_scale", ctypes.c_int32), ("steal_ring", ctypes.c_int32)]
 
 
 class hf_graph_info_t(ctypes.Structure):
@@ -588,7 +588,7 @@ def hf_batch_run_until(b, pred, max_runs, stream=None, opts=None):
 
 
 STAT_NAMES = ["rounds", "items", "idle", "edges", "cas", "push_local", "push_global", "claims", "pops", "pieces",
-              "cyc_round", "cyc_release", "cyc_cas", "cyc_push"]
+              "cyc_round", "cyc_release", "cyc_cas", "cyc_push", "push_ring", "steals"]
 
 
 def hf_batch_get_stats(b):

@@ -31,6 +31,12 @@ EXECUTORS = {
     "persistent_wide": dict(mode=hf.HF_MODE_PERSISTENT, ctas=148 * 8, claim=4),
     "persistent_payw2": dict(mode=hf.HF_MODE_PERSISTENT, payload_warps=2, claim=8, local_keep=8),
     "persistent_payw7": dict(mode=hf.HF_MODE_PERSISTENT, payload_warps=7, ctas=16),
+    # work stealing: per-CTA rings; small rings overflow to the global queue, few CTAs steal a lot
+    "steal": dict(mode=hf.HF_MODE_PERSISTENT, steal_ring=4096),
+    "steal_small": dict(mode=hf.HF_MODE_PERSISTENT, steal_ring=64, claim=4),
+    "steal_2cta": dict(mode=hf.HF_MODE_PERSISTENT, steal_ring=64, ctas=2),
+    "steal_1cta": dict(mode=hf.HF_MODE_PERSISTENT, steal_ring=128, ctas=1),
+    "steal_payw2": dict(mode=hf.HF_MODE_PERSISTENT, steal_ring=256, payload_warps=2),
     "team": dict(mode=hf.HF_MODE_TEAM),
     "team_heur": dict(mode=hf.HF_MODE_TEAM, priority=hf.HF_PRIO_HEURISTIC),
     "team_k2": dict(mode=hf.HF_MODE_TEAM, team_size=2),
@@ -69,7 +75,7 @@ def test_layered10k_bit_exact(ex):
     gd.close()
 
 
-@pytest.mark.parametrize("ex", ["levelsync", "persistent", "persistent_claim8", "team", "team_k5"])
+@pytest.mark.parametrize("ex", ["levelsync", "persistent", "persistent_claim8", "steal_small", "team", "team_k5"])
 def test_random_graphs_100_seeds(ex):
     rng = np.random.default_rng(5)
     for seed in range(100):
@@ -89,10 +95,11 @@ def test_random_graphs_100_seeds(ex):
         gd.close()
 
 
-def test_validate_exactly_once_and_order():
+@pytest.mark.parametrize("ex", ["persistent", "steal", "steal_2cta"])
+def test_validate_exactly_once_and_order(ex):
     spec = S.circuit(1, 200_000, 400)
     gd = GraphOnDevice(spec)
-    gd.run(mode=hf.HF_MODE_PERSISTENT, validate=1)
+    gd.run(validate=1, **EXECUTORS[ex])
     gd.sync()
     s0, s1, cnt = hf.hf_get_stamps(gd.g, spec.n)
     assert np.all(cnt == 1)
@@ -102,7 +109,7 @@ def test_validate_exactly_once_and_order():
     gd.close()
 
 
-@pytest.mark.parametrize("ex", ["levelsync", "persistent", "persistent_claim8", "team_heur", "team_k5"])
+@pytest.mark.parametrize("ex", ["levelsync", "persistent", "persistent_claim8", "steal", "team_heur", "team_k5"])
 def test_circuit1m_full_size(ex):
     spec = S.config("circuit1m").graphs[0]
     ref = oracle.run_spec(spec)["arr"]
@@ -123,7 +130,7 @@ def _check_payloads(gd, ref):
 
 @pytest.mark.parametrize("chunk", [0, 64, 4096])
 @pytest.mark.parametrize("ex", ["levelsync", "persistent", "persistent_claim8", "persistent_payw2", "persistent_payw7",
-                                "team", "team_k2", "team_k5"])
+                                "steal", "steal_small", "steal_2cta", "steal_payw2", "team", "team_k2", "team_k5"])
 def test_mixed_small_with_payloads(ex, chunk):
     spec = S.mixed(3, n=6000, nmin=1, nmax=20000, n_copy=300)
     ref = oracle.run_spec(spec)
@@ -140,7 +147,7 @@ def test_mixed100k_full_size_sampled():
     gd = GraphOnDevice(spec)
     rng = np.random.default_rng(0)
     sample = rng.choice(spec.sx_task.size, 64, replace=False)
-    for ex in ["levelsync", "persistent", "team_heur"]:
+    for ex in ["levelsync", "persistent", "steal", "team_heur"]:
         gd.reset_y()
         arr = _run(gd, **EXECUTORS[ex])
         np.testing.assert_array_equal(bits(arr), bits(ref["arr"]))
@@ -155,7 +162,7 @@ def test_mixed100k_full_size_sampled():
     gd.close()
 
 
-@pytest.mark.parametrize("ex", ["levelsync", "persistent", "team", "team_heur"])
+@pytest.mark.parametrize("ex", ["levelsync", "persistent", "steal", "team", "team_heur"])
 def test_batch256_full_size(ex):
     wl = S.config("batch256")
     bd = BatchOnDevice(wl)
@@ -167,7 +174,8 @@ def test_batch256_full_size(ex):
     bd.close()
 
 
-@pytest.mark.parametrize("ex", ["levelsync", "persistent", "persistent_payw2", "team", "team_heur", "team_k2"])
+@pytest.mark.parametrize("ex", ["levelsync", "persistent", "persistent_payw2", "steal_small", "steal_payw2", "team",
+                                "team_heur", "team_k2"])
 def test_batch_mixed_small(ex):
     wl = S.batch(2, graphs=12, nmin=500, nmax=20000, frac_saxpy=0.1, sx_min=1, sx_max=3000)
     bd = BatchOnDevice(wl)
@@ -461,15 +469,16 @@ def test_arrivals_on_device():
     gd.close()
 
 
-def test_stalled_task_times_out_and_context_survives():
+@pytest.mark.parametrize("ring", [0, 256])
+def test_stalled_task_times_out_and_context_survives(ring):
     """Failure path without a GPU fault: one task's counter starts one too high, so it never
     becomes ready; the persistent kernel's bounded waits end the run with HF_ETIMEDOUT and the
-    next run on the same context is correct."""
+    next run on the same context is correct (global queue, and work stealing)."""
     spec = S.layered(8, 20000, 40, 1, 4)
     gd = GraphOnDevice(spec)
-    gd.run(mode=hf.HF_MODE_PERSISTENT, stall_task=12345, spin_limit_ns=50_000_000)
+    gd.run(mode=hf.HF_MODE_PERSISTENT, stall_task=12345, spin_limit_ns=50_000_000, steal_ring=ring)
     assert gd.sync(check=False) == hf.HF_ETIMEDOUT
-    gd.run(mode=hf.HF_MODE_PERSISTENT)
+    gd.run(mode=hf.HF_MODE_PERSISTENT, steal_ring=ring)
     gd.sync()
     np.testing.assert_array_equal(bits(gd.arrivals()), bits(oracle.run_spec(spec)["arr"]))
     gd.close()
@@ -572,3 +581,27 @@ def test_unpinned_pull_buffer_rejected():
         hf.hf_run(g, None, hf.hf_run_opts_default())
     assert ei.value.status == hf.HF_EINVAL
     hf.hf_graph_destroy(g)
+
+
+def test_work_stealing_counters():
+    """Work stealing moves work between CTAs: with rings, ready tasks go to the owner's ring and
+    idle CTAs steal; without, no ring is touched. Arrivals are the oracle's either way."""
+    wl = S.batch(5, graphs=8, nmin=2000, nmax=30000)
+    ref = [oracle.run_spec(g)["arr"] for g in wl.graphs]
+    bd = BatchOnDevice(wl)
+    seen = {}
+    for ring in (0, 64, 4096):
+        bd.run(mode=hf.HF_MODE_PERSISTENT, steal_ring=ring, ctas=8, instrument=2)
+        bd.sync()
+        st = hf.hf_batch_get_stats(bd.b)
+        seen[ring] = st
+        for i in range(len(wl.graphs)):
+            np.testing.assert_array_equal(bits(bd.arrivals(i)), bits(ref[i]), err_msg="ring %d graph %d" % (ring, i))
+        n = sum(g.n for g in wl.graphs)
+        assert st["items"] == n
+    assert seen[0]["push_ring"] == 0 and seen[0]["steals"] == 0
+    for ring in (64, 4096):
+        assert seen[ring]["push_ring"] > 0 and seen[ring]["steals"] > 0, seen[ring]
+    # a 64-slot ring overflows into the global queue more than a 4096-slot one
+    assert seen[64]["push_global"] >= seen[4096]["push_global"]
+    bd.close()
