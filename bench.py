@@ -407,7 +407,7 @@ def main():
     if not args.no_e2e:
         delays = torch.cat([torch.from_numpy(g.delay) for g in wl.graphs]).pin_memory()
         arr_host = torch.empty(N, dtype=torch.float32, pin_memory=True)
-        steps = max(3, args.steps // 4)
+        steps = args.steps  # the same K steps as the device-timed loop
         # the public call a user makes per timing view: delays in from page-locked host memory,
         # run, every arrival out to page-locked host memory (non-blocking; the device orders
         # consecutive steps; synchronised once at the end of the timed region)

@@ -66,9 +66,11 @@ struct Plan {
         int32_t grid;   // CTAs launched
     };
     std::vector<TeamClass> tclass;    // one launch per class, run concurrently
-    cudaStream_t tstream[4] = {nullptr, nullptr, nullptr, nullptr};
+    // one stream per class at the device's highest stream priority: pending team CTAs are
+    // dispatched before those of the plan's helper kernels (the next view's delay gather)
+    cudaStream_t tstream[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     cudaEvent_t tev_fork = nullptr;
-    cudaEvent_t tev_join[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t tev_join[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     int32_t* d_team = nullptr;        // control words (job counters), kTeamWords per class
     int32_t stage_n = 4, stage_e = 2;  // stage buffer capacities (tasks, in-edges per level)
     int32_t stage_p = 0;               // ... piece descriptors per level (per piece size)
@@ -167,11 +169,18 @@ struct Plan {
     // host-buffer runs (hf_run_host): the arrivals go to the host from d_arr on a stream of the
     // plan's own, overlapping the caller's next work; d_arr is reused only after that copy.
     // New delays come in by copy engine on another plan stream into d_hstage (waiting only until
-    // the previous view's gather has read it), then a gather puts them in ls_in.
-    cudaStream_t cstream = nullptr, istream = nullptr;
+    // the previous view's gather has read it), then a gather puts them in ls_in. The level-sync
+    // and team executors alternate two staging buffers with the copies on a stream of their own
+    // (hstream), so that the next view's copy starts as soon as the copy engine is free.
+    cudaStream_t cstream = nullptr, istream = nullptr, hstream = nullptr;
     cudaEvent_t ev_conv = nullptr, ev_d2h = nullptr, ev_h2d = nullptr, ev_gather = nullptr;
     bool d2h_pending = false, gather_pending = false;
     float* d_hstage = nullptr;      // host-buffer delays on the device (m)
+    float* d_hstage2 = nullptr;     // the second staging buffer (level-sync and team)
+    cudaEvent_t ev_hcopy[2] = {nullptr, nullptr};  // staging buffer j: its copy landed
+    cudaEvent_t ev_hread[2] = {nullptr, nullptr};  // staging buffer j: last read by a gather/scatter
+    bool hread_pending[2] = {false, false};
+    int hsb = 0;                    // staging buffer the next level-sync/team upload fills
     int32_t* d_ls_edge = nullptr;   // in-edge position -> edge in insertion order (m)
     bool erec_stale = false;        // erec's delays older than ls_in's (refreshed before a persistent run)
     float4* d_gstat = nullptr;
@@ -255,6 +264,7 @@ void plan_destroy(Plan* p) {
     if (p->h_post) cudaFreeHost(p->h_post);
     if (p->h_hdone) cudaFreeHost(p->h_hdone);
     if (p->istream) cudaStreamSynchronize(p->istream);
+    if (p->hstream) cudaStreamSynchronize(p->hstream);
     if (p->lexec) cudaGraphExecDestroy(p->lexec);
     if (p->lgraph) cudaGraphDestroy(p->lgraph);
     if (p->lexec_alt) cudaGraphExecDestroy(p->lexec_alt);
@@ -266,13 +276,18 @@ void plan_destroy(Plan* p) {
     if (p->done_ev) cudaEventDestroy(p->done_ev);
     if (p->kev0) cudaEventDestroy(p->kev0);
     if (p->kev1) cudaEventDestroy(p->kev1);
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < 5; ++i) {
         if (p->tstream[i]) cudaStreamDestroy(p->tstream[i]);
         if (p->tev_join[i]) cudaEventDestroy(p->tev_join[i]);
     }
     if (p->tev_fork) cudaEventDestroy(p->tev_fork);
     if (p->cstream) cudaStreamDestroy(p->cstream);
     if (p->istream) cudaStreamDestroy(p->istream);
+    if (p->hstream) cudaStreamDestroy(p->hstream);
+    for (int i = 0; i < 2; ++i) {
+        if (p->ev_hcopy[i]) cudaEventDestroy(p->ev_hcopy[i]);
+        if (p->ev_hread[i]) cudaEventDestroy(p->ev_hread[i]);
+    }
     if (p->ev_conv) cudaEventDestroy(p->ev_conv);
     if (p->ev_d2h) cudaEventDestroy(p->ev_d2h);
     if (p->ev_h2d) cudaEventDestroy(p->ev_h2d);
@@ -858,38 +873,52 @@ __global__ void k_invert_pos(const int32_t* __restrict__ pos_ls, int32_t* __rest
 }
 
 // New delays for the level-synchronous or team run about to be enqueued on s: copied by the
-// copy engine and gathered, both on the plan's input stream, into the in-edge buffer the run
-// before it did not use (waiting only for the last run that read that buffer), so that both
-// overlap that run; s waits for the gather, then the buffers (and level graphs) swap.
+// copy engine into one of two staging buffers on the plan's copy stream (waiting only for the
+// gather that last read that staging buffer), then gathered on the plan's input stream into the
+// in-edge buffer the run before it did not use (waiting only for the last run that read that
+// buffer), so that copy and gather overlap the runs before; s waits for the gather, then the
+// buffers (and level graphs) swap.
 static hf_status delays_double_buffered(Plan* p, cudaStream_t s, const float* host) {
     cudaError_t e = cudaSuccess;
     const int grid = (int)std::min<int64_t>((p->m + 255) / 256, (int64_t)p->num_sms * 16);
     if (!p->d_ls_in_alt) {
         p->d_hstage = p->d_hstage ? p->d_hstage : (float*)palloc(p, 4 * (size_t)p->m, s);
+        p->d_hstage2 = (float*)palloc(p, 4 * (size_t)p->m, s);
         p->d_ls_edge = p->d_ls_edge ? p->d_ls_edge : (int32_t*)palloc(p, 4 * (size_t)p->m, s);
         p->d_ls_in_alt = (int2*)palloc(p, 8 * (size_t)p->m + 64, s);
         p->d_bad2 = (int32_t*)palloc(p, 16, s);
-        if (!p->d_hstage || !p->d_ls_edge || !p->d_ls_in_alt || !p->d_bad2)
+        if (!p->d_hstage || !p->d_hstage2 || !p->d_ls_edge || !p->d_ls_in_alt || !p->d_bad2)
             return fail(HF_ENOMEM, "device allocation failed: delay buffers");
         k_invert_pos<<<grid, 256, 0, s>>>(p->d_epos_ls, p->d_ls_edge, p->m);
         // the second buffer starts as a copy (predecessor ids and delays)
         if ((e = cudaMemcpyAsync(p->d_ls_in_alt, p->d_ls_in, 8 * (size_t)p->m, cudaMemcpyDeviceToDevice, s)) != cudaSuccess ||
             (e = cudaEventRecord(p->ev_gather, s)) != cudaSuccess ||  // nothing on istream overtakes this
-            (e = cudaStreamWaitEvent(p->istream, p->ev_gather, 0)) != cudaSuccess)
+            (e = cudaStreamWaitEvent(p->istream, p->ev_gather, 0)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(p->hstream, p->ev_gather, 0)) != cudaSuccess)  // nor on hstream
             return cuda_fail(e, "delay buffers");
     }
     if (p->ran && p->last_stream != s && (e = cudaStreamWaitEvent(s, p->done_ev, 0)) != cudaSuccess)
         return cuda_fail(e, "delay upload");
     const int nb = 1 - p->lsb;        // the buffer the coming run reads
     int2* other = p->d_ls_in_alt;     // (d_ls_in_alt always names the buffer that is not d_ls_in)
-    // the staging buffer is free once the last gather or scatter has read it
-    if ((p->gather_pending && (e = cudaStreamWaitEvent(p->istream, p->ev_gather, 0)) != cudaSuccess) ||
-        (e = cudaMemcpyAsync(p->d_hstage, host, 4 * (size_t)p->m, cudaMemcpyHostToDevice, p->istream)) != cudaSuccess ||
+    // staging buffer j is free once the last gather or scatter that read it is done; the copy
+    // runs on hstream, the gather on istream once the copy has landed and once the run that
+    // last read in-edge buffer nb is done
+    const int j = p->hsb;
+    float* stage = j ? p->d_hstage2 : p->d_hstage;
+    if ((p->hread_pending[j] && (e = cudaStreamWaitEvent(p->hstream, p->ev_hread[j], 0)) != cudaSuccess) ||
+        (e = cudaMemcpyAsync(stage, host, 4 * (size_t)p->m, cudaMemcpyHostToDevice, p->hstream)) != cudaSuccess ||
+        (e = cudaEventRecord(p->ev_hcopy[j], p->hstream)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(p->istream, p->ev_hcopy[j], 0)) != cudaSuccess ||
         (p->buf_used[nb] && (e = cudaStreamWaitEvent(p->istream, p->ev_buf[nb], 0)) != cudaSuccess) ||
         (e = cudaMemsetAsync(p->d_bad2 + nb, 0, sizeof(int32_t), p->istream)) != cudaSuccess)
         return cuda_fail(e, "delay upload");
-    k_gather_delays<<<grid, 256, 0, p->istream>>>(p->d_hstage, p->d_ls_edge, other, p->m, p->d_bad2 + nb);
-    if ((e = cudaGetLastError()) != cudaSuccess || (e = cudaEventRecord(p->ev_gather, p->istream)) != cudaSuccess ||
+    k_gather_delays<<<grid, 256, 0, p->istream>>>(stage, p->d_ls_edge, other, p->m, p->d_bad2 + nb);
+    if ((e = cudaGetLastError()) != cudaSuccess || (e = cudaEventRecord(p->ev_hread[j], p->istream)) != cudaSuccess)
+        return cuda_fail(e, "delay gather");
+    p->hread_pending[j] = true;
+    p->hsb = j ^ 1;
+    if ((e = cudaEventRecord(p->ev_gather, p->istream)) != cudaSuccess ||
         (e = cudaStreamWaitEvent(s, p->ev_gather, 0)) != cudaSuccess ||
         (e = cudaMemcpyAsync(&p->d_ctrl->bad_input, p->d_bad2 + nb, sizeof(int32_t), cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
         return cuda_fail(e, "delay gather");
@@ -903,17 +932,21 @@ static hf_status delays_double_buffered(Plan* p, cudaStream_t s, const float* ho
     return HF_OK;
 }
 
-// New delays for the run about to be enqueued on s, from page-locked host memory: copied by
-// the copy engine on the plan's input stream, which waits only until the previous view's
-// gather has read the staging buffer (so the copy overlaps the previous run), then gathered on s
-// into the level-sorted in-edges (the persistent executor: scattered into both layouts).
+// New delays for the run about to be enqueued on s, from page-locked host memory. Level-sync
+// and team runs: delays_double_buffered. Persistent runs: copied by the copy engine on the
+// plan's input stream, which waits only until the previous view's gather or scatter has read
+// the staging buffer (so the copy overlaps the previous run), then scattered on s into both
+// edge layouts.
 static hf_status delays_from_host(Plan* p, cudaStream_t s, const float* host, int mode) {
     cudaError_t e = cudaSuccess;
     if (!p->istream) {
         e = cudaStreamCreateWithFlags(&p->istream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->hstream, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_h2d, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_gather, cudaEventDisableTiming);
         for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&p->ev_buf[i], cudaEventDisableTiming);
+        for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&p->ev_hcopy[i], cudaEventDisableTiming);
+        for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&p->ev_hread[i], cudaEventDisableTiming);
         if (e != cudaSuccess) return cuda_fail(e, "delay upload stream");
     }
     if (mode != HF_MODE_PERSISTENT) return delays_double_buffered(p, s, host);
@@ -934,16 +967,14 @@ static hf_status delays_from_host(Plan* p, cudaStream_t s, const float* host, in
         (e = cudaEventRecord(p->ev_h2d, p->istream)) != cudaSuccess || (e = cudaStreamWaitEvent(s, p->ev_h2d, 0)) != cudaSuccess ||
         (e = cudaMemsetAsync(&p->d_ctrl->bad_input, 0, sizeof(int32_t), s)) != cudaSuccess)
         return cuda_fail(e, "delay upload");
-    if (mode == HF_MODE_PERSISTENT) {
-        k_set_delays<<<grid, 256, 0, s>>>(p->d_hstage, p->d_epos_csr, p->d_epos_ls, p->d_erec, p->d_ls_in, p->m,
-                                          &p->d_ctrl->bad_input);
-        p->erec_stale = false;
-    } else {
-        k_gather_delays<<<grid, 256, 0, s>>>(p->d_hstage, p->d_ls_edge, p->d_ls_in, p->m, &p->d_ctrl->bad_input);
-        p->erec_stale = true;
-    }
-    if ((e = cudaEventRecord(p->ev_gather, s)) != cudaSuccess) return cuda_fail(e, "delay upload");
+    k_set_delays<<<grid, 256, 0, s>>>(p->d_hstage, p->d_epos_csr, p->d_epos_ls, p->d_erec, p->d_ls_in, p->m,
+                                      &p->d_ctrl->bad_input);
+    p->erec_stale = false;
+    if ((e = cudaEventRecord(p->ev_gather, s)) != cudaSuccess ||
+        (e = cudaEventRecord(p->ev_hread[0], s)) != cudaSuccess)  // d_hstage is staging buffer 0
+        return cuda_fail(e, "delay upload");
     p->gather_pending = true;
+    p->hread_pending[0] = true;
     return HF_OK;
 }
 
@@ -1060,15 +1091,13 @@ hf_status plan_run(Plan* p, cudaStream_t s, const hf_run_opts& o, bool keep_stat
             e = cudaMemsetAsync(p->d_team, 0, sizeof(int32_t) * (size_t)kTeamWords * p->tclass.size(), s);
             if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
             if (o.time_kernel) cudaEventRecord(p->kev0, s);
-            // one launch per team class, all at once: the first on the caller's stream, the
-            // others on the plan's streams forked from it and joined back
+            // one launch per team class, all at once, on the plan's class streams forked from
+            // the caller's stream and joined back into it
             const size_t nc = p->tclass.size();
-            if (nc > 1) {
-                if ((e = cudaEventRecord(p->tev_fork, s)) != cudaSuccess) return cuda_fail(e, "team fork");
-                for (size_t i = 1; i < nc; ++i)
-                    if ((e = cudaStreamWaitEvent(p->tstream[i - 1], p->tev_fork, 0)) != cudaSuccess)
-                        return cuda_fail(e, "team fork");
-            }
+            if ((e = cudaEventRecord(p->tev_fork, s)) != cudaSuccess) return cuda_fail(e, "team fork");
+            for (size_t i = 0; i < nc; ++i)
+                if ((e = cudaStreamWaitEvent(p->tstream[i], p->tev_fork, 0)) != cudaSuccess)
+                    return cuda_fail(e, "team fork");
             for (size_t i = 0; i < nc; ++i) {
                 const Plan::TeamClass& c = p->tclass[i];
                 TeamArgs ai = a;
@@ -1080,7 +1109,7 @@ hf_status plan_run(Plan* p, cudaStream_t s, const hf_run_opts& o, bool keep_stat
                 cfg.gridDim = dim3((unsigned)c.grid);
                 cfg.blockDim = dim3(kTeamThreads);
                 cfg.dynamicSmemBytes = team_smem(p);
-                cfg.stream = i == 0 ? s : p->tstream[i - 1];
+                cfg.stream = p->tstream[i];
                 cudaLaunchAttribute at[1];
                 at[0].id = cudaLaunchAttributeClusterDimension;
                 at[0].val.clusterDim.x = (unsigned)c.k;
@@ -1091,9 +1120,9 @@ hf_status plan_run(Plan* p, cudaStream_t s, const hf_run_opts& o, bool keep_stat
                 e = p->npay ? cudaLaunchKernelEx(&cfg, k_team<true>, ai) : cudaLaunchKernelEx(&cfg, k_team<false>, ai);
                 if (e != cudaSuccess) return cuda_fail(e, "k_team launch");
             }
-            for (size_t i = 1; i < nc; ++i) {
-                if ((e = cudaEventRecord(p->tev_join[i - 1], p->tstream[i - 1])) != cudaSuccess ||
-                    (e = cudaStreamWaitEvent(s, p->tev_join[i - 1], 0)) != cudaSuccess)
+            for (size_t i = 0; i < nc; ++i) {
+                if ((e = cudaEventRecord(p->tev_join[i], p->tstream[i])) != cudaSuccess ||
+                    (e = cudaStreamWaitEvent(s, p->tev_join[i], 0)) != cudaSuccess)
                     return cuda_fail(e, "team join");
             }
             if (o.time_kernel) cudaEventRecord(p->kev1, s);
@@ -1224,7 +1253,6 @@ hf_status plan_run(Plan* p, cudaStream_t s, const hf_run_opts& o, bool keep_stat
                 p->proxy = std::thread(team_host_proxy, p, limit);
             }
         }
-        if (io_arr && (st = arrivals_to_host(p, s, io_arr)) != HF_OK) return st;
         e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
     }
@@ -1235,7 +1263,11 @@ hf_status plan_run(Plan* p, cudaStream_t s, const hf_run_opts& o, bool keep_stat
     }
     e = cudaMemcpyAsync(p->h_status, &p->d_ctrl->status, 3 * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) return cuda_fail(e, "status copy");
-    e = cudaEventRecord(p->done_ev, s);
+    // arrivals to the host after the status copy: both are device-to-host copies, and the small
+    // one, which the caller's stream waits for, must not queue behind the large one on the copy
+    // engine (the synchronisation calls wait for the arrival copy separately)
+    if (io_arr && p->n > 0 && (st = arrivals_to_host(p, s, io_arr)) != HF_OK) return st;
+    e = cudaEventRecord(p->done_ev, s);  // after the conversion kernel, which reads the keys
     if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
     p->last_stream = s;
     p->ran = true;
@@ -2114,9 +2146,11 @@ static hf_status plan_team_jobs(Plan* p, const hf_run_opts& o, cudaStream_t s) {
         if (!p->d_team) return fail(HF_ENOMEM, "device allocation failed: team control");
     }
     if (!p->tev_fork) {
-        cudaError_t e = cudaEventCreateWithFlags(&p->tev_fork, cudaEventDisableTiming);
-        for (int i = 0; i < 4 && e == cudaSuccess; ++i) {
-            e = cudaStreamCreateWithFlags(&p->tstream[i], cudaStreamNonBlocking);
+        int least = 0, greatest = 0;
+        cudaError_t e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->tev_fork, cudaEventDisableTiming);
+        for (int i = 0; i < 5 && e == cudaSuccess; ++i) {
+            e = cudaStreamCreateWithPriority(&p->tstream[i], cudaStreamNonBlocking, greatest);
             if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->tev_join[i], cudaEventDisableTiming);
         }
         if (e != cudaSuccess) return cuda_fail(e, "team streams");
