@@ -551,6 +551,28 @@ def test_run_host_streams_timing_views(ex):
     bd.close()
 
 
+def test_run_host_pipelined_views_across_executors():
+    """Eight timing views enqueued back to back without synchronising (each with its own
+    page-locked delay and arrival buffers), the executor changing between views: the copies,
+    gathers and runs of consecutive views overlap, and every view's arrivals are the oracle's
+    on its own delays."""
+    wl = S.batch(8, graphs=12, nmin=500, nmax=40000)
+    bd = BatchOnDevice(wl)
+    N = wl.n_tasks
+    order = ["team", "team", "levelsync", "team", "persistent", "team", "levelsync", "persistent"]
+    views = [[S.uniform_f32(131 + v, i, g.m, 0.0, 3.0) for i, g in enumerate(wl.graphs)] for v in range(len(order))]
+    ins = [torch.from_numpy(np.concatenate(new)).pin_memory() for new in views]
+    outs = [torch.full((N,), float("nan"), dtype=torch.float32).pin_memory() for _ in views]
+    stream = torch.cuda.current_stream()
+    for v, ex in enumerate(order):
+        bd.run_host(ins[v], outs[v], stream, **EXECUTORS[ex])
+    bd.sync()
+    for v, new in enumerate(views):
+        ref = np.concatenate([oracle.kahn(g.n, g.src, g.dst, new[i])[0] for i, g in enumerate(wl.graphs)])
+        np.testing.assert_array_equal(bits(outs[v].numpy()), bits(ref), err_msg="view %d (%s)" % (v, order[v]))
+    bd.close()
+
+
 def test_run_host_payloads_and_bad_delay():
     """Payload results through hf_batch_run_host equal the oracle's; a non-finite delay is
     reported by the next synchronisation, as with hf_batch_set_delays."""
