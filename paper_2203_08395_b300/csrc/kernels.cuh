@@ -516,7 +516,8 @@ __device__ __forceinline__ void ring_push(const PersistArgs& a, int* rt, int cnt
 // Takes up to `most` (<= 32) published items from the front of CTA c's ring into lanes
 // 0..k-1 (`item`) and returns k: the published run at the front (half of it when stealing),
 // 0 when the front is not published or another warp took it first. h: the take position the
-// front is read at (the CAS fails if it moved); own: it came from this CTA's shared hint.
+// front is read at (the CAS fails if it moved); rt: the owner's shared positions, whose take
+// hint follows the head (NULL when stealing).
 __device__ __forceinline__ int ring_take_at(const PersistArgs& a, int c, int h, int most, bool half, int* rt,
                                             int lane, int& item) {
     int32_t* hp = a.ring_head + (size_t)c * 32;
