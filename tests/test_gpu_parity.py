@@ -271,7 +271,9 @@ def test_paper_saxpy_graph_through_c_abi():
 @pytest.mark.parametrize("opts", [dict(mode=hf.HF_MODE_TEAM), dict(mode=hf.HF_MODE_TEAM, team_size=4),
                                   dict(mode=hf.HF_MODE_TEAM, priority=hf.HF_PRIO_HEURISTIC),
                                   dict(mode=hf.HF_MODE_PERSISTENT), dict(mode=hf.HF_MODE_PERSISTENT, ctas=4),
-                                  dict(mode=hf.HF_MODE_PERSISTENT, priority=hf.HF_PRIO_HEURISTIC, payload_warps=2)])
+                                  dict(mode=hf.HF_MODE_PERSISTENT, priority=hf.HF_PRIO_HEURISTIC, payload_warps=2),
+                                  dict(mode=hf.HF_MODE_PERSISTENT, steal_ring=256),
+                                  dict(mode=hf.HF_MODE_PERSISTENT, steal_ring=64, ctas=4)])
 def test_host_tasks_in_a_batch(opts):
     """Host tasks inside a batch run by the team or the persistent executor: each runs exactly
     once, after its predecessors and before its successors (callbacks record the order), and
@@ -313,7 +315,8 @@ def test_host_tasks_in_a_batch(opts):
         hf.hf_graph_destroy(g)
 
 
-def test_paper_saxpy_graph_persistent_without_host_tasks():
+@pytest.mark.parametrize("ring", [0, 128])
+def test_paper_saxpy_graph_persistent_without_host_tasks(ring):
     N = 65536
     x = torch.full((N,), 1, dtype=torch.int32, pin_memory=True)
     y = torch.full((N,), 2, dtype=torch.int32, pin_memory=True)
@@ -325,7 +328,7 @@ def test_paper_saxpy_graph_persistent_without_host_tasks():
     sy = hf.hf_add_task(g, hf.HF_PUSH, hf.hf_push_payload(src_pull=py, host_ptr=y.data_ptr(), bytes=4 * N))
     for a, b in [(px, k), (py, k), (k, sx), (k, sy)]:
         hf.hf_precede(g, a, b)
-    hf.hf_run(g, None, hf.hf_run_opts_default(mode=hf.HF_MODE_PERSISTENT, chunk_elems=4096, validate=1))
+    hf.hf_run(g, None, hf.hf_run_opts_default(mode=hf.HF_MODE_PERSISTENT, chunk_elems=4096, validate=1, steal_ring=ring))
     hf.hf_sync_status(g)
     assert bool((y == 4).all()) and bool((x == 1).all())
     s0, s1, c = hf.hf_get_stamps(g, 5)
@@ -335,7 +338,7 @@ def test_paper_saxpy_graph_persistent_without_host_tasks():
     hf.hf_graph_destroy(g)
 
 
-@pytest.mark.parametrize("ex", ["levelsync", "persistent", "team", "team_k2"])
+@pytest.mark.parametrize("ex", ["levelsync", "persistent", "steal_small", "team", "team_k2"])
 def test_saxpy_unaligned_and_ragged(ex):
     """Saxpy tasks on device pointers at every 4-byte offset of x and y (shared and different
     16-byte alignment) and every length 0..40 plus longer ragged ones, chained on the same y
@@ -387,7 +390,7 @@ def test_paper_dependency_graph_order():
 
 # ------------------------------------------------------------------ edge cases
 
-@pytest.mark.parametrize("ex", ["levelsync", "persistent", "team", "team_k5"])
+@pytest.mark.parametrize("ex", ["levelsync", "persistent", "steal_2cta", "team", "team_k5"])
 def test_edge_cases(ex):
     o = EXECUTORS[ex]
     # empty graph
