@@ -425,7 +425,7 @@ def test_edge_cases(ex):
         gd.close()
 
 
-@pytest.mark.parametrize("ex", ["levelsync", "persistent", "team", "auto"])
+@pytest.mark.parametrize("ex", ["levelsync", "persistent", "steal", "team", "auto"])
 def test_run_host_edge_cases(ex):
     """hf_run_host / hf_batch_run_host on degenerate inputs: an empty graph, a graph without
     edges (NULL and non-NULL delays), a single task, and a batch mixing them with a chain."""
@@ -487,7 +487,7 @@ def test_stalled_task_times_out_and_context_survives(ring):
     gd.close()
 
 
-@pytest.mark.parametrize("ex", ["levelsync", "persistent", "team_heur"])
+@pytest.mark.parametrize("ex", ["levelsync", "persistent", "steal_small", "team_heur"])
 def test_new_timing_view_through_set_delays(ex):
     """A second timing view of the same circuit: new delays in place, arrivals as the oracle
     computes them on the new delays; a non-finite delay is reported, then recovered from."""
@@ -517,7 +517,7 @@ def test_new_timing_view_through_set_delays(ex):
     bd.close()
 
 
-@pytest.mark.parametrize("ex", ["levelsync", "persistent", "team", "team_heur", "team_k2"])
+@pytest.mark.parametrize("ex", ["levelsync", "persistent", "steal", "team", "team_heur", "team_k2"])
 def test_run_host_streams_timing_views(ex):
     """hf_batch_run_host: delays in from page-locked memory and arrivals out to it, in one call,
     for several timing views in a row (each the oracle's arrivals on its delays); payloads run as
