@@ -14,7 +14,8 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-MODES = {"levelsync": hf.HF_MODE_LEVELSYNC, "persistent": hf.HF_MODE_PERSISTENT, "team": hf.HF_MODE_TEAM}
+MODES = {"levelsync": dict(mode=hf.HF_MODE_LEVELSYNC), "persistent": dict(mode=hf.HF_MODE_PERSISTENT),
+         "steal": dict(mode=hf.HF_MODE_PERSISTENT, steal_ring=128), "team": dict(mode=hf.HF_MODE_TEAM)}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -49,7 +50,7 @@ def _saxpy_chain(n_elems, a):
 def test_run_n_applies_payloads_n_times(mode):
     g, x, y = _saxpy_chain(5000, 0.5)
     x0, y0 = x.cpu().numpy(), y.cpu().numpy()
-    hf.hf_run_n(g, 3, opts=hf.hf_run_opts_default(mode=MODES[mode]))
+    hf.hf_run_n(g, 3, opts=hf.hf_run_opts_default(**MODES[mode]))
     hf.hf_sync_status(g)
     want = y0
     for _ in range(3):
@@ -83,13 +84,13 @@ def test_run_until_stops_on_the_predicate(mode):
         calls.append(1)
         return len(calls) == 4
 
-    runs = hf.hf_run_until(g, pred, 10, opts=hf.hf_run_opts_default(mode=MODES[mode]))
+    runs = hf.hf_run_until(g, pred, 10, opts=hf.hf_run_opts_default(**MODES[mode]))
     assert runs == 4 and len(calls) == 4
     want = y0
     for _ in range(4):
         want = oracle.saxpy_f32(2.0, x0, want)
     np.testing.assert_array_equal(bits(y.cpu().numpy()), bits(want))
-    assert hf.hf_run_until(g, lambda: False, 2, opts=hf.hf_run_opts_default(mode=MODES[mode])) == 2
+    assert hf.hf_run_until(g, lambda: False, 2, opts=hf.hf_run_opts_default(**MODES[mode])) == 2
     hf.hf_graph_destroy(g)
 
 
