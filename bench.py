@@ -172,6 +172,76 @@ def train_workloads(name, seeds):
     return [S.config(name, seed=s) for s in seeds]
 
 
+def headline_plan(bd, wl, stream, workload, executor="auto", learned=True, tune=True, rank=0):
+    """The plan the benchmark times on batch `bd` (a workload.BatchOnDevice of workload `wl`):
+
+    * learned part: a cost model trained on timings recorded from two other seeds of the same
+      workload family (the benchmark's own batch stays held out), attached to the batch;
+    * executor: the cost model's choice (the library's HF_MODE_AUTO rule from
+      hf_batch_predict), or the one forced by `executor`;
+    * launch parameters: autotuned for the executor that runs.
+
+    Returns a dict: opts (hf_run_opts fields of a timed run), chosen (executor), prio, cm (the
+    model or None; the caller destroys it), learned (training report), predicted_ms, tuned_ms.
+    """
+    from paper_2203_08395_b300 import hf, learn
+    from paper_2203_08395_b300.workload import BatchOnDevice
+
+    info = None
+    prio = hf.HF_PRIO_HEURISTIC
+    cm = None
+    if learned:
+        cm = hf.hf_costmodel_create(0)
+        t_tr = time.time()
+        recs = []
+        for twl in train_workloads(workload, (101 + 10 * rank, 102 + 10 * rank)):
+            tb = BatchOnDevice(twl)
+            recs.append(learn.record(tb, stream))
+            tb.close()
+        loss = learn.train(cm, recs)
+        t_tr = time.time() - t_tr
+        err = learn.evaluate(bd, cm, learn.record(bd, stream), stream)
+        del recs
+        hf.hf_batch_set_costmodel(bd.b, cm)
+        prio = hf.HF_PRIO_LEARNED
+        info = {"train_mse_log": loss, "train_s": t_tr, "held_out_error": err}
+    forced = {"auto": hf.HF_MODE_AUTO, "persistent": hf.HF_MODE_PERSISTENT, "levelsync": hf.HF_MODE_LEVELSYNC,
+              "team": hf.HF_MODE_TEAM}
+    pred = {"levelsync": None, "persistent": None, "team": None}
+    if executor == "auto":
+        ls, pe, tm = hf.hf_batch_predict(bd.b, prio, stream)
+        pred = {"levelsync": ls, "persistent": pe, "team": tm}
+        chosen = hf.HF_MODE_PERSISTENT if pe <= ls else hf.HF_MODE_LEVELSYNC
+        if tm < min(ls, pe):
+            chosen = hf.HF_MODE_TEAM
+    else:
+        chosen = forced[executor]
+    base = hf.hf_run_opts_default(priority=prio, mode=chosen)
+    tuned_ms = None
+    best = base
+    if tune and chosen in (hf.HF_MODE_PERSISTENT, hf.HF_MODE_TEAM):
+        best, tuned_ms = hf.hf_batch_autotune(bd.b, stream, base)
+    opts = {k: v for k, v in hf.opts_dict(best).items() if k not in ("time_kernel", "instrument", "validate")}
+    opts.update(mode=forced[executor], priority=prio)
+    return {"opts": opts, "chosen": chosen, "prio": prio, "cm": cm, "learned": info, "predicted_ms": pred,
+            "tuned_ms": tuned_ms}
+
+
+def workload_config(name, wl):
+    """The JSON line's config: the workload alone, identical in both arms of the benchmark."""
+    return {"workload": name, "tasks": wl.n_tasks, "edges": wl.n_edges, "graphs": len(wl.graphs),
+            "saxpy_elems": wl.saxpy_elems,
+            "l2": "inputs larger than L2 (graph %.0f MB + payload %.0f MB)" % (
+                (16 * wl.n_edges + 24 * wl.n_tasks) / 1e6, 8 * wl.saxpy_elems / 1e6)}
+
+
+def plan_depth(bd):
+    """Levels of the batch's deepest graph (1 + its longest hop count), from the library."""
+    from paper_2203_08395_b300 import hf
+
+    return max(hf.hf_graph_info(gd.g)["levels"] for gd in bd.graphs)
+
+
 def cpu_oracle_rate(wl, budget_s=15.0):
     """The oracle (single thread) on whole graphs of the workload, in order, until about
     budget_s of oracle time. Returns (tasks/s, edges/s, description)."""
@@ -268,7 +338,7 @@ def run_reference(args, rank, world):
         "steps": len(times), "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "edges_per_s": m_s / (ms / 1e3),
-        "config": {"workload": args.workload, "l2": "n/a (CPU)"},
+        "config": workload_config(args.workload, wl),
         "cpu_baseline": {"value": value, "unit": "tasks/s", "cores": 1, "kind": "oracle", "sample": desc},
         "e2e": {"value": value, "unit": "tasks/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
@@ -309,45 +379,10 @@ def main():
         if world > 1:
             torch.distributed.barrier()
 
-    # ---- learned part: train on recorded timings of other seeds, evaluate on this batch
-    learned = None
-    prio = hf.HF_PRIO_HEURISTIC
-    cm = None
-    if not args.no_learned:
-        cm = hf.hf_costmodel_create(0)
-        t_tr = time.time()
-        recs = []
-        for twl in train_workloads(args.workload, (101 + 10 * rank, 102 + 10 * rank)):
-            tb = BatchOnDevice(twl)
-            recs.append(learn.record(tb, stream))
-            tb.close()
-        loss = learn.train(cm, recs)
-        t_tr = time.time() - t_tr
-        err = learn.evaluate(bd, cm, learn.record(bd, stream), stream)
-        del recs
-        hf.hf_batch_set_costmodel(bd.b, cm)
-        prio = hf.HF_PRIO_LEARNED
-        learned = {"train_mse_log": loss, "train_s": t_tr, "held_out_error": err}
-
-    # executor: the cost model's choice (the library's HF_MODE_AUTO rule), or forced
-    ls_pred = pe_pred = tm_pred = None
-    forced = {"auto": hf.HF_MODE_AUTO, "persistent": hf.HF_MODE_PERSISTENT, "levelsync": hf.HF_MODE_LEVELSYNC,
-              "team": hf.HF_MODE_TEAM}
-    if args.executor == "auto":
-        ls_pred, pe_pred, tm_pred = hf.hf_batch_predict(bd.b, prio, stream)
-        chosen = hf.HF_MODE_PERSISTENT if pe_pred <= ls_pred else hf.HF_MODE_LEVELSYNC
-        if tm_pred < min(ls_pred, pe_pred):
-            chosen = hf.HF_MODE_TEAM
-    else:
-        chosen = forced[args.executor]
-    # launch parameters: autotuned for the executor that runs
-    base = hf.hf_run_opts_default(priority=prio, mode=chosen)
-    tuned_ms = None
-    best = base
-    if not args.no_tune and chosen in (hf.HF_MODE_PERSISTENT, hf.HF_MODE_TEAM):
-        best, tuned_ms = hf.hf_batch_autotune(bd.b, stream, base)
-    head = {k: v for k, v in hf.opts_dict(best).items() if k not in ("time_kernel", "instrument", "validate")}
-    head.update(mode=forced[args.executor], priority=prio)
+    # ---- the headline plan: learned costs (trained on other seeds), executor choice, autotuning
+    hp = headline_plan(bd, wl, stream, args.workload, args.executor, not args.no_learned, not args.no_tune, rank)
+    head, chosen, prio, cm, learned = hp["opts"], hp["chosen"], hp["prio"], hp["cm"], hp["learned"]
+    tuned_ms = hp["tuned_ms"]
     bd.reset_y()
     t_setup = time.time() - t_setup
 
@@ -436,7 +471,8 @@ def main():
     # per launch of the dominant kernel: one k_persist per step, one k_level per merged level; the
     # team executor's launches of one step (one per team class) run concurrently and count as
     # one unit, timed together
-    k_launches = 1 if chosen in (hf.HF_MODE_PERSISTENT, hf.HF_MODE_TEAM) else max(g.levels for g in wl.graphs)
+    depth = plan_depth(bd)  # merged levels of the batch = its deepest graph's levels
+    k_launches = 1 if chosen in (hf.HF_MODE_PERSISTENT, hf.HF_MODE_TEAM) else depth
     achieved = (b_alg / k_launches) / (kernel_ms / k_launches / 1e3) / 1e9
     roof = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": traffic_for(kname, args.workload),
@@ -449,7 +485,6 @@ def main():
     # dependency-latency bound beside the bandwidth bound: the deepest graph's chain of levels at
     # the per-level (per-hop) times measured on the calibration chain
     t_lvl, t_hop, t_solo, t_cl = hf.hf_calibration(stream)
-    depth = max(g.levels for g in wl.graphs)
     roof["critical_path"] = {"levels": depth, "ns_per_level": {"levelsync": t_lvl, "persistent_hop": t_hop,
                                                                 "team_cta": t_solo, "team_cluster": t_cl},
                              "bound_ms": {"levelsync": depth * t_lvl / 1e6, "persistent": depth * t_hop / 1e6,
@@ -462,16 +497,13 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms, "ms_per_step_median": ms_med, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "edges_per_s": job_rate(E_all, ms),
-        "config": {"workload": args.workload, "tasks": N, "edges": E, "graphs": len(wl.graphs),
-                   "saxpy_elems": wl.saxpy_elems, "executor": args.executor,
-                   "chosen": {hf.HF_MODE_PERSISTENT: "persistent", hf.HF_MODE_TEAM: "team"}.get(chosen, "levelsync"),
-                   "priority": {0: "fifo", 1: "heuristic", 2: "learned"}[prio],
-                   "launch": {k: head[k] for k in ("ctas", "claim", "local_keep", "chunk_elems", "payload_warps", "steal_ring")},
-                   "autotuned_ms": tuned_ms,
-                   "predicted_ms": {"levelsync": ls_pred, "persistent": pe_pred, "team": tm_pred},
-                   "l2": "inputs larger than L2 (graph %.0f MB + payload %.0f MB)" % (
-                       (16 * E + 24 * N) / 1e6, 8 * wl.saxpy_elems / 1e6),
-                   "setup_s": t_setup},
+        "config": workload_config(args.workload, wl),
+        "plan": {"executor": args.executor,
+                 "chosen": {hf.HF_MODE_PERSISTENT: "persistent", hf.HF_MODE_TEAM: "team"}.get(chosen, "levelsync"),
+                 "priority": {0: "fifo", 1: "heuristic", 2: "learned"}[prio],
+                 "launch": {k: head[k] for k in ("ctas", "claim", "local_keep", "chunk_elems", "payload_warps",
+                                                 "steal_ring", "team_size", "team_scale")},
+                 "autotuned_ms": tuned_ms, "predicted_ms": hp["predicted_ms"], "setup_s": t_setup},
         "learned": learned, "compare": compare, "e2e": e2e, "roofline": roof, "cpu_baseline": cpu,
         "clocks": clk, "gpu_launches": launches * args.steps,
     }

@@ -443,14 +443,16 @@ hf_status hf_calibration(void* stream, float* out);
  *   row_ptr  int32[n_tasks + 1], CSR row starts: the successors of task v are
  *            succ[row_ptr[v] .. row_ptr[v+1]), row_ptr[0] = 0, row_ptr[n_tasks] = n_edges;
  *   succ     int32[n_edges] successor ids; delay float[n_edges] finite edge delays d(u, v);
- *   arr0     float[n_tasks] finite source arrivals (read for tasks without predecessors),
- *            or NULL for +0;
+ *   arr0     float[n_tasks] source arrivals, or NULL for +0: entry v is read only when task v
+ *            has no predecessor, and must then be finite (other entries may hold anything);
  *   arr      float[n_tasks] output arrivals;
  *   spin_limit_ns  give up with HF_ETIMEDOUT after this long without progress (0 = 2 s);
  *   stream   cudaStream_t the work is enqueued on; the call then waits for that stream.
  * Errors: HF_EINVAL for sizes, NULL pointers or (found on the device) a malformed CSR, an
- * out-of-range successor or a non-finite delay/arr0, with arr left unwritten; HF_ETIMEDOUT
- * when the edges form a cycle (arr partly written); HF_ECUDA for a CUDA failure.
+ * out-of-range successor, a non-finite delay or a non-finite arr0 of a source, with arr left
+ * unwritten; HF_ETIMEDOUT when the edges form a cycle (arr partly written); HF_ECUDA for a
+ * CUDA failure. The call returns only after `stream` has completed the work (it reads the
+ * result status back from the device).
  * The first call on each device looks up the array's device address and sizes the grid
  * (with that device current); make that first call before any stream capture. Every call
  * on a device uses the same array: it clears what it reads before use, but two calls whose

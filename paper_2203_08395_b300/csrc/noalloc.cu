@@ -125,7 +125,8 @@ __global__ void k_na_count(void* scratch, int n, int m, const int32_t* row_ptr, 
     }
 }
 
-// Sources (no predecessor) take their arrival and enter the ready queue.
+// Sources (no predecessor) take their arrival and enter the ready queue; arr0 of a task with
+// predecessors is never read.
 __global__ void k_na_seed(void* scratch, int n, const float* arr0) {
     const NaView s = na_view(scratch);
     if (s.ctrl[kBad]) return;
@@ -135,10 +136,11 @@ __global__ void k_na_seed(void* scratch, int n, const float* arr0) {
         const int64_t i = i0 + lane;
         bool seed = false;
         uint32_t k = 0;
-        if (i < n) {
+        if (i < n && (uint32_t)s.state[i] == 0u) {  // arr0 is read for sources only
             const float a = arr0 ? arr0[i] : 0.f;
-            if (!isfinite(a)) atomicOr(s.ctrl + kBad, 1);
-            else if ((uint32_t)s.state[i] == 0u) {
+            if (!isfinite(a)) {
+                atomicOr(s.ctrl + kBad, 1);
+            } else {
                 seed = true;
                 k = na_key(a);
             }

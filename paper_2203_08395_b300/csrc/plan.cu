@@ -1089,6 +1089,8 @@ hf_status plan_run(Plan* p, cudaStream_t s, const hf_run_opts& o, bool keep_stat
             }
             p->last_gtimes = instr;
             e = cudaMemsetAsync(p->d_team, 0, sizeof(int32_t) * (size_t)kTeamWords * p->tclass.size(), s);
+            // a failed team raises ctrl->abort so that no new job starts; every run starts clear
+            if (e == cudaSuccess) e = cudaMemsetAsync(&p->d_ctrl->abort, 0, sizeof(int32_t), s);
             if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
             if (o.time_kernel) cudaEventRecord(p->kev0, s);
             // one launch per team class, all at once, on the plan's class streams forked from

@@ -151,10 +151,14 @@ __device__ __forceinline__ void team_prefetch_seg(const TeamSrc& a, const int4 s
 // look-ahead for one level, by the lead thread of each CTA: stage it if it fits, else (CTA 0 of
 // the team) prefetch it into L2. Inline: the sources come from shared memory, so the address
 // arithmetic stays within the three-CTAs-per-SM register budget.
-__device__ __forceinline__ void team_ahead(const TeamSrc& a, int rank, const TeamStage& st, unsigned long long* bar,
+__device__ __forceinline__ bool team_ahead(const TeamSrc& a, int rank, const TeamStage& st, unsigned long long* bar,
                                            const int4 sg, const int2 si) {
-    if (team_fits(a, sg)) team_stage(a, st, bar, sg, si);
-    else if (rank == 0) team_prefetch_seg(a, sg);
+    if (team_fits(a, sg)) {
+        team_stage(a, st, bar, sg, si);
+        return true;
+    }
+    if (rank == 0) team_prefetch_seg(a, sg);
+    return false;
 }
 
 // The slice [x0 + n * r / k, x0 + n * (r + 1) / k) of a range of n that CTA r of a team of k takes.
@@ -231,25 +235,26 @@ __device__ __forceinline__ void team_run_piece(const TeamPiece& d, int lane) {
 
 // The host tasks of one level (thread 0 of the team's first CTA, after the level's device work):
 // post each to the mailbox in mapped host memory, where the host proxy thread runs it, and
-// wait until all of them have run (bounded: HF_ETIMEDOUT after spin_limit_ns). The system-scope
-// fence makes the graph's earlier device writes (push copies into host memory) visible to the
-// callbacks; the acquire of each done flag orders the callbacks' writes before later levels.
-__device__ __noinline__ void team_host_tasks(const TeamArgs& a, int seg) {
+// wait until all of them have run (bounded by spin_limit_ns). The system-scope fence makes the
+// graph's earlier device writes (push copies into host memory) visible to the callbacks; the
+// acquire of each done flag orders the callbacks' writes before later levels. Returns false
+// when a callback did not finish in time, or when the run is already aborting (nothing is
+// posted then): the caller ends the team's run.
+__device__ __noinline__ bool team_host_tasks(const TeamArgs& a, int seg) {
     const int2 hr = __ldg(a.seg_host + seg);
-    if (hr.y <= hr.x) return;
+    if (hr.y <= hr.x) return true;
+    if (ld_relaxed(&a.ctrl->abort)) return false;
     __threadfence_system();
     for (int h = hr.x; h < hr.y; ++h) st_release_sys(a.post + atomicAdd(a.post_ctr, 1), __ldg(a.host_order + h));
     for (int h = hr.x; h < hr.y; ++h) {
         const int k = __ldg(a.host_order + h);
         const uint64_t t0 = gtimer();
         while (ld_acquire_sys(a.hdone + k) == 0) {
-            if (gtimer() - t0 > a.spin_limit_ns) {
-                atomicCAS(&a.ctrl->status, 0, (int)HF_ETIMEDOUT);
-                return;
-            }
+            if (gtimer() - t0 > a.spin_limit_ns) return false;
             __nanosleep(200);
         }
     }
+    return true;
 }
 
 // ---------------------------------------------------------------- thread-block cluster helpers
@@ -279,6 +284,26 @@ __device__ __forceinline__ void st_cluster_job(TeamJob* local, unsigned rank, co
     asm volatile("st.shared::cluster.v4.s32 [%0], {%1, %2, %3, %4};" ::"r"(d), "r"(j.graph), "r"(j.pad_), "r"(j.seg0),
                  "r"(j.levels)
                  : "memory");
+}
+
+// Failure of a team (a staged copy or a host task ran out of its time limit): the run's status
+// becomes `status` (first failure wins), the run aborts (no new job starts), and the team's
+// failure flag -- in the shared memory of every CTA of the team -- is raised. Every CTA reads
+// its own flag after the level's barrier, so all threads of all CTAs of the team see the same
+// value there and leave the job together; no CTA is left waiting at a barrier.
+__device__ __noinline__ void team_fail(const TeamArgs& a, int* s_fail, int k, int status) {
+    atomicCAS(&a.ctrl->status, 0, status);
+    atomicExch(&a.ctrl->abort, 1);
+    if (k == 1) {
+        *(volatile int*)s_fail = 1;
+        return;
+    }
+    const unsigned s = (unsigned)__cvta_generic_to_shared(s_fail);
+    for (int r = 0; r < k; ++r) {
+        unsigned d;
+        asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(d) : "r"(s), "r"(r));
+        asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(d), "r"(1) : "memory");
+    }
 }
 
 // ---------------------------------------------------------------- one level
@@ -337,19 +362,35 @@ __device__ __forceinline__ uint32_t team_task_key(const TeamArgs& a, int v, cons
 
 // ---------------------------------------------------------------- one graph
 
+// Bounded wait (spin_limit_ns) for stage buffer b's next completion; false if it never came.
+__device__ __forceinline__ bool team_wait_stage(unsigned long long* bar, unsigned parity, uint64_t limit_ns) {
+    uint64_t t0 = 0;
+    while (!mbar_try_wait(bar, parity)) {
+        const uint64_t now = gtimer();
+        if (!t0) t0 = now;
+        else if (now - t0 > limit_ns) return false;
+    }
+    return true;
+}
+
 // Runs job `job` on a team of k CTAs (this one is `rank`; SOLO: k = 1): level by level, staged
 // levels (task list, in-edges, piece descriptors) from shared memory, the rest from global
 // memory (prefetched into L2), payload pieces spread over the team's warps, then the team
-// barrier (CTA barrier for a solo job, cluster barrier otherwise). Returns false if a staged
-// copy never landed (the kernel must end).
+// barrier (CTA barrier for a solo job, cluster barrier otherwise). Returns false when the team
+// failed (a staged copy or a host task ran out of time, see team_fail): every thread of every
+// CTA of the team returns false after the same level barrier, and the lead thread has first
+// waited (bounded) for the stage copies it still had in flight; the kernel then ends.
+// A thread whose wait for a staged level runs out reads that level from global memory instead
+// (the same data), so the level completes and the team reaches its barrier.
 template <bool PAY, bool SOLO>
 __device__ __forceinline__ bool team_run_graph(const TeamArgs& a, const TeamJob& job, int k, int rank,
                                                const TeamSrc& src, const TeamStage* sview, unsigned long long* mbar,
-                                               int4* ring, int2* iring, int* pcnt, unsigned& phase) {
+                                               int4* ring, int2* iring, int* pcnt, int* s_fail, unsigned& phase) {
     const int t = threadIdx.x;
     const int lane = t & 31;
     const int L = job.levels;
     const int2 z2 = make_int2(0, 0);
+    unsigned inflight = 0;  // lead thread: stage buffers with a copy issued and not yet seen complete
     // segment descriptors and item ranges ride a ring in shared memory, fetched by the lead
     // thread three levels ahead (asynchronous copies, completed before the level's barrier, so
     // that their latency stays off the level's path); level l uses stage buffer l % kTeamBufs,
@@ -360,8 +401,8 @@ __device__ __forceinline__ bool team_run_graph(const TeamArgs& a, const TeamJob&
             ring[q] = __ldg(a.seg + job.seg0 + q);
             iring[q] = PAY ? __ldg(a.seg_items + job.seg0 + q) : z2;
         }
-        if (L > 0) team_ahead(src, rank, sview[0], &mbar[0], ring[0], PAY ? iring[0] : z2);
-        if (L > 1) team_ahead(src, rank, sview[1], &mbar[1], ring[1], PAY ? iring[1] : z2);
+        if (L > 0 && team_ahead(src, rank, sview[0], &mbar[0], ring[0], PAY ? iring[0] : z2)) inflight |= 1u;
+        if (L > 1 && team_ahead(src, rank, sview[1], &mbar[1], ring[1], PAY ? iring[1] : z2)) inflight |= 2u;
     }
     __syncthreads();
     if (a.g_start && rank == 0 && t == 0) a.g_start[job.graph] = (int64_t)gtimer();
@@ -370,9 +411,9 @@ __device__ __forceinline__ bool team_run_graph(const TeamArgs& a, const TeamJob&
         const int4 s0 = ring[l & 3];
         const int2 i0 = PAY ? iring[l & 3] : z2;
         if (t == kTeamLead) {
-            if (l + 2 < L)
-                team_ahead(src, rank, sview[(l + 2) % kTeamBufs], &mbar[(l + 2) % kTeamBufs], ring[(l + 2) & 3],
-                           PAY ? iring[(l + 2) & 3] : z2);  // the item ring is filled only with payloads
+            if (l + 2 < L && team_ahead(src, rank, sview[(l + 2) % kTeamBufs], &mbar[(l + 2) % kTeamBufs],
+                                        ring[(l + 2) & 3], PAY ? iring[(l + 2) & 3] : z2))
+                inflight |= 1u << ((l + 2) % kTeamBufs);  // (the item ring is filled only with payloads)
             if (l + 3 < L) {
                 cp_async16(&ring[(l + 3) & 3], a.seg + job.seg0 + l + 3);
                 if (PAY) cp_async8(&iring[(l + 3) & 3], a.seg_items + job.seg0 + l + 3);
@@ -388,29 +429,22 @@ __device__ __forceinline__ bool team_run_graph(const TeamArgs& a, const TeamJob&
         const int2* in = a.ls_in;
         const TeamPiece* dsc = PAY ? a.pdesc : nullptr;
         int nb = 0, eb = 0, ib = 0;
-        const bool staged = team_fits(a, s0);
-        if (staged) {
-            uint64_t t0 = 0;
-            while (!mbar_try_wait(&mbar[b], (phase >> b) & 1u)) {
-                const uint64_t now = gtimer();
-                if (!t0) {
-                    t0 = now;
-                } else if (now - t0 > a.spin_limit_ns) {  // a bulk copy that never lands
-                    if (t == 0) atomicCAS(&a.ctrl->status, 0, (int)HF_ETIMEDOUT);
-                    cp_async_wait_all();
-                    return false;
+        if (team_fits(a, s0)) {
+            if (team_wait_stage(&mbar[b], (phase >> b) & 1u, a.spin_limit_ns)) {
+                phase ^= 1u << b;
+                if (t == kTeamLead) inflight &= ~(1u << b);
+                nb = s0.x & ~3;
+                eb = s0.z & ~1;
+                const TeamStage sv = sview[b];
+                node = sv.node;
+                ptr = sv.ptr;
+                in = sv.in;
+                if (PAY && team_desc_fits(a, i0)) {
+                    dsc = sv.pdesc;
+                    ib = i0.x;
                 }
-            }
-            phase ^= 1u << b;
-            nb = s0.x & ~3;
-            eb = s0.z & ~1;
-            const TeamStage sv = sview[b];
-            node = sv.node;
-            ptr = sv.ptr;
-            in = sv.in;
-            if (PAY && team_desc_fits(a, i0)) {
-                dsc = sv.pdesc;
-                ib = i0.x;
+            } else {  // a bulk copy that never landed: this level from memory, then the team ends
+                team_fail(a, s_fail, k, (int)HF_ETIMEDOUT);
             }
         }
         // this CTA's slice of the level's tasks: one per thread
@@ -445,10 +479,17 @@ __device__ __forceinline__ bool team_run_graph(const TeamArgs& a, const TeamJob&
                 team_run_piece(dsc[it - ib], lane);
             }
         }
-        if (a.seg_host && rank == 0 && t == 0) team_host_tasks(a, job.seg0 + l);
+        if (a.seg_host && rank == 0 && t == 0 && !team_host_tasks(a, job.seg0 + l))
+            team_fail(a, s_fail, k, (int)HF_ETIMEDOUT);
         if (t == kTeamLead) cp_async_wait_all();  // ring entry l + 3
         if (SOLO) __syncthreads();
         else cluster_sync();
+        if (*(volatile int*)s_fail) {  // the same value in every thread of the team (see team_fail)
+            if (t == kTeamLead)        // stage copies still in flight land before the CTA ends
+                for (int q = 0; q < kTeamBufs; ++q)
+                    if ((inflight >> q) & 1u) team_wait_stage(&mbar[q], (phase >> q) & 1u, a.spin_limit_ns);
+            return false;
+        }
     }
     if (a.g_end && rank == 0 && t == 0) a.g_end[job.graph] = (int64_t)gtimer();
     return true;
@@ -469,8 +510,10 @@ __global__ void __launch_bounds__(kTeamThreads, 3) k_team(const TeamArgs a) {
     __shared__ int4 s_ring[4];
     __shared__ int2 s_iring[4];
     __shared__ int s_pcnt[2];  // payload piece counters, alternating by level
+    __shared__ int s_fail;     // the team failed (team_fail); read after each level's barrier
     const int t = threadIdx.x;
     if (t == 0) {
+        s_fail = 0;
         s_src = TeamSrc{a.ls_node, a.ls_ptr, a.ls_in, a.pdesc, a.stage_n, a.stage_e, a.stage_p, 0};
         for (int b = 0; b < kTeamBufs; ++b) {
             mbar_init(&mbar[b], 1);
@@ -486,8 +529,8 @@ __global__ void __launch_bounds__(kTeamThreads, 3) k_team(const TeamArgs a) {
         const int rank = (int)cluster_rank();
         cluster_sync();  // every CTA of the cluster has started before any DSMEM store
         for (;;) {
-            if (rank == 0 && t == 0) {
-                const int j = atomicAdd(a.team + kTeamNextC, 1);
+            if (rank == 0 && t == 0) {  // no new job once the run is aborting
+                const int j = ld_relaxed(&a.ctrl->abort) ? a.ncjobs : atomicAdd(a.team + kTeamNextC, 1);
                 const TeamJob job = j < a.ncjobs ? a.jobs[j] : TeamJob{-1, 0, 0, 0};
                 for (int r = 0; r < k; ++r) st_cluster_job(&s_job, (unsigned)r, job);
             }
@@ -495,19 +538,22 @@ __global__ void __launch_bounds__(kTeamThreads, 3) k_team(const TeamArgs a) {
             const TeamJob job = s_job;
             cluster_sync();  // all have read s_job before CTA 0 may overwrite it
             if (job.graph < 0) break;
-            if (!team_run_graph<PAY, false>(a, job, k, rank, s_src, s_view, mbar, s_ring, s_iring, s_pcnt, phase)) return;
+            if (!team_run_graph<PAY, false>(a, job, k, rank, s_src, s_view, mbar, s_ring, s_iring, s_pcnt, &s_fail,
+                                            phase))
+                return;
         }
     }
     for (;;) {
         if (t == 0) {
-            const int j = a.ncjobs + atomicAdd(a.team + kTeamNext, 1);
+            const int j = ld_relaxed(&a.ctrl->abort) ? a.njobs : a.ncjobs + atomicAdd(a.team + kTeamNext, 1);
             s_job = j < a.njobs ? a.jobs[j] : TeamJob{-1, 0, 0, 0};
         }
         __syncthreads();
         const TeamJob job = s_job;
         __syncthreads();
         if (job.graph < 0) break;
-        if (!team_run_graph<PAY, true>(a, job, 1, 0, s_src, s_view, mbar, s_ring, s_iring, s_pcnt, phase)) return;
+        if (!team_run_graph<PAY, true>(a, job, 1, 0, s_src, s_view, mbar, s_ring, s_iring, s_pcnt, &s_fail, phase))
+            return;
     }
 }
 

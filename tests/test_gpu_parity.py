@@ -95,6 +95,49 @@ def test_random_graphs_100_seeds(ex):
         gd.close()
 
 
+def _permuted(spec, seed):
+    """The same graph under a random relabelling of its task ids and a random order of its
+    edges: predecessors no longer have lower ids (the generators draw them from lower ids),
+    and each task's successor list comes in another order. Saxpy tasks keep their buffers."""
+    rng = np.random.default_rng(seed)
+    perm = rng.permutation(spec.n).astype(np.int32)  # old id -> new id
+    eo = rng.permutation(spec.m)
+    kind = np.empty_like(spec.kind)
+    kind[perm] = spec.kind
+    arr0 = None
+    if spec.arr0 is not None:
+        arr0 = np.empty_like(spec.arr0)
+        arr0[perm] = spec.arr0
+    ps = S.GraphSpec(name=spec.name + "_perm", n=spec.n, src=perm[spec.src][eo], dst=perm[spec.dst][eo],
+                     delay=spec.delay[eo], kind=kind, sx_task=perm[spec.sx_task] if spec.sx_task.size else spec.sx_task,
+                     sx_n=spec.sx_n, sx_a=spec.sx_a, sx_pull=spec.sx_pull, arr0=arr0, data_seed=spec.data_seed)
+    return ps, perm
+
+
+@pytest.mark.parametrize("ex", ["levelsync", "persistent", "persistent_payw2", "steal_small", "team", "team_heur",
+                                "team_k5"])
+def test_permuted_ids(ex):
+    """Layered, circuit-like and random DAGs (and a layered graph with saxpy tasks) with their
+    task ids relabelled at random: arrivals and saxpy results are the oracle's."""
+    rng = np.random.default_rng(3)
+    specs = [S.layered(41, 20_000, 60, 1, 5), S.circuit(42, 40_000, 80), S.mixed(43, n=15_000, nmin=1, nmax=3000, n_copy=0,
+                                                                              window=64)]
+    n_, _, src, dst, dly = S.random_dag(44, 25_000, 1, 6, window=128)
+    dly = rng.normal(0, 3, dly.size).astype(np.float32)
+    specs.append(S.GraphSpec(name="signed", n=n_, src=src, dst=dst, delay=dly, kind=np.zeros(n_, np.uint8),
+                             arr0=rng.choice([0.0, -0.0, 2.5, -7.0], n_).astype(np.float32)))
+    for k, spec in enumerate(specs):
+        ps, perm = _permuted(spec, 100 + k)
+        ref = oracle.run_spec(ps)
+        # relabelling moves every arrival with its task and changes none
+        np.testing.assert_array_equal(bits(ref["arr"])[perm], bits(oracle.run_spec(spec, with_data=False)["arr"]))
+        gd = GraphOnDevice(ps)
+        np.testing.assert_array_equal(bits(_run(gd, chunk_elems=256, **EXECUTORS[ex])), bits(ref["arr"]),
+                                      err_msg=ps.name)
+        _check_payloads(gd, ref)
+        gd.close()
+
+
 @pytest.mark.parametrize("ex", ["persistent", "steal", "steal_2cta"])
 def test_validate_exactly_once_and_order(ex):
     spec = S.circuit(1, 200_000, 400)

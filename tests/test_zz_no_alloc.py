@@ -1,17 +1,19 @@
-"""The allocation-free entry point hf_run_csr_noalloc against hf_run.
+"""The allocation-free entry point hf_run_csr_noalloc against the CPU oracle and hf_run.
 
 Some callers cannot allocate device memory (code inside another framework's memory pool or
 under a fixed budget, plug-ins whose host forbids cudaMalloc, loops that cannot afford an
 allocation's synchronisation). For them the library exposes hf_run_csr_noalloc, whose scratch
 is a fixed device array inside the library. These tests call it through the C ABI several
 times in a row -- the array keeps each call's leftovers, so every call must clear what it
-reads -- and require the same arrival bits as the regular entry point (hf_run on a graph built
-with hf_add_tasks_bulk / hf_precede_bulk), the exact-match bar of every arrival test here.
-The file's name makes pytest collect it last; it passes alone in a fresh process as well.
+reads -- and require the arrival bits of the sequential Kahn oracle and of the regular entry
+point (hf_run on a graph built with hf_add_tasks_bulk / hf_precede_bulk), the exact-match bar
+of every arrival test here. The file's name makes pytest collect it last; it passes alone in a
+fresh process as well.
 """
 import numpy as np
 import pytest
 
+import oracle
 from paper_2203_08395_b300 import build as B
 from paper_2203_08395_b300 import hf
 from paper_2203_08395_b300 import synth as S
@@ -70,15 +72,16 @@ def test_rejects_sizes_beyond_the_static_limit():
 
 
 @pytest.mark.gpu
-def test_noalloc_matches_hf_run_on_calls_in_a_row():
+def test_noalloc_matches_oracle_and_hf_run_on_calls_in_a_row():
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no GPU")
     B.build()
     hf.load()
     graphs = {k: _graph(k, 31 + i) for i, k in enumerate(("layered", "random"))}
-    expect, dev = {}, {}
+    expect, dev, oracle_arr = {}, {}, {}
     for k, (n, src, dst, dly, arr0) in graphs.items():
+        oracle_arr[k] = oracle.kahn(n, src, dst, dly, arr0)[0]
         expect[k] = _hf_run_arrivals(n, src, dst, dly, arr0, hf.HF_MODE_PERSISTENT)
         np.testing.assert_array_equal(bits(_hf_run_arrivals(n, src, dst, dly, arr0, hf.HF_MODE_LEVELSYNC)),
                                       bits(expect[k]))
@@ -91,4 +94,37 @@ def test_noalloc_matches_hf_run_on_calls_in_a_row():
         n, m, row_ptr, succ, d, arr0 = dev[k]
         arr = torch.full((n,), float("nan"), device="cuda")
         hf.hf_run_csr_noalloc(n, m, row_ptr, succ, d, arr0, arr, stream=stream)
-        np.testing.assert_array_equal(bits(arr.cpu().numpy()), bits(expect[k]))
+        got = bits(arr.cpu().numpy())
+        np.testing.assert_array_equal(got, bits(expect[k]))
+        np.testing.assert_array_equal(got, bits(oracle_arr[k]))
+
+
+@pytest.mark.gpu
+def test_noalloc_reads_arr0_of_sources_only():
+    """arr0 entries of tasks with predecessors are never read: NaN there changes nothing, while
+    a NaN source arrival is rejected with HF_EINVAL."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    B.build()
+    hf.load()
+    n, src, dst, dly, arr0 = _graph("layered", 47)
+    ref = oracle.kahn(n, src, dst, dly, arr0)[0]
+    has_pred = np.zeros(n, bool)
+    has_pred[dst] = True
+    junk = arr0.copy()
+    junk[has_pred] = np.nan
+    row_ptr, succ, d = _csr(n, src, dst, dly)
+    dv = [torch.from_numpy(a).cuda() for a in (row_ptr, succ, d, junk)]
+    stream = torch.cuda.current_stream()
+    arr = torch.full((n,), float("nan"), device="cuda")
+    hf.hf_run_csr_noalloc(n, succ.size, *dv, arr, stream=stream)
+    np.testing.assert_array_equal(bits(arr.cpu().numpy()), bits(ref))
+    bad = junk.copy()
+    bad[np.flatnonzero(~has_pred)[0]] = np.nan
+    with pytest.raises(hf.HfError) as e:
+        hf.hf_run_csr_noalloc(n, succ.size, *dv[:3], torch.from_numpy(bad).cuda(), arr, stream=stream)
+    assert e.value.status == hf.HF_EINVAL
+    # and the next call is exact again
+    hf.hf_run_csr_noalloc(n, succ.size, *dv, arr, stream=stream)
+    np.testing.assert_array_equal(bits(arr.cpu().numpy()), bits(ref))
