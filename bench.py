@@ -59,6 +59,9 @@ def parse():
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--shard", default="none", choices=["none", "lpt"],
+                    help="with several ranks: none = every rank runs its own batch (weak scaling); lpt = one "
+                         "batch split over the ranks by hf_batch_partition (strong scaling)")
     return ap.parse_args()
 
 
@@ -366,11 +369,17 @@ def main():
     from paper_2203_08395_b300 import hf, learn
     from paper_2203_08395_b300 import synth as S
     from paper_2203_08395_b300.workload import BatchOnDevice
+    from paper_2203_08395_b300.workload import share as shard_share
 
     hf.install_torch_allocator()
     stream = torch.cuda.current_stream()
     t_setup = time.time()
-    wl = S.config(args.workload, seed=rank)  # weak scaling: every rank runs its own instance
+    full, shard_idx = None, None
+    if args.shard == "lpt" and world > 1:  # strong scaling: one batch, each rank its LPT share
+        full = S.config(args.workload, seed=0)
+        wl, shard_idx = shard_share(full, rank, world)
+    else:  # weak scaling: every rank runs its own instance
+        wl = S.config(args.workload, seed=rank)
     bd = BatchOnDevice(wl)
     N, E = wl.n_tasks, wl.n_edges
 
@@ -429,6 +438,8 @@ def main():
                 ("persistent_steal", dict(mode=hf.HF_MODE_PERSISTENT, priority=hf.HF_PRIO_FIFO, steal_ring=1024)),
                 ("team_fifo", dict(mode=hf.HF_MODE_TEAM, priority=hf.HF_PRIO_FIFO)),
                 ("team_heuristic", dict(mode=hf.HF_MODE_TEAM, priority=hf.HF_PRIO_HEURISTIC))]
+        if any(g.pl_task.size or g.ps_task.size for g in wl.graphs):
+            arms += [("persistent_copy_warps", dict(mode=hf.HF_MODE_PERSISTENT, priority=hf.HF_PRIO_FIFO, copy_warps=1))]
         if cm is not None:
             arms += [("persistent_learned", dict(mode=hf.HF_MODE_PERSISTENT, priority=hf.HF_PRIO_LEARNED)),
                      ("team_learned", dict(mode=hf.HF_MODE_TEAM, priority=hf.HF_PRIO_LEARNED))]
@@ -484,25 +495,41 @@ def main():
         roof["dram_gbs"] = roof["traffic"] / (kernel_ms / k_launches / 1e3) / 1e9
     # dependency-latency bound beside the bandwidth bound: the deepest graph's chain of levels at
     # the per-level (per-hop) times measured on the calibration chain
-    t_lvl, t_hop, t_solo, t_cl = hf.hf_calibration(stream)
+    t_lvl, t_hop, t_solo, t_cl, link_h2d, link_d2h = hf.hf_calibration(stream)
     roof["critical_path"] = {"levels": depth, "ns_per_level": {"levelsync": t_lvl, "persistent_hop": t_hop,
                                                                 "team_cta": t_solo, "team_cluster": t_cl},
                              "bound_ms": {"levelsync": depth * t_lvl / 1e6, "persistent": depth * t_hop / 1e6,
                                           "team": depth * t_solo / 1e6}}
-    copy_bytes = sum(4 * int(g.sx_n[j]) for g in wl.graphs for j in list(g.pl_saxpy) + list(g.ps_saxpy))
-    if copy_bytes:
-        roof["host_link"] = {"bytes_per_step": copy_bytes, "gbs": copy_bytes / (ms / 1e3) / 1e9}
+    # pull and push copies cross the host link, each direction at its own bandwidth (measured in
+    # this process: the best of three 64 MiB copies by the copy engine); when the busier
+    # direction's bytes take longer there than all bytes take in HBM, the link is the bound
+    h2d = sum(4 * int(g.sx_n[j]) for g in wl.graphs for j in g.pl_saxpy)
+    d2h = sum(4 * int(g.sx_n[j]) for g in wl.graphs for j in g.ps_saxpy)
+    if h2d or d2h:
+        link = {"h2d_bytes": h2d, "d2h_bytes": d2h, "h2d_peak_gbs": link_h2d, "d2h_peak_gbs": link_d2h,
+                "bound_ms": max(h2d / (link_h2d * 1e6), d2h / (link_d2h * 1e6)),
+                "hbm_bound_ms": b_alg / (peak * 1e6),
+                "peak_source": "measured in this run (copy engine, page-locked memory, best of three 64 MiB copies)"}
+        roof["host_link"] = link
+        if link["bound_ms"] > link["hbm_bound_ms"]:
+            busy, bpeak = (h2d, link_h2d) if h2d / link_h2d >= d2h / link_d2h else (d2h, link_d2h)
+            ach = busy / (kernel_ms / 1e3) / 1e9
+            roof["hbm"] = {k: roof[k] for k in ("achieved", "peak", "frac", "peak_source")}
+            roof.update(bound="host_link", achieved=ach, peak=bpeak, frac=ach / bpeak,
+                        peak_source=link["peak_source"],
+                        per="step; achieved = bytes of the busier host-link direction over the step's kernel time")
     line = {
         "metric": "DAG tasks/s", "value": value, "unit": "tasks/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "ms_per_step_median": ms_med, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": "strong" if full is not None else "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "edges_per_s": job_rate(E_all, ms),
-        "config": workload_config(args.workload, wl),
+        "config": dict(workload_config(args.workload, full if full is not None else wl),
+                       **({"shard": "lpt over %d ranks (hf_batch_partition)" % world} if full is not None else {})),
         "plan": {"executor": args.executor,
                  "chosen": {hf.HF_MODE_PERSISTENT: "persistent", hf.HF_MODE_TEAM: "team"}.get(chosen, "levelsync"),
                  "priority": {0: "fifo", 1: "heuristic", 2: "learned"}[prio],
                  "launch": {k: head[k] for k in ("ctas", "claim", "local_keep", "chunk_elems", "payload_warps",
-                                                 "steal_ring", "team_size", "team_scale")},
+                                                 "steal_ring", "copy_warps", "team_size", "team_scale")},
                  "autotuned_ms": tuned_ms, "predicted_ms": hp["predicted_ms"], "setup_s": t_setup},
         "learned": learned, "compare": compare, "e2e": e2e, "roofline": roof, "cpu_baseline": cpu,
         "clocks": clk, "gpu_launches": launches * args.steps,

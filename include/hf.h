@@ -157,6 +157,14 @@ typedef struct {
                                and payload pieces to and take from first; a warp with nothing in
                                its ring or the global queue (sources, ring overflow) steals half
                                of the published front of a random other CTA's ring */
+    int32_t copy_warps;     /* persistent: warps per CTA (0..2) that run only pull copies, and as
+                               many that run only push copies, each direction from a queue of its
+                               own, so that host-to-device and device-to-host copies share the
+                               host link's two directions instead of queueing behind each other
+                               and behind the other tasks; 0 = copies run like other payloads.
+                               (The level-synchronous executor always runs copies as copy-engine
+                               nodes of its CUDA graph, each ordered only by its own edges.) */
+    int32_t pad_;
 } hf_run_opts;
 
 void hf_run_opts_default(hf_run_opts* opts);
@@ -410,8 +418,9 @@ hf_status hf_batch_autotune(hf_batch* b, void* stream, const hf_run_opts* base, 
  * calibration chain (level-synchronous time per level, persistent time per hop, team time per
  * level for one CTA and for a cluster):
  *   level-sync  = levels * t_level (x 2.5 when the level data exceed half the L2) + sum over
- *                 levels of the largest payload-task cost in it
+ *                 levels of the largest saxpy- or host-task cost in it
  *   persistent  = critical path of costs + depth * t_hop + total cost / warps
+ *   (both at least the copies' bytes of the busier host-link direction over its bandwidth)
  *   team        = the team executor's planned makespan: per graph and cluster size k,
  *                 T(k) = sum over levels of t_lvl(k) * ceil(width / 256k) + payload cost / 8k
  *                 (t_lvl x 2.5 for levels too large to stage in shared memory),
@@ -420,10 +429,12 @@ hf_status hf_batch_autotune(hf_batch* b, void* stream, const hf_run_opts* base, 
  * attached, else HEURISTIC). */
 hf_status hf_batch_predict(hf_batch* b, int32_t priority, void* stream, float* levelsync_ms, float* persistent_ms,
                            float* team_ms);
-/* The machine constants behind the predictions (ns), measured on the calibration chain on first
- * use in this process (2,048 tasks, one per level, on the current device): level-synchronous time
- * per level, persistent time per dependent hop, team time per level on one CTA and on a
- * cluster. out[4]. Blocks the first time. */
+/* The machine constants behind the predictions, measured on first use in this process on the
+ * current device: on the calibration chain (2,048 tasks, one per level) the level-synchronous
+ * time per level, the persistent time per dependent hop, the team time per level on one CTA and
+ * on a cluster (ns); and the host link's bandwidth host to device and device to host (GB/s, the
+ * best of three 64 MiB copies between page-locked memory and the device). out[6]. Blocks the
+ * first time. */
 hf_status hf_calibration(void* stream, float* out);
 
 /* --- allocation-free entry point -------------------------------------------------------

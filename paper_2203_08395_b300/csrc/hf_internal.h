@@ -61,6 +61,14 @@ struct alignas(128) Ctrl {
     int32_t pad5[31];
     int32_t ptail;
     int32_t pad6[31];
+    int32_t lhead0;  // copy queues (runs with copy warps): pull copies ...
+    int32_t pad7[31];
+    int32_t ltail0;
+    int32_t pad8[31];
+    int32_t lhead1;  // ... and push copies
+    int32_t pad9[31];
+    int32_t ltail1;
+    int32_t pad10[31];
 };
 
 // Arguments of the persistent executor kernel (by value, < 4 KB).
@@ -100,6 +108,14 @@ struct PersistArgs {
     // position to take; positions count from 0 in every run
     unsigned long long* ring;
     int32_t* ring_head;
+    // copy warps (pdir NULL: none): per payload 0 (not a copy), 1 (pull: host to device) or 2
+    // (push: device to host); copies of direction d + 1 go to queue lqueue_d, served by the
+    // copy_warps warps of each CTA given to that direction
+    const uint8_t* pdir;
+    int32_t* lqueue0;
+    int32_t* lqueue1;
+    int32_t lqcap;
+    int32_t copy_warps;
 };
 
 // Executor counters recorded by runs with instrument & 2 (hf_get_stats).
@@ -157,6 +173,13 @@ struct ResetArgs {
     int64_t ring_cells;
     int32_t* ring_head;        // ring_heads counters cleared
     int32_t ring_heads;
+    // payload seeds are pseeds[0, n_pseed) (no copy), then pull copies [n_pseed, + n_cseed0),
+    // then push copies [.., + n_cseed1); with copy warps (link) the copies seed lqueue0/1
+    int32_t n_cseed0, n_cseed1;
+    int32_t link;
+    int32_t lqcap;
+    int32_t* lqueue0;
+    int32_t* lqueue1;
 };
 
 // Team executor: a job is one graph, run by one CTA (solo job) or by the CTAs of one thread-block

@@ -342,6 +342,40 @@ __device__ __forceinline__ void prefetch_l2(const void* p) {
     asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
+// L2 residency. The per-task state words (8 bytes per task, one compare-and-swap per edge at a
+// random task) must stay in L2 across the run, while the edge records stream past them once:
+// the reset kernel stores the state words with an evict-last policy, the executor reads them
+// with it, and reads edge records with an evict-first policy (and without L1 allocation).
+__device__ __forceinline__ uint64_t l2_policy_last() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+__device__ __forceinline__ uint64_t l2_policy_first() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+__device__ __forceinline__ int4 ld_stream_int4(const int4* p, uint64_t pol) {
+    int4 r;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.s32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+                 : "l"(p), "l"(pol));
+    return r;
+}
+
+__device__ __forceinline__ void st_keep_u64(unsigned long long* p, unsigned long long v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.b64 [%0], %1, %2;" ::"l"(p), "l"(v), "l"(pol) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long ld_relaxed_keep_u64(const unsigned long long* p, uint64_t pol) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.L2::cache_hint.b64 %0, [%1], %2;" : "=l"(v) : "l"(p), "l"(pol) : "memory");
+    return v;
+}
+
 __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
     unsigned long long v;
     asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
@@ -357,11 +391,12 @@ __device__ __forceinline__ int atom_dec_relaxed(int32_t* p) {
 __global__ void k_reset(const ResetArgs a) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t keep = l2_policy_last();
     for (int64_t i = tid; i < a.n_tasks; i += stride) {
         const int d = a.indeg0[i];
         const uint32_t k = d ? kKeyNegInf : (a.key0 ? a.key0[i] : kKeyPosZero);
         const uint32_t c = (uint32_t)d + (i == a.stall_task ? 1u : 0u);
-        a.state[i] = ((unsigned long long)k << 32) | c;
+        st_keep_u64(a.state + i, ((unsigned long long)k << 32) | c, keep);
         if (a.t_start) {
             a.t_start[i] = INT64_MAX;
             a.t_end[i] = 0;
@@ -372,9 +407,12 @@ __global__ void k_reset(const ResetArgs a) {
             a.tk_end[i] = -1;
         }
     }
-    // sources without payload seed the main queue; sources with one seed the payload queue in
-    // warp-specialised runs, else they follow in the main queue
-    const int64_t nmain = a.split ? a.n_seed : (int64_t)a.n_seed + a.n_pseed;
+    // sources without payload seed the main queue; sources with one (pseeds: non-copy payloads,
+    // then pull copies, then push copies) seed the payload queue in warp-specialised runs, else
+    // they follow in the main queue; with copy warps the copies seed their own queues instead
+    const int64_t nc = (int64_t)a.n_cseed0 + a.n_cseed1;
+    const int64_t npay_seed = a.link ? a.n_pseed : (int64_t)a.n_pseed + nc;
+    const int64_t nmain = a.split ? a.n_seed : (int64_t)a.n_seed + npay_seed;
     for (int64_t i = tid; i < a.qcap; i += stride) {
         int v = -1;
         if (i < a.n_seed) v = a.seeds[i];
@@ -384,9 +422,18 @@ __global__ void k_reset(const ResetArgs a) {
     }
     if (a.split)
         for (int64_t i = tid; i < a.pqcap; i += stride) {
-            int v = i < a.n_pseed ? a.pseeds[i] : -1;
+            int v = i < npay_seed ? a.pseeds[i] : -1;
             if (v >= 0 && v == a.stall_task) v = -2;
             a.pqueue[i] = v;
+        }
+    if (a.link)
+        for (int64_t i = tid; i < a.lqcap; i += stride) {
+            int v0 = i < a.n_cseed0 ? a.pseeds[a.n_pseed + i] : -1;
+            int v1 = i < a.n_cseed1 ? a.pseeds[a.n_pseed + a.n_cseed0 + i] : -1;
+            if (v0 >= 0 && v0 == a.stall_task) v0 = -2;
+            if (v1 >= 0 && v1 == a.stall_task) v1 = -2;
+            a.lqueue0[i] = v0;
+            a.lqueue1[i] = v1;
         }
     for (int64_t i = tid; i < a.n_pay; i += stride) a.chunks_left[i] = a.pay[i].nchunks;
     if (a.ring) {  // work stealing: empty rings, positions from 0
@@ -397,7 +444,11 @@ __global__ void k_reset(const ResetArgs a) {
         a.ctrl->head = 0;
         a.ctrl->tail = (int32_t)nmain;
         a.ctrl->phead = 0;
-        a.ctrl->ptail = a.split ? a.n_pseed : 0;
+        a.ctrl->ptail = a.split ? (int32_t)npay_seed : 0;
+        a.ctrl->lhead0 = 0;
+        a.ctrl->ltail0 = a.link ? a.n_cseed0 : 0;
+        a.ctrl->lhead1 = 0;
+        a.ctrl->ltail1 = a.link ? a.n_cseed1 : 0;
         a.ctrl->done = 0;
         if (!a.keep_status) a.ctrl->status = 0;
         a.ctrl->abort = 0;
@@ -568,8 +619,10 @@ __device__ __forceinline__ void push_ready(const PersistArgs& a, int4 r, int pr,
     const long long c_push = clk(ws);
     const int v = r.x;
     const bool haspay = PAY && v >= 0 && r.w < 0;
-    const bool topay = haspay && a.pay_warps > 0;
-    const bool single = v >= 0 && !topay;
+    // copies go to the copy queue of their direction when the run has copy warps (1: pull, 2: push)
+    const int cls = (haspay && a.pdir) ? (int)__ldg(a.pdir + r.z) : 0;
+    const bool topay = haspay && cls == 0 && a.pay_warps > 0;
+    const bool single = v >= 0 && !topay && cls == 0;
     const unsigned sm = __ballot_sync(kFull, single);
     const int room = a.local_keep - top;
     int rank;
@@ -597,9 +650,14 @@ __device__ __forceinline__ void push_ready(const PersistArgs& a, int4 r, int pr,
     top += min(__popc(sm), max(room, 0));
     ws.local += (uint32_t)min(__popc(sm), max(room, 0));
     const int item = haspay ? a.n_tasks + a.npieces + r.z : v;
-    if (a.ring) ring_push(a, rt, (go_global && !topay) ? 1 : 0, item, false, lane, ws);
-    else push_items(a, a.queue, a.qcap, &a.ctrl->tail, (go_global && !topay) ? 1 : 0, item, false, lane, ws);
+    const int to_main = (go_global && !topay && cls == 0) ? 1 : 0;
+    if (a.ring) ring_push(a, rt, to_main, item, false, lane, ws);
+    else push_items(a, a.queue, a.qcap, &a.ctrl->tail, to_main, item, false, lane, ws);
     if (PAY && a.pay_warps > 0) push_items(a, a.pqueue, a.pqcap, &a.ctrl->ptail, topay ? 1 : 0, item, false, lane, ws);
+    if (PAY && a.pdir) {
+        push_items(a, a.lqueue0, a.lqcap, &a.ctrl->ltail0, cls == 1 ? 1 : 0, item, false, lane, ws);
+        push_items(a, a.lqueue1, a.lqcap, &a.ctrl->ltail1, cls == 2 ? 1 : 0, item, false, lane, ws);
+    }
     if (ws.on) ws.cyc_push += (unsigned long long)(clk(ws) - c_push);
 }
 
@@ -675,7 +733,7 @@ __device__ __forceinline__ void release_all(const PersistArgs& a, int fin, uint3
         int4 rec = make_int4(-1, 0, 0, 0);
         if (e < total) {
             const int j = e - o_ex;  // the first kStage edges of a stacked task are staged
-            rec = (o_st && j < kStage) ? cedg[owner * kStage + j] : __ldg(a.erec + o_rs + j);
+            rec = (o_st && j < kStage) ? cedg[owner * kStage + j] : ld_stream_int4(a.erec + o_rs + j, l2_policy_first());
             // warm what the successor needs next while its CAS is in flight
             if ((uint32_t)rec.w & kPayBit) prefetch_l2(a.pay + rec.z);
             else prefetch_l2(a.erec + rec.z);
@@ -725,16 +783,28 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 2) k_persist(const PersistA
     const int n_tasks = a.n_tasks;
     const int start_base = n_tasks + a.npieces;  // payload-start items begin here
     // role: in warp-specialised runs the last pay_warps warps of each CTA take their work from
-    // the payload queue (payload starts and pieces), the others from the main queue
-    const bool payw = PAY && a.pay_warps > 0 && wid >= kWarpsPerCta - a.pay_warps;
-    int32_t* const qslots = payw ? a.pqueue : a.queue;
-    const int qcap = payw ? a.pqcap : a.qcap;
-    int32_t* const qhead = payw ? &a.ctrl->phead : &a.ctrl->head;
-    int32_t* const qtail = payw ? &a.ctrl->ptail : &a.ctrl->tail;
-    const int nwarps = (int)gridDim.x * (PAY && a.pay_warps > 0 ? (payw ? a.pay_warps : kWarpsPerCta - a.pay_warps)
-                                                                  : kWarpsPerCta);
-    // work stealing: main-queue warps take from rings (payload warps keep the payload queue)
-    const bool steal = a.ring != nullptr && !payw;
+    // the payload queue (payload starts and pieces); with copy warps, the copy_warps warps before
+    // them take pull copies and the copy_warps before those push copies, each from their own
+    // queue; the others take from the main queue
+    const int pw = PAY ? a.pay_warps : 0;
+    const int cw = (PAY && a.pdir) ? a.copy_warps : 0;
+    const int role = wid >= kWarpsPerCta - pw            ? 1
+                     : wid >= kWarpsPerCta - pw - cw     ? 2
+                     : wid >= kWarpsPerCta - pw - 2 * cw ? 3
+                                                         : 0;
+    int32_t* const qslots = role == 1 ? a.pqueue : role == 2 ? a.lqueue0 : role == 3 ? a.lqueue1 : a.queue;
+    const int qcap = role == 1 ? a.pqcap : role >= 2 ? a.lqcap : a.qcap;
+    int32_t* const qhead = role == 1   ? &a.ctrl->phead
+                           : role == 2 ? &a.ctrl->lhead0
+                           : role == 3 ? &a.ctrl->lhead1
+                                       : &a.ctrl->head;
+    int32_t* const qtail = role == 1   ? &a.ctrl->ptail
+                           : role == 2 ? &a.ctrl->ltail0
+                           : role == 3 ? &a.ctrl->ltail1
+                                       : &a.ctrl->tail;
+    const int nwarps = (int)gridDim.x * (role == 1 ? pw : role >= 2 ? cw : kWarpsPerCta - pw - 2 * cw);
+    // work stealing: main-queue warps take from rings (the other roles keep their queues)
+    const bool steal = a.ring != nullptr && role == 0;
     uint32_t rng = ((uint32_t)blockIdx.x * kWarpsPerCta + (uint32_t)wid) * 2654435761u + 0x9e3779b9u;  // victims
     uint32_t ndone = 0;  // completions not yet added to ctrl->done (warp-uniform)
     uint32_t iter = 0;
@@ -859,7 +929,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 2) k_persist(const PersistA
                     const int2 mt = __ldg(a.meta + t);
                     rs = mt.x;
                     deg = mt.y;
-                    kt = (uint32_t)(ld_relaxed_u64(a.state + t) >> 32);
+                    kt = (uint32_t)(ld_relaxed_keep_u64(a.state + t, l2_policy_last()) >> 32);
                     key_known = true;
                 }
             } else if (PAY) {
@@ -940,7 +1010,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 2) k_persist(const PersistA
                 if (fin2 >= 0) {
                     rs = a.pay[p].row;
                     deg = a.pay[p].deg;
-                    if (!key_known) kt = (uint32_t)(ld_relaxed_u64(a.state + t) >> 32);
+                    if (!key_known) kt = (uint32_t)(ld_relaxed_keep_u64(a.state + t, l2_policy_last()) >> 32);
                     if (a.exec_count) {
                         a.tk_end[fin2] = (int64_t)atomicAdd(&a.ctrl->ticket, 1ull);
                         atomicAdd(a.exec_count + fin2, 1);

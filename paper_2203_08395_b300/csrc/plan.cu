@@ -46,6 +46,20 @@ struct Plan {
     std::vector<int32_t> pay_task;  // payload -> task
     std::vector<int32_t> pay_level; // payload -> level
     std::vector<int32_t> hpidx;     // task -> payload or -1
+    std::vector<uint8_t> hpdir;     // payload -> 0, or 1 for a pull copy, 2 for a push copy
+    std::vector<int32_t> pay_succ_level;  // payload -> its task's successors' lowest level (-1: none)
+    int32_t ncopy[2] = {0, 0};      // pull copies, push copies
+    // the level-synchronous executor's copy nodes: one per pull / push task with bytes, run by
+    // the copy engines, after the level before the task's and before its first successor's level
+    struct CopyNode {
+        void* dst;
+        const void* src;
+        size_t bytes;
+        int32_t level;       // the task's level
+        int32_t succ_level;  // its successors' lowest level (-1: none)
+        bool pull;           // host to device (else device to host)
+    };
+    std::vector<CopyNode> copies;
     std::vector<int32_t> sources;   // task ids with no predecessor
     std::vector<int32_t> level_ptr; // merged level-sorted positions (levels + 1)
     // team executor
@@ -112,7 +126,11 @@ struct Plan {
     int32_t nseed = 0;
     int32_t* d_chunk_task = nullptr;  // sized for nitems
     int32_t* d_seeds = nullptr;
-    int32_t* d_pseeds = nullptr;  // items of sources with a payload
+    int32_t* d_pseeds = nullptr;  // items of sources with a payload: non-copies, pull copies, push copies
+    int32_t ncseed[2] = {0, 0};   // ... of which pull copies, push copies
+    uint8_t* d_pdir = nullptr;    // hpdir on the device (plans with copies)
+    int32_t* d_lqueue[2] = {nullptr, nullptr};  // copy queues (persistent runs with copy warps)
+    size_t cap_lqueue = 0;
     int32_t* d_pqueue = nullptr;  // payload queue (warp-specialised runs)
     int32_t npseed = 0, pqcap = 0;
     int32_t* d_queue = nullptr;
@@ -450,6 +468,7 @@ hf_status plan_build(const std::vector<hf_graph*>& graphs, Plan** out) {
                 const PayloadRec& r = g->payloads[(size_t)k];
                 DevPayload d;
                 std::memset(&d, 0, sizeof(d));
+                uint8_t dir = 0;  // 1: pull copy, 2: push copy
                 d.nchunks = 1;
                 d.chunk_first = -1;
                 d.task = toff + v;
@@ -472,6 +491,8 @@ hf_status plan_build(const std::vector<hf_graph*>& graphs, Plan** out) {
                     d.n = (int64_t)r.bytes;
                     d.dst = pull_buf[(size_t)i][(size_t)k];
                     d.src = r.bytes ? host_dev_ptr(r.host_src) : nullptr;
+                    dir = 1;
+                    if (r.bytes) p->copies.push_back(Plan::CopyNode{d.dst, r.host_src, r.bytes, g->fin.level[(size_t)v], -1, true});
                 } else {  // HF_PUSH
                     void* hd = r.bytes ? host_dev_ptr(r.host_dst) : nullptr;
                     if (r.bytes && !hd) return bail(fail(HF_EINVAL, "push host buffer is not page-locked"));
@@ -479,7 +500,22 @@ hf_status plan_build(const std::vector<hf_graph*>& graphs, Plan** out) {
                     d.n = (int64_t)r.bytes;
                     d.dst = hd;
                     d.src = r.src_pull >= 0 ? pull_buf[(size_t)i][(size_t)g->pay[(size_t)r.src_pull]] : r.src_dev;
+                    dir = 2;
+                    if (r.bytes) p->copies.push_back(Plan::CopyNode{r.host_dst, d.src, r.bytes, g->fin.level[(size_t)v], -1, false});
                 }
+                int32_t sl = -1;  // the task's successors' lowest level
+                {
+                    const Final& f = g->fin;
+                    for (int32_t e = f.row_ptr[(size_t)v]; e < f.row_ptr[(size_t)v + 1]; ++e) {
+                        const int32_t w = f.succ[(size_t)e].x;
+                        if (sl < 0 || f.level[(size_t)w] < sl) sl = f.level[(size_t)w];
+                    }
+                }
+                if (dir && r.bytes) p->copies.back().succ_level = sl;
+                p->pay_succ_level.push_back(sl);
+                p->ncopy[0] += dir == 1;
+                p->ncopy[1] += dir == 2;
+                p->hpdir.push_back((uint8_t)dir);
                 p->hpidx[(size_t)toff + v] = (int32_t)p->hpay.size();
                 p->hpay.push_back(d);
                 p->pay_task.push_back(toff + v);
@@ -521,6 +557,9 @@ hf_status plan_build(const std::vector<hf_graph*>& graphs, Plan** out) {
         if (p->any_key0 && (st = upload(p, &p->d_key0, key0.data(), key0.size(), s, "key0")) != HF_OK) return bail(st);
         if (p->npay && (st = upload(p, &p->d_pidx, p->hpidx.data(), p->hpidx.size(), s, "pidx")) != HF_OK)
             return bail(st);
+        if (p->ncopy[0] + p->ncopy[1] > 0 &&
+            (st = upload(p, &p->d_pdir, p->hpdir.data(), p->hpdir.size(), s, "pdir")) != HF_OK)
+            return bail(st);
         if ((st = upload(p, &p->d_ls_node, ls_node.data(), ls_node.size(), s, "ls_node", 64)) != HF_OK) return bail(st);
         if ((st = upload(p, &p->d_ls_ptr, ls_ptr.data(), ls_ptr.size(), s, "ls_ptr", 64)) != HF_OK) return bail(st);
         if ((st = upload(p, &p->d_ls_in, ls_in.data(), ls_in.size(), s, "ls_in", 64)) != HF_OK) return bail(st);
@@ -558,10 +597,10 @@ static hf_status plan_set_chunk(Plan* p, int64_t chunk_elems, cudaStream_t s) {
     int64_t items = 0;
     std::vector<int32_t> chunk_task;
     std::vector<int32_t> seeds, pseeds;
-    std::vector<int2> litems, seg_items;
+    std::vector<int2> litems, seg_items, litems_ls;
     std::vector<TeamPiece> pdesc;  // team executor: litems resolved
-    int32_t stage_p = 0;
-    std::vector<int32_t> item_ptr((size_t)p->levels + 1, 0);
+    int32_t stage_p = 0, ncseed0 = 0, ncseed1 = 0, npseed_nc = 0;
+    std::vector<int32_t> item_ptr((size_t)p->levels + 1, 0), item_ptr_ls;
     try {
         for (int32_t k = 0; k < p->npay; ++k) {
             DevPayload& d = p->hpay[(size_t)k];
@@ -589,10 +628,36 @@ static hf_status plan_set_chunk(Plan* p, int64_t chunk_elems, cudaStream_t s) {
                 for (int32_t c = 0; c < p->hpay[(size_t)k].nchunks; ++c) litems[(size_t)fill[(size_t)l]++] = make_int2(k, c);
             }
         }
-        for (int32_t t : p->sources) {  // payload sources enter the queues as payload starts
+        // payload sources enter the queues as payload starts: non-copies first, then pull copies,
+        // then push copies (each group in source order)
+        std::vector<int32_t> cseeds[2];
+        for (int32_t t : p->sources) {
             const int32_t k = p->hpidx.empty() ? -1 : p->hpidx[(size_t)t];
             if (k < 0) seeds.push_back(t);
+            else if (p->hpdir[(size_t)k]) cseeds[p->hpdir[(size_t)k] - 1].push_back(p->n + (int32_t)items + k);
             else pseeds.push_back(p->n + (int32_t)items + k);
+        }
+        // pull copies in the order their successors' levels come (none: last), so that the copy
+        // queue delivers first what the graph needs first and unblocks its pushes early
+        {
+            const int32_t base = p->n + (int32_t)items;
+            auto need = [&](int32_t it) {
+                const int32_t sl = p->pay_succ_level[(size_t)(it - base)];
+                return sl < 0 ? INT32_MAX : sl;
+            };
+            std::stable_sort(cseeds[0].begin(), cseeds[0].end(), [&](int32_t x, int32_t y) { return need(x) < need(y); });
+        }
+        ncseed0 = (int32_t)cseeds[0].size();
+        ncseed1 = (int32_t)cseeds[1].size();
+        npseed_nc = (int32_t)pseeds.size();
+        pseeds.insert(pseeds.end(), cseeds[0].begin(), cseeds[0].end());
+        pseeds.insert(pseeds.end(), cseeds[1].begin(), cseeds[1].end());
+        // the level-synchronous executor's items: the same without copies (its copy nodes)
+        item_ptr_ls.assign((size_t)p->levels + 1, 0);
+        for (int32_t l = 0; l < p->levels; ++l) {
+            for (int32_t q = item_ptr[(size_t)l]; q < item_ptr[(size_t)l + 1]; ++q)
+                if (!p->hpdir[(size_t)litems[(size_t)q].x]) litems_ls.push_back(litems[(size_t)q]);
+            item_ptr_ls[(size_t)l + 1] = (int32_t)litems_ls.size();
         }
         // team executor: each (graph, level) segment's run of items (payloads are numbered
         // graph by graph, so a level's items are grouped by graph in batch order)
@@ -635,9 +700,11 @@ static hf_status plan_set_chunk(Plan* p, int64_t chunk_elems, cudaStream_t s) {
     p->nitems = (int32_t)items;
     p->qcap = p->n + (int32_t)items + p->npay;  // tasks, pieces and payload starts
     p->nseed = (int32_t)seeds.size();
-    p->npseed = (int32_t)pseeds.size();
+    p->npseed = npseed_nc;
+    p->ncseed[0] = ncseed0;
+    p->ncseed[1] = ncseed1;
     p->pqcap = p->npay + (int32_t)items;
-    p->item_ptr = item_ptr;
+    p->item_ptr = item_ptr_ls;
     p->stage_p = stage_p;
     auto grow = [&](void** ptr, size_t& cap, size_t bytes) -> bool {
         bytes = std::max<size_t>(bytes, 16);
@@ -652,7 +719,7 @@ static hf_status plan_set_chunk(Plan* p, int64_t chunk_elems, cudaStream_t s) {
         !grow((void**)&p->d_pseeds, p->cap_pseeds, 4 * pseeds.size()) ||
         !grow((void**)&p->d_pqueue, p->cap_pqueue, 4 * (size_t)p->pqcap) ||
         !grow((void**)&p->d_queue, p->cap_queue, 4 * (size_t)p->qcap) ||
-        !grow((void**)&p->d_items, p->cap_items, 8 * litems.size()) ||
+        !grow((void**)&p->d_items, p->cap_items, 8 * litems_ls.size()) ||
         !grow((void**)&p->d_seg_items, p->cap_seg_items, 8 * seg_items.size()) ||
         !grow((void**)&p->d_pdesc, p->cap_pdesc, sizeof(TeamPiece) * pdesc.size()))
         return fail(HF_ENOMEM, "device allocation failed: queue");
@@ -660,7 +727,8 @@ static hf_status plan_set_chunk(Plan* p, int64_t chunk_elems, cudaStream_t s) {
     if (!chunk_task.empty()) e = cudaMemcpyAsync(p->d_chunk_task, chunk_task.data(), 4 * chunk_task.size(), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && !seeds.empty()) e = cudaMemcpyAsync(p->d_seeds, seeds.data(), 4 * seeds.size(), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && !pseeds.empty()) e = cudaMemcpyAsync(p->d_pseeds, pseeds.data(), 4 * pseeds.size(), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess && !litems.empty()) e = cudaMemcpyAsync(p->d_items, litems.data(), 8 * litems.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && !litems_ls.empty())
+        e = cudaMemcpyAsync(p->d_items, litems_ls.data(), 8 * litems_ls.size(), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && !seg_items.empty())
         e = cudaMemcpyAsync(p->d_seg_items, seg_items.data(), 8 * seg_items.size(), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && !pdesc.empty())
@@ -699,18 +767,59 @@ static hf_status ensure_instr(Plan* p, bool instrument, bool validate, cudaStrea
 }
 
 // Level-synchronous executor: one kernel node per level (arrivals + payload pieces of that
-// level) and one host node per host task, chained level after level in a CUDA graph.
+// level), one host node per host task and one copy node per pull or push task, in a CUDA graph.
+// Levels follow each other. A host task's node runs after the level before its own; a copy's
+// node (run by the copy engines, the paper's pull and push as asynchronous copies, Section
+// III-A) also starts after the level before its task's and must finish before the level of
+// its task's first successor, so copies overlap the levels in between and one another, pulls
+// and pushes using the two directions of the host link at once.
 static hf_status build_level_graph(Plan* p) {
     cudaError_t e = cudaGraphCreate(&p->lgraph, 0);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphCreate");
     p->largs.assign((size_t)p->levels, LevelArgs());
-    std::vector<cudaGraphNode_t> prev, cur;
+    std::vector<cudaGraphNode_t> prev, cur, extra;
     bool prev_kernel_only = false;  // the previous level is one kernel node (no host node)
     std::vector<std::vector<const HostTask*>> host_at((size_t)p->levels);
     for (const HostTask& h : p->host_tasks) host_at[(size_t)h.level].push_back(&h);
+    std::vector<std::vector<const Plan::CopyNode*>> copy_at((size_t)p->levels);
+    for (const Plan::CopyNode& c : p->copies) copy_at[(size_t)c.level].push_back(&c);
+    std::vector<std::vector<cudaGraphNode_t>> copies_before((size_t)p->levels);  // copy nodes a level waits for
+    // pulls (host to device) of a level run in kPullChains chains, each in the order their
+    // successors' levels come, so that the link delivers first what the levels need first (the
+    // copy engine keeps no order among independent nodes); pushes wait only for their levels
+    constexpr int kPullChains = 4;
+    cudaGraphNode_t chain_tail[kPullChains] = {};
+    int chain_next = 0;
     const bool pay = p->npay > 0;
     for (int32_t l = 0; l < p->levels; ++l) {
         cur.clear();
+        std::vector<const Plan::CopyNode*>& cl = copy_at[(size_t)l];
+        std::stable_sort(cl.begin(), cl.end(), [](const Plan::CopyNode* x, const Plan::CopyNode* y) {
+            const bool px = x->pull, py = y->pull;
+            if (px != py) return px;  // pulls first
+            const int32_t a = x->succ_level < 0 ? INT32_MAX : x->succ_level;
+            const int32_t b = y->succ_level < 0 ? INT32_MAX : y->succ_level;
+            return a < b;
+        });
+        // copy nodes of this level's copy tasks: after the previous level, before their
+        // successors' level
+        for (const Plan::CopyNode* c : cl) {
+            std::vector<cudaGraphNode_t> cdeps(prev);
+            cudaGraphNode_t* tail = c->pull ? &chain_tail[chain_next] : nullptr;
+            if (tail && *tail) cdeps.push_back(*tail);
+            cudaGraphNode_t node;
+            e = cudaGraphAddMemcpyNode1D(&node, p->lgraph, cdeps.data(), cdeps.size(), c->dst, c->src, c->bytes,
+                                         cudaMemcpyDefault);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaGraphAddMemcpyNode1D (copy task)");
+            if (tail) {
+                *tail = node;
+                chain_next = (chain_next + 1) % kPullChains;
+            }
+            if (c->succ_level > l) copies_before[(size_t)c->succ_level].push_back(node);
+        }
+        extra = copies_before[(size_t)l];
+        std::vector<cudaGraphNode_t> deps(prev);
+        deps.insert(deps.end(), extra.begin(), extra.end());
         LevelArgs& a = p->largs[(size_t)l];
         a.ls_node = p->d_ls_node;
         a.ls_ptr = p->d_ls_ptr;
@@ -728,8 +837,9 @@ static hf_status build_level_graph(Plan* p) {
         const int nb_pay = items ? std::min((items + 7) / 8, p->num_sms * 8) : 0;
         const int grid = a.nb_mp + nb_pay;
         if (grid > 0) {
-            // a level after a level of one kernel node depends on it programmatically: it launches
-            // while that kernel runs and waits inside (griddepcontrol.wait) for its results
+            // a level after a level of one kernel node (and nothing else to wait for) depends on it
+            // programmatically: it launches while that kernel runs and waits inside
+            // (griddepcontrol.wait) for its results
             cudaGraphNodeParams np = {};
             np.type = cudaGraphNodeTypeKernel;
             np.kernel.func = pay ? (void*)k_level<true> : (void*)k_level<false>;
@@ -740,9 +850,9 @@ static hf_status build_level_graph(Plan* p) {
             cudaGraphEdgeData ed = {};
             ed.from_port = cudaGraphKernelNodePortProgrammatic;
             ed.type = cudaGraphDependencyTypeProgrammatic;
-            const bool pdl = prev_kernel_only && prev.size() == 1;
+            const bool pdl = prev_kernel_only && prev.size() == 1 && extra.empty();
             cudaGraphNode_t node;
-            e = cudaGraphAddNode(&node, p->lgraph, prev.data(), pdl ? &ed : nullptr, prev.size(), &np);
+            e = cudaGraphAddNode(&node, p->lgraph, deps.data(), pdl ? &ed : nullptr, deps.size(), &np);
             if (e != cudaSuccess) return cuda_fail(e, "cudaGraphAddNode (level kernel)");
             cur.push_back(node);
         }
@@ -751,13 +861,16 @@ static hf_status build_level_graph(Plan* p) {
             hp.fn = h->fn;
             hp.userData = h->arg;
             cudaGraphNode_t node;
-            e = cudaGraphAddHostNode(&node, p->lgraph, prev.data(), prev.size(), &hp);
+            e = cudaGraphAddHostNode(&node, p->lgraph, deps.data(), deps.size(), &hp);
             if (e != cudaSuccess) return cuda_fail(e, "cudaGraphAddHostNode");
             cur.push_back(node);
         }
         if (!cur.empty()) {
             prev_kernel_only = grid > 0 && host_at[(size_t)l].empty();
             prev.swap(cur);
+        } else if (!extra.empty()) {  // a level without nodes still passes its copies on
+            prev.insert(prev.end(), extra.begin(), extra.end());
+            prev_kernel_only = false;
         }
     }
     e = cudaGraphInstantiate(&p->lexec, p->lgraph, 0);
@@ -1147,6 +1260,28 @@ hf_status plan_run(Plan* p, cudaStream_t s, const hf_run_opts& o, bool keep_stat
             r.pqueue = p->d_pqueue;
             const int pay_warps = p->npay ? std::min(std::max(o.payload_warps, 0), kWarpsPerCta - 1) : 0;
             r.split = pay_warps > 0 ? 1 : 0;
+            // copy warps: as many per direction, at least one warp left for the main queue
+            const bool has_copies = p->ncopy[0] + p->ncopy[1] > 0;
+            const int copy_warps =
+                has_copies ? std::min(std::max(o.copy_warps, 0), (kWarpsPerCta - 1 - pay_warps) / 2) : 0;
+            r.link = copy_warps > 0 ? 1 : 0;
+            r.n_cseed0 = p->ncseed[0];
+            r.n_cseed1 = p->ncseed[1];
+            r.lqcap = p->pqcap;
+            r.lqueue0 = r.lqueue1 = nullptr;
+            if (copy_warps > 0) {
+                const size_t need = 4 * (size_t)std::max(p->pqcap, 4);
+                if (p->cap_lqueue < need) {
+                    for (int d = 0; d < 2; ++d) {
+                        free_owned(p, p->d_lqueue[d]);
+                        p->d_lqueue[d] = (int32_t*)palloc(p, need, s);
+                    }
+                    p->cap_lqueue = (p->d_lqueue[0] && p->d_lqueue[1]) ? need : 0;
+                    if (!p->cap_lqueue) return fail(HF_ENOMEM, "device allocation failed: copy queues");
+                }
+                r.lqueue0 = p->d_lqueue[0];
+                r.lqueue1 = p->d_lqueue[1];
+            }
             r.pay = p->d_pay;
             r.state = p->d_state;
             r.queue = p->d_queue;
@@ -1227,6 +1362,11 @@ hf_status plan_run(Plan* p, cudaStream_t s, const hf_run_opts& o, bool keep_stat
             a.ring = r.ring;
             a.ring_head = r.ring_head;
             a.ring_mask = ring_slots > 0 ? ring_slots - 1 : 0;
+            a.pdir = copy_warps > 0 ? p->d_pdir : nullptr;
+            a.lqueue0 = r.lqueue0;
+            a.lqueue1 = r.lqueue1;
+            a.lqcap = r.lqcap;
+            a.copy_warps = copy_warps;
             a.stats = nullptr;
             if (o.instrument & 2) {
                 if (!p->d_stats) {
@@ -1732,6 +1872,7 @@ hf_status plan_autotune(Plan* p, cudaStream_t s, const hf_run_opts& base, int fo
             best->team_size = it->second.first.team_size;
             best->team_scale = it->second.first.team_scale;
             best->steal_ring = it->second.first.steal_ring;
+            best->copy_warps = it->second.first.copy_warps;
             *best_ms = it->second.second;
             return HF_OK;
         }
@@ -1761,11 +1902,15 @@ hf_status plan_autotune(Plan* p, cudaStream_t s, const hf_run_opts& base, int fo
     const std::vector<int64_t> chunk_v{1024, 4096, 16384};
     const std::vector<int> payw_v{0, 1, 2, 4};
     const std::vector<int> ring_v{0, 1024};  // global queue alone, or work stealing
+    const std::vector<int> copyw_v{0, 1, 2};
+    const bool has_copies = p->ncopy[0] + p->ncopy[1] > 0;
     for (int round = 0; round < 2; ++round) {
-        for (int dim = 0; dim < 6; ++dim) {
+        for (int dim = 0; dim < 7; ++dim) {
             if ((dim == 3 || dim == 4) && p->npay == 0) continue;
+            if (dim == 6 && !has_copies) continue;
             const size_t nv = dim == 0 ? ctas_v.size() : dim == 1 ? claim_v.size() : dim == 2 ? keep_v.size()
-                              : dim == 3 ? chunk_v.size() : dim == 4 ? payw_v.size() : ring_v.size();
+                              : dim == 3 ? chunk_v.size() : dim == 4 ? payw_v.size() : dim == 5 ? ring_v.size()
+                              : copyw_v.size();
             for (size_t i = 0; i < nv; ++i) {
                 hf_run_opts t = cur;
                 if (dim == 0) t.ctas = ctas_v[i];
@@ -1773,10 +1918,11 @@ hf_status plan_autotune(Plan* p, cudaStream_t s, const hf_run_opts& base, int fo
                 else if (dim == 2) t.local_keep = keep_v[i];
                 else if (dim == 3) t.chunk_elems = chunk_v[i];
                 else if (dim == 4) t.payload_warps = payw_v[i];
-                else t.steal_ring = ring_v[i];
+                else if (dim == 5) t.steal_ring = ring_v[i];
+                else t.copy_warps = copyw_v[i];
                 if (t.ctas == cur.ctas && t.claim == cur.claim && t.local_keep == cur.local_keep &&
                     t.chunk_elems == cur.chunk_elems && t.payload_warps == cur.payload_warps &&
-                    t.steal_ring == cur.steal_ring)
+                    t.steal_ring == cur.steal_ring && t.copy_warps == cur.copy_warps)
                     continue;
                 float ms = 0.f;
                 if ((st = time_runs(p, s, t, 3, &ms)) != HF_OK) return st;
@@ -1802,6 +1948,40 @@ hf_status plan_autotune(Plan* p, cudaStream_t s, const hf_run_opts& base, int fo
 static std::mutex g_cal_mu;
 static bool g_cal_done = false;
 static float g_t_level_ns = 0.f, g_t_hop_ns = 0.f, g_t_team_solo_ns = 0.f, g_t_team_cluster_ns = 0.f;
+static float g_link_gbs[2] = {0.f, 0.f};  // host link: host to device, device to host (GB/s)
+
+// Bandwidth of the host link in each direction: the best of three 64 MiB copies between
+// page-locked host memory and the device (copy engine), timed with CUDA events on s.
+static hf_status measure_link(cudaStream_t s) {
+    const size_t bytes = 64u << 20;
+    void* h = nullptr;
+    void* d = dev_alloc(bytes, s);
+    if (!d) return fail(HF_ENOMEM, "device allocation failed: link calibration");
+    cudaError_t e = cudaHostAlloc(&h, bytes, cudaHostAllocDefault);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    for (int dir = 0; dir < 2 && e == cudaSuccess; ++dir) {
+        float best = 0.f;
+        for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+            e = cudaEventRecord(e0, s);
+            if (e == cudaSuccess)
+                e = dir == 0 ? cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, s)
+                             : cudaMemcpyAsync(h, d, bytes, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e == cudaSuccess && rep > 0 && (best == 0.f || ms < best)) best = ms;  // rep 0 warms up
+        }
+        if (e == cudaSuccess) g_link_gbs[dir] = (float)((double)bytes / (best * 1e-3) / 1e9);
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (h) cudaFreeHost(h);
+    dev_free(d, s);
+    return e == cudaSuccess ? HF_OK : cuda_fail(e, "link calibration");
+}
 
 static hf_status calibrate(cudaStream_t s) {
     std::lock_guard<std::mutex> lk(g_cal_mu);
@@ -1836,6 +2016,7 @@ static hf_status calibrate(cudaStream_t s) {
     }
     if (p) plan_destroy(p);
     hf_graph_destroy(g);
+    if (st == HF_OK) st = measure_link(s);
     if (st != HF_OK) return st;
     g_t_level_ns = 1e6f * tl / (float)n;
     g_t_hop_ns = 1e6f * tp / (float)n;
@@ -1852,6 +2033,8 @@ hf_status plan_calibration(cudaStream_t s, float* out) {
     out[1] = g_t_hop_ns;
     out[2] = g_t_team_solo_ns;
     out[3] = g_t_team_cluster_ns;
+    out[4] = g_link_gbs[0];
+    out[5] = g_link_gbs[1];
     return HF_OK;
 }
 
@@ -1883,17 +2066,34 @@ hf_status plan_predict(Plan* p, int32_t priority, const hf_costmodel* cm, cudaSt
     dev_free(b, s);
     if (st != HF_OK) return st;
     double cp = 0.0, work = 0.0;
-    std::vector<double> lmax((size_t)std::max(p->levels, 1), 0.0);
+    // a level-synchronous level costs t_level plus its payload: its saxpy tasks split into
+    // 512-element pieces spread over the level kernel's warps (at most 64 per SM), so the slowest
+    // piece or the level's payload work over those warps, whichever is longer; a host task as a
+    // whole (a max-plus task is one gather, part of t_level; copies run beside the levels on the
+    // copy engines)
+    std::vector<double> lmax((size_t)std::max(p->levels, 1), 0.0), lwork((size_t)std::max(p->levels, 1), 0.0);
     for (int32_t v = 0; v < p->n; ++v) {
         cp = std::max(cp, (double)hb[(size_t)v]);
         work += hc[(size_t)v];
-        // a level-synchronous level costs t_level plus its slowest payload task (a max-plus task
-        // is one gather, part of t_level)
-        if (p->h_cat[(size_t)v] != 0) {
-            double& m = lmax[(size_t)p->h_level[(size_t)v]];
-            m = std::max(m, (double)hc[(size_t)v]);
+        const uint8_t c = p->h_cat[(size_t)v];
+        const size_t l = (size_t)p->h_level[(size_t)v];
+        if (c == 1) {
+            const double n = (double)std::max<int64_t>(p->hpay[(size_t)p->hpidx[(size_t)v]].n, 1);
+            lmax[l] = std::max(lmax[l], (double)hc[(size_t)v] * std::min(1.0, 512.0 / n));
+            lwork[l] += hc[(size_t)v];
+        } else if (c == 4) {
+            lmax[l] = std::max(lmax[l], (double)hc[(size_t)v]);
         }
     }
+    const double ls_warps = 64.0 * (double)p->num_sms;
+    for (size_t l = 0; l < lmax.size(); ++l) lmax[l] = std::max(lmax[l], lwork[l] / ls_warps);
+    // the host link: every copy's bytes cross it, each direction at its measured bandwidth
+    double link_bytes[2] = {0.0, 0.0};
+    for (int32_t q = 0; q < p->npay; ++q)
+        if (p->hpdir[(size_t)q]) link_bytes[p->hpdir[(size_t)q] - 1] += (double)p->hpay[(size_t)q].n;
+    double link_ns = 0.0;
+    for (int d = 0; d < 2; ++d)
+        if (g_link_gbs[d] > 0.f) link_ns = std::max(link_ns, link_bytes[d] / (double)g_link_gbs[d]);
     double lsum = 0.0;
     for (double x : lmax) lsum += x;
     int occ = 0;
@@ -1907,8 +2107,8 @@ hf_status plan_predict(Plan* p, int32_t priority, const hf_costmodel* cm, cudaSt
     cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
     const double ls_bytes = 8.0 * (double)p->m + 8.0 * (double)p->n;
     const double dram = ls_bytes > 0.5 * (double)l2 ? 2.5 : 1.0;
-    *ls_ms = (float)(((double)p->levels * dram * g_t_level_ns + lsum) / 1e6);
-    *p_ms = (float)((cp + (double)p->levels * g_t_hop_ns + work / warps) / 1e6);
+    *ls_ms = (float)(std::max((double)p->levels * dram * g_t_level_ns + lsum, link_ns) / 1e6);
+    *p_ms = (float)(std::max(cp + (double)p->levels * g_t_hop_ns + work / warps, link_ns) / 1e6);
     // team executor: its own plan under the same cost source (host tasks: not available)
     *t_ms = INFINITY;
     if (p->host_tasks.empty()) {

@@ -65,7 +65,8 @@ class hf_run_opts(ctypes.Structure):
                 ("instrument", ctypes.c_int32), ("validate", ctypes.c_int32),
                 ("stall_task", ctypes.c_int32), ("time_kernel", ctypes.c_int32),
                 ("payload_warps", ctypes.c_int32), ("team_size", ctypes.c_int32),
-                ("team_scale", ctypes.c_int32), ("steal_ring", ctypes.c_int32)]
+                ("team_scale", ctypes.c_int32), ("steal_ring", ctypes.c_int32),
+                ("copy_warps", ctypes.c_int32), ("pad_", ctypes.c_int32)]
 
 
 class hf_graph_info_t(ctypes.Structure):
@@ -533,8 +534,9 @@ def hf_batch_team_plan(b, ngraphs):
 
 
 def hf_calibration(stream=None):
-    """(level-sync ns/level, persistent ns/hop, team ns/level on one CTA, on a cluster)."""
-    out = np.zeros(4, np.float32)
+    """(level-sync ns/level, persistent ns/hop, team ns/level on one CTA, on a cluster,
+    host link GB/s host to device, device to host)."""
+    out = np.zeros(6, np.float32)
     _check(load().hf_calibration(_stream_handle(stream), out.ctypes.data), "hf_calibration")
     return tuple(float(x) for x in out)
 
@@ -610,7 +612,7 @@ def hf_run_csr_noalloc(n_tasks, n_edges, row_ptr, succ, delay, arr0, arr, spin_l
 
 
 def opts_dict(o):
-    return {k: getattr(o, k) for k, _ in hf_run_opts._fields_}
+    return {k: getattr(o, k) for k, _ in hf_run_opts._fields_ if not k.endswith("_")}
 
 
 def hf_status_string(s):

@@ -225,3 +225,75 @@ class BatchOnDevice:
             self.close()
         except Exception:
             pass
+
+
+# placeholder payload address for partitioning-only graphs: aligned and non-NULL, never
+# dereferenced (such graphs are never run)
+_NO_BUFFER = 256
+
+
+def _structure_graph(spec: S.GraphSpec):
+    """An hf graph with the tasks, kinds, payload sizes and edges of `spec` but no payload
+    buffers, for host-side analysis only (placement, sharding): it must never run."""
+    g = hf.hf_graph_create(spec.n, spec.m)
+    kind = spec.kind
+    sx_index = {int(t): j for j, t in enumerate(spec.sx_task)}
+    pl_index = {int(t): i for i, t in enumerate(spec.pl_task)}
+    ps_index = {int(t): i for i, t in enumerate(spec.ps_task)}
+    special = np.nonzero(kind != S.KIND_MAXPLUS)[0]
+    v, sp_i, n = 0, 0, spec.n
+    while v < n:
+        nxt = int(special[sp_i]) if sp_i < special.size else n
+        if nxt > v:
+            hf.hf_add_tasks_bulk(g, nxt - v, None if spec.arr0 is None else spec.arr0[v:nxt])
+            v = nxt
+            continue
+        kd = int(kind[v])
+        if kd in (S.KIND_SAXPY, S.KIND_SAXPY_I32):
+            j = sx_index[v]
+            p = hf.hf_saxpy_payload(op=hf.HF_K_SAXPY_I32 if kd == S.KIND_SAXPY_I32 else hf.HF_K_SAXPY_F32,
+                                    a_f=float(spec.sx_a[j]), a_i=int(spec.sx_a[j]), n=int(spec.sx_n[j]),
+                                    x_pull=int(spec.sx_pull[j]), y_pull=-1, x_dev=_NO_BUFFER, y_dev=_NO_BUFFER)
+            hf.hf_add_task(g, hf.HF_KERNEL, p)
+        elif kd == S.KIND_PULL:
+            j = int(spec.pl_saxpy[pl_index[v]])
+            hf.hf_add_task(g, hf.HF_PULL, hf.hf_pull_payload(host_ptr=_NO_BUFFER, bytes=4 * int(spec.sx_n[j])))
+        elif kd == S.KIND_PUSH:
+            j = int(spec.ps_saxpy[ps_index[v]])
+            hf.hf_add_task(g, hf.HF_PUSH, hf.hf_push_payload(src_pull=-1, src_dev=_NO_BUFFER, host_ptr=_NO_BUFFER,
+                                                             bytes=4 * int(spec.sx_n[j])))
+        else:
+            raise ValueError("unknown task kind %d" % kd)
+        v += 1
+        sp_i += 1
+    hf.hf_precede_bulk(g, spec.src, spec.dst, spec.delay)
+    return g
+
+
+def partition(wl: S.Workload, ndev: int):
+    """Sharding of a workload's graphs over `ndev` devices with hf_batch_partition (graphs packed
+    by decreasing heuristic cost, each onto the least-loaded device: the balanced bin packing of
+    the paper's Algorithm 1). Host only: it works on structure-only copies of the graphs, so a
+    rank can learn its share before it puts any graph on its device. Returns (device of each
+    graph, predicted load per device)."""
+    b = hf.hf_batch_create()
+    gs = []
+    try:
+        for spec in wl.graphs:
+            g = _structure_graph(spec)
+            gs.append(g)
+            hf.hf_batch_add(b, g)
+        return hf.hf_batch_partition(b, len(wl.graphs), ndev)
+    finally:
+        hf.hf_batch_destroy(b)
+        for g in gs:
+            hf.hf_graph_destroy(g)
+
+
+def share(wl: S.Workload, rank: int, world: int):
+    """Rank `rank`'s share of `wl` under `partition` (a Workload of its graphs, in batch order)."""
+    if world <= 1:
+        return wl, list(range(len(wl.graphs)))
+    dev, _ = partition(wl, world)
+    idx = [i for i in range(len(wl.graphs)) if dev[i] == rank]
+    return S.Workload("%s_shard%dof%d" % (wl.name, rank, world), [wl.graphs[i] for i in idx]), idx

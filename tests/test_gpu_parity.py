@@ -37,6 +37,10 @@ EXECUTORS = {
     "steal_2cta": dict(mode=hf.HF_MODE_PERSISTENT, steal_ring=64, ctas=2),
     "steal_1cta": dict(mode=hf.HF_MODE_PERSISTENT, steal_ring=128, ctas=1),
     "steal_payw2": dict(mode=hf.HF_MODE_PERSISTENT, steal_ring=256, payload_warps=2),
+    # copy warps: pulls and pushes from queues of their own (one or two warps per CTA and direction)
+    "persistent_copyw1": dict(mode=hf.HF_MODE_PERSISTENT, copy_warps=1),
+    "persistent_copyw2_payw2": dict(mode=hf.HF_MODE_PERSISTENT, copy_warps=2, payload_warps=2, claim=4),
+    "steal_copyw1": dict(mode=hf.HF_MODE_PERSISTENT, steal_ring=128, copy_warps=1, ctas=6),
     "team": dict(mode=hf.HF_MODE_TEAM),
     "team_heur": dict(mode=hf.HF_MODE_TEAM, priority=hf.HF_PRIO_HEURISTIC),
     "team_k2": dict(mode=hf.HF_MODE_TEAM, team_size=2),
@@ -173,7 +177,8 @@ def _check_payloads(gd, ref):
 
 @pytest.mark.parametrize("chunk", [0, 64, 4096])
 @pytest.mark.parametrize("ex", ["levelsync", "persistent", "persistent_claim8", "persistent_payw2", "persistent_payw7",
-                                "steal", "steal_small", "steal_2cta", "steal_payw2", "team", "team_k2", "team_k5"])
+                                "persistent_copyw1", "persistent_copyw2_payw2", "steal", "steal_small", "steal_2cta",
+                                "steal_payw2", "steal_copyw1", "team", "team_k2", "team_k5"])
 def test_mixed_small_with_payloads(ex, chunk):
     spec = S.mixed(3, n=6000, nmin=1, nmax=20000, n_copy=300)
     ref = oracle.run_spec(spec)
@@ -190,7 +195,7 @@ def test_mixed100k_full_size_sampled():
     gd = GraphOnDevice(spec)
     rng = np.random.default_rng(0)
     sample = rng.choice(spec.sx_task.size, 64, replace=False)
-    for ex in ["levelsync", "persistent", "steal", "team_heur"]:
+    for ex in ["levelsync", "persistent", "persistent_copyw1", "steal", "team_heur"]:
         gd.reset_y()
         arr = _run(gd, **EXECUTORS[ex])
         np.testing.assert_array_equal(bits(arr), bits(ref["arr"]))
@@ -295,7 +300,8 @@ def test_paper_saxpy_graph_through_c_abi():
     for a, b in gold["edges"]:
         hf.hf_precede(g, ids[a], ids[b])
     for opts in (dict(mode=hf.HF_MODE_LEVELSYNC), dict(mode=hf.HF_MODE_TEAM), dict(mode=hf.HF_MODE_TEAM, team_size=2),
-                 dict(mode=hf.HF_MODE_PERSISTENT), dict(mode=hf.HF_MODE_PERSISTENT, validate=1, chunk_elems=4096)):
+                 dict(mode=hf.HF_MODE_PERSISTENT), dict(mode=hf.HF_MODE_PERSISTENT, validate=1, chunk_elems=4096),
+                 dict(mode=hf.HF_MODE_PERSISTENT, validate=1, copy_warps=1, chunk_elems=4096)):
         x.zero_()
         y.zero_()
         calls.clear()
@@ -358,8 +364,8 @@ def test_host_tasks_in_a_batch(opts):
         hf.hf_graph_destroy(g)
 
 
-@pytest.mark.parametrize("ring", [0, 128])
-def test_paper_saxpy_graph_persistent_without_host_tasks(ring):
+@pytest.mark.parametrize("ring,copyw", [(0, 0), (128, 0), (0, 1), (128, 2)])
+def test_paper_saxpy_graph_persistent_without_host_tasks(ring, copyw):
     N = 65536
     x = torch.full((N,), 1, dtype=torch.int32, pin_memory=True)
     y = torch.full((N,), 2, dtype=torch.int32, pin_memory=True)
@@ -371,7 +377,8 @@ def test_paper_saxpy_graph_persistent_without_host_tasks(ring):
     sy = hf.hf_add_task(g, hf.HF_PUSH, hf.hf_push_payload(src_pull=py, host_ptr=y.data_ptr(), bytes=4 * N))
     for a, b in [(px, k), (py, k), (k, sx), (k, sy)]:
         hf.hf_precede(g, a, b)
-    hf.hf_run(g, None, hf.hf_run_opts_default(mode=hf.HF_MODE_PERSISTENT, chunk_elems=4096, validate=1, steal_ring=ring))
+    hf.hf_run(g, None, hf.hf_run_opts_default(mode=hf.HF_MODE_PERSISTENT, chunk_elems=4096, validate=1, steal_ring=ring,
+                                              copy_warps=copyw))
     hf.hf_sync_status(g)
     assert bool((y == 4).all()) and bool((x == 1).all())
     s0, s1, c = hf.hf_get_stamps(g, 5)

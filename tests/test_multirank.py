@@ -73,3 +73,50 @@ def test_reference_arm_runs_on_rank_zero_only():
     line = json.loads(r.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["value"] > 0 and line["cpu_baseline"]["kind"] == "oracle"
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["config"]["workload"] == "layered10k"
+
+
+def _shard_rank(rank, world, port, out):
+    import torch
+    import torch.distributed as dist
+
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2203_08395_b300 import synth as S
+    from paper_2203_08395_b300.workload import share
+
+    dist.init_process_group("gloo", init_method="tcp://127.0.0.1:%d" % port, rank=rank, world_size=world)
+    # the benchmark's strong-scaling path: the same batch on every rank, each taking its LPT share
+    full = S.batch(5, graphs=14, nmin=200, nmax=6000, frac_saxpy=0.1, sx_min=16, sx_max=512)
+    full.graphs.append(S.mixed(6, n=800, nmin=16, nmax=256, n_copy=20))  # pulls and pushes too
+    mine, idx = share(full, rank, world)
+    flags = torch.zeros(len(full.graphs), dtype=torch.int64)
+    flags[idx] = 1
+    gathered = [torch.empty_like(flags) for _ in range(world)]
+    dist.all_gather(gathered, flags)
+    n_all = bench.sum_over_ranks(mine.n_tasks)
+    out.put((rank, [int(x) for x in sum(gathered)], n_all, full.n_tasks, [g.name for g in mine.graphs],
+             [full.graphs[i].name for i in idx]))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_split_one_batch_by_lpt():
+    """bench.py --shard lpt on CPU ranks: each rank's share (workload.share, i.e.
+    hf_batch_partition's balanced bin packing, the paper's Algorithm 1) is disjoint from the other's,
+    together they cover the batch, and the tasks summed over ranks are the batch's."""
+    import torch.multiprocessing as mp
+
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_shard_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got = sorted(q.get(timeout=180) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, covered, n_all, n_full, names, want in got:
+        assert covered == [1] * len(covered)
+        assert n_all == n_full
+        assert names == want and len(names) > 0
