@@ -134,7 +134,8 @@ typedef struct {
     int32_t instrument;     /* bit 0: record per-task %globaltimer start/end (hf_get_task_times;
                                persistent executor) or per-graph start/end (team executor,
                                hf_batch_get_graph_times); bit 1: record persistent-executor
-                               counters (hf_batch_get_stats) */
+                               counters (hf_batch_get_stats); bit 2: record per-task costs in the
+                               team executor (hf_batch_get_task_costs) */
     int32_t validate;       /* record per-task start/finish tickets and execution counts */
     int32_t stall_task;     /* failure-injection hook for tests: -1 = off; else this task's
                                pending-predecessor counter starts one too high, so it never
@@ -148,9 +149,10 @@ typedef struct {
                                costs (one CTA per graph under HF_PRIO_FIFO) */
     int32_t team_scale;     /* team planner: factor on the predicted payload cost, standing for
                                the slowdown of memory traffic when every graph streams at once;
-                               larger values give payload-heavy graphs larger teams; 0 = 4 (a
-                               512-element piece: ~0.75 us for a warp alone, ~3 us when every SM
-                               streams, measured on B300) */
+                               larger values give payload-heavy graphs larger teams; 0 = 4 for
+                               heuristic costs (a 512-element piece: ~0.75 us for a warp alone,
+                               ~3 us when every SM streams, measured on B300), 1 for learned costs
+                               (recorded under the team executor's real load) */
     int32_t steal_ring;     /* persistent: 0 = one global ready queue; > 0 = work stealing
                                (Section III-C): every CTA owns a ring of this many slots (rounded
                                up to a power of two, 64..16384) that its warps push ready tasks
@@ -325,6 +327,13 @@ hf_status hf_batch_get_stats(hf_batch* b, int64_t* out, int32_t n);
  * team-executor run with instrument bit 0: when the graph's job started and when its last
  * level ended. */
 hf_status hf_batch_get_graph_times(hf_batch* b, int64_t* start_ns, int64_t* end_ns);
+/* Per-task costs (ns) recorded by the last team-executor run with instrument bit 2, into a host
+ * array: for graph `index` its task count, for index -1 every graph's tasks concatenated in batch
+ * order. A task's cost is what the team spent on it under the run's real load: for every task the
+ * time of its thread's gather (predecessor keys in, arrival key stored), plus, for a payload
+ * task, the summed times of the warps that ran its pieces. These are the costs the team planner
+ * consumes, and the cost model's training target. */
+hf_status hf_batch_get_task_costs(hf_batch* b, int32_t index, float* cost_ns);
 /* Kernels the last run launched (executor kernels; copies and memsets not counted): one per
  * level for the level-synchronous executor, 2 for the persistent one (reset + executor), one
  * per team class for the team executor. */
@@ -341,11 +350,13 @@ hf_status hf_batch_set_delays(hf_batch* b, const float* delay, int on_device, vo
  * The paper's scheduler (Section III-C) orders ready tasks with a plain heuristic (FIFO work
  * stealing); it has no learned component. This library adds one, kept beside the heuristic:
  * an MLP 12 -> 64 -> 64 -> 1 (ReLU, BF16 weights and activations, FP32 accumulation and FP32
- * master weights) maps per-task features to a predicted log task cost (log ns of the time a
- * warp spends on the task, as the instrumented executor records it). Predicted costs give
- * bottom-level weights b(v) = c(v) + max over successors b(s) (the remaining critical path)
- * that order the persistent executor's ready tasks; predicted makespans choose between the
- * executors in HF_MODE_AUTO. Results (arrivals, payload data) never depend on the model.
+ * master weights) maps per-task features to a predicted log task cost (log ns that the team
+ * executor spends on the task, as its cost recording measures it: hf_batch_get_task_costs).
+ * Predicted costs plan the team executor (its payload cost per level, hence team sizes and job
+ * order), give bottom-level weights b(v) = c(v) + max over successors b(s) (the remaining
+ * critical path) that order the persistent executor's initial ready queue (its sources), and
+ * give the predicted makespans that choose between the executors in HF_MODE_AUTO. Results
+ * (arrivals, payload data) never depend on the model.
  *
  * Parameter vector (HF_COSTMODEL_PARAMS floats, row-major): W1[64][12], b1[64], W2[64][64],
  * b2[64], w3[64], b3. W1, W2, w3 are used rounded to BF16 (round to nearest even).
@@ -420,7 +431,8 @@ hf_status hf_batch_autotune(hf_batch* b, void* stream, const hf_run_opts* base, 
  *   level-sync  = levels * t_level (x 2.5 when the level data exceed half the L2) + sum over
  *                 levels of the largest saxpy- or host-task cost in it
  *   persistent  = critical path of costs + depth * t_hop + total cost / warps
- *   (both at least the copies' bytes of the busier host-link direction over its bandwidth)
+ *   (both at least the copies' host-link time: each direction's bytes over its bandwidth, and
+ *   all copy bytes over the bandwidth of both directions at once)
  *   team        = the team executor's planned makespan: per graph and cluster size k,
  *                 T(k) = sum over levels of t_lvl(k) * ceil(width / 256k) + payload cost / 8k
  *                 (t_lvl x 2.5 for levels too large to stage in shared memory),
@@ -432,9 +444,10 @@ hf_status hf_batch_predict(hf_batch* b, int32_t priority, void* stream, float* l
 /* The machine constants behind the predictions, measured on first use in this process on the
  * current device: on the calibration chain (2,048 tasks, one per level) the level-synchronous
  * time per level, the persistent time per dependent hop, the team time per level on one CTA and
- * on a cluster (ns); and the host link's bandwidth host to device and device to host (GB/s, the
- * best of three 64 MiB copies between page-locked memory and the device). out[6]. Blocks the
- * first time. */
+ * on a cluster (ns); and the host link's bandwidth host to device, device to host, and both
+ * directions at once (GB/s, the best of three 64 MiB copies between page-locked memory and the
+ * device; both at once: the bytes of two concurrent copies over their common time). out[7].
+ * Blocks the first time. */
 hf_status hf_calibration(void* stream, float* out);
 
 /* --- allocation-free entry point -------------------------------------------------------

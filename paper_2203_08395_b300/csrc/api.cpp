@@ -933,6 +933,13 @@ hf_status hf_batch_get_graph_times(hf_batch* b, int64_t* start, int64_t* end) {
     return plan_get_graph_times(b->plan, start, end);
 }
 
+hf_status hf_batch_get_task_costs(hf_batch* b, int32_t index, float* cost_ns) {
+    if (!b || !cost_ns) return fail(HF_EINVAL, "NULL argument");
+    if (!b->plan) return fail(HF_ESTATE, "batch has not run");
+    if (index < -1 || index >= (int32_t)b->graphs.size()) return fail(HF_EINVAL, "graph index out of range");
+    return plan_get_task_costs(b->plan, index, cost_ns);
+}
+
 hf_status hf_batch_last_launches(hf_batch* b, int32_t* n) {
     if (!b || !n) return fail(HF_EINVAL, "NULL argument");
     if (!b->plan) return fail(HF_ESTATE, "batch has not run");

@@ -200,7 +200,7 @@ struct alignas(16) TeamPiece {
     int32_t cnt;
     uint32_t a;
     uint32_t op;
-    int32_t pad_;
+    int32_t task;  // the task the piece belongs to (cost recording)
 };
 
 // Team-executor control words (zeroed before every run): solo-job counter, cluster-job counter.
@@ -232,6 +232,8 @@ struct TeamArgs {
     uint64_t spin_limit_ns;
     int64_t* g_start;        // instrument: %globaltimer per graph at job start / end (else NULL)
     int64_t* g_end;
+    float* t_cost;           // instrument bit 2: per-task cost in ns (a task's gather; a payload task's
+                             // pieces summed), else NULL
     const int2* seg_host;    // host tasks: (graph, level) segment -> range in host_order (NULL: none)
     const int32_t* host_order;
     int32_t* post;           // mapped host memory: the i-th posted host task
@@ -349,6 +351,7 @@ hf_status plan_kernel_ms(Plan* p, float* ms);
 hf_status plan_get_stats(Plan* p, int64_t* out, int32_t n);
 hf_status plan_get_graph_times(Plan* p, int64_t* start, int64_t* end);
 hf_status plan_last_launches(Plan* p, int32_t* n);
+hf_status plan_get_task_costs(Plan* p, int32_t gi, float* out);
 hf_status plan_team_plan(Plan* p, int32_t* team_size);
 hf_status plan_set_delays(Plan* p, const float* delay, int on_device, cudaStream_t s);
 hf_status plan_run_host(Plan* p, cudaStream_t s, const hf_run_opts& o, const float* delay, float* arr_out);

@@ -329,13 +329,10 @@ __global__ void __launch_bounds__(256) k_level(const LevelArgs a) {
 // kNarrowIn predecessors use a 32-bit max on the key half, a fence and an atomic decrement on
 // the count half instead, which avoids CAS retry storms on wide joins.
 
-// Edge record word w: bits 0-6 successor's in-degree (kWideMark: wide join), bits 7-14 its
-// priority bucket (0 = lowest; all 0 under FIFO), bit 15 set when it has a payload, bits 16-31
-// its out-degree (kLongMark: look it up in meta).
+// Edge record word w: bits 0-6 successor's in-degree (kWideMark: wide join), bits 7-14 zero,
+// bit 15 set when it has a payload, bits 16-31 its out-degree (kLongMark: look it up in meta).
 constexpr uint32_t kWideMark = 0x7Fu;
 constexpr uint32_t kLongMark = 0xFFFFu;
-constexpr int kPrioShift = 7;
-constexpr uint32_t kPrioMask = 0xFFu;
 constexpr uint32_t kPayBit = 1u << 15;
 
 __device__ __forceinline__ void prefetch_l2(const void* p) {
@@ -609,12 +606,13 @@ __device__ __forceinline__ int ring_steal(const PersistArgs& a, int c, int most,
 
 // Pushes this warp's ready tasks (lane: r.x >= 0 with r = {task, key, first out-edge (payload
 // index for payload tasks), out-degree | payload flag << 31}). Tasks go to the warp's stack
-// while it has room (up to local_keep) -- plain tasks with their first kStage out-edges staged
-// in shared memory for the next round -- except payload tasks in warp-specialised runs, which
-// go to the payload queue; the rest go to the main queue (with work stealing: to the CTA's ring,
-// rt). nstk / nedg: the stack buffer filled this round and its staging area.
+// while it has room (up to local_keep; the first lanes' tasks) -- plain tasks with their first
+// kStage out-edges staged in shared memory for the next round -- except payload tasks in
+// warp-specialised runs, which go to the payload queue, and copies in runs with copy warps,
+// which go to their direction's queue; the rest go to the main queue (with work stealing: to
+// the CTA's ring, rt). nstk / nedg: the stack buffer filled this round and its staging area.
 template <bool PAY>
-__device__ __forceinline__ void push_ready(const PersistArgs& a, int4 r, int pr, int4* nstk, int4* nedg, int& top,
+__device__ __forceinline__ void push_ready(const PersistArgs& a, int4 r, int4* nstk, int4* nedg, int& top,
                                            int* rt, int lane, WStats& ws) {
     const long long c_push = clk(ws);
     const int v = r.x;
@@ -625,17 +623,7 @@ __device__ __forceinline__ void push_ready(const PersistArgs& a, int4 r, int pr,
     const bool single = v >= 0 && !topay && cls == 0;
     const unsigned sm = __ballot_sync(kFull, single);
     const int room = a.local_keep - top;
-    int rank;
-    if (__popc(sm) <= room) {
-        rank = __popc(sm & lanemask_lt());
-    } else {  // spill: the highest priority buckets stay in the warp's stack (ties: lane order)
-        rank = 0;
-#pragma unroll 8
-        for (int j = 0; j < 32; ++j) {
-            const int pj = __shfl_sync(kFull, pr, j);
-            if (((sm >> j) & 1u) && (pj > pr || (pj == pr && j < lane))) ++rank;
-        }
-    }
+    const int rank = __popc(sm & lanemask_lt());
     bool go_global = v >= 0;
     if (single && rank < room) {
         const int slot = top + rank;
@@ -743,7 +731,6 @@ __device__ __forceinline__ void release_all(const PersistArgs& a, int fin, uint3
         if (PAY && a.pay_warps == 0 && __ballot_sync(kFull, rec.x >= 0 && (w & kPayBit))) fence_acq_rel();
         const long long c_cas = clk(ws);
         int4 r = make_int4(-1, 0, 0, 0);
-        int pr = 0;
         if (rec.x >= 0) {
             const float cand = __fadd_rn(key2f(o_k), __int_as_float(rec.y));
             uint32_t kv;
@@ -751,12 +738,11 @@ __device__ __forceinline__ void release_all(const PersistArgs& a, int fin, uint3
                 int len = (int)(w >> 16);
                 if ((uint32_t)len == kLongMark) len = __ldg(a.meta + rec.x).y;
                 r = make_int4(rec.x, (int)kv, rec.z, len | ((w & kPayBit) ? (int)0x80000000u : 0));
-                pr = (int)((w >> kPrioShift) & kPrioMask);
             }
         }
         const bool any_ready = __ballot_sync(kFull, r.x >= 0) != 0;
         if (ws.on) ws.cyc_cas += (unsigned long long)(clk(ws) - c_cas);
-        if (any_ready) push_ready<PAY>(a, r, pr, nstk, nedg, top, rt, lane, ws);
+        if (any_ready) push_ready<PAY>(a, r, nstk, nedg, top, rt, lane, ws);
     }
     if (ws.on) ws.cyc_release += (unsigned long long)(clk(ws) - c_rel);
 }

@@ -148,6 +148,8 @@ struct Plan {
     int32_t* d_ring_head = nullptr;         // their take positions (one 128-byte line per CTA)
     size_t cap_ring = 0, cap_ring_head = 0;
     int64_t* d_gtime = nullptr;             // team executor: per-graph start, then end (instrument & 1)
+    float* d_tcost = nullptr;               // team executor: per-task cost in ns (instrument & 4)
+    bool last_tcost = false;
     int32_t last_launches = 0;              // executor kernels of the last run
     bool last_gtimes = false;
     bool last_stats = false;
@@ -217,6 +219,9 @@ static hf_status plan_team_jobs(Plan* p, const hf_run_opts& o, cudaStream_t s);
 // default payload-cost scale: a 512-element piece takes ~0.75 us for a warp alone and ~3 us when
 // every SM streams (measured on this B300), so concurrent graphs see about 4x the unloaded cost
 constexpr int kTeamScaleDefault = 4;
+// Learned costs are recorded by the team executor under its real load (contention included), so
+// the planner takes them as they are.
+static int team_scale_default(int32_t prio) { return prio == HF_PRIO_LEARNED ? 1 : kTeamScaleDefault; }
 static int team_capacity(const Plan* p, int k);
 static size_t team_smem(const Plan* p);
 static void team_smem_attr(const Plan* p);
@@ -692,7 +697,7 @@ static hf_status plan_set_chunk(Plan* p, int64_t chunk_elems, cudaStream_t s) {
             t.cnt = (int32_t)std::max<int64_t>(b1 - b0, 0);
             t.a = d.a_bits;
             t.op = d.op;
-            t.pad_ = 0;
+            t.task = d.task;
         }
     } catch (const std::bad_alloc&) {
         return fail(HF_ENOMEM, "host allocation failed");
@@ -1201,6 +1206,18 @@ hf_status plan_run(Plan* p, cudaStream_t s, const hf_run_opts& o, bool keep_stat
                 a.g_end = p->d_gtime + p->ngraphs;
             }
             p->last_gtimes = instr;
+            // instrument bit 2: per-task costs (ns), accumulated from zero
+            const bool rec = (o.instrument & 4) != 0;
+            if (rec) {
+                if (!p->d_tcost) {
+                    p->d_tcost = (float*)palloc(p, sizeof(float) * std::max<size_t>((size_t)p->n, 4), s);
+                    if (!p->d_tcost) return fail(HF_ENOMEM, "device allocation failed: task costs");
+                }
+                e = cudaMemsetAsync(p->d_tcost, 0, sizeof(float) * (size_t)p->n, s);
+                if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+                a.t_cost = p->d_tcost;
+            }
+            p->last_tcost = rec;
             e = cudaMemsetAsync(p->d_team, 0, sizeof(int32_t) * (size_t)kTeamWords * p->tclass.size(), s);
             // a failed team raises ctrl->abort so that no new job starts; every run starts clear
             if (e == cudaSuccess) e = cudaMemsetAsync(&p->d_ctrl->abort, 0, sizeof(int32_t), s);
@@ -1232,7 +1249,10 @@ hf_status plan_run(Plan* p, cudaStream_t s, const hf_run_opts& o, bool keep_stat
                 at[0].val.clusterDim.z = 1;
                 cfg.attrs = at;
                 cfg.numAttrs = c.k > 1 ? 1 : 0;
-                e = p->npay ? cudaLaunchKernelEx(&cfg, k_team<true>, ai) : cudaLaunchKernelEx(&cfg, k_team<false>, ai);
+                if (rec) e = p->npay ? cudaLaunchKernelEx(&cfg, k_team<true, true>, ai)
+                                     : cudaLaunchKernelEx(&cfg, k_team<false, true>, ai);
+                else e = p->npay ? cudaLaunchKernelEx(&cfg, k_team<true, false>, ai)
+                                 : cudaLaunchKernelEx(&cfg, k_team<false, false>, ai);
                 if (e != cudaSuccess) return cuda_fail(e, "k_team launch");
             }
             for (size_t i = 0; i < nc; ++i) {
@@ -1510,6 +1530,15 @@ hf_status plan_get_graph_times(Plan* p, int64_t* start, int64_t* end) {
     return e == cudaSuccess ? HF_OK : cuda_fail(e, "graph timer copy");
 }
 
+hf_status plan_get_task_costs(Plan* p, int32_t gi, float* out) {
+    if (!p->ran || !p->last_tcost) return fail(HF_ESTATE, "last run was not a team run with instrument bit 2");
+    const int32_t off = gi < 0 ? 0 : p->task_off[(size_t)gi];
+    const int64_t cnt = gi < 0 ? p->n : p->task_off[(size_t)gi + 1] - off;
+    cudaError_t e = cudaStreamSynchronize(p->last_stream);
+    if (e == cudaSuccess && cnt) e = cudaMemcpy(out, p->d_tcost + off, sizeof(float) * (size_t)cnt, cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? HF_OK : cuda_fail(e, "task cost copy");
+}
+
 hf_status plan_last_launches(Plan* p, int32_t* n) {
     if (!p->ran) return fail(HF_ESTATE, "not run");
     *n = p->last_launches;
@@ -1641,27 +1670,6 @@ __global__ void k_bottom(int p0, int p1, const int32_t* __restrict__ ls_node, co
     b[v] = __fadd_rn(mx, c[v]);
 }
 
-// Priority bucket of each edge's successor into its edge record: round(511 * b(v) / b_max)
-// (scale = 511 / b_max), or 0 everywhere when scale is 0 (FIFO).
-__global__ void k_set_prio_bits(int4* __restrict__ erec, int64_t m, const float* __restrict__ b, float scale) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
-        int4 r = erec[e];
-        uint32_t q = 0;
-        if (scale > 0.f) q = (uint32_t)fminf(fmaxf(rintf(b[r.x] * scale), 0.f), (float)kPrioMask);
-        r.w = (int)(((uint32_t)r.w & ~(kPrioMask << kPrioShift)) | (q << kPrioShift));
-        erec[e] = r;
-    }
-}
-
-static hf_status set_prio_bits(Plan* p, const float* b, float scale, cudaStream_t s) {
-    if (p->m == 0) return HF_OK;
-    const int grid = (int)std::min<int64_t>((p->m + 255) / 256, (int64_t)p->num_sms * 16);
-    k_set_prio_bits<<<grid, 256, 0, s>>>(p->d_erec, p->m, b, scale);
-    cudaError_t e = cudaGetLastError();
-    return e == cudaSuccess ? HF_OK : cuda_fail(e, "k_set_prio_bits");
-}
-
 static hf_status ensure_cm_inputs(Plan* p, cudaStream_t s) {
     if (p->d_level) return HF_OK;
     hf_status st;
@@ -1727,14 +1735,15 @@ hf_status plan_task_costs(Plan* p, int32_t priority, const hf_costmodel* cm, flo
     return st;
 }
 
-// Orders the persistent executor's seed tasks by decreasing bottom-level weight (longest
-// remaining predicted critical path first) for HEURISTIC / LEARNED runs; FIFO keeps id order.
+// The persistent executor's ready-queue priority: its seed tasks (the sources) enter the
+// queue by decreasing bottom-level weight (longest remaining predicted critical path first) for
+// HEURISTIC / LEARNED runs; FIFO keeps id order. Later ready tasks keep release order: ranking
+// them by bottom level when a warp's stack overflows (which of them stay in shared memory) was
+// measured and made runs 15-55 % slower on the batch workloads.
 hf_status plan_prepare_priority(Plan* p, int32_t priority, const hf_costmodel* cm, cudaStream_t s) {
     if (priority == p->seed_prio && (priority == HF_PRIO_FIFO || p->d_prio)) return HF_OK;
     if (priority == HF_PRIO_FIFO) {
         std::sort(p->sources.begin(), p->sources.end());
-        hf_status st = set_prio_bits(p, nullptr, 0.f, s);
-        if (st != HF_OK) return st;
     } else {
         if (!p->d_prio) {
             p->d_prio = (float*)palloc(p, sizeof(float) * std::max<size_t>((size_t)p->n, 4), s);
@@ -1748,12 +1757,9 @@ hf_status plan_prepare_priority(Plan* p, int32_t priority, const hf_costmodel* c
         std::vector<float> b((size_t)p->n);
         cudaError_t e = cudaMemcpy(b.data(), p->d_prio, sizeof(float) * (size_t)p->n, cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return cuda_fail(e, "priority download");
+        std::sort(p->sources.begin(), p->sources.end());
         std::stable_sort(p->sources.begin(), p->sources.end(),
                          [&](int32_t x, int32_t y) { return b[(size_t)x] > b[(size_t)y]; });
-        float bmax = 0.f;
-        for (float x : b) bmax = std::max(bmax, x);
-        st = set_prio_bits(p, p->d_prio, bmax > 0.f ? (float)kPrioMask / bmax : 0.f, s);
-        if (st != HF_OK) return st;
     }
     p->seed_prio = priority;
     p->chunk_elems = -1;  // seeds are rebuilt with the next piece layout
@@ -1819,7 +1825,7 @@ static hf_status autotune_team(Plan* p, cudaStream_t s, const hf_run_opts& base,
     cur.instrument = cur.validate = cur.time_kernel = 0;
     cur.stall_task = -1;
     cur.team_size = 0;
-    cur.team_scale = kTeamScaleDefault;
+    cur.team_scale = team_scale_default(cur.priority);
     if (cur.chunk_elems <= 0) cur.chunk_elems = 512;
     float best_t = 0.f;
     hf_status st = time_runs(p, s, cur, 3, &best_t);
@@ -1948,37 +1954,54 @@ hf_status plan_autotune(Plan* p, cudaStream_t s, const hf_run_opts& base, int fo
 static std::mutex g_cal_mu;
 static bool g_cal_done = false;
 static float g_t_level_ns = 0.f, g_t_hop_ns = 0.f, g_t_team_solo_ns = 0.f, g_t_team_cluster_ns = 0.f;
-static float g_link_gbs[2] = {0.f, 0.f};  // host link: host to device, device to host (GB/s)
+// host link (GB/s): host to device, device to host, and both directions at once (bytes of both
+// copies over their common time)
+static float g_link_gbs[3] = {0.f, 0.f, 0.f};
 
-// Bandwidth of the host link in each direction: the best of three 64 MiB copies between
-// page-locked host memory and the device (copy engine), timed with CUDA events on s.
+// Bandwidth of the host link: the best of three 64 MiB copies between page-locked host memory
+// and the device (copy engine) in each direction, then both directions at once on two streams
+// (what pulls and pushes running together get), timed with CUDA events.
 static hf_status measure_link(cudaStream_t s) {
     const size_t bytes = 64u << 20;
     void* h = nullptr;
-    void* d = dev_alloc(bytes, s);
+    void* h2 = nullptr;
+    void* d = dev_alloc(2 * bytes, s);
     if (!d) return fail(HF_ENOMEM, "device allocation failed: link calibration");
     cudaError_t e = cudaHostAlloc(&h, bytes, cudaHostAllocDefault);
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (e == cudaSuccess) e = cudaHostAlloc(&h2, bytes, cudaHostAllocDefault);
+    cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
+    cudaStream_t s2 = nullptr;
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
-    for (int dir = 0; dir < 2 && e == cudaSuccess; ++dir) {
+    if (e == cudaSuccess) e = cudaEventCreate(&e2);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking);
+    char* d2 = static_cast<char*>(d) + bytes;
+    for (int dir = 0; dir < 3 && e == cudaSuccess; ++dir) {
         float best = 0.f;
         for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
             e = cudaEventRecord(e0, s);
-            if (e == cudaSuccess)
-                e = dir == 0 ? cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, s)
-                             : cudaMemcpyAsync(h, d, bytes, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess && dir != 1) e = cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess && dir == 1) e = cudaMemcpyAsync(h, d, bytes, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess && dir == 2) {  // the other direction at the same time on s2
+                e = cudaStreamWaitEvent(s2, e0, 0);
+                if (e == cudaSuccess) e = cudaMemcpyAsync(h2, d2, bytes, cudaMemcpyDeviceToHost, s2);
+                if (e == cudaSuccess) e = cudaEventRecord(e2, s2);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(s, e2, 0);
+            }
             if (e == cudaSuccess) e = cudaEventRecord(e1, s);
             if (e == cudaSuccess) e = cudaEventSynchronize(e1);
             float ms = 0.f;
             if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
             if (e == cudaSuccess && rep > 0 && (best == 0.f || ms < best)) best = ms;  // rep 0 warms up
         }
-        if (e == cudaSuccess) g_link_gbs[dir] = (float)((double)bytes / (best * 1e-3) / 1e9);
+        if (e == cudaSuccess) g_link_gbs[dir] = (float)((double)(dir == 2 ? 2 : 1) * bytes / (best * 1e-3) / 1e9);
     }
+    if (s2) cudaStreamDestroy(s2);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
+    if (e2) cudaEventDestroy(e2);
     if (h) cudaFreeHost(h);
+    if (h2) cudaFreeHost(h2);
     dev_free(d, s);
     return e == cudaSuccess ? HF_OK : cuda_fail(e, "link calibration");
 }
@@ -2035,6 +2058,7 @@ hf_status plan_calibration(cudaStream_t s, float* out) {
     out[3] = g_t_team_cluster_ns;
     out[4] = g_link_gbs[0];
     out[5] = g_link_gbs[1];
+    out[6] = g_link_gbs[2];
     return HF_OK;
 }
 
@@ -2094,6 +2118,7 @@ hf_status plan_predict(Plan* p, int32_t priority, const hf_costmodel* cm, cudaSt
     double link_ns = 0.0;
     for (int d = 0; d < 2; ++d)
         if (g_link_gbs[d] > 0.f) link_ns = std::max(link_ns, link_bytes[d] / (double)g_link_gbs[d]);
+    if (g_link_gbs[2] > 0.f) link_ns = std::max(link_ns, (link_bytes[0] + link_bytes[1]) / (double)g_link_gbs[2]);
     double lsum = 0.0;
     for (double x : lmax) lsum += x;
     int occ = 0;
@@ -2117,7 +2142,7 @@ hf_status plan_predict(Plan* p, int32_t priority, const hf_costmodel* cm, cudaSt
         double M = 0.0;
         const hf_costmodel* keep = p->cm;
         p->cm = cm;
-        st = team_decide(p, priority, 0, (double)kTeamScaleDefault, s, &k, &order, &M);
+        st = team_decide(p, priority, 0, (double)team_scale_default(priority), s, &k, &order, &M);
         p->cm = keep;
         if (st != HF_OK) return st;
         *t_ms = (float)(M / 1e6);
@@ -2155,14 +2180,15 @@ static void team_smem_attr(const Plan* p) {
     std::lock_guard<std::mutex> lk(mu);
     const size_t need = team_smem(p);
     if (need > set_to) {
-        cudaFuncSetAttribute(k_team<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
-        cudaFuncSetAttribute(k_team<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
+        for (const void* f : {(const void*)k_team<true, false>, (const void*)k_team<false, false>,
+                              (const void*)k_team<true, true>, (const void*)k_team<false, true>})
+            cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
         set_to = need;
     }
 }
 
 static int team_capacity(const Plan* p, int k) {
-    const void* fn = p->npay ? (const void*)k_team<true> : (const void*)k_team<false>;
+    const void* fn = p->npay ? (const void*)k_team<true, false> : (const void*)k_team<false, false>;
     team_smem_attr(p);
     if (k == 1) {
         int occ = 0;
@@ -2170,8 +2196,9 @@ static int team_capacity(const Plan* p, int k) {
         return p->num_sms * std::max(occ, 1);
     }
     if (k > 8) {
-        cudaFuncSetAttribute(k_team<true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        cudaFuncSetAttribute(k_team<false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        for (const void* f : {(const void*)k_team<true, false>, (const void*)k_team<false, false>,
+                              (const void*)k_team<true, true>, (const void*)k_team<false, true>})
+            cudaFuncSetAttribute(f, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)k);
@@ -2301,7 +2328,7 @@ static hf_status team_decide(Plan* p, int32_t prio, int32_t ctas_opt, double sca
 // when there are more than CTAs). team_size k > 0: every graph in one class of min(k, 16).
 static hf_status plan_team_jobs(Plan* p, const hf_run_opts& o, cudaStream_t s) {
     const int32_t prio = o.priority;
-    const int32_t scale = o.team_scale > 0 ? o.team_scale : kTeamScaleDefault;
+    const int32_t scale = o.team_scale > 0 ? o.team_scale : team_scale_default(prio);
     if (p->team_for[0] == prio && p->team_for[1] == o.team_size && p->team_for[2] == o.ctas &&
         p->team_for[3] == scale && (prio != HF_PRIO_LEARNED || p->team_cm == p->cm))
         return HF_OK;

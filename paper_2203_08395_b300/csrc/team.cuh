@@ -382,7 +382,7 @@ __device__ __forceinline__ bool team_wait_stage(unsigned long long* bar, unsigne
 // waited (bounded) for the stage copies it still had in flight; the kernel then ends.
 // A thread whose wait for a staged level runs out reads that level from global memory instead
 // (the same data), so the level completes and the team reaches its barrier.
-template <bool PAY, bool SOLO>
+template <bool PAY, bool SOLO, bool REC>
 __device__ __forceinline__ bool team_run_graph(const TeamArgs& a, const TeamJob& job, int k, int rank,
                                                const TeamSrc& src, const TeamStage* sview, unsigned long long* mbar,
                                                int4* ring, int2* iring, int* pcnt, int* s_fail, unsigned& phase) {
@@ -453,8 +453,10 @@ __device__ __forceinline__ bool team_run_graph(const TeamArgs& a, const TeamJob&
             const uint64_t pol = l2_keep_policy();
             for (int p = team_slice(s0.x, s0.y - s0.x, rank, k) + t; p < p1; p += kTeamThreads) {
                 const int v = node[p - nb];
+                const uint64_t c0 = REC ? gtimer() : 0;
                 team_store_key(a.key + v,
                                team_task_key<SOLO>(a, v, in, ptr[p - nb] - eb, ptr[p + 1 - nb] - eb, pol), pol);
+                if (REC) a.t_cost[v] = (float)(gtimer() - c0);  // the gather's time (loads in, key out)
             }
         }
         // this CTA's slice of the level's payload pieces: each warp takes the next piece from a
@@ -476,7 +478,12 @@ __device__ __forceinline__ bool team_run_graph(const TeamArgs& a, const TeamJob&
                 if (lane == 0) it = q0 + atomicAdd(&pcnt[l & 1], 1);
                 it = __shfl_sync(0xffffffffu, it, 0);
                 if (it >= q1) break;
+                const uint64_t c0 = REC ? gtimer() : 0;
                 team_run_piece(dsc[it - ib], lane);
+                if (REC) {  // a payload task's cost: its pieces' warp times summed
+                    __syncwarp();
+                    if (lane == 0) atomicAdd(a.t_cost + dsc[it - ib].task, (float)(gtimer() - c0));
+                }
             }
         }
         if (a.seg_host && rank == 0 && t == 0 && !team_host_tasks(a, job.seg0 + l))
@@ -500,7 +507,9 @@ __device__ __forceinline__ bool team_run_graph(const TeamArgs& a, const TeamJob&
 // Phase 1 (cluster launches with cluster jobs): CTA 0 of each cluster takes the next cluster
 // job and hands it to every CTA of its cluster through distributed shared memory; the cluster
 // runs it as one team. Phase 2: every CTA takes solo jobs until none is left.
-template <bool PAY>
+// REC: instrument bit 2 runs, which record per-task costs (t_cost); a separate instantiation, so
+// that the kernel of ordinary runs carries no recording code.
+template <bool PAY, bool REC>
 __global__ void __launch_bounds__(kTeamThreads, 3) k_team(const TeamArgs a) {
     extern __shared__ __align__(16) unsigned char s_stage[];  // kTeamBufs stage buffers
     __shared__ TeamStage s_view[kTeamBufs];
@@ -538,8 +547,8 @@ __global__ void __launch_bounds__(kTeamThreads, 3) k_team(const TeamArgs a) {
             const TeamJob job = s_job;
             cluster_sync();  // all have read s_job before CTA 0 may overwrite it
             if (job.graph < 0) break;
-            if (!team_run_graph<PAY, false>(a, job, k, rank, s_src, s_view, mbar, s_ring, s_iring, s_pcnt, &s_fail,
-                                            phase))
+            if (!team_run_graph<PAY, false, REC>(a, job, k, rank, s_src, s_view, mbar, s_ring, s_iring, s_pcnt,
+                                                 &s_fail, phase))
                 return;
         }
     }
@@ -552,7 +561,8 @@ __global__ void __launch_bounds__(kTeamThreads, 3) k_team(const TeamArgs a) {
         const TeamJob job = s_job;
         __syncthreads();
         if (job.graph < 0) break;
-        if (!team_run_graph<PAY, true>(a, job, 1, 0, s_src, s_view, mbar, s_ring, s_iring, s_pcnt, &s_fail, phase))
+        if (!team_run_graph<PAY, true, REC>(a, job, 1, 0, s_src, s_view, mbar, s_ring, s_iring, s_pcnt, &s_fail,
+                                            phase))
             return;
     }
 }

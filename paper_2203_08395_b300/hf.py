@@ -145,6 +145,7 @@ def load():
         "hf_batch_predict": [vp, i32, vp, P(ctypes.c_float), P(ctypes.c_float), P(ctypes.c_float)],
         "hf_run_csr_noalloc": [i32, i32, vp, vp, vp, vp, vp, ctypes.c_uint64, vp],
         "hf_batch_get_graph_times": [vp, vp, vp],
+        "hf_batch_get_task_costs": [vp, i32, vp],
         "hf_batch_last_launches": [vp, P(i32)],
         "hf_batch_team_plan": [vp, vp],
         "hf_calibration": [vp, vp],
@@ -520,6 +521,14 @@ def hf_batch_get_graph_times(b, ngraphs):
     return s0, s1
 
 
+def hf_batch_get_task_costs(b, index, n):
+    """Per-task costs (ns, float32[n]) of the last team run with instrument bit 2: graph `index`,
+    or every graph concatenated in batch order for index -1."""
+    out = np.empty(n, np.float32)
+    _check(load().hf_batch_get_task_costs(b, index, out.ctypes.data), "hf_batch_get_task_costs")
+    return out
+
+
 def hf_batch_last_launches(b):
     n = ctypes.c_int32()
     _check(load().hf_batch_last_launches(b, ctypes.byref(n)), "hf_batch_last_launches")
@@ -535,8 +544,8 @@ def hf_batch_team_plan(b, ngraphs):
 
 def hf_calibration(stream=None):
     """(level-sync ns/level, persistent ns/hop, team ns/level on one CTA, on a cluster,
-    host link GB/s host to device, device to host)."""
-    out = np.zeros(6, np.float32)
+    host link GB/s host to device, device to host, both directions at once)."""
+    out = np.zeros(7, np.float32)
     _check(load().hf_calibration(_stream_handle(stream), out.ctypes.data), "hf_calibration")
     return tuple(float(x) for x in out)
 

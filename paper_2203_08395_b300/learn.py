@@ -1,9 +1,12 @@
 """Training the cost model on timings the executor records (argument marshalling and data
 plumbing only: features, timing, the MLP and its training all run in libhf.so kernels).
 
-record()   runs a batch with per-task %globaltimer stamps (instrument=1) and returns, on the
-           device, every task's 12 features and its log cost (log ns from start to the end of
-           its successors' release);
+record()   runs a batch with the executor's cost recording on and returns, on the device, every
+           task's 12 features and its log cost in ns. By default the team executor records (the
+           executor whose planner consumes the costs): a task's cost is its thread's gather plus,
+           for a payload task, the summed warp times of its pieces, under the run's real load
+           (hf_batch_get_task_costs). executor="persistent" records the persistent executor's
+           per-task time from pop to the end of its successors' release instead;
 train()    trains a model on rows pooled from several recordings (hf_costmodel_train);
 evaluate() compares the model's and the plain heuristic's cost predictions on a recording:
            MSE of log costs, median |log(predicted / actual)| and symmetric mean absolute
@@ -18,25 +21,33 @@ from . import hf
 MIN_NS = 16.0  # costs below the timer's resolution are clamped (the timer ticks every 32 ns)
 
 
-def record(bd, stream=None, **opts):
-    """Instrumented persistent run of `bd` (a workload.BatchOnDevice); returns (X, t) CUDA
-    tensors: X [N, 12] features, t [N] log ns."""
+def record(bd, stream=None, executor="team", **opts):
+    """Instrumented run of `bd` (a workload.BatchOnDevice) by `executor` ("team": the team
+    executor under the heuristic plan, cost recording bit 2; "persistent": per-task timestamps);
+    returns (X, t) CUDA tensors: X [N, 12] features, t [N] log ns."""
     import torch
 
     o = dict(opts)
-    o.setdefault("mode", hf.HF_MODE_PERSISTENT)
-    bd.run(stream, instrument=1, **o)
-    bd.sync()
     N = bd.n_tasks
-    t0 = np.empty(N, np.int64)
-    t1 = np.empty(N, np.int64)
-    off = 0
-    for i, g in enumerate(bd.wl.graphs):
-        a, b = hf.hf_batch_get_task_times(bd.b, i, g.n)
-        t0[off:off + g.n] = a
-        t1[off:off + g.n] = b
-        off += g.n
-    dt = np.maximum((t1 - t0).astype(np.float64), MIN_NS)
+    if executor == "team":
+        o.setdefault("mode", hf.HF_MODE_TEAM)
+        o.setdefault("priority", hf.HF_PRIO_HEURISTIC)
+        bd.run(stream, instrument=4, **o)
+        bd.sync()
+        dt = np.maximum(hf.hf_batch_get_task_costs(bd.b, -1, N).astype(np.float64), MIN_NS)
+    else:
+        o.setdefault("mode", hf.HF_MODE_PERSISTENT)
+        bd.run(stream, instrument=1, **o)
+        bd.sync()
+        t0 = np.empty(N, np.int64)
+        t1 = np.empty(N, np.int64)
+        off = 0
+        for i, g in enumerate(bd.wl.graphs):
+            a, b = hf.hf_batch_get_task_times(bd.b, i, g.n)
+            t0[off:off + g.n] = a
+            t1[off:off + g.n] = b
+            off += g.n
+        dt = np.maximum((t1 - t0).astype(np.float64), MIN_NS)
     X = torch.empty((N, hf.HF_FEATURES), dtype=torch.float32, device="cuda")
     hf.hf_batch_features(bd.b, X, stream)
     t = torch.from_numpy(np.log(dt).astype(np.float32)).cuda()

@@ -1,9 +1,9 @@
-"""Kernel order in a fresh process: the benchmark's sequence (instrumented persistent runs with
-payloads, cost-model training and evaluation, then the machine-constant calibration, the
-prediction and a team run). Shared memory is not cleared between kernels, so the first team
-launches of a process run on whatever the earlier kernels left there; this runs them after the
-cost-model kernels, as the benchmark does, in a process of its own (calibration happens once
-per process)."""
+"""Kernel order in a fresh process: the benchmark's sequence (instrumented team runs with
+payloads recording task costs, an instrumented persistent run, cost-model training and
+evaluation, then the machine-constant calibration, the prediction and a team run). Shared
+memory is not cleared between kernels, so the first team launches of a process run on whatever
+the earlier kernels left there; this runs them after the cost-model kernels, as the benchmark
+does, in a process of its own (calibration happens once per process)."""
 import os
 import subprocess
 import sys
@@ -25,7 +25,7 @@ CODE = textwrap.dedent("""
     wl = S.batch(7, graphs=24, nmin=1000, nmax=40000, frac_saxpy=0.1)
     bd = BatchOnDevice(wl)
     train = [BatchOnDevice(S.batch(s, graphs=16, nmin=1000, nmax=40000, frac_saxpy=0.1)) for s in (101, 102)]
-    recs = [learn.record(tb, stream) for tb in train]
+    recs = [learn.record(tb, stream) for tb in train] + [learn.record(train[0], stream, executor="persistent")]
     for tb in train:
         tb.close()
     cm = hf.hf_costmodel_create(0)
