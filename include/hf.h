@@ -412,15 +412,16 @@ hf_status hf_batch_bottom_levels(hf_batch* b, const float* cost, float* bottom, 
 /* --- autotuning and executor choice ----------------------------------------------------- */
 
 /* Times trial runs on this batch and writes the fastest options to *best (other fields from
- * `base`, NULL = defaults) and its time to *best_ms; each trial the median of 3 timed runs
- * after one warm-up. base->mode HF_MODE_TEAM tunes the team executor (coordinate descent over
- * the cluster size for every graph, 0 = the cost model's plan, and the payload piece size);
- * any other mode tunes the persistent executor (CTA count, queue claim size, shared-memory
- * stack depth, payload piece size, payload warps, global queue or work stealing; mode
- * PERSISTENT in *best). Results are
- * cached per executor and size bucket (tasks, edges per task, payload share, depth, batch or
- * single graph), so a later call on a similar batch returns without trials unless `force`.
- * Runs the batch many times: payloads run each time (saxpy updates y). Blocks. */
+ * `base`, NULL = defaults) and its time to *best_ms; each trial is one warm-up run, then three
+ * blocks of three runs enqueued back to back (as a caller streaming runs issues them), timed
+ * by CUDA events: the median block's time per run. base->mode HF_MODE_TEAM tunes the team
+ * executor (coordinate descent over the planner's payload-cost scale, the cluster size for
+ * every graph, 0 = the cost model's plan, and the payload piece size); any other mode tunes the
+ * persistent executor (CTA count, queue claim size, shared-memory stack depth, payload piece
+ * size, payload warps, global queue or work stealing, copy warps; mode PERSISTENT in *best).
+ * Results are cached per executor and size bucket (tasks, edges per task, payload share, depth,
+ * batch or single graph), so a later call on a similar batch returns without trials unless
+ * `force`. Runs the batch many times: payloads run each time (saxpy updates y). Blocks. */
 hf_status hf_batch_autotune(hf_batch* b, void* stream, const hf_run_opts* base, int force, hf_run_opts* best,
                             float* best_ms);
 

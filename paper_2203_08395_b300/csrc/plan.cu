@@ -1775,6 +1775,9 @@ hf_status plan_refresh_priorities(Plan* p, const hf_costmodel* cm, cudaStream_t 
 
 // ------------------------------------------------------------------ autotuning
 
+// Time per run of back-to-back runs (as a caller streaming runs sees it): one warm-up run, then
+// three blocks of `reps` runs enqueued without synchronisation, each timed by CUDA events on s;
+// the median block's time per run.
 static hf_status time_runs(Plan* p, cudaStream_t s, const hf_run_opts& o, int reps, float* ms) {
     hf_run_opts w = o;
     w.time_kernel = 0;
@@ -1788,13 +1791,13 @@ static hf_status time_runs(Plan* p, cudaStream_t s, const hf_run_opts& o, int re
         return fail(HF_ECUDA, "cudaEventCreate");
     }
     std::vector<float> t;
-    for (int i = 0; i < reps && st == HF_OK; ++i) {
+    for (int blk = 0; blk < 3 && st == HF_OK; ++blk) {
         cudaEventRecord(e0, s);
-        st = plan_run(p, s, w);
+        for (int i = 0; i < reps && st == HF_OK; ++i) st = plan_run(p, s, w);
         cudaEventRecord(e1, s);
         if (st == HF_OK) st = plan_sync(p);
         float x = 0.f;
-        if (st == HF_OK && cudaEventElapsedTime(&x, e0, e1) == cudaSuccess) t.push_back(x);
+        if (st == HF_OK && cudaEventElapsedTime(&x, e0, e1) == cudaSuccess) t.push_back(x / (float)std::max(reps, 1));
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -2375,11 +2378,17 @@ static hf_status plan_team_jobs(Plan* p, const hf_run_opts& o, cudaStream_t s) {
         if (!p->d_team) return fail(HF_ENOMEM, "device allocation failed: team control");
     }
     if (!p->tev_fork) {
+        // class i (classes in decreasing cluster size) runs on stream i; the largest clusters get
+        // the highest priority, so that when every class becomes ready at once (runs enqueued
+        // back to back) the CTAs of clusters, which need whole groups of free SMs, are dispatched
+        // before single CTAs take those SMs; every class stays above the default priority of the
+        // plan's helper streams (the next view's delay gather)
         int least = 0, greatest = 0;
         cudaError_t e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->tev_fork, cudaEventDisableTiming);
         for (int i = 0; i < 5 && e == cudaSuccess; ++i) {
-            e = cudaStreamCreateWithPriority(&p->tstream[i], cudaStreamNonBlocking, greatest);
+            const int prio = least > greatest ? std::min(greatest + i, least - 1) : greatest;
+            e = cudaStreamCreateWithPriority(&p->tstream[i], cudaStreamNonBlocking, prio);
             if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->tev_join[i], cudaEventDisableTiming);
         }
         if (e != cudaSuccess) return cuda_fail(e, "team streams");
