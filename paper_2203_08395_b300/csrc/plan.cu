@@ -2029,16 +2029,16 @@ static hf_status calibrate(cudaStream_t s) {
         hf_run_opts o;
         hf_run_opts_default(&o);
         o.mode = HF_MODE_LEVELSYNC;
-        st = time_runs(p, s, o, 3, &tl);
+        st = time_runs(p, s, o, 1, &tl);
         o.mode = HF_MODE_PERSISTENT;
         o.ctas = p->num_sms;
-        if (st == HF_OK) st = time_runs(p, s, o, 3, &tp);
+        if (st == HF_OK) st = time_runs(p, s, o, 1, &tp);
         hf_run_opts_default(&o);
         o.mode = HF_MODE_TEAM;
         o.team_size = 1;
-        if (st == HF_OK) st = time_runs(p, s, o, 3, &ts);
+        if (st == HF_OK) st = time_runs(p, s, o, 1, &ts);
         o.team_size = 2;
-        if (st == HF_OK) st = time_runs(p, s, o, 3, &tc);
+        if (st == HF_OK) st = time_runs(p, s, o, 1, &tc);
     }
     if (p) plan_destroy(p);
     hf_graph_destroy(g);
