@@ -96,21 +96,27 @@ def traffic_for(kernel, workload):
 
 
 class Clocks:
-    """nvidia-smi sampler for SM clocks and throttle reasons during the timed region."""
+    """nvidia-smi sampler for SM clocks and throttle reasons during the timed region.
 
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
-         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-         "clocks_event_reasons.sw_power_cap")
+    The sampler starts before the warm-up steps (nvidia-smi takes a while to start), samples
+    every 20 ms with a timestamp, and keeps the samples taken between mark_start() and
+    mark_end() (host wall clock around the timed region: from just before its first launch to
+    the synchronisation after its last)."""
+
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index):
         self.index = index
         self.proc = None
         self.lines = []
+        self.t0 = self.t1 = None
 
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -121,6 +127,20 @@ class Clocks:
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
+    def mark_start(self):
+        self.t0 = time.time()
+
+    def mark_end(self):
+        self.t1 = time.time()
+
+    @staticmethod
+    def _when(stamp):
+        import datetime
+        try:
+            return datetime.datetime.strptime(stamp.strip(), "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            return None
+
     def stop(self):
         if not self.proc:
             return None
@@ -130,23 +150,26 @@ class Clocks:
         except Exception:
             self.proc.kill()
         self.t.join(timeout=2)
-        sm, mx, reasons = [], 0.0, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        rows = []
         for ln in self.lines:
             f = [x.strip() for x in ln.split(",")]
-            if len(f) < 9:
+            if len(f) < 10:
                 continue
             try:
-                sm.append(float(f[1]))
-                mx = max(mx, float(f[2]))
+                rows.append((self._when(f[0]), float(f[2]), float(f[3]), f[6:10]))
             except ValueError:
                 continue
-            for nm, v in zip(names, f[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(nm)
-        if not sm:
+        inside = [r for r in rows if r[0] is not None and self.t0 is not None and self.t0 <= r[0] <= self.t1]
+        window = "timed region"
+        if not inside:  # a region shorter than the sampling period: the samples nearest to it
+            window = "nearest samples (timed region shorter than the sampling period)"
+            inside = sorted(rows, key=lambda r: abs((r[0] or 0) - (self.t0 or 0)))[:2]
+        if not inside:
             return None
-        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({nm for r in inside for nm, v in zip(names, r[3]) if v.lower().startswith("active")})
+        return {"sm_mhz": float(np.median([r[1] for r in inside])), "sm_max_mhz": max(r[2] for r in inside),
+                "reasons": reasons, "samples": len(inside), "window": window}
 
 
 def algorithmic_bytes(wl):
@@ -396,18 +419,22 @@ def main():
     t_setup = time.time() - t_setup
 
     def timed(opts_, steps, warmup, clocks=None):
+        if clocks:
+            clocks.start()
         for _ in range(warmup):
             bd.run(stream, **opts_)
         bd.sync()
         barrier()
         evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
         if clocks:
-            clocks.start()
+            clocks.mark_start()
         evs[0].record(stream)
         for i in range(steps):
             bd.run(stream, **opts_)
             evs[i + 1].record(stream)
         torch.cuda.synchronize()
+        if clocks:
+            clocks.mark_end()
         clk = clocks.stop() if clocks else None
         st = bd.sync(check=False)
         barrier()
