@@ -149,10 +149,11 @@ typedef struct {
                                costs (one CTA per graph under HF_PRIO_FIFO) */
     int32_t team_scale;     /* team planner: factor on the predicted payload cost, standing for
                                the slowdown of memory traffic when every graph streams at once;
-                               larger values give payload-heavy graphs larger teams; 0 = 4 for
-                               heuristic costs (a 512-element piece: ~0.75 us for a warp alone,
-                               ~3 us when every SM streams, measured on B300), 1 for learned costs
-                               (recorded under the team executor's real load) */
+                               larger values give payload-heavy graphs larger teams; s > 0: s,
+                               s < 0: 1 / -s; 0 = 4 for heuristic costs (a 512-element piece:
+                               ~0.75 us for a warp alone, ~3 us when every SM streams, measured on
+                               B300), 1 for learned costs (recorded under the team executor's
+                               real load) */
     int32_t steal_ring;     /* persistent: 0 = one global ready queue; > 0 = work stealing
                                (Section III-C): every CTA owns a ring of this many slots (rounded
                                up to a power of two, 64..16384) that its warps push ready tasks
@@ -166,7 +167,11 @@ typedef struct {
                                and behind the other tasks; 0 = copies run like other payloads.
                                (The level-synchronous executor always runs copies as copy-engine
                                nodes of its CUDA graph, each ordered only by its own edges.) */
-    int32_t pad_;
+    int32_t team_fold;      /* team planner (team_size 0): 0 = one launch per team size, run
+                               concurrently; K in {2, 4, 8, 16} = one launch with cluster size K:
+                               every graph gets a K-CTA cluster or one CTA, the clusters take their
+                               graphs first and then, like the other CTAs, single-CTA graphs; -1 =
+                               one launch, K chosen by the planner's predicted makespan */
 } hf_run_opts;
 
 void hf_run_opts_default(hf_run_opts* opts);
@@ -415,8 +420,9 @@ hf_status hf_batch_bottom_levels(hf_batch* b, const float* cost, float* bottom, 
  * `base`, NULL = defaults) and its time to *best_ms; each trial is one warm-up run, then three
  * blocks of three runs enqueued back to back (as a caller streaming runs issues them), timed
  * by CUDA events: the median block's time per run. base->mode HF_MODE_TEAM tunes the team
- * executor (coordinate descent over the planner's payload-cost scale, the cluster size for
- * every graph, 0 = the cost model's plan, and the payload piece size); any other mode tunes the
+ * executor (coordinate descent over the planner's payload-cost scale from 1/4 to 16, the
+ * cluster size for every graph, 0 = the cost model's plan, the payload piece size, and one launch
+ * per team size or one folded launch); any other mode tunes the
  * persistent executor (CTA count, queue claim size, shared-memory stack depth, payload piece
  * size, payload warps, global queue or work stealing, copy warps; mode PERSISTENT in *best).
  * Results are cached per executor and size bucket (tasks, edges per task, payload share, depth,

@@ -74,10 +74,11 @@ struct Plan {
     size_t cap_jobs = 0;
     int32_t njobs = 0;
     struct TeamClass {
-        int32_t k;      // cluster size of the class's launch (1: single CTAs)
-        int32_t job0;   // its jobs in d_jobs
+        int32_t k;       // cluster size of the class's launch (1: single CTAs)
+        int32_t job0;    // its jobs in d_jobs
         int32_t njobs;
-        int32_t grid;   // CTAs launched
+        int32_t ncjobs;  // of which cluster jobs (first; the rest are single-CTA jobs)
+        int32_t grid;    // CTAs launched
     };
     std::vector<TeamClass> tclass;    // one launch per class, run concurrently
     // one stream per class at the device's highest stream priority: pending team CTAs are
@@ -99,7 +100,7 @@ struct Plan {
     int32_t* d_hdone = nullptr;
     int32_t* d_post_ctr = nullptr;    // posts so far (device counter)
     std::thread proxy;                // runs the host tasks of the current run
-    int32_t team_for[4] = {-1, -1, -1, -1};  // priority, team_size, CTAs, scale the jobs were built for
+    int32_t team_for[5] = {-1, -1, -1, -1, -2};  // priority, team_size, CTAs, scale, fold the jobs were built for
     const hf_costmodel* team_cm = nullptr;
 
     // device buffers
@@ -222,11 +223,16 @@ constexpr int kTeamScaleDefault = 4;
 // Learned costs are recorded by the team executor under its real load (contention included), so
 // the planner takes them as they are.
 static int team_scale_default(int32_t prio) { return prio == HF_PRIO_LEARNED ? 1 : kTeamScaleDefault; }
+// hf_run_opts::team_scale as a factor: s > 0 is s, s < 0 is 1 / -s, 0 is the default
+static double team_scale_factor(int32_t s, int32_t prio) {
+    if (s == 0) s = team_scale_default(prio);
+    return s > 0 ? (double)s : 1.0 / (double)(-s);
+}
 static int team_capacity(const Plan* p, int k);
 static size_t team_smem(const Plan* p);
 static void team_smem_attr(const Plan* p);
 static hf_status team_decide(Plan* p, int32_t prio, int32_t ctas_opt, double scale, cudaStream_t s,
-                             std::vector<int>* k_out, std::vector<int32_t>* order_out, double* M_out);
+                             std::vector<int>* k_out, std::vector<int32_t>* order_out, double* M_out, int fold_k = 0);
 hf_status plan_prepare_priority(Plan* p, int32_t priority, const hf_costmodel* cm, cudaStream_t s);
 
 void plan_set_costmodel(Plan* p, const hf_costmodel* cm) {
@@ -1223,43 +1229,54 @@ hf_status plan_run(Plan* p, cudaStream_t s, const hf_run_opts& o, bool keep_stat
             if (e == cudaSuccess) e = cudaMemsetAsync(&p->d_ctrl->abort, 0, sizeof(int32_t), s);
             if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
             if (o.time_kernel) cudaEventRecord(p->kev0, s);
-            // one launch per team class, all at once, on the plan's class streams forked from
-            // the caller's stream and joined back into it
+            // one launch per team class, in decreasing cluster size, on the plan's high-priority
+            // stream (forked from the caller's stream and joined back into it), each after the
+            // first a programmatic dependent of the one before: a class is launched once every CTA
+            // of the previous class has started, so the clusters, which need whole groups of free
+            // SMs, are placed before smaller teams and single CTAs fill the GPU, and the classes
+            // then run concurrently; every kernel waits for its predecessor only at its end, so the
+            // last one's completion covers them all
             const size_t nc = p->tclass.size();
-            if ((e = cudaEventRecord(p->tev_fork, s)) != cudaSuccess) return cuda_fail(e, "team fork");
-            for (size_t i = 0; i < nc; ++i)
-                if ((e = cudaStreamWaitEvent(p->tstream[i], p->tev_fork, 0)) != cudaSuccess)
-                    return cuda_fail(e, "team fork");
+            if ((e = cudaEventRecord(p->tev_fork, s)) != cudaSuccess ||
+                (e = cudaStreamWaitEvent(p->tstream[0], p->tev_fork, 0)) != cudaSuccess)
+                return cuda_fail(e, "team fork");
             for (size_t i = 0; i < nc; ++i) {
                 const Plan::TeamClass& c = p->tclass[i];
                 TeamArgs ai = a;
                 ai.jobs = p->d_jobs + c.job0;
                 ai.njobs = c.njobs;
-                ai.ncjobs = c.k > 1 ? c.njobs : 0;
+                ai.ncjobs = c.ncjobs;
                 ai.team = p->d_team + (size_t)kTeamWords * i;
                 cudaLaunchConfig_t cfg = {};
                 cfg.gridDim = dim3((unsigned)c.grid);
                 cfg.blockDim = dim3(kTeamThreads);
                 cfg.dynamicSmemBytes = team_smem(p);
-                cfg.stream = p->tstream[i];
-                cudaLaunchAttribute at[1];
-                at[0].id = cudaLaunchAttributeClusterDimension;
-                at[0].val.clusterDim.x = (unsigned)c.k;
-                at[0].val.clusterDim.y = 1;
-                at[0].val.clusterDim.z = 1;
+                cfg.stream = p->tstream[0];
+                cudaLaunchAttribute at[2];
+                unsigned na = 0;
+                if (c.k > 1) {
+                    at[na].id = cudaLaunchAttributeClusterDimension;
+                    at[na].val.clusterDim.x = (unsigned)c.k;
+                    at[na].val.clusterDim.y = 1;
+                    at[na].val.clusterDim.z = 1;
+                    ++na;
+                }
+                if (i > 0) {
+                    at[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+                    at[na].val.programmaticStreamSerializationAllowed = 1;
+                    ++na;
+                }
                 cfg.attrs = at;
-                cfg.numAttrs = c.k > 1 ? 1 : 0;
+                cfg.numAttrs = na;
                 if (rec) e = p->npay ? cudaLaunchKernelEx(&cfg, k_team<true, true>, ai)
                                      : cudaLaunchKernelEx(&cfg, k_team<false, true>, ai);
                 else e = p->npay ? cudaLaunchKernelEx(&cfg, k_team<true, false>, ai)
                                  : cudaLaunchKernelEx(&cfg, k_team<false, false>, ai);
                 if (e != cudaSuccess) return cuda_fail(e, "k_team launch");
             }
-            for (size_t i = 0; i < nc; ++i) {
-                if ((e = cudaEventRecord(p->tev_join[i], p->tstream[i])) != cudaSuccess ||
-                    (e = cudaStreamWaitEvent(s, p->tev_join[i], 0)) != cudaSuccess)
-                    return cuda_fail(e, "team join");
-            }
+            if ((e = cudaEventRecord(p->tev_join[0], p->tstream[0])) != cudaSuccess ||
+                (e = cudaStreamWaitEvent(s, p->tev_join[0], 0)) != cudaSuccess)
+                return cuda_fail(e, "team join");
             if (o.time_kernel) cudaEventRecord(p->kev1, s);
             if (!p->host_tasks.empty()) {
                 const uint64_t limit = o.spin_limit_ns ? o.spin_limit_ns : 2000000000ull;
@@ -1835,18 +1852,23 @@ static hf_status autotune_team(Plan* p, cudaStream_t s, const hf_run_opts& base,
     if (st != HF_OK) return st;
     const std::vector<int> size_v{0, 1, 2, 4, 8, 16};
     const std::vector<int64_t> chunk_v{256, 512, 1024, 2048};
-    const std::vector<int> scale_v{1, 2, 4, 8, 16};
+    const std::vector<int> scale_v{-4, -2, 1, 2, 4, 8, 16};  // (negative: 1/4, 1/2)
+    const std::vector<int> fold_v{0, -1, 4, 8, 16};
     for (int round = 0; round < 2; ++round) {
-        for (int dim = 0; dim < 3; ++dim) {  // planner scale, then cluster size, then piece size
-            if (dim != 1 && p->npay == 0) continue;
-            if (dim == 0 && (cur.team_size != 0 || cur.priority == HF_PRIO_FIFO)) continue;
-            const size_t nv = dim == 0 ? scale_v.size() : dim == 1 ? size_v.size() : chunk_v.size();
+        for (int dim = 0; dim < 4; ++dim) {  // planner scale, cluster size, piece size, one launch or one per size
+            if (dim == 2 && p->npay == 0) continue;
+            if ((dim == 0 || dim == 3) && (cur.team_size != 0 || cur.priority == HF_PRIO_FIFO)) continue;
+            if (dim == 0 && p->npay == 0) continue;
+            const size_t nv = dim == 0 ? scale_v.size() : dim == 1 ? size_v.size() : dim == 2 ? chunk_v.size()
+                                                                                               : fold_v.size();
             for (size_t i = 0; i < nv; ++i) {
                 hf_run_opts t = cur;
                 if (dim == 0) t.team_scale = scale_v[i];
                 else if (dim == 1) t.team_size = size_v[i];
-                else t.chunk_elems = chunk_v[i];
-                if (t.team_size == cur.team_size && t.chunk_elems == cur.chunk_elems && t.team_scale == cur.team_scale)
+                else if (dim == 2) t.chunk_elems = chunk_v[i];
+                else t.team_fold = fold_v[i];
+                if (t.team_size == cur.team_size && t.chunk_elems == cur.chunk_elems && t.team_scale == cur.team_scale &&
+                    t.team_fold == cur.team_fold)
                     continue;
                 float ms = 0.f;
                 if ((st = time_runs(p, s, t, 3, &ms)) != HF_OK) return st;
@@ -1882,6 +1904,7 @@ hf_status plan_autotune(Plan* p, cudaStream_t s, const hf_run_opts& base, int fo
             best->team_scale = it->second.first.team_scale;
             best->steal_ring = it->second.first.steal_ring;
             best->copy_warps = it->second.first.copy_warps;
+            best->team_fold = it->second.first.team_fold;
             *best_ms = it->second.second;
             return HF_OK;
         }
@@ -2232,7 +2255,7 @@ static int team_capacity(const Plan* p, int k) {
 // plan's makespan in unscaled costs, comparable with the other executors' predictions. FIFO:
 // one CTA per graph in batch order, M = 0.
 static hf_status team_decide(Plan* p, int32_t prio, int32_t ctas_opt, double scale, cudaStream_t s,
-                             std::vector<int>* k_out, std::vector<int32_t>* order_out, double* M_out) {
+                             std::vector<int>* k_out, std::vector<int32_t>* order_out, double* M_out, int fold_k) {
     const int32_t G = p->ngraphs;
     std::vector<int32_t>& order = *order_out;
     std::vector<int>& k = *k_out;
@@ -2272,10 +2295,12 @@ static hf_status team_decide(Plan* p, int32_t prio, int32_t ctas_opt, double sca
         T[(size_t)g] = team_time(p, pay_ns, g, 1, scale);
         work += T[(size_t)g];
     }
-    int cap1 = team_capacity(p, 1);
-    if (ctas_opt > 0) cap1 = std::min(cap1, ctas_opt);
     int capk[17] = {0};
-    for (int kk = 2; kk <= kTeamMaxCluster; kk *= 2) capk[kk] = ctas_opt > 0 ? 0 : team_capacity(p, kk);
+    for (int kk = 2; kk <= kTeamMaxCluster; kk *= 2)
+        capk[kk] = ctas_opt > 0 || (fold_k > 0 && kk != fold_k) ? 0 : team_capacity(p, kk);
+    // folded: one launch of fold_k-CTA clusters, whose CTAs also run the single-CTA graphs
+    int cap1 = fold_k > 0 ? capk[fold_k] : team_capacity(p, 1);
+    if (ctas_opt > 0) cap1 = std::min(cap1, ctas_opt);
     // predicted makespan: the longest team, or the single-CTA graphs' total over the CTAs left
     // to them (they queue when there are more of them than CTAs)
     int cl_ctas = 0, inclass[17] = {0};
@@ -2290,7 +2315,7 @@ static hf_status team_decide(Plan* p, int32_t prio, int32_t ctas_opt, double sca
     while (!heap.empty()) {
         const Item top = heap.top();
         const int32_t g = top.second;
-        const int k0 = k[(size_t)g], k1 = 2 * k0;
+        const int k0 = k[(size_t)g], k1 = fold_k > 0 ? (k0 == 1 ? fold_k : 2 * kTeamMaxCluster) : 2 * k0;
         if (k1 > kTeamMaxCluster || (inclass[k1] + 1) * k1 > capk[k1]) break;
         const int cl1 = cl_ctas + k1 - (k0 > 1 ? k0 : 0);
         const int ns1 = nsolo - (k0 == 1 ? 1 : 0);
@@ -2331,14 +2356,41 @@ static hf_status team_decide(Plan* p, int32_t prio, int32_t ctas_opt, double sca
 // when there are more than CTAs). team_size k > 0: every graph in one class of min(k, 16).
 static hf_status plan_team_jobs(Plan* p, const hf_run_opts& o, cudaStream_t s) {
     const int32_t prio = o.priority;
-    const int32_t scale = o.team_scale > 0 ? o.team_scale : team_scale_default(prio);
+    const int32_t scale = o.team_scale != 0 ? o.team_scale : team_scale_default(prio);
+    const int32_t fold = o.team_size > 0 ? 0 : o.team_fold;
+    if (fold != 0 && fold != -1 && fold != 2 && fold != 4 && fold != 8 && fold != 16)
+        return fail(HF_EINVAL, "team_fold must be 0, -1, 2, 4, 8 or 16");
     if (p->team_for[0] == prio && p->team_for[1] == o.team_size && p->team_for[2] == o.ctas &&
-        p->team_for[3] == scale && (prio != HF_PRIO_LEARNED || p->team_cm == p->cm))
+        p->team_for[3] == scale && p->team_for[4] == fold && (prio != HF_PRIO_LEARNED || p->team_cm == p->cm))
         return HF_OK;
     std::vector<int32_t> order;
     std::vector<int> k;
     double M = 0.0;
-    hf_status st = team_decide(p, o.team_size > 0 ? HF_PRIO_FIFO : prio, o.ctas, (double)scale, s, &k, &order, &M);
+    const int32_t dprio = o.team_size > 0 ? HF_PRIO_FIFO : prio;
+    int fold_k = fold;
+    hf_status st = HF_OK;
+    if (fold == -1) {  // one launch: the cluster size whose plan has the smallest predicted makespan
+        double best = INFINITY;
+        for (int kk = 2; kk <= kTeamMaxCluster && st == HF_OK; kk *= 2) {
+            std::vector<int32_t> o2;
+            std::vector<int> k2;
+            double m2 = 0.0;
+            if (team_capacity(p, kk) < kk) continue;
+            st = team_decide(p, dprio, o.ctas, team_scale_factor(scale, prio), s, &k2, &o2, &m2, kk);
+            if (st == HF_OK && m2 < best) {
+                best = m2;
+                fold_k = kk;
+                k.swap(k2);
+                order.swap(o2);
+                M = m2;
+            }
+        }
+        if (st == HF_OK && fold_k < 0) fold_k = 0;  // no cluster fits: single CTAs
+        if (st == HF_OK && fold_k == 0)
+            st = team_decide(p, dprio, o.ctas, team_scale_factor(scale, prio), s, &k, &order, &M);
+    } else {
+        st = team_decide(p, dprio, o.ctas, team_scale_factor(scale, prio), s, &k, &order, &M, fold_k);
+    }
     if (st != HF_OK) return st;
     if (o.team_size > 0)
         for (auto& x : k) x = std::min(o.team_size, kTeamMaxCluster);
@@ -2348,22 +2400,41 @@ static hf_status plan_team_jobs(Plan* p, const hf_run_opts& o, cudaStream_t s) {
     p->tclass.clear();
     int cap1 = team_capacity(p, 1);
     if (o.ctas > 0) cap1 = std::min(cap1, o.ctas);
-    int used = 0;
-    for (int kk = kTeamMaxCluster; kk >= 1; --kk) {
-        Plan::TeamClass c{kk, (int32_t)jobs.size(), 0, 0};
+    int nclustered = 0;
+    for (int32_t g : order) nclustered += k[(size_t)g] > 1 ? 1 : 0;
+    if (fold_k > 0 && nclustered > 0) {
+        // one launch with cluster size fold_k: its cluster jobs first, then every single-CTA job
+        Plan::TeamClass c{fold_k, 0, 0, 0, 0};
         for (int32_t g : order)
-            if (k[(size_t)g] == kk) jobs.push_back(TeamJob{g, 0, p->seg_first[(size_t)g], p->glevels[(size_t)g]});
-        c.njobs = (int32_t)jobs.size() - c.job0;
-        if (c.njobs == 0) continue;
-        if (kk > 1) {
-            const int capk = team_capacity(p, kk);
-            if (capk < kk) return fail(HF_ENOTSUP, "no resident cluster of " + std::to_string(kk) + " CTAs");
-            c.grid = std::min(c.njobs * kk, (capk / kk) * kk);
-        } else {
-            c.grid = std::max(1, std::min(c.njobs, std::max(cap1 - used, 1)));
-        }
-        used += c.grid;
+            if (k[(size_t)g] == fold_k) jobs.push_back(TeamJob{g, 0, p->seg_first[(size_t)g], p->glevels[(size_t)g]});
+        c.ncjobs = (int32_t)jobs.size();
+        for (int32_t g : order)
+            if (k[(size_t)g] == 1) jobs.push_back(TeamJob{g, 0, p->seg_first[(size_t)g], p->glevels[(size_t)g]});
+        c.njobs = (int32_t)jobs.size();
+        const int capk = team_capacity(p, fold_k);
+        if (capk < fold_k) return fail(HF_ENOTSUP, "no resident cluster of " + std::to_string(fold_k) + " CTAs");
+        const int want = c.ncjobs * fold_k + (c.njobs - c.ncjobs);
+        c.grid = std::min((want + fold_k - 1) / fold_k, capk / fold_k) * fold_k;
         p->tclass.push_back(c);
+    } else {
+        int used = 0;
+        for (int kk = kTeamMaxCluster; kk >= 1; --kk) {
+            Plan::TeamClass c{kk, (int32_t)jobs.size(), 0, 0, 0};
+            for (int32_t g : order)
+                if (k[(size_t)g] == kk) jobs.push_back(TeamJob{g, 0, p->seg_first[(size_t)g], p->glevels[(size_t)g]});
+            c.njobs = (int32_t)jobs.size() - c.job0;
+            if (c.njobs == 0) continue;
+            c.ncjobs = kk > 1 ? c.njobs : 0;
+            if (kk > 1) {
+                const int capk = team_capacity(p, kk);
+                if (capk < kk) return fail(HF_ENOTSUP, "no resident cluster of " + std::to_string(kk) + " CTAs");
+                c.grid = std::min(c.njobs * kk, (capk / kk) * kk);
+            } else {
+                c.grid = std::max(1, std::min(c.njobs, std::max(cap1 - used, 1)));
+            }
+            used += c.grid;
+            p->tclass.push_back(c);
+        }
     }
     if (p->tclass.size() > 5) return fail(HF_ENOTSUP, "too many team classes");
     const size_t bytes = std::max<size_t>(sizeof(TeamJob) * jobs.size(), 16);
@@ -2378,19 +2449,13 @@ static hf_status plan_team_jobs(Plan* p, const hf_run_opts& o, cudaStream_t s) {
         if (!p->d_team) return fail(HF_ENOMEM, "device allocation failed: team control");
     }
     if (!p->tev_fork) {
-        // class i (classes in decreasing cluster size) runs on stream i; the largest clusters get
-        // the highest priority, so that when every class becomes ready at once (runs enqueued
-        // back to back) the CTAs of clusters, which need whole groups of free SMs, are dispatched
-        // before single CTAs take those SMs; every class stays above the default priority of the
-        // plan's helper streams (the next view's delay gather)
+        // the classes run on a stream at the device's highest priority, above the default priority
+        // of the plan's helper streams (the next view's delay gather)
         int least = 0, greatest = 0;
         cudaError_t e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->tev_fork, cudaEventDisableTiming);
-        for (int i = 0; i < 5 && e == cudaSuccess; ++i) {
-            const int prio = least > greatest ? std::min(greatest + i, least - 1) : greatest;
-            e = cudaStreamCreateWithPriority(&p->tstream[i], cudaStreamNonBlocking, prio);
-            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->tev_join[i], cudaEventDisableTiming);
-        }
+        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&p->tstream[0], cudaStreamNonBlocking, greatest);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->tev_join[0], cudaEventDisableTiming);
         if (e != cudaSuccess) return cuda_fail(e, "team streams");
     }
     cudaError_t e = cudaSuccess;
@@ -2402,6 +2467,7 @@ static hf_status plan_team_jobs(Plan* p, const hf_run_opts& o, cudaStream_t s) {
     p->team_for[1] = o.team_size;
     p->team_for[2] = o.ctas;
     p->team_for[3] = scale;
+    p->team_for[4] = fold;
     p->team_cm = p->cm;
     return HF_OK;
 }

@@ -510,7 +510,7 @@ __device__ __forceinline__ bool team_run_graph(const TeamArgs& a, const TeamJob&
 // REC: instrument bit 2 runs, which record per-task costs (t_cost); a separate instantiation, so
 // that the kernel of ordinary runs carries no recording code.
 template <bool PAY, bool REC>
-__global__ void __launch_bounds__(kTeamThreads, 3) k_team(const TeamArgs a) {
+__device__ __forceinline__ void k_team_body(const TeamArgs& a) {
     extern __shared__ __align__(16) unsigned char s_stage[];  // kTeamBufs stage buffers
     __shared__ TeamStage s_view[kTeamBufs];
     __shared__ TeamSrc s_src;
@@ -565,6 +565,17 @@ __global__ void __launch_bounds__(kTeamThreads, 3) k_team(const TeamArgs a) {
                                             phase))
             return;
     }
+}
+
+// The class launches of a run are chained by programmatic dependent launch (see plan_run): each
+// CTA allows the next class to launch as soon as it starts, and waits for the previous class's
+// grid to complete only when it is done (a no-op for the first class), so the next class's
+// kernel completes after every earlier one.
+template <bool PAY, bool REC>
+__global__ void __launch_bounds__(kTeamThreads, 3) k_team(const TeamArgs a) {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    k_team_body<PAY, REC>(a);
+    asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
 }  // namespace hf

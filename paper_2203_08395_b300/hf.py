@@ -66,7 +66,7 @@ class hf_run_opts(ctypes.Structure):
                 ("stall_task", ctypes.c_int32), ("time_kernel", ctypes.c_int32),
                 ("payload_warps", ctypes.c_int32), ("team_size", ctypes.c_int32),
                 ("team_scale", ctypes.c_int32), ("steal_ring", ctypes.c_int32),
-                ("copy_warps", ctypes.c_int32), ("pad_", ctypes.c_int32)]
+                ("copy_warps", ctypes.c_int32), ("team_fold", ctypes.c_int32)]
 
 
 class hf_graph_info_t(ctypes.Structure):

@@ -45,6 +45,9 @@ EXECUTORS = {
     "team_heur": dict(mode=hf.HF_MODE_TEAM, priority=hf.HF_PRIO_HEURISTIC),
     "team_k2": dict(mode=hf.HF_MODE_TEAM, team_size=2),
     "team_k5": dict(mode=hf.HF_MODE_TEAM, team_size=5, ctas=12),
+    # one launch: graphs on 8-CTA clusters (or the planner's cluster size) and single CTAs together
+    "team_fold8": dict(mode=hf.HF_MODE_TEAM, priority=hf.HF_PRIO_HEURISTIC, team_fold=8, team_scale=1),
+    "team_fold_auto": dict(mode=hf.HF_MODE_TEAM, priority=hf.HF_PRIO_HEURISTIC, team_fold=-1),
 }
 
 
@@ -79,7 +82,8 @@ def test_layered10k_bit_exact(ex):
     gd.close()
 
 
-@pytest.mark.parametrize("ex", ["levelsync", "persistent", "persistent_claim8", "steal_small", "team", "team_k5"])
+@pytest.mark.parametrize("ex", ["levelsync", "persistent", "persistent_claim8", "steal_small", "team", "team_k5",
+                                "team_fold_auto"])
 def test_random_graphs_100_seeds(ex):
     rng = np.random.default_rng(5)
     for seed in range(100):
@@ -210,7 +214,7 @@ def test_mixed100k_full_size_sampled():
     gd.close()
 
 
-@pytest.mark.parametrize("ex", ["levelsync", "persistent", "steal", "team", "team_heur"])
+@pytest.mark.parametrize("ex", ["levelsync", "persistent", "steal", "team", "team_heur", "team_fold8", "team_fold_auto"])
 def test_batch256_full_size(ex):
     wl = S.config("batch256")
     bd = BatchOnDevice(wl)
@@ -223,7 +227,7 @@ def test_batch256_full_size(ex):
 
 
 @pytest.mark.parametrize("ex", ["levelsync", "persistent", "persistent_payw2", "steal_small", "steal_payw2", "team",
-                                "team_heur", "team_k2"])
+                                "team_heur", "team_k2", "team_fold8", "team_fold_auto"])
 def test_batch_mixed_small(ex):
     wl = S.batch(2, graphs=12, nmin=500, nmax=20000, frac_saxpy=0.1, sx_min=1, sx_max=3000)
     bd = BatchOnDevice(wl)
@@ -253,6 +257,13 @@ def test_team_plan_reports_team_sizes():
     bd.sync()
     k = hf.hf_batch_team_plan(bd.b, G)
     assert set(k.tolist()) <= {1, 2, 4, 8, 16}
+    for i, spec in enumerate(wl.graphs):
+        np.testing.assert_array_equal(bits(bd.arrivals(i)), bits(oracle.run_spec(spec)["arr"]))
+    # one launch with 4-CTA clusters: every graph on a 4-CTA cluster or one CTA, a single kernel
+    bd.run(mode=hf.HF_MODE_TEAM, priority=hf.HF_PRIO_HEURISTIC, team_fold=4, team_scale=1)
+    bd.sync()
+    k = hf.hf_batch_team_plan(bd.b, G)
+    assert set(k.tolist()) <= {1, 4} and hf.hf_batch_last_launches(bd.b) == 1
     for i, spec in enumerate(wl.graphs):
         np.testing.assert_array_equal(bits(bd.arrivals(i)), bits(oracle.run_spec(spec)["arr"]))
     bd.close()
