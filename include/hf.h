@@ -168,7 +168,8 @@ typedef struct {
                                (The level-synchronous executor always runs copies as copy-engine
                                nodes of its CUDA graph, each ordered only by its own edges.) */
     int32_t team_fold;      /* team planner (team_size 0): 0 = one launch per team size, run
-                               concurrently; K in {2, 4, 8, 16} = one launch with cluster size K:
+                               concurrently (each launched once the larger clusters before it
+                               are resident); K in {2, 4, 8, 16} = one launch with cluster size K:
                                every graph gets a K-CTA cluster or one CTA, the clusters take their
                                graphs first and then, like the other CTAs, single-CTA graphs; -1 =
                                one launch, K chosen by the planner's predicted makespan */

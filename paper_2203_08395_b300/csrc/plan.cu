@@ -80,9 +80,9 @@ struct Plan {
         int32_t ncjobs;  // of which cluster jobs (first; the rest are single-CTA jobs)
         int32_t grid;    // CTAs launched
     };
-    std::vector<TeamClass> tclass;    // one launch per class, run concurrently
-    // one stream per class at the device's highest stream priority: pending team CTAs are
-    // dispatched before those of the plan's helper kernels (the next view's delay gather)
+    std::vector<TeamClass> tclass;    // one launch per class, chained (plan_run), run concurrently
+    // the classes' stream (tstream[0]) at the device's highest stream priority: pending team
+    // CTAs are dispatched before those of the plan's helper kernels (the next view's delay gather)
     cudaStream_t tstream[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     cudaEvent_t tev_fork = nullptr;
     cudaEvent_t tev_join[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
