@@ -3,13 +3,14 @@
 // Algorithm 1). It predicts a task's log cost (log ns) from 12 per-task features; the
 // executor turns predictions into critical-path priorities and an executor choice (plan.cu).
 //
-// Kernels: forward (one thread per row, parameters staged in shared memory with the weights
-// rounded to BF16), a fused forward+backward that reduces the batch's weight gradients in
-// shared memory (one block of 64 rows) before one atomicAdd per parameter and block, and an
-// element-wise Adam step. The model is tiny (5,057 parameters, ~10 kFLOP per row), so these
-// run on CUDA cores; on the hot path the executor only reads the resulting priorities.
+// Kernels: forward on the tensor cores (warp-level BF16 MMAs with FP32 accumulation, 16 rows per
+// warp tile), a fused forward+backward that reduces the batch's weight gradients in shared
+// memory (one block of 64 rows, one thread per row on CUDA cores) before one atomicAdd per
+// parameter and block, and an element-wise Adam step. On the hot path the executor only reads
+// the resulting priorities and plans.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -71,17 +72,120 @@ __device__ __forceinline__ float row_forward(const float* s, const float* x, flo
     return y;
 }
 
+// ---- forward pass on the tensor cores (inference over every task of a plan)
+//
+// Each warp runs 16-row tiles through warp-level BF16 MMAs with FP32 accumulation
+// (mma.sync m16n8k16): layer 1 is one 16x16 A tile (the 12 features, zero-padded to 16) times
+// eight 16x8 B tiles of W1^T, layer 2 four 16x16 A tiles times eight B tiles of W2^T per k-step;
+// the FP32 accumulators of layer 1, after bias, ReLU and BF16 rounding, are exactly the A
+// fragments of layer 2 (the accumulator of n-tiles 2k and 2k + 1 is A's k-tile k), so the
+// activations never leave registers; layer 3 (64 -> 1) is a dot product reduced over the four
+// threads that hold a row. Same rounding points as row_forward (BF16 inputs, weights and hidden
+// activations; FP32 accumulation in a different order).
+constexpr int kW1Ld = 24;  // bf16 row pitch of W1 (16 used): conflict-free fragment loads
+constexpr int kW2Ld = 72;  // bf16 row pitch of W2 (64 used)
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);  // .x = lo (low half), .y = hi
+    return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
 __global__ void __launch_bounds__(128) k_mlp_forward(const float* __restrict__ P, const float* __restrict__ X,
                                                      int64_t n, float* __restrict__ y) {
-    __shared__ float s[kNP];
-    stage_params(s, P);
+    __shared__ __align__(16) __nv_bfloat16 w1[kH * kW1Ld];
+    __shared__ __align__(16) __nv_bfloat16 w2[kH * kW2Ld];
+    __shared__ float b1[kH], b2[kH], w3[kH];
+    __shared__ float b3;
+    for (int i = threadIdx.x; i < kH * kW1Ld; i += blockDim.x) {
+        const int o = i / kW1Ld, k = i % kW1Ld;
+        w1[i] = __float2bfloat16_rn(k < kIn ? P[kOffW1 + o * kIn + k] : 0.f);
+    }
+    for (int i = threadIdx.x; i < kH * kW2Ld; i += blockDim.x) {
+        const int o = i / kW2Ld, k = i % kW2Ld;
+        w2[i] = __float2bfloat16_rn(k < kH ? P[kOffW2 + o * kH + k] : 0.f);
+    }
+    for (int i = threadIdx.x; i < kH; i += blockDim.x) {
+        b1[i] = P[kOffB1 + i];
+        b2[i] = P[kOffB2 + i];
+        w3[i] = bf16r(P[kOffW3 + i]);
+    }
+    if (threadIdx.x == 0) b3 = P[kOffB3];
     __syncthreads();
-    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n) return;
-    float x[kIn], h1[kH], h2[kH];
+    const int lane = threadIdx.x & 31, g = lane >> 2, tq = lane & 3;
+    const int64_t tiles = (n + 15) / 16;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t tile = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); tile < tiles; tile += nwarps) {
+        const int64_t r0 = tile * 16 + g, r1 = r0 + 8;
+        // layer 1: A = features of rows r0 / r1, columns 2tq, 2tq+1 (and +8 when below 12)
+        uint32_t a[4];
+        {
+            float x0 = 0.f, x1 = 0.f, x2 = 0.f, x3 = 0.f, x4 = 0.f, x5 = 0.f, x6 = 0.f, x7 = 0.f;
+            if (r0 < n) {
+                x0 = X[r0 * kIn + 2 * tq];
+                x1 = X[r0 * kIn + 2 * tq + 1];
+                if (tq < 2) {
+                    x4 = X[r0 * kIn + 2 * tq + 8];
+                    x5 = X[r0 * kIn + 2 * tq + 9];
+                }
+            }
+            if (r1 < n) {
+                x2 = X[r1 * kIn + 2 * tq];
+                x3 = X[r1 * kIn + 2 * tq + 1];
+                if (tq < 2) {
+                    x6 = X[r1 * kIn + 2 * tq + 8];
+                    x7 = X[r1 * kIn + 2 * tq + 9];
+                }
+            }
+            a[0] = pack_bf16x2(x0, x1);
+            a[1] = pack_bf16x2(x2, x3);
+            a[2] = pack_bf16x2(x4, x5);
+            a[3] = pack_bf16x2(x6, x7);
+        }
+        uint32_t h[4][4];  // layer-2 A fragments: k-tile kk from layer-1 n-tiles 2kk, 2kk+1
 #pragma unroll
-    for (int k = 0; k < kIn; ++k) x[k] = bf16r(X[r * kIn + k]);
-    y[r] = row_forward(s, x, h1, h2);
+        for (int j = 0; j < 8; ++j) {
+            const int c = 8 * j + 2 * tq;
+            float d[4] = {b1[c], b1[c + 1], b1[c], b1[c + 1]};
+            const __nv_bfloat16* wr = w1 + (8 * j + g) * kW1Ld + 2 * tq;
+            mma_bf16_16816(d, a, *reinterpret_cast<const uint32_t*>(wr), *reinterpret_cast<const uint32_t*>(wr + 8));
+            const uint32_t lo = pack_bf16x2(fmaxf(d[0], 0.f), fmaxf(d[1], 0.f));  // row g
+            const uint32_t hi = pack_bf16x2(fmaxf(d[2], 0.f), fmaxf(d[3], 0.f));  // row g + 8
+            h[j >> 1][(j & 1) * 2 + 0] = lo;
+            h[j >> 1][(j & 1) * 2 + 1] = hi;
+        }
+        // layer 2 and the 64 -> 1 dot product
+        float s0 = 0.f, s1 = 0.f;  // rows g, g + 8: this thread's columns
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int c = 8 * j + 2 * tq;
+            float d[4] = {b2[c], b2[c + 1], b2[c], b2[c + 1]};
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+                const __nv_bfloat16* wr = w2 + (8 * j + g) * kW2Ld + 16 * kk + 2 * tq;
+                mma_bf16_16816(d, h[kk], *reinterpret_cast<const uint32_t*>(wr), *reinterpret_cast<const uint32_t*>(wr + 8));
+            }
+            s0 = fmaf(w3[c], bf16r(fmaxf(d[0], 0.f)), s0);
+            s0 = fmaf(w3[c + 1], bf16r(fmaxf(d[1], 0.f)), s0);
+            s1 = fmaf(w3[c], bf16r(fmaxf(d[2], 0.f)), s1);
+            s1 = fmaf(w3[c + 1], bf16r(fmaxf(d[3], 0.f)), s1);
+        }
+        s0 += __shfl_xor_sync(0xffffffffu, s0, 1);
+        s0 += __shfl_xor_sync(0xffffffffu, s0, 2);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, 1);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, 2);
+        if (tq == 0) {
+            if (r0 < n) y[r0] = b3 + s0;
+            if (r1 < n) y[r1] = b3 + s1;
+        }
+    }
 }
 
 // Fused forward + backward of mean((y - t)^2) over `total` rows; this block takes rows
@@ -199,7 +303,16 @@ static size_t grad_smem() { return sizeof(float) * (kNP + 3 + kRows * kIn + 4 * 
 
 hf_status mlp_forward(const float* params, const float* X, int64_t n, float* y, cudaStream_t s) {
     if (n <= 0) return HF_OK;
-    const int64_t blocks = (n + 127) / 128;
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    // 4 warps per block, one 16-row tile per warp at a time; at most 8 blocks per SM
+    const int64_t tiles = (n + 15) / 16;
+    const int64_t blocks = std::min<int64_t>((tiles + 3) / 4, (int64_t)sms * 8);
     k_mlp_forward<<<(unsigned)blocks, 128, 0, s>>>(params, X, n, y);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? HF_OK : cuda_fail(e, "k_mlp_forward");
