@@ -61,3 +61,14 @@ def test_config_is_the_workload_alone():
     c = bench.workload_config("layered10k", wl)
     assert c["workload"] == "layered10k" and c["tasks"] == wl.n_tasks and c["edges"] == wl.n_edges
     assert set(c) == {"workload", "tasks", "edges", "graphs", "saxpy_elems", "l2"}
+
+
+def test_small_workloads_are_timed_after_an_l2_flush():
+    from types import SimpleNamespace
+
+    small = SimpleNamespace(n_tasks=10_000, n_edges=24_000, saxpy_elems=0, graphs=[None])
+    large = SimpleNamespace(n_tasks=10_000_000, n_edges=35_000_000, saxpy_elems=0, graphs=[None] * 256)
+    assert bench.l2_flush_needed(small) and not bench.l2_flush_needed(large)
+    assert bench.FLUSH_BYTES >= 2 * bench.L2_BYTES
+    assert bench.workload_config("s", small)["l2"].startswith("L2 flushed before every timed step")
+    assert bench.workload_config("l", large)["l2"].startswith("inputs larger than L2")
