@@ -173,6 +173,14 @@ typedef struct {
                                every graph gets a K-CTA cluster or one CTA, the clusters take their
                                graphs first and then, like the other CTAs, single-CTA graphs; -1 =
                                one launch, K chosen by the planner's predicted makespan */
+    int32_t team_global_keys; /* team executor, batches without payloads: 0 = a graph run on a
+                               thread-block cluster of 2^j CTAs whose arrival keys fit in the
+                               cluster's shared memory (task count / cluster size entries per CTA,
+                               every CTA of its class still resident) keeps them there for the
+                               whole job, loaded and stored through distributed shared memory, and
+                               writes them out after its last level; 1 = every key in global
+                               memory. Single-CTA jobs always keep theirs in global memory.
+                               Results are identical either way. */
 } hf_run_opts;
 
 void hf_run_opts_default(hf_run_opts* opts);
@@ -348,6 +356,11 @@ hf_status hf_batch_last_launches(hf_batch* b, int32_t* n);
  * array of the batch's graph count: 1 for a single-CTA job, 2, 4, 8 or 16 for a thread-block
  * cluster, 0 for a graph without tasks. HF_ESTATE before the first team-executor run. */
 hf_status hf_batch_team_plan(hf_batch* b, int32_t* team_size);
+/* Whether each graph of the batch kept its arrival keys in its cluster's distributed shared
+ * memory in the last team-executor run (1) or in global memory (0), into a host array of the
+ * batch's graph count (see hf_run_opts::team_global_keys). HF_ESTATE before the first
+ * team-executor run. */
+hf_status hf_batch_team_keys(hf_batch* b, int32_t* shared);
 /* As hf_set_delays for every graph of the batch: delay holds the graphs' edge delays
  * concatenated in batch order (sum of their edge counts). */
 hf_status hf_batch_set_delays(hf_batch* b, const float* delay, int on_device, void* stream);

@@ -952,6 +952,12 @@ hf_status hf_batch_team_plan(hf_batch* b, int32_t* team_size) {
     return plan_team_plan(b->plan, team_size);
 }
 
+hf_status hf_batch_team_keys(hf_batch* b, int32_t* shared) {
+    if (!b || !shared) return fail(HF_EINVAL, "NULL argument");
+    if (!b->plan) return fail(HF_ESTATE, "batch has not run");
+    return plan_team_keys(b->plan, shared);
+}
+
 hf_status hf_batch_kernel_ms(hf_batch* b, float* ms) {
     if (!b || !ms) return fail(HF_EINVAL, "NULL argument");
     if (!b->plan) return fail(HF_ESTATE, "batch has not run");

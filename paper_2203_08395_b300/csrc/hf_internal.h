@@ -186,7 +186,7 @@ struct ResetArgs {
 // cluster (cluster job; jobs [0, ncjobs) of the list).
 struct TeamJob {
     int32_t graph;
-    int32_t pad_;
+    int32_t skeys;   // 1: the graph's keys live in the team's shared memory (TeamArgs::key_cap)
     int32_t seg0;    // first (graph, level) segment of the graph
     int32_t levels;  // levels of the graph
 };
@@ -225,7 +225,7 @@ struct TeamArgs {
     int32_t stage_n;         // stage buffer capacity: tasks and in-edges of a level
     int32_t stage_e;
     int32_t stage_p;         // ... and payload piece descriptors (0: none staged)
-    int32_t pad2_;
+    int32_t key_cap;         // key table entries per CTA in shared memory (0: none; see TeamJob)
     const TeamPiece* pdesc;  // piece descriptors, in item order
     int32_t* team;           // control words (kTeam*)
     Ctrl* ctrl;              // status word (HF_ETIMEDOUT when a staged copy never lands)
@@ -239,6 +239,7 @@ struct TeamArgs {
     int32_t* post;           // mapped host memory: the i-th posted host task
     const int32_t* hdone;    // mapped host memory: host task k has run
     int32_t* post_ctr;       // device counter of posts
+    const int32_t* task_off; // first task id of each graph (ngraphs + 1)
 };
 
 // Arguments of one level kernel of the level-synchronous executor.
@@ -353,6 +354,7 @@ hf_status plan_get_graph_times(Plan* p, int64_t* start, int64_t* end);
 hf_status plan_last_launches(Plan* p, int32_t* n);
 hf_status plan_get_task_costs(Plan* p, int32_t gi, float* out);
 hf_status plan_team_plan(Plan* p, int32_t* team_size);
+hf_status plan_team_keys(Plan* p, int32_t* shared);
 hf_status plan_set_delays(Plan* p, const float* delay, int on_device, cudaStream_t s);
 hf_status plan_run_host(Plan* p, cudaStream_t s, const hf_run_opts& o, const float* delay, float* arr_out);
 hf_status plan_features(Plan* p, float* X, cudaStream_t s);

@@ -79,6 +79,7 @@ struct Plan {
         int32_t njobs;
         int32_t ncjobs;  // of which cluster jobs (first; the rest are single-CTA jobs)
         int32_t grid;    // CTAs launched
+        int32_t key_cap; // key table entries per CTA in shared memory (0: keys in global memory)
     };
     std::vector<TeamClass> tclass;    // one launch per class, chained (plan_run), run concurrently
     // the classes' stream (tstream[0]) at the device's highest stream priority: pending team
@@ -100,7 +101,9 @@ struct Plan {
     int32_t* d_hdone = nullptr;
     int32_t* d_post_ctr = nullptr;    // posts so far (device counter)
     std::thread proxy;                // runs the host tasks of the current run
-    int32_t team_for[5] = {-1, -1, -1, -1, -2};  // priority, team_size, CTAs, scale, fold the jobs were built for
+    // priority, team_size, CTAs, scale, fold, global keys the jobs were built for
+    int32_t team_for[6] = {-1, -1, -1, -1, -2, -1};
+    std::vector<int32_t> team_sk;  // per graph: 1 when its keys live in shared memory (last team plan)
     const hf_costmodel* team_cm = nullptr;
 
     // device buffers
@@ -228,9 +231,10 @@ static double team_scale_factor(int32_t s, int32_t prio) {
     if (s == 0) s = team_scale_default(prio);
     return s > 0 ? (double)s : 1.0 / (double)(-s);
 }
-static int team_capacity(const Plan* p, int k);
+static int team_capacity(const Plan* p, int k, size_t smem = 0);
 static size_t team_smem(const Plan* p);
-static void team_smem_attr(const Plan* p);
+static size_t team_class_smem(const Plan* p, int32_t key_cap);
+static void team_smem_attr(const Plan* p, size_t need = 0);
 static hf_status team_decide(Plan* p, int32_t prio, int32_t ctas_opt, double scale, cudaStream_t s,
                              std::vector<int>* k_out, std::vector<int32_t>* order_out, double* M_out, int fold_k = 0);
 hf_status plan_prepare_priority(Plan* p, int32_t priority, const hf_costmodel* cm, cudaStream_t s);
@@ -1247,10 +1251,13 @@ hf_status plan_run(Plan* p, cudaStream_t s, const hf_run_opts& o, bool keep_stat
                 ai.njobs = c.njobs;
                 ai.ncjobs = c.ncjobs;
                 ai.team = p->d_team + (size_t)kTeamWords * i;
+                ai.key_cap = c.key_cap;
+                ai.task_off = p->d_toff;
                 cudaLaunchConfig_t cfg = {};
                 cfg.gridDim = dim3((unsigned)c.grid);
                 cfg.blockDim = dim3(kTeamThreads);
-                cfg.dynamicSmemBytes = team_smem(p);
+                cfg.dynamicSmemBytes = team_class_smem(p, c.key_cap);
+                team_smem_attr(p, cfg.dynamicSmemBytes);
                 cfg.stream = p->tstream[0];
                 cudaLaunchAttribute at[2];
                 unsigned na = 0;
@@ -1565,6 +1572,12 @@ hf_status plan_last_launches(Plan* p, int32_t* n) {
 hf_status plan_team_plan(Plan* p, int32_t* team_size) {
     if (p->team_k.size() != (size_t)p->ngraphs) return fail(HF_ESTATE, "no team-executor run yet");
     std::memcpy(team_size, p->team_k.data(), sizeof(int32_t) * p->team_k.size());
+    return HF_OK;
+}
+
+hf_status plan_team_keys(Plan* p, int32_t* shared) {
+    if (p->team_sk.size() != (size_t)p->ngraphs) return fail(HF_ESTATE, "no team-executor run yet");
+    std::memcpy(shared, p->team_sk.data(), sizeof(int32_t) * p->team_sk.size());
     return HF_OK;
 }
 
@@ -2198,13 +2211,21 @@ static double team_time(const Plan* p, const std::vector<double>& pay_ns, int32_
 }
 
 // CTAs of cluster size k resident at once (k = 1: plain occupancy).
-static size_t team_smem(const Plan* p) { return kTeamBufs * team_stage_bytes(p->stage_n, p->stage_e, p->stage_p); }
+// the stage buffers (the kernel places its key table right after them: same sizes as TeamArgs)
+static size_t team_smem(const Plan* p) {
+    return kTeamBufs * team_stage_bytes(p->stage_n, p->stage_e, p->npay ? p->stage_p : 0);
+}
 
-static void team_smem_attr(const Plan* p) {
+// a class's dynamic shared memory: the stage buffers, then its key table (16-byte multiple)
+static size_t team_class_smem(const Plan* p, int32_t key_cap) {
+    return team_smem(p) + (((size_t)key_cap * 4 + 15) & ~(size_t)15);
+}
+
+static void team_smem_attr(const Plan* p, size_t need) {
     static std::mutex mu;
     static size_t set_to = 0;
     std::lock_guard<std::mutex> lk(mu);
-    const size_t need = team_smem(p);
+    if (need == 0) need = team_smem(p);
     if (need > set_to) {
         for (const void* f : {(const void*)k_team<true, false>, (const void*)k_team<false, false>,
                               (const void*)k_team<true, true>, (const void*)k_team<false, true>})
@@ -2213,12 +2234,14 @@ static void team_smem_attr(const Plan* p) {
     }
 }
 
-static int team_capacity(const Plan* p, int k) {
+// smem: the class's dynamic shared memory (0: stage buffers only)
+static int team_capacity(const Plan* p, int k, size_t smem) {
     const void* fn = p->npay ? (const void*)k_team<true, false> : (const void*)k_team<false, false>;
-    team_smem_attr(p);
+    if (smem == 0) smem = team_smem(p);
+    team_smem_attr(p, smem);
     if (k == 1) {
         int occ = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kTeamThreads, team_smem(p));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kTeamThreads, smem);
         return p->num_sms * std::max(occ, 1);
     }
     if (k > 8) {
@@ -2229,7 +2252,7 @@ static int team_capacity(const Plan* p, int k) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)k);
     cfg.blockDim = dim3(kTeamThreads);
-    cfg.dynamicSmemBytes = team_smem(p);
+    cfg.dynamicSmemBytes = smem;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
     at[0].val.clusterDim.x = (unsigned)k;
@@ -2360,8 +2383,10 @@ static hf_status plan_team_jobs(Plan* p, const hf_run_opts& o, cudaStream_t s) {
     const int32_t fold = o.team_size > 0 ? 0 : o.team_fold;
     if (fold != 0 && fold != -1 && fold != 2 && fold != 4 && fold != 8 && fold != 16)
         return fail(HF_EINVAL, "team_fold must be 0, -1, 2, 4, 8 or 16");
+    if (o.team_global_keys != 0 && o.team_global_keys != 1) return fail(HF_EINVAL, "team_global_keys must be 0 or 1");
     if (p->team_for[0] == prio && p->team_for[1] == o.team_size && p->team_for[2] == o.ctas &&
-        p->team_for[3] == scale && p->team_for[4] == fold && (prio != HF_PRIO_LEARNED || p->team_cm == p->cm))
+        p->team_for[3] == scale && p->team_for[4] == fold && p->team_for[5] == o.team_global_keys &&
+        (prio != HF_PRIO_LEARNED || p->team_cm == p->cm))
         return HF_OK;
     std::vector<int32_t> order;
     std::vector<int> k;
@@ -2437,6 +2462,60 @@ static hf_status plan_team_jobs(Plan* p, const hf_run_opts& o, cudaStream_t s) {
         }
     }
     if (p->tclass.size() > 5) return fail(HF_ENOTSUP, "too many team classes");
+    // Keys in distributed shared memory (team.cuh): per cluster class of a power-of-two size, the
+    // largest share of a graph's keys per CTA (ceil(n_g / k)) such that every CTA of the class is
+    // still resident with it and the shared memory of all classes' CTAs together stays within
+    // 90 % of the GPU's (the classes run concurrently); the largest clusters are served first.
+    // The graphs whose share fits run with their keys there. Not for single CTAs, not in folded
+    // launches, not in batches with payloads (their kernel keeps every key in global memory).
+    bool any_sk = false;
+    p->team_sk.assign((size_t)p->ngraphs, 0);
+    if (fold_k == 0 && p->npay == 0 && o.team_global_keys == 0) {
+        int max_dyn = 0, sm_smem = 0, dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&max_dyn, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        cudaFuncAttributes fa = {};
+        const void* fn = (const void*)k_team<false, false>;
+        cudaFuncGetAttributes(&fa, fn);
+        const size_t dyn_cap = (size_t)std::max(max_dyn - (int)fa.sharedSizeBytes, 0);
+        const size_t per_cta = fa.sharedSizeBytes + 1024;  // static shared memory + the CTA's reserve
+        const double budget = 0.9 * (double)p->num_sms * (double)sm_smem;
+        double used = 0.0;
+        for (const Plan::TeamClass& c : p->tclass) used += (double)c.grid * (double)(team_smem(p) + per_cta);
+        for (Plan::TeamClass& c : p->tclass) {  // (largest clusters first)
+            c.key_cap = 0;
+            if (c.k == 1 || (c.k & (c.k - 1))) continue;
+            std::vector<int32_t> share;
+            for (int32_t j = c.job0; j < c.job0 + c.njobs; ++j) {
+                const int32_t g = jobs[(size_t)j].graph;
+                share.push_back((p->task_off[(size_t)g + 1] - p->task_off[(size_t)g] + c.k - 1) / c.k);
+            }
+            std::sort(share.begin(), share.end(), std::greater<int32_t>());
+            share.erase(std::unique(share.begin(), share.end()), share.end());
+            for (int32_t cap : share) {
+                const size_t smem = team_class_smem(p, cap);
+                if (smem > dyn_cap) continue;
+                const double grow = (double)c.grid * (double)(smem - team_smem(p));
+                if (used + grow > budget) continue;
+                if (team_capacity(p, c.k, smem) < c.grid) continue;
+                c.key_cap = cap;
+                used += grow;
+                break;
+            }
+            for (int32_t j = c.job0; j < c.job0 + c.njobs; ++j) {
+                const int32_t g = jobs[(size_t)j].graph;
+                const int32_t sh = (p->task_off[(size_t)g + 1] - p->task_off[(size_t)g] + c.k - 1) / c.k;
+                jobs[(size_t)j].skeys = c.key_cap > 0 && sh <= c.key_cap ? 1 : 0;
+                p->team_sk[(size_t)g] = jobs[(size_t)j].skeys;
+                any_sk |= jobs[(size_t)j].skeys != 0;
+            }
+        }
+    }
+    if (any_sk && !p->d_toff) {
+        hf_status su = upload(p, &p->d_toff, p->task_off.data(), p->task_off.size(), s, "task offsets");
+        if (su != HF_OK) return su;
+    }
     const size_t bytes = std::max<size_t>(sizeof(TeamJob) * jobs.size(), 16);
     if (p->cap_jobs < bytes) {
         free_owned(p, p->d_jobs);
@@ -2468,6 +2547,7 @@ static hf_status plan_team_jobs(Plan* p, const hf_run_opts& o, cudaStream_t s) {
     p->team_for[2] = o.ctas;
     p->team_for[3] = scale;
     p->team_for[4] = fold;
+    p->team_for[5] = o.team_global_keys;
     p->team_cm = p->cm;
     return HF_OK;
 }

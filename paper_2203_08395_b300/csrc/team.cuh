@@ -9,8 +9,9 @@
 //
 // Latency hiding. A level's critical path should be one gather of the predecessors' arrival
 // keys. Everything that does not depend on the previous level is fetched ahead:
-//   * segment descriptors (positions, in-edge and payload-piece ranges of each level) three
-//     levels ahead, by asynchronous copies into a ring in shared memory;
+//   * segment descriptors (positions, in-edge and payload-piece ranges of each level) four
+//     levels ahead, by asynchronous copies into a ring in shared memory, each waited for one
+//     level after it was issued;
 //   * every CTA stages the task list, row starts, in-edges and payload-piece descriptors of the
 //     next two levels in shared memory with TMA bulk copies (three buffers, completion on
 //     mbarriers); segments too large to stage are prefetched into L2 two levels ahead;
@@ -26,6 +27,14 @@ namespace hf {
 
 constexpr int kTeamThreads = 256;
 constexpr int kTeamBufs = 3;       // staged levels: the current one and two ahead
+// Segment descriptors ride a ring in shared memory, fetched kRingAhead levels ahead by
+// asynchronous copies (one commit group per level); a level's barrier waits only for the group
+// of the level before, so no fetch latency sits on a level's own path. An entry must have landed
+// when the look-ahead stages its level (kTeamBufs - 1 levels ahead): kRingAhead = kTeamBufs + 1.
+constexpr int kStageAhead = kTeamBufs - 1;  // levels staged ahead of the current one
+constexpr int kRingAhead = kTeamBufs + 1;
+constexpr int kRing = 8;           // ring slots (a power of two above kRingAhead)
+static_assert(kRing > kRingAhead && (kRing & (kRing - 1)) == 0, "ring slots");
 // The thread that runs a CTA's look-ahead (segment ring, stage copies): lane 0 of the last warp,
 // which takes arrivals only when the CTA's slice of a level exceeds 224 tasks.
 constexpr int kTeamLead = kTeamThreads - 32;
@@ -77,6 +86,9 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned 
         : "memory");
     return ok != 0;
 }
+
+// all but the most recent commit group of this thread's asynchronous copies have landed
+__device__ __forceinline__ void cp_async_wait_group1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 // asynchronous 8-byte global -> shared copy (completion: cp_async_wait_all by the issuer)
 __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
@@ -162,8 +174,11 @@ __device__ __forceinline__ bool team_ahead(const TeamSrc& a, int rank, const Tea
 }
 
 // The slice [x0 + n * r / k, x0 + n * (r + 1) / k) of a range of n that CTA r of a team of k takes.
-__device__ __forceinline__ int team_slice(int x0, int n, int r, int k) {
-    return x0 + (int)(((int64_t)n * r) / k);
+// lk = log2(k) when k is a power of two (every planned team), else -1 (a 64-bit division, which
+// costs as much as a level's gather).
+__device__ __forceinline__ int team_slice(int x0, int n, int r, int k, int lk) {
+    const int64_t m = (int64_t)n * r;
+    return x0 + (int)(lk >= 0 ? m >> lk : m / k);
 }
 
 // L2 prefetch of the x and y ranges of staged pieces [i0, i1) (indices into the stage buffer's
@@ -281,7 +296,7 @@ __device__ __forceinline__ void st_cluster_job(TeamJob* local, unsigned rank, co
     const unsigned s = (unsigned)__cvta_generic_to_shared(local);
     unsigned d;
     asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(d) : "r"(s), "r"(rank));
-    asm volatile("st.shared::cluster.v4.s32 [%0], {%1, %2, %3, %4};" ::"r"(d), "r"(j.graph), "r"(j.pad_), "r"(j.seg0),
+    asm volatile("st.shared::cluster.v4.s32 [%0], {%1, %2, %3, %4};" ::"r"(d), "r"(j.graph), "r"(j.skeys), "r"(j.seg0),
                  "r"(j.levels)
                  : "memory");
 }
@@ -360,6 +375,64 @@ __device__ __forceinline__ uint32_t team_task_key(const TeamArgs& a, int v, cons
     return team_fold<SOLO>(a, in, e0, e1, pol);
 }
 
+// ---------------------------------------------------------------- keys in distributed shared memory
+//
+// A level's gather in a cluster job loads its predecessors' keys, written by the team's CTAs at
+// earlier levels, through L2 (0.6-0.9 us per level measured; a load from a cluster peer's shared
+// memory is about 0.1-0.2 us). A graph whose keys fit in the shared memory of its cluster's CTAs
+// therefore keeps them there for the whole job: task i of the graph (its id minus the graph's
+// first id) in CTA i & (k - 1) of the cluster of k = 2^lk CTAs, at slot i >> lk, loaded and
+// stored through distributed shared memory; the cluster barrier orders a level's stores before
+// the next level's loads. The keys go to global memory once, after the last level, each CTA
+// writing its own slots. (Single-CTA jobs keep their keys in global memory: measured, a table in
+// their own shared memory did not shorten a level, and the larger shared-memory carve-out left
+// less L1 to the other single-CTA jobs' key loads.)
+
+// distributed-shared-memory address of task i's key in its owner CTA
+__device__ __forceinline__ unsigned sk_addr(unsigned skey_s, int i, int lk) {
+    unsigned d;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;"
+                 : "=r"(d)
+                 : "r"(skey_s + 4u * (unsigned)(i >> lk)), "r"(i & ((1 << lk) - 1)));
+    return d;
+}
+
+// (no memory clobber: the loads may be scheduled freely within the level; the level barriers
+// are volatile and order them)
+__device__ __forceinline__ uint32_t sk_load(unsigned addr) {
+    uint32_t v;
+    asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(addr));
+    return v;
+}
+
+__device__ __forceinline__ void sk_store(unsigned addr, uint32_t v) {
+    asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+
+// team_task_key with the graph's keys in distributed shared memory (kbase: the graph's first
+// task id): the in-edge records of a batch of up to 8 are read first, then every key load is
+// issued, then they are combined
+__device__ __forceinline__ uint32_t team_task_key_sk(const TeamArgs& a, int v, const int2* in, int e0, int e1,
+                                                     unsigned skey_s, int kbase, int lk) {
+    if (e0 == e1) return a.key0 ? __ldg(a.key0 + v) : kKeyPosZero;
+    uint32_t best = 0u;
+    for (int e = e0; e < e1; e += 8) {
+        const int cnt = e1 - e < 8 ? e1 - e : 8;
+        int2 r[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if (j < cnt) r[j] = in[e + j];
+        uint32_t kk[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if (j < cnt) kk[j] = sk_load(sk_addr(skey_s, r[j].x - kbase, lk));
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if (j < cnt) best = max(best, f2key(__fadd_rn(key2f(kk[j]), __int_as_float(r[j].y))));
+    }
+    return best;
+}
+
 // ---------------------------------------------------------------- one graph
 
 // Bounded wait (spin_limit_ns) for stage buffer b's next completion; false if it never came.
@@ -382,43 +455,52 @@ __device__ __forceinline__ bool team_wait_stage(unsigned long long* bar, unsigne
 // waited (bounded) for the stage copies it still had in flight; the kernel then ends.
 // A thread whose wait for a staged level runs out reads that level from global memory instead
 // (the same data), so the level completes and the team reaches its barrier.
-template <bool PAY, bool SOLO, bool REC>
+// SK (cluster jobs only): the graph's keys live in distributed shared memory (see above; skey:
+// this CTA's table). Only in the kernel without payloads: with them the extra path would spill
+// registers.
+template <bool PAY, bool SOLO, bool REC, bool SK>
 __device__ __forceinline__ bool team_run_graph(const TeamArgs& a, const TeamJob& job, int k, int rank,
                                                const TeamSrc& src, const TeamStage* sview, unsigned long long* mbar,
-                                               int4* ring, int2* iring, int* pcnt, int* s_fail, unsigned& phase) {
+                                               int4* ring, int2* iring, int* pcnt, int* s_fail, unsigned& phase,
+                                               uint32_t* skey) {
     const int t = threadIdx.x;
     const int lane = t & 31;
+    static_assert(!(SK && SOLO), "shared key tables are for cluster jobs");
     const int L = job.levels;
+    const int lk = (k & (k - 1)) == 0 ? __ffs(k) - 1 : -1;
     const int2 z2 = make_int2(0, 0);
+    const int kbase = SK ? __ldg(a.task_off + job.graph) : 0;
+    const unsigned skey_s = SK ? (unsigned)__cvta_generic_to_shared(skey) : 0u;
     unsigned inflight = 0;  // lead thread: stage buffers with a copy issued and not yet seen complete
     // segment descriptors and item ranges ride a ring in shared memory, fetched by the lead
-    // thread three levels ahead (asynchronous copies, completed before the level's barrier, so
-    // that their latency stays off the level's path); level l uses stage buffer l % kTeamBufs,
-    // staged two levels ahead
+    // thread kRingAhead levels ahead (the first kRingAhead here); level l uses stage buffer
+    // l % kTeamBufs, staged kTeamBufs - 1 levels ahead
     if (t == kTeamLead) {
+        cp_async_wait_all();  // (the previous job's ring copies have all landed; none in flight)
         pcnt[0] = pcnt[1] = 0;
-        for (int q = 0; q < 3 && q < L; ++q) {
+        for (int q = 0; q < kRingAhead && q < L; ++q) {
             ring[q] = __ldg(a.seg + job.seg0 + q);
             iring[q] = PAY ? __ldg(a.seg_items + job.seg0 + q) : z2;
         }
-        if (L > 0 && team_ahead(src, rank, sview[0], &mbar[0], ring[0], PAY ? iring[0] : z2)) inflight |= 1u;
-        if (L > 1 && team_ahead(src, rank, sview[1], &mbar[1], ring[1], PAY ? iring[1] : z2)) inflight |= 2u;
+        for (int q = 0; q < kStageAhead && q < L; ++q)
+            if (team_ahead(src, rank, sview[q], &mbar[q], ring[q], PAY ? iring[q] : z2)) inflight |= 1u << q;
     }
     __syncthreads();
     if (a.g_start && rank == 0 && t == 0) a.g_start[job.graph] = (int64_t)gtimer();
     for (int l = 0; l < L; ++l) {
         const int b = l % kTeamBufs;
-        const int4 s0 = ring[l & 3];
-        const int2 i0 = PAY ? iring[l & 3] : z2;
+        const int4 s0 = ring[l & (kRing - 1)];
+        const int2 i0 = PAY ? iring[l & (kRing - 1)] : z2;
         if (t == kTeamLead) {
-            if (l + 2 < L && team_ahead(src, rank, sview[(l + 2) % kTeamBufs], &mbar[(l + 2) % kTeamBufs],
-                                        ring[(l + 2) & 3], PAY ? iring[(l + 2) & 3] : z2))
-                inflight |= 1u << ((l + 2) % kTeamBufs);  // (the item ring is filled only with payloads)
-            if (l + 3 < L) {
-                cp_async16(&ring[(l + 3) & 3], a.seg + job.seg0 + l + 3);
-                if (PAY) cp_async8(&iring[(l + 3) & 3], a.seg_items + job.seg0 + l + 3);
-                cp_async_commit();
+            const int la = l + kStageAhead;
+            if (la < L && team_ahead(src, rank, sview[la % kTeamBufs], &mbar[la % kTeamBufs],
+                                     ring[la & (kRing - 1)], PAY ? iring[la & (kRing - 1)] : z2))
+                inflight |= 1u << (la % kTeamBufs);  // (the item ring is filled only with payloads)
+            if (l + kRingAhead < L) {
+                cp_async16(&ring[(l + kRingAhead) & (kRing - 1)], a.seg + job.seg0 + l + kRingAhead);
+                if (PAY) cp_async8(&iring[(l + kRingAhead) & (kRing - 1)], a.seg_items + job.seg0 + l + kRingAhead);
             }
+            cp_async_commit();  // one group per level (empty near the end)
         }
         if (PAY && t == kTeamLead) pcnt[(l + 1) & 1] = 0;  // the next level's piece counter (free since the barrier)
         // level l's task list, row starts and in-edges (every CTA of a team stages the whole level):
@@ -449,13 +531,17 @@ __device__ __forceinline__ bool team_run_graph(const TeamArgs& a, const TeamJob&
         }
         // this CTA's slice of the level's tasks: one per thread
         {
-            const int p1 = team_slice(s0.x, s0.y - s0.x, rank + 1, k);
+            const int p1 = team_slice(s0.x, s0.y - s0.x, rank + 1, k, lk);
             const uint64_t pol = l2_keep_policy();
-            for (int p = team_slice(s0.x, s0.y - s0.x, rank, k) + t; p < p1; p += kTeamThreads) {
+            for (int p = team_slice(s0.x, s0.y - s0.x, rank, k, lk) + t; p < p1; p += kTeamThreads) {
                 const int v = node[p - nb];
                 const uint64_t c0 = REC ? gtimer() : 0;
-                team_store_key(a.key + v,
-                               team_task_key<SOLO>(a, v, in, ptr[p - nb] - eb, ptr[p + 1 - nb] - eb, pol), pol);
+                if (SK)
+                    sk_store(sk_addr(skey_s, v - kbase, lk),
+                             team_task_key_sk(a, v, in, ptr[p - nb] - eb, ptr[p + 1 - nb] - eb, skey_s, kbase, lk));
+                else
+                    team_store_key(a.key + v,
+                                   team_task_key<SOLO>(a, v, in, ptr[p - nb] - eb, ptr[p + 1 - nb] - eb, pol), pol);
                 if (REC) a.t_cost[v] = (float)(gtimer() - c0);  // the gather's time (loads in, key out)
             }
         }
@@ -466,13 +552,14 @@ __device__ __forceinline__ bool team_run_graph(const TeamArgs& a, const TeamJob&
         if (PAY) {
             if (!SOLO && (t >> 5) == (kTeamLead >> 5) && l + 1 < L) {
                 const int b1 = (l + 1) % kTeamBufs;
-                const int2 i1 = iring[(l + 1) & 3];
-                if (team_fits(a, ring[(l + 1) & 3]) && team_desc_fits(a, i1) &&
+                const int2 i1 = iring[(l + 1) & (kRing - 1)];
+                if (team_fits(a, ring[(l + 1) & (kRing - 1)]) && team_desc_fits(a, i1) &&
                     mbar_try_wait(&mbar[b1], (phase >> b1) & 1u))
-                    team_prefetch_pieces(sview[b1].pdesc, team_slice(i1.x, i1.y - i1.x, rank, k) - i1.x,
-                                         team_slice(i1.x, i1.y - i1.x, rank + 1, k) - i1.x, lane);
+                    team_prefetch_pieces(sview[b1].pdesc, team_slice(i1.x, i1.y - i1.x, rank, k, lk) - i1.x,
+                                         team_slice(i1.x, i1.y - i1.x, rank + 1, k, lk) - i1.x, lane);
             }
-            const int q0 = team_slice(i0.x, i0.y - i0.x, rank, k), q1 = team_slice(i0.x, i0.y - i0.x, rank + 1, k);
+            const int q0 = team_slice(i0.x, i0.y - i0.x, rank, k, lk);
+            const int q1 = team_slice(i0.x, i0.y - i0.x, rank + 1, k, lk);
             for (;;) {
                 int it = 0;
                 if (lane == 0) it = q0 + atomicAdd(&pcnt[l & 1], 1);
@@ -488,15 +575,24 @@ __device__ __forceinline__ bool team_run_graph(const TeamArgs& a, const TeamJob&
         }
         if (a.seg_host && rank == 0 && t == 0 && !team_host_tasks(a, job.seg0 + l))
             team_fail(a, s_fail, k, (int)HF_ETIMEDOUT);
-        if (t == kTeamLead) cp_async_wait_all();  // ring entry l + 3
+        // the ring group of level l - 1 (entry l - 1 + kRingAhead, staged at level l + 1); this
+        // level's own group stays in flight across the barrier
+        if (t == kTeamLead) cp_async_wait_group1();
         if (SOLO) __syncthreads();
         else cluster_sync();
         if (*(volatile int*)s_fail) {  // the same value in every thread of the team (see team_fail)
-            if (t == kTeamLead)        // stage copies still in flight land before the CTA ends
+            if (t == kTeamLead) {      // stage and ring copies still in flight land before the CTA ends
                 for (int q = 0; q < kTeamBufs; ++q)
                     if ((inflight >> q) & 1u) team_wait_stage(&mbar[q], (phase >> q) & 1u, a.spin_limit_ns);
+                cp_async_wait_all();
+            }
             return false;
         }
+    }
+    if (SK) {  // after the last level's barrier: each CTA writes its own slots out
+        const int n = __ldg(a.task_off + job.graph + 1) - kbase;
+        const int ns = n > rank ? (n - rank + k - 1) >> lk : 0;  // tasks rank, rank + k, ... below n
+        for (int q = t; q < ns; q += kTeamThreads) a.key[kbase + rank + (q << lk)] = skey[q];
     }
     if (a.g_end && rank == 0 && t == 0) a.g_end[job.graph] = (int64_t)gtimer();
     return true;
@@ -516,8 +612,8 @@ __device__ __forceinline__ void k_team_body(const TeamArgs& a) {
     __shared__ TeamSrc s_src;
     __shared__ __align__(8) unsigned long long mbar[kTeamBufs];
     __shared__ __align__(16) TeamJob s_job;
-    __shared__ int4 s_ring[4];
-    __shared__ int2 s_iring[4];
+    __shared__ int4 s_ring[kRing];
+    __shared__ int2 s_iring[kRing];
     __shared__ int s_pcnt[2];  // payload piece counters, alternating by level
     __shared__ int s_fail;     // the team failed (team_fail); read after each level's barrier
     const int t = threadIdx.x;
@@ -532,6 +628,8 @@ __device__ __forceinline__ void k_team_body(const TeamArgs& a) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     __syncthreads();
+    // the key table follows the stage buffers (a.key_cap entries; 16-byte aligned offset)
+    uint32_t* skey = reinterpret_cast<uint32_t*>(s_stage + kTeamBufs * team_stage_bytes(a.stage_n, a.stage_e, a.stage_p));
     unsigned phase = 0;  // bit b: parity of buffer b's next completion
     const int k = (int)cluster_size();
     if (k > 1 && a.ncjobs > 0) {
@@ -547,9 +645,11 @@ __device__ __forceinline__ void k_team_body(const TeamArgs& a) {
             const TeamJob job = s_job;
             cluster_sync();  // all have read s_job before CTA 0 may overwrite it
             if (job.graph < 0) break;
-            if (!team_run_graph<PAY, false, REC>(a, job, k, rank, s_src, s_view, mbar, s_ring, s_iring, s_pcnt,
-                                                 &s_fail, phase))
-                return;
+            const bool ok = !PAY && job.skeys ? team_run_graph<PAY, false, REC, !PAY>(a, job, k, rank, s_src, s_view, mbar, s_ring,
+                                                                             s_iring, s_pcnt, &s_fail, phase, skey)
+                                     : team_run_graph<PAY, false, REC, false>(a, job, k, rank, s_src, s_view, mbar, s_ring,
+                                                                              s_iring, s_pcnt, &s_fail, phase, skey);
+            if (!ok) return;
         }
     }
     for (;;) {
@@ -561,8 +661,8 @@ __device__ __forceinline__ void k_team_body(const TeamArgs& a) {
         const TeamJob job = s_job;
         __syncthreads();
         if (job.graph < 0) break;
-        if (!team_run_graph<PAY, true, REC>(a, job, 1, 0, s_src, s_view, mbar, s_ring, s_iring, s_pcnt, &s_fail,
-                                            phase))
+        if (!team_run_graph<PAY, true, REC, false>(a, job, 1, 0, s_src, s_view, mbar, s_ring, s_iring, s_pcnt,
+                                                   &s_fail, phase, skey))
             return;
     }
 }

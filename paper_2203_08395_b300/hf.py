@@ -66,7 +66,8 @@ class hf_run_opts(ctypes.Structure):
                 ("stall_task", ctypes.c_int32), ("time_kernel", ctypes.c_int32),
                 ("payload_warps", ctypes.c_int32), ("team_size", ctypes.c_int32),
                 ("team_scale", ctypes.c_int32), ("steal_ring", ctypes.c_int32),
-                ("copy_warps", ctypes.c_int32), ("team_fold", ctypes.c_int32)]
+                ("copy_warps", ctypes.c_int32), ("team_fold", ctypes.c_int32),
+                ("team_global_keys", ctypes.c_int32)]
 
 
 class hf_graph_info_t(ctypes.Structure):
@@ -148,6 +149,7 @@ def load():
         "hf_batch_get_task_costs": [vp, i32, vp],
         "hf_batch_last_launches": [vp, P(i32)],
         "hf_batch_team_plan": [vp, vp],
+        "hf_batch_team_keys": [vp, vp],
         "hf_calibration": [vp, vp],
         "hf_dump": [vp, ctypes.c_char_p],
         "hf_place": [vp, i32, vp, vp],
@@ -539,6 +541,13 @@ def hf_batch_team_plan(b, ngraphs):
     """Team size each graph ran on in the last team-executor run (int32 array)."""
     k = np.zeros(ngraphs, np.int32)
     _check(load().hf_batch_team_plan(b, k.ctypes.data), "hf_batch_team_plan")
+    return k
+
+
+def hf_batch_team_keys(b, ngraphs):
+    """1 where a graph kept its keys in shared memory in the last team-executor run (int32 array)."""
+    k = np.zeros(ngraphs, np.int32)
+    _check(load().hf_batch_team_keys(b, k.ctypes.data), "hf_batch_team_keys")
     return k
 
 

@@ -45,6 +45,9 @@ EXECUTORS = {
     "team_heur": dict(mode=hf.HF_MODE_TEAM, priority=hf.HF_PRIO_HEURISTIC),
     "team_k2": dict(mode=hf.HF_MODE_TEAM, team_size=2),
     "team_k5": dict(mode=hf.HF_MODE_TEAM, team_size=5, ctas=12),
+    # every key in global memory (the default keeps a graph's keys in shared memory where they fit)
+    "team_global_keys": dict(mode=hf.HF_MODE_TEAM, team_global_keys=1),
+    "team_k4_global_keys": dict(mode=hf.HF_MODE_TEAM, team_size=4, team_global_keys=1),
     # one launch: graphs on 8-CTA clusters (or the planner's cluster size) and single CTAs together
     "team_fold8": dict(mode=hf.HF_MODE_TEAM, priority=hf.HF_PRIO_HEURISTIC, team_fold=8, team_scale=1),
     "team_fold_auto": dict(mode=hf.HF_MODE_TEAM, priority=hf.HF_PRIO_HEURISTIC, team_fold=-1),
