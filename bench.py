@@ -509,10 +509,20 @@ def main():
         if cm is not None:
             arms += [("persistent_learned", dict(mode=hf.HF_MODE_PERSISTENT, priority=hf.HF_PRIO_LEARNED)),
                      ("team_learned", dict(mode=hf.HF_MODE_TEAM, priority=hf.HF_PRIO_LEARNED))]
+        if chosen in (hf.HF_MODE_PERSISTENT, hf.HF_MODE_TEAM) and not args.no_tune and cm is not None:
+            # the heuristic fallback, autotuned the same way as the headline: the judge of the
+            # learned plan's gain
+            hb, _ = hf.hf_batch_autotune(bd.b, stream, hf.hf_run_opts_default(priority=hf.HF_PRIO_HEURISTIC, mode=chosen))
+            ho = {kk: v for kk, v in hf.opts_dict(hb).items() if kk not in ("time_kernel", "instrument", "validate")}
+            ho.update(mode=chosen, priority=hf.HF_PRIO_HEURISTIC)
+            arms += [("%s_heuristic_tuned" % ("team" if chosen == hf.HF_MODE_TEAM else "persistent"), ho)]
         for name, o in arms:
             c_ms, c_med, c_st, _ = timed(o, k, 3)
             compare[name] = {"ms_per_step": c_ms, "ms_median": c_med, "tasks_per_s": N / (c_ms / 1e3),
                              "edges_per_s": E / (c_ms / 1e3), "status": hf.hf_status_string(c_st)}
+            if name.endswith("_heuristic_tuned"):
+                compare[name]["launch"] = {kk: o[kk] for kk in ("team_size", "team_scale", "chunk_elems", "ctas", "claim",
+                                                               "team_fold") if kk in o}
         compare["headline_over_levelsync"] = compare["levelsync"]["ms_per_step"] / ms
 
     e2e = None

@@ -439,9 +439,9 @@ hf_status hf_batch_bottom_levels(hf_batch* b, const float* cost, float* bottom, 
  * per team size or one folded launch); any other mode tunes the
  * persistent executor (CTA count, queue claim size, shared-memory stack depth, payload piece
  * size, payload warps, global queue or work stealing, copy warps; mode PERSISTENT in *best).
- * Results are cached per executor and size bucket (tasks, edges per task, payload share, depth,
- * batch or single graph), so a later call on a similar batch returns without trials unless
- * `force`. Runs the batch many times: payloads run each time (saxpy updates y). Blocks. */
+ * Results are cached per executor, priority source (base->priority) and size bucket (tasks,
+ * edges per task, payload share, depth, batch or single graph), so a later call on a similar
+ * batch returns without trials unless `force`. Runs the batch many times: payloads run each time (saxpy updates y). Blocks. */
 hf_status hf_batch_autotune(hf_batch* b, void* stream, const hf_run_opts* base, int force, hf_run_opts* best,
                             float* best_ms);
 

@@ -80,6 +80,7 @@ struct Plan {
         int32_t ncjobs;  // of which cluster jobs (first; the rest are single-CTA jobs)
         int32_t grid;    // CTAs launched
         int32_t key_cap; // key table entries per CTA in shared memory (0: keys in global memory)
+        int32_t csk;     // 1: every graph of the class keeps its keys there (the k_team<., ., true> kernel)
     };
     std::vector<TeamClass> tclass;    // one launch per class, chained (plan_run), run concurrently
     // the classes' stream (tstream[0]) at the device's highest stream priority: pending team
@@ -231,7 +232,8 @@ static double team_scale_factor(int32_t s, int32_t prio) {
     if (s == 0) s = team_scale_default(prio);
     return s > 0 ? (double)s : 1.0 / (double)(-s);
 }
-static int team_capacity(const Plan* p, int k, size_t smem = 0);
+static int team_capacity(const Plan* p, int k, size_t smem = 0, bool csk = false);
+static const void* team_kernel(bool pay, bool rec, bool csk);
 static size_t team_smem(const Plan* p);
 static size_t team_class_smem(const Plan* p, int32_t key_cap);
 static void team_smem_attr(const Plan* p, size_t need = 0);
@@ -1275,10 +1277,8 @@ hf_status plan_run(Plan* p, cudaStream_t s, const hf_run_opts& o, bool keep_stat
                 }
                 cfg.attrs = at;
                 cfg.numAttrs = na;
-                if (rec) e = p->npay ? cudaLaunchKernelEx(&cfg, k_team<true, true>, ai)
-                                     : cudaLaunchKernelEx(&cfg, k_team<false, true>, ai);
-                else e = p->npay ? cudaLaunchKernelEx(&cfg, k_team<true, false>, ai)
-                                 : cudaLaunchKernelEx(&cfg, k_team<false, false>, ai);
+                void* kargs[] = {&ai};
+                e = cudaLaunchKernelExC(&cfg, team_kernel(p->npay != 0, rec, c.csk != 0), kargs);
                 if (e != cudaSuccess) return cuda_fail(e, "k_team launch");
             }
             if ((e = cudaEventRecord(p->tev_join[0], p->tstream[0])) != cudaSuccess ||
@@ -1837,7 +1837,7 @@ static hf_status time_runs(Plan* p, cudaStream_t s, const hf_run_opts& o, int re
     return HF_OK;
 }
 
-using TuneKey = std::tuple<int, int, int, int, int>;
+using TuneKey = std::tuple<int, int, int, int, int, int>;
 static std::mutex g_tune_mu;
 static std::map<TuneKey, std::pair<hf_run_opts, float>> g_tune_cache;
 
@@ -1846,7 +1846,7 @@ static TuneKey tune_key(const Plan* p) {
     const int epn = p->n > 0 ? (int)std::lround(10.0 * (double)p->m / (double)p->n) : 0;
     const int payq = p->n > 0 ? (int)std::lround(20.0 * (double)p->npay / (double)p->n) : 0;
     const int logd = p->levels > 0 ? (int)std::floor(std::log2((double)p->levels)) : 0;
-    return TuneKey(logn, epn, payq, logd, p->ngraphs > 1 ? 1 : 0);
+    return TuneKey(logn, epn, payq, logd, p->ngraphs > 1 ? 1 : 0, 0);
 }
 
 // Team executor: coordinate descent over the planner's payload-cost scale (contention), the
@@ -1902,6 +1902,7 @@ hf_status plan_autotune(Plan* p, cudaStream_t s, const hf_run_opts& base, int fo
     const bool team = base.mode == HF_MODE_TEAM;
     TuneKey key = tune_key(p);
     std::get<4>(key) += team ? 2 : 0;
+    std::get<5>(key) = base.priority;  // the tuned plan depends on the cost source
     if (!force) {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune_cache.find(key);
@@ -2221,22 +2222,37 @@ static size_t team_class_smem(const Plan* p, int32_t key_cap) {
     return team_smem(p) + (((size_t)key_cap * 4 + 15) & ~(size_t)15);
 }
 
+// The team kernel's instantiations: payloads, cost recording, cluster class with shared keys.
+static const void* team_kernel(bool pay, bool rec, bool csk) {
+    if (csk) {
+        if (rec) return pay ? (const void*)k_team<true, true, true> : (const void*)k_team<false, true, true>;
+        return pay ? (const void*)k_team<true, false, true> : (const void*)k_team<false, false, true>;
+    }
+    if (rec) return pay ? (const void*)k_team<true, true> : (const void*)k_team<false, true>;
+    return pay ? (const void*)k_team<true, false> : (const void*)k_team<false, false>;
+}
+
+static std::vector<const void*> team_kernels() {
+    std::vector<const void*> v;
+    for (int i = 0; i < 8; ++i) v.push_back(team_kernel(i & 1, (i >> 1) & 1, (i >> 2) & 1));
+    return v;
+}
+
 static void team_smem_attr(const Plan* p, size_t need) {
     static std::mutex mu;
     static size_t set_to = 0;
     std::lock_guard<std::mutex> lk(mu);
     if (need == 0) need = team_smem(p);
     if (need > set_to) {
-        for (const void* f : {(const void*)k_team<true, false>, (const void*)k_team<false, false>,
-                              (const void*)k_team<true, true>, (const void*)k_team<false, true>})
-            cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
+        for (const void* f : team_kernels()) cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
         set_to = need;
     }
 }
 
-// smem: the class's dynamic shared memory (0: stage buffers only)
-static int team_capacity(const Plan* p, int k, size_t smem) {
-    const void* fn = p->npay ? (const void*)k_team<true, false> : (const void*)k_team<false, false>;
+// smem: the class's dynamic shared memory (0: stage buffers only); csk: the class runs the
+// kernel with every cluster job's keys in shared memory
+static int team_capacity(const Plan* p, int k, size_t smem, bool csk) {
+    const void* fn = team_kernel(p->npay != 0, false, csk);
     if (smem == 0) smem = team_smem(p);
     team_smem_attr(p, smem);
     if (k == 1) {
@@ -2244,11 +2260,8 @@ static int team_capacity(const Plan* p, int k, size_t smem) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kTeamThreads, smem);
         return p->num_sms * std::max(occ, 1);
     }
-    if (k > 8) {
-        for (const void* f : {(const void*)k_team<true, false>, (const void*)k_team<false, false>,
-                              (const void*)k_team<true, true>, (const void*)k_team<false, true>})
-            cudaFuncSetAttribute(f, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    }
+    if (k > 8)
+        for (const void* f : team_kernels()) cudaFuncSetAttribute(f, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)k);
     cfg.blockDim = dim3(kTeamThreads);
@@ -2462,52 +2475,66 @@ static hf_status plan_team_jobs(Plan* p, const hf_run_opts& o, cudaStream_t s) {
         }
     }
     if (p->tclass.size() > 5) return fail(HF_ENOTSUP, "too many team classes");
-    // Keys in distributed shared memory (team.cuh): per cluster class of a power-of-two size, the
-    // largest share of a graph's keys per CTA (ceil(n_g / k)) such that every CTA of the class is
-    // still resident with it and the shared memory of all classes' CTAs together stays within
-    // 90 % of the GPU's (the classes run concurrently); the largest clusters are served first.
-    // The graphs whose share fits run with their keys there. Not for single CTAs, not in folded
-    // launches, not in batches with payloads (their kernel keeps every key in global memory).
+    // Keys in distributed shared memory (team.cuh), per cluster class of a power-of-two size, in
+    // batches without payloads, the largest clusters first. A key table of `cap` entries per CTA
+    // must leave every CTA of the class resident and the shared memory of all classes' CTAs
+    // together within 90 % of the GPU's (the classes run concurrently). When the largest share of
+    // the class's graphs (ceil(n_g / k)) fits, the class runs the kernel with shared keys only
+    // (every graph); otherwise the largest share that fits, for the graphs whose share fits. Not
+    // for single CTAs, not in folded launches, and not with payloads: on batch256_mixed the
+    // payload kernel with shared keys (118 registers, two CTAs per SM) ran its 2-CTA class so
+    // much slower that the step took 4.74 instead of 3.28-3.48 ms.
     bool any_sk = false;
     p->team_sk.assign((size_t)p->ngraphs, 0);
+    for (Plan::TeamClass& c : p->tclass) c.key_cap = c.csk = 0;
     if (fold_k == 0 && p->npay == 0 && o.team_global_keys == 0) {
         int max_dyn = 0, sm_smem = 0, dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&max_dyn, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
         cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-        cudaFuncAttributes fa = {};
-        const void* fn = (const void*)k_team<false, false>;
-        cudaFuncGetAttributes(&fa, fn);
-        const size_t dyn_cap = (size_t)std::max(max_dyn - (int)fa.sharedSizeBytes, 0);
-        const size_t per_cta = fa.sharedSizeBytes + 1024;  // static shared memory + the CTA's reserve
+        size_t stat = 0;
+        for (const void* f : team_kernels()) {
+            cudaFuncAttributes fa = {};
+            cudaFuncGetAttributes(&fa, f);
+            stat = std::max(stat, fa.sharedSizeBytes);
+        }
+        const size_t dyn_cap = (size_t)std::max(max_dyn - (int)stat, 0);
+        const size_t per_cta = stat + 1024;  // static shared memory + the CTA's reserve
         const double budget = 0.9 * (double)p->num_sms * (double)sm_smem;
         double used = 0.0;
         for (const Plan::TeamClass& c : p->tclass) used += (double)c.grid * (double)(team_smem(p) + per_cta);
-        for (Plan::TeamClass& c : p->tclass) {  // (largest clusters first)
-            c.key_cap = 0;
-            if (c.k == 1 || (c.k & (c.k - 1))) continue;
+        auto share_of = [&](const Plan::TeamClass& c, int32_t j) {
+            const int32_t g = jobs[(size_t)j].graph;
+            return (p->task_off[(size_t)g + 1] - p->task_off[(size_t)g] + c.k - 1) / c.k;
+        };
+        auto fits = [&](const Plan::TeamClass& c, int32_t cap, bool csk, double* grow) {
+            const size_t smem = team_class_smem(p, cap);
+            if (smem > dyn_cap) return false;
+            *grow = (double)c.grid * (double)(smem - team_smem(p));
+            return used + *grow <= budget && team_capacity(p, c.k, smem, csk) >= c.grid;
+        };
+        for (Plan::TeamClass& c : p->tclass) {
+            if (c.k == 1 || (c.k & (c.k - 1)) || c.njobs == 0) continue;
             std::vector<int32_t> share;
-            for (int32_t j = c.job0; j < c.job0 + c.njobs; ++j) {
-                const int32_t g = jobs[(size_t)j].graph;
-                share.push_back((p->task_off[(size_t)g + 1] - p->task_off[(size_t)g] + c.k - 1) / c.k);
-            }
+            for (int32_t j = c.job0; j < c.job0 + c.njobs; ++j) share.push_back(share_of(c, j));
             std::sort(share.begin(), share.end(), std::greater<int32_t>());
             share.erase(std::unique(share.begin(), share.end()), share.end());
-            for (int32_t cap : share) {
-                const size_t smem = team_class_smem(p, cap);
-                if (smem > dyn_cap) continue;
-                const double grow = (double)c.grid * (double)(smem - team_smem(p));
-                if (used + grow > budget) continue;
-                if (team_capacity(p, c.k, smem) < c.grid) continue;
-                c.key_cap = cap;
+            double grow = 0.0;
+            if (fits(c, share[0], true, &grow)) {
+                c.key_cap = share[0];
+                c.csk = 1;
                 used += grow;
-                break;
+            } else {
+                for (size_t q = 0; q < share.size(); ++q)
+                    if (fits(c, share[q], false, &grow)) {
+                        c.key_cap = share[q];
+                        used += grow;
+                        break;
+                    }
             }
             for (int32_t j = c.job0; j < c.job0 + c.njobs; ++j) {
-                const int32_t g = jobs[(size_t)j].graph;
-                const int32_t sh = (p->task_off[(size_t)g + 1] - p->task_off[(size_t)g] + c.k - 1) / c.k;
-                jobs[(size_t)j].skeys = c.key_cap > 0 && sh <= c.key_cap ? 1 : 0;
-                p->team_sk[(size_t)g] = jobs[(size_t)j].skeys;
+                jobs[(size_t)j].skeys = c.key_cap > 0 && share_of(c, j) <= c.key_cap ? 1 : 0;
+                p->team_sk[(size_t)jobs[(size_t)j].graph] = jobs[(size_t)j].skeys;
                 any_sk |= jobs[(size_t)j].skeys != 0;
             }
         }

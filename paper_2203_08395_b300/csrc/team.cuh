@@ -605,7 +605,10 @@ __device__ __forceinline__ bool team_run_graph(const TeamArgs& a, const TeamJob&
 // runs it as one team. Phase 2: every CTA takes solo jobs until none is left.
 // REC: instrument bit 2 runs, which record per-task costs (t_cost); a separate instantiation, so
 // that the kernel of ordinary runs carries no recording code.
-template <bool PAY, bool REC>
+// CSK: a cluster class whose every graph keeps its keys in distributed shared memory; its kernel
+// has the cluster path with shared keys alone (no single-CTA phase), which keeps the payload
+// kernel within its register budget.
+template <bool PAY, bool REC, bool CSK>
 __device__ __forceinline__ void k_team_body(const TeamArgs& a) {
     extern __shared__ __align__(16) unsigned char s_stage[];  // kTeamBufs stage buffers
     __shared__ TeamStage s_view[kTeamBufs];
@@ -645,13 +648,21 @@ __device__ __forceinline__ void k_team_body(const TeamArgs& a) {
             const TeamJob job = s_job;
             cluster_sync();  // all have read s_job before CTA 0 may overwrite it
             if (job.graph < 0) break;
-            const bool ok = !PAY && job.skeys ? team_run_graph<PAY, false, REC, !PAY>(a, job, k, rank, s_src, s_view, mbar, s_ring,
-                                                                             s_iring, s_pcnt, &s_fail, phase, skey)
-                                     : team_run_graph<PAY, false, REC, false>(a, job, k, rank, s_src, s_view, mbar, s_ring,
-                                                                              s_iring, s_pcnt, &s_fail, phase, skey);
+            bool ok;
+            if constexpr (CSK)
+                ok = team_run_graph<PAY, false, REC, true>(a, job, k, rank, s_src, s_view, mbar, s_ring, s_iring,
+                                                           s_pcnt, &s_fail, phase, skey);
+            else
+                ok = !PAY && job.skeys ? team_run_graph<PAY, false, REC, !PAY>(a, job, k, rank, s_src, s_view, mbar,
+                                                                               s_ring, s_iring, s_pcnt, &s_fail, phase,
+                                                                               skey)
+                                       : team_run_graph<PAY, false, REC, false>(a, job, k, rank, s_src, s_view, mbar,
+                                                                                s_ring, s_iring, s_pcnt, &s_fail,
+                                                                                phase, skey);
             if (!ok) return;
         }
     }
+    if constexpr (CSK) return;  // (a cluster class has no single-CTA jobs)
     for (;;) {
         if (t == 0) {
             const int j = ld_relaxed(&a.ctrl->abort) ? a.njobs : a.ncjobs + atomicAdd(a.team + kTeamNext, 1);
@@ -671,10 +682,12 @@ __device__ __forceinline__ void k_team_body(const TeamArgs& a) {
 // CTA allows the next class to launch as soon as it starts, and waits for the previous class's
 // grid to complete only when it is done (a no-op for the first class), so the next class's
 // kernel completes after every earlier one.
-template <bool PAY, bool REC>
-__global__ void __launch_bounds__(kTeamThreads, 3) k_team(const TeamArgs a) {
+// (The shared-key cluster kernel is launched with larger key tables, at two CTAs per SM or
+// fewer: its register budget follows.)
+template <bool PAY, bool REC, bool CSK = false>
+__global__ void __launch_bounds__(kTeamThreads, CSK ? 2 : 3) k_team(const TeamArgs a) {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    k_team_body<PAY, REC>(a);
+    k_team_body<PAY, REC, CSK>(a);
     asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 

@@ -46,6 +46,10 @@ def test_autotune_choice_is_exact_and_cached():
     again, ms2 = hf.hf_batch_autotune(bd.b)
     assert time.perf_counter() - t0 < 0.5 and ms2 == ms
     assert (again.ctas, again.claim, again.local_keep) == (best.ctas, best.claim, best.local_keep)
+    # the cache is per priority source: another one runs trials of its own (a fresh timing, not
+    # the cached one)
+    other, ms3 = hf.hf_batch_autotune(bd.b, None, hf.hf_run_opts_default(priority=hf.HF_PRIO_HEURISTIC))
+    assert other.priority == hf.HF_PRIO_HEURISTIC and ms3 > 0 and ms3 != ms
     bd.close()
 
 

@@ -68,7 +68,7 @@ def test_graph_too_large_for_shared_memory_runs_from_global():
     bd.close()
 
 
-def test_non_power_of_two_team_and_payloads_keep_global_keys():
+def test_non_power_of_two_team_keeps_global_keys():
     wl = S.Workload("sk3", [S.layered(900 + i, n, max(4, n // 200), 1, 5, name="q%d" % i)
                             for i, n in enumerate([3000, 9000])])
     bd = BatchOnDevice(wl)
@@ -77,12 +77,35 @@ def test_non_power_of_two_team_and_payloads_keep_global_keys():
     assert not hf.hf_batch_team_keys(bd.b, 2).any()
     _check(bd, wl)
     bd.close()
-    # a batch with saxpy payloads runs the payload kernel, which keeps keys in global memory
+
+
+def test_payload_batch_keeps_global_keys():
+    # the payload kernel keeps every key in global memory
     wl = S.batch(5, graphs=4, nmin=1000, nmax=8000, frac_saxpy=0.1)
     bd = BatchOnDevice(wl)
     bd.run(mode=hf.HF_MODE_TEAM, team_size=2)
     bd.sync()
     assert not hf.hf_batch_team_keys(bd.b, 4).any()
+    _check(bd, wl)
+    bd.close()
+
+
+def test_whole_class_kernel_and_per_graph_tables():
+    # every graph of the 4-CTA class fits: the class runs the kernel with shared keys only; with
+    # one graph too large the class runs the general kernel, shared keys for the graphs that fit
+    small = [S.layered(950 + i, n, max(4, n // 150), 1, 6, name="w%d" % i) for i, n in enumerate([2500, 7000, 11_000])]
+    wl = S.Workload("sk5", small)
+    bd = BatchOnDevice(wl)
+    bd.run(mode=hf.HF_MODE_TEAM, team_size=4)
+    bd.sync()
+    assert hf.hf_batch_team_keys(bd.b, 3).all()
+    _check(bd, wl)
+    bd.close()
+    wl = S.Workload("sk6", small + [S.layered(960, 600_000, 2400, 1, 4, name="big")])
+    bd = BatchOnDevice(wl)
+    bd.run(mode=hf.HF_MODE_TEAM, team_size=4)
+    bd.sync()
+    np.testing.assert_array_equal(hf.hf_batch_team_keys(bd.b, 4), [1, 1, 1, 0])
     _check(bd, wl)
     bd.close()
 
