@@ -184,9 +184,17 @@ struct ResetArgs {
 
 // Team executor: a job is one graph, run by one CTA (solo job) or by the CTAs of one thread-block
 // cluster (cluster job; jobs [0, ncjobs) of the list).
+// TeamJob::flags: the graph's keys live in the team's shared memory (TeamArgs::key_cap); its
+// levels are software-pipelined (each thread reads its next level's task while the current
+// level's key loads are in flight: pays where the keys come from L2, not where they fit in L1)
+constexpr int32_t kJobSharedKeys = 1;
+constexpr int32_t kJobPipelined = 2;
+// graphs of at least this many tasks run pipelined (their keys outgrow an SM's L1)
+constexpr int32_t kPipeMinTasks = 32768;
+
 struct TeamJob {
     int32_t graph;
-    int32_t skeys;   // 1: the graph's keys live in the team's shared memory (TeamArgs::key_cap)
+    int32_t flags;   // kJobSharedKeys | kJobPipelined
     int32_t seg0;    // first (graph, level) segment of the graph
     int32_t levels;  // levels of the graph
 };

@@ -1257,7 +1257,7 @@ hf_status plan_run(Plan* p, cudaStream_t s, const hf_run_opts& o, bool keep_stat
                 ai.task_off = p->d_toff;
                 cudaLaunchConfig_t cfg = {};
                 cfg.gridDim = dim3((unsigned)c.grid);
-                cfg.blockDim = dim3(kTeamThreads);
+                cfg.blockDim = dim3(kTeamBlock);
                 cfg.dynamicSmemBytes = team_class_smem(p, c.key_cap);
                 team_smem_attr(p, cfg.dynamicSmemBytes);
                 cfg.stream = p->tstream[0];
@@ -2257,14 +2257,14 @@ static int team_capacity(const Plan* p, int k, size_t smem, bool csk) {
     team_smem_attr(p, smem);
     if (k == 1) {
         int occ = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kTeamThreads, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kTeamBlock, smem);
         return p->num_sms * std::max(occ, 1);
     }
     if (k > 8)
         for (const void* f : team_kernels()) cudaFuncSetAttribute(f, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)k);
-    cfg.blockDim = dim3(kTeamThreads);
+    cfg.blockDim = dim3(kTeamBlock);
     cfg.dynamicSmemBytes = smem;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
@@ -2475,6 +2475,8 @@ static hf_status plan_team_jobs(Plan* p, const hf_run_opts& o, cudaStream_t s) {
         }
     }
     if (p->tclass.size() > 5) return fail(HF_ENOTSUP, "too many team classes");
+    for (TeamJob& j : jobs)
+        if (p->task_off[(size_t)j.graph + 1] - p->task_off[(size_t)j.graph] >= kPipeMinTasks) j.flags |= kJobPipelined;
     // Keys in distributed shared memory (team.cuh), per cluster class of a power-of-two size, in
     // batches without payloads, the largest clusters first. A key table of `cap` entries per CTA
     // must leave every CTA of the class resident and the shared memory of all classes' CTAs
@@ -2533,9 +2535,9 @@ static hf_status plan_team_jobs(Plan* p, const hf_run_opts& o, cudaStream_t s) {
                     }
             }
             for (int32_t j = c.job0; j < c.job0 + c.njobs; ++j) {
-                jobs[(size_t)j].skeys = c.key_cap > 0 && share_of(c, j) <= c.key_cap ? 1 : 0;
-                p->team_sk[(size_t)jobs[(size_t)j].graph] = jobs[(size_t)j].skeys;
-                any_sk |= jobs[(size_t)j].skeys != 0;
+                if (c.key_cap > 0 && share_of(c, j) <= c.key_cap) jobs[(size_t)j].flags |= kJobSharedKeys;
+                p->team_sk[(size_t)jobs[(size_t)j].graph] = jobs[(size_t)j].flags & kJobSharedKeys;
+                any_sk |= (jobs[(size_t)j].flags & kJobSharedKeys) != 0;
             }
         }
     }

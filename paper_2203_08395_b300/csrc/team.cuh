@@ -9,13 +9,21 @@
 //
 // Latency hiding. A level's critical path should be one gather of the predecessors' arrival
 // keys. Everything that does not depend on the previous level is fetched ahead:
-//   * segment descriptors (positions, in-edge and payload-piece ranges of each level) four
+//   * segment descriptors (positions, in-edge and payload-piece ranges of each level) five
 //     levels ahead, by asynchronous copies into a ring in shared memory, each waited for one
 //     level after it was issued;
 //   * every CTA stages the task list, row starts, in-edges and payload-piece descriptors of the
-//     next two levels in shared memory with TMA bulk copies (three buffers, completion on
-//     mbarriers); segments too large to stage are prefetched into L2 two levels ahead;
-//   * in cluster jobs, each CTA prefetches the x and y ranges of its next-level pieces into L2.
+//     next three levels in shared memory with TMA bulk copies (four buffers, completion on
+//     mbarriers); segments too large to stage are prefetched into L2 three levels ahead. All of
+//     it is issued by a producer warp that takes no arrivals, so its issue time (~0.35 us per
+//     level) is off the arrival warps' path;
+//   * in cluster jobs, each CTA prefetches the x and y ranges of its next-level pieces into L2;
+//   * graphs whose keys outgrow L1 run software-pipelined: a thread reads its next level's task
+//     (id, in-edge range) while its current key loads are in flight, and issues that task's
+//     first key loads as the very first thing of the next level. A level's gather is bound by
+//     the SM's rate of scattered L1 misses (about one per cycle: ~900 for a 250-task level with
+//     3.5 in-edges a task) plus an L2 round trip; set-up work beside it costs nothing as long as
+//     it does not wait in the same queue.
 // Balance. Each CTA of a team takes a contiguous slice of every level's tasks (one per thread)
 // and of its payload pieces; the CTA's warps claim pieces one at a time from a shared counter,
 // warps without arrivals at once, the others when their arrivals are done.
@@ -26,7 +34,7 @@
 namespace hf {
 
 constexpr int kTeamThreads = 256;
-constexpr int kTeamBufs = 3;       // staged levels: the current one and two ahead
+constexpr int kTeamBufs = 4;       // staged levels: the current one and three ahead
 // Segment descriptors ride a ring in shared memory, fetched kRingAhead levels ahead by
 // asynchronous copies (one commit group per level); a level's barrier waits only for the group
 // of the level before, so no fetch latency sits on a level's own path. An entry must have landed
@@ -35,9 +43,11 @@ constexpr int kStageAhead = kTeamBufs - 1;  // levels staged ahead of the curren
 constexpr int kRingAhead = kTeamBufs + 1;
 constexpr int kRing = 8;           // ring slots (a power of two above kRingAhead)
 static_assert(kRing > kRingAhead && (kRing & (kRing - 1)) == 0, "ring slots");
-// The thread that runs a CTA's look-ahead (segment ring, stage copies): lane 0 of the last warp,
-// which takes arrivals only when the CTA's slice of a level exceeds 224 tasks.
-constexpr int kTeamLead = kTeamThreads - 32;
+// kTeamThreads arrival threads (one task each per level) and a producer warp: the thread that
+// runs a CTA's look-ahead (segment ring, stage copies) is its lane 0; the warp also claims
+// payload pieces and, in cluster jobs, warms L2 with the next level's pieces.
+constexpr int kTeamLead = kTeamThreads;
+constexpr int kTeamBlock = kTeamThreads + 32;
 // Stage buffers live in dynamic shared memory, sized per plan (TeamArgs::stage_n tasks,
 // stage_e in-edges and stage_p piece descriptors per level; stage_n a multiple of 4, stage_e of
 // 2): node[stage_n + 8] (copied from a 16-byte aligned start, up to 3 extra entries in front),
@@ -80,6 +90,21 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned 
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(s), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// non-blocking: has the phase with this parity completed? (acquire at CTA scope, like try_wait,
+// but never suspends the thread)
+__device__ __forceinline__ bool mbar_test_wait(unsigned long long* bar, unsigned parity) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(bar);
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
         : "r"(s), "r"(parity)
@@ -296,7 +321,7 @@ __device__ __forceinline__ void st_cluster_job(TeamJob* local, unsigned rank, co
     const unsigned s = (unsigned)__cvta_generic_to_shared(local);
     unsigned d;
     asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(d) : "r"(s), "r"(rank));
-    asm volatile("st.shared::cluster.v4.s32 [%0], {%1, %2, %3, %4};" ::"r"(d), "r"(j.graph), "r"(j.skeys), "r"(j.seg0),
+    asm volatile("st.shared::cluster.v4.s32 [%0], {%1, %2, %3, %4};" ::"r"(d), "r"(j.graph), "r"(j.flags), "r"(j.seg0),
                  "r"(j.levels)
                  : "memory");
 }
@@ -373,6 +398,33 @@ __device__ __forceinline__ uint32_t team_task_key(const TeamArgs& a, int v, cons
                                                   uint64_t pol) {
     if (e0 == e1) return a.key0 ? __ldg(a.key0 + v) : kKeyPosZero;
     return team_fold<SOLO>(a, in, e0, e1, pol);
+}
+
+// team_task_key, running `between()` once while the first batch of key loads is in flight (the
+// loads are issued, their first use comes after it), so that work for the next level costs no
+// time on this level's path
+template <bool SOLO, class F>
+__device__ __forceinline__ uint32_t team_task_key_hook(const TeamArgs& a, int v, const int2* in, int e0, int e1,
+                                                       uint64_t pol, F&& between) {
+    if (e0 == e1) {
+        const uint32_t k0 = a.key0 ? __ldg(a.key0 + v) : kKeyPosZero;
+        between();
+        return k0;
+    }
+    uint32_t best = 0u;
+    for (int e = e0; e < e1; e += 8) {
+        const int cnt = e1 - e < 8 ? e1 - e : 8;
+        uint32_t kk[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if (j < cnt) kk[j] = team_pred_key<SOLO>(a, in[e + j].x, pol);
+        if (e == e0) between();
+        const volatile int* dl = reinterpret_cast<const volatile int*>(in + e) + 1;
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if (j < cnt) best = max(best, f2key(__fadd_rn(key2f(kk[j]), __int_as_float(dl[2 * j]))));
+    }
+    return best;
 }
 
 // ---------------------------------------------------------------- keys in distributed shared memory
@@ -472,6 +524,16 @@ __device__ __forceinline__ bool team_run_graph(const TeamArgs& a, const TeamJob&
     const int kbase = SK ? __ldg(a.task_off + job.graph) : 0;
     const unsigned skey_s = SK ? (unsigned)__cvta_generic_to_shared(skey) : 0u;
     unsigned inflight = 0;  // lead thread: stage buffers with a copy issued and not yet seen complete
+    // Software pipelining across levels: while its first task's key loads are in flight, a thread
+    // tests (without waiting) whether the next level's stage buffer has landed and, if so, reads
+    // its first task of that level (id and in-edge range) from it. `seen`: buffers whose current
+    // completion this thread has already observed; pv/pe0/pe1 (valid: pvalid): the task read ahead.
+    unsigned seen = 0;
+    int pv = 0, pe0 = 0, pe1 = 0;
+    bool pvalid = false;
+    const int2* pin = nullptr;  // the read-ahead task's in-edges (its level's stage buffer)
+    const bool pipe = (job.flags & kJobPipelined) != 0;
+    const uint64_t pol = l2_keep_policy();
     // segment descriptors and item ranges ride a ring in shared memory, fetched by the lead
     // thread kRingAhead levels ahead (the first kRingAhead here); level l uses stage buffer
     // l % kTeamBufs, staged kTeamBufs - 1 levels ahead
@@ -489,6 +551,15 @@ __device__ __forceinline__ bool team_run_graph(const TeamArgs& a, const TeamJob&
     if (a.g_start && rank == 0 && t == 0) a.g_start[job.graph] = (int64_t)gtimer();
     for (int l = 0; l < L; ++l) {
         const int b = l % kTeamBufs;
+        // the read-ahead task's first key loads go out before the rest of the level's set-up
+        uint32_t kk0[8];
+        int c0n = -1;
+        if (!PAY && !REC && !SK && pvalid) {  // (the payload kernel has no registers to spare)
+            c0n = min(pe1 - pe0, 8);
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                if (j < c0n) kk0[j] = team_pred_key<SOLO>(a, pin[pe0 + j].x, pol);
+        }
         const int4 s0 = ring[l & (kRing - 1)];
         const int2 i0 = PAY ? iring[l & (kRing - 1)] : z2;
         if (t == kTeamLead) {
@@ -512,8 +583,13 @@ __device__ __forceinline__ bool team_run_graph(const TeamArgs& a, const TeamJob&
         const TeamPiece* dsc = PAY ? a.pdesc : nullptr;
         int nb = 0, eb = 0, ib = 0;
         if (team_fits(a, s0)) {
-            if (team_wait_stage(&mbar[b], (phase >> b) & 1u, a.spin_limit_ns)) {
+            bool landed = ((seen >> b) & 1u) != 0;  // observed during the previous level
+            seen &= ~(1u << b);
+            if (!landed && team_wait_stage(&mbar[b], (phase >> b) & 1u, a.spin_limit_ns)) {
                 phase ^= 1u << b;
+                landed = true;
+            }
+            if (landed) {
                 if (t == kTeamLead) inflight &= ~(1u << b);
                 nb = s0.x & ~3;
                 eb = s0.z & ~1;
@@ -532,8 +608,71 @@ __device__ __forceinline__ bool team_run_graph(const TeamArgs& a, const TeamJob&
         // this CTA's slice of the level's tasks: one per thread
         {
             const int p1 = team_slice(s0.x, s0.y - s0.x, rank + 1, k, lk);
-            const uint64_t pol = l2_keep_policy();
-            for (int p = team_slice(s0.x, s0.y - s0.x, rank, k, lk) + t; p < p1; p += kTeamThreads) {
+            bool nvalid = false;
+            int nv = 0, ne0 = 0, ne1 = 0;
+            const int2* nin = nullptr;
+            auto look_next = [&]() {
+                if (!pipe || l + 1 >= L) return;
+                const int4 s1 = ring[(l + 1) & (kRing - 1)];
+                if (!team_fits(a, s1)) return;
+                const int b1 = (l + 1) % kTeamBufs;
+                if (!mbar_test_wait(&mbar[b1], (phase >> b1) & 1u)) return;
+                phase ^= 1u << b1;
+                seen |= 1u << b1;
+                if (t == kTeamLead) inflight &= ~(1u << b1);
+                const int q = team_slice(s1.x, s1.y - s1.x, rank, k, lk) + t;
+                if (t < kTeamThreads && q < team_slice(s1.x, s1.y - s1.x, rank + 1, k, lk)) {
+                    const TeamStage sv = sview[b1];
+                    const int nb1 = s1.x & ~3, eb1 = s1.z & ~1;
+                    nv = sv.node[q - nb1];
+                    ne0 = sv.ptr[q - nb1] - eb1;
+                    ne1 = sv.ptr[q + 1 - nb1] - eb1;
+                    nin = sv.in;
+                    nvalid = true;
+                }
+            };
+            int p = team_slice(s0.x, s0.y - s0.x, rank, k, lk) + t;
+            if (!pipe) {
+                // (jobs that are not pipelined keep the plain loop: with the pipelined path compiled
+                // in their levels measured slower, keys in L1 leaving nothing to hide)
+            } else if (t < kTeamThreads && p < p1) {  // the first task: pipelined
+                int v, e0, e1;
+                if (pvalid) {
+                    v = pv;
+                    e0 = pe0;
+                    e1 = pe1;
+                } else {
+                    v = node[p - nb];
+                    e0 = ptr[p - nb] - eb;
+                    e1 = ptr[p + 1 - nb] - eb;
+                }
+                const uint64_t c0 = REC ? gtimer() : 0;
+                if (c0n >= 0) {  // its first key loads went out at the top of the level
+                    look_next();
+                    uint32_t best = e0 == e1 ? (a.key0 ? __ldg(a.key0 + v) : kKeyPosZero) : 0u;
+                    const volatile int* dl = reinterpret_cast<const volatile int*>(in + e0) + 1;
+#pragma unroll
+                    for (int j = 0; j < 8; ++j)
+                        if (j < c0n) best = max(best, f2key(__fadd_rn(key2f(kk0[j]), __int_as_float(dl[2 * j]))));
+                    if (e1 - e0 > 8) best = max(best, team_fold<SOLO>(a, in, e0 + 8, e1, pol));
+                    team_store_key(a.key + v, best, pol);
+                } else if (SK) {
+                    sk_store(sk_addr(skey_s, v - kbase, lk), team_task_key_sk(a, v, in, e0, e1, skey_s, kbase, lk));
+                    if (REC) a.t_cost[v] = (float)(gtimer() - c0);
+                    look_next();
+                } else if (REC) {
+                    team_store_key(a.key + v, team_task_key<SOLO>(a, v, in, e0, e1, pol), pol);
+                    a.t_cost[v] = (float)(gtimer() - c0);
+                    look_next();
+                } else {
+                    team_store_key(a.key + v, team_task_key_hook<SOLO>(a, v, in, e0, e1, pol, look_next), pol);
+                }
+                p += kTeamThreads;
+            } else {
+                look_next();
+            }
+            pvalid = false;
+            for (; t < kTeamThreads && p < p1; p += kTeamThreads) {
                 const int v = node[p - nb];
                 const uint64_t c0 = REC ? gtimer() : 0;
                 if (SK)
@@ -544,6 +683,11 @@ __device__ __forceinline__ bool team_run_graph(const TeamArgs& a, const TeamJob&
                                    team_task_key<SOLO>(a, v, in, ptr[p - nb] - eb, ptr[p + 1 - nb] - eb, pol), pol);
                 if (REC) a.t_cost[v] = (float)(gtimer() - c0);  // the gather's time (loads in, key out)
             }
+            pvalid = nvalid;
+            pv = nv;
+            pe0 = ne0;
+            pe1 = ne1;
+            pin = nin;
         }
         // this CTA's slice of the level's payload pieces: each warp takes the next piece from a
         // shared counter, the warps without arrivals at once, the others after them. In cluster
@@ -553,8 +697,10 @@ __device__ __forceinline__ bool team_run_graph(const TeamArgs& a, const TeamJob&
             if (!SOLO && (t >> 5) == (kTeamLead >> 5) && l + 1 < L) {
                 const int b1 = (l + 1) % kTeamBufs;
                 const int2 i1 = iring[(l + 1) & (kRing - 1)];
+                // landed: observed by this thread's look at the next level, or by a test now
+                // (never a wait: the prefetch is not worth holding the warp)
                 if (team_fits(a, ring[(l + 1) & (kRing - 1)]) && team_desc_fits(a, i1) &&
-                    mbar_try_wait(&mbar[b1], (phase >> b1) & 1u))
+                    (((seen >> b1) & 1u) || mbar_test_wait(&mbar[b1], (phase >> b1) & 1u)))
                     team_prefetch_pieces(sview[b1].pdesc, team_slice(i1.x, i1.y - i1.x, rank, k, lk) - i1.x,
                                          team_slice(i1.x, i1.y - i1.x, rank + 1, k, lk) - i1.x, lane);
             }
@@ -592,7 +738,7 @@ __device__ __forceinline__ bool team_run_graph(const TeamArgs& a, const TeamJob&
     if (SK) {  // after the last level's barrier: each CTA writes its own slots out
         const int n = __ldg(a.task_off + job.graph + 1) - kbase;
         const int ns = n > rank ? (n - rank + k - 1) >> lk : 0;  // tasks rank, rank + k, ... below n
-        for (int q = t; q < ns; q += kTeamThreads) a.key[kbase + rank + (q << lk)] = skey[q];
+        for (int q = t; q < ns; q += kTeamBlock) a.key[kbase + rank + (q << lk)] = skey[q];
     }
     if (a.g_end && rank == 0 && t == 0) a.g_end[job.graph] = (int64_t)gtimer();
     return true;
@@ -653,7 +799,7 @@ __device__ __forceinline__ void k_team_body(const TeamArgs& a) {
                 ok = team_run_graph<PAY, false, REC, true>(a, job, k, rank, s_src, s_view, mbar, s_ring, s_iring,
                                                            s_pcnt, &s_fail, phase, skey);
             else
-                ok = !PAY && job.skeys ? team_run_graph<PAY, false, REC, !PAY>(a, job, k, rank, s_src, s_view, mbar,
+                ok = !PAY && (job.flags & kJobSharedKeys) ? team_run_graph<PAY, false, REC, !PAY>(a, job, k, rank, s_src, s_view, mbar,
                                                                                s_ring, s_iring, s_pcnt, &s_fail, phase,
                                                                                skey)
                                        : team_run_graph<PAY, false, REC, false>(a, job, k, rank, s_src, s_view, mbar,
@@ -682,10 +828,11 @@ __device__ __forceinline__ void k_team_body(const TeamArgs& a) {
 // CTA allows the next class to launch as soon as it starts, and waits for the previous class's
 // grid to complete only when it is done (a no-op for the first class), so the next class's
 // kernel completes after every earlier one.
-// (The shared-key cluster kernel is launched with larger key tables, at two CTAs per SM or
-// fewer: its register budget follows.)
+// Register budgets: the kernel without payloads runs one CTA per SM (the pipelined levels keep
+// ~150 registers a thread live; a second CTA on the SM would share its L1 miss rate anyway), the
+// payload kernel two (96 registers: piece streaming wants the warps).
 template <bool PAY, bool REC, bool CSK = false>
-__global__ void __launch_bounds__(kTeamThreads, CSK ? 2 : 3) k_team(const TeamArgs a) {
+__global__ void __launch_bounds__(kTeamBlock, PAY ? 2 : 1) k_team(const TeamArgs a) {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     k_team_body<PAY, REC, CSK>(a);
     asm volatile("griddepcontrol.wait;" ::: "memory");
