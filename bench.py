@@ -584,7 +584,7 @@ def main():
         roof["dram_gbs"] = roof["traffic"] / (kernel_ms / k_launches / 1e3) / 1e9
     # dependency-latency bound beside the bandwidth bound: the deepest graph's chain of levels at
     # the per-level (per-hop) times measured on the calibration chain
-    t_lvl, t_hop, t_solo, t_cl, link_h2d, link_d2h, link_both = hf.hf_calibration(stream)
+    t_lvl, t_hop, t_solo, t_cl, link_h2d, link_d2h, link_both = hf.hf_calibration(stream)[:7]
     roof["critical_path"] = {"levels": depth, "ns_per_level": {"levelsync": t_lvl, "persistent_hop": t_hop,
                                                                 "team_cta": t_solo, "team_cluster": t_cl},
                              "bound_ms": {"levelsync": depth * t_lvl / 1e6, "persistent": depth * t_hop / 1e6,

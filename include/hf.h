@@ -450,13 +450,15 @@ hf_status hf_batch_autotune(hf_batch* b, void* stream, const hf_run_opts* base, 
  * calibration chain (level-synchronous time per level, persistent time per hop, team time per
  * level for one CTA and for a cluster):
  *   level-sync  = levels * t_level (x 2.5 when the level data exceed half the L2) + sum over
+ *                 levels of r_level * its in-edges over the SMs its CTAs occupy + sum over
  *                 levels of the largest saxpy- or host-task cost in it
  *   persistent  = critical path of costs + depth * t_hop + total cost / warps
  *   (both at least the copies' host-link time: each direction's bytes over its bandwidth, and
  *   all copy bytes over the bandwidth of both directions at once)
  *   team        = the team executor's planned makespan: per graph and cluster size k,
- *                 T(k) = sum over levels of t_lvl(k) * ceil(width / 256k) + payload cost / 8k
- *                 (t_lvl x 2.5 for levels too large to stage in shared memory),
+ *                 T(k) = sum over levels of t_lvl(k) * ceil(width / 256k) + r(k) * in-edges / k
+ *                 + payload cost / 8k (t_lvl x 2.5 for levels too large to stage in shared
+ *                 memory; r(k): hf_calibration's time per in-edge gathered on one SM),
  *                 the longest graphs on clusters, the rest on single CTAs (+inf with host tasks)
  * HF_MODE_AUTO runs the executor with the smallest prediction (LEARNED costs when a model is
  * attached, else HEURISTIC). */
@@ -465,9 +467,12 @@ hf_status hf_batch_predict(hf_batch* b, int32_t priority, void* stream, float* l
 /* The machine constants behind the predictions, measured on first use in this process on the
  * current device: on the calibration chain (2,048 tasks, one per level) the level-synchronous
  * time per level, the persistent time per dependent hop, the team time per level on one CTA and
- * on a cluster (ns); and the host link's bandwidth host to device, device to host, and both
+ * on a cluster (ns); the host link's bandwidth host to device, device to host, and both
  * directions at once (GB/s, the best of three 64 MiB copies between page-locked memory and the
- * device; both at once: the bytes of two concurrent copies over their common time). out[7].
+ * device; both at once: the bytes of two concurrent copies over their common time); and, from a
+ * wide calibration graph (512 levels of 256 tasks, 4 in-edges a task), the time per in-edge
+ * gathered on one SM in a level (ns): level-synchronous, team on one CTA, team on a 4-CTA
+ * cluster (a level's gather is bound by the SM's rate of scattered key loads). out[10].
  * Blocks the first time. */
 hf_status hf_calibration(void* stream, float* out);
 

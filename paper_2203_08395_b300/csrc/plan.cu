@@ -1994,6 +1994,11 @@ hf_status plan_autotune(Plan* p, cudaStream_t s, const hf_run_opts& base, int fo
 static std::mutex g_cal_mu;
 static bool g_cal_done = false;
 static float g_t_level_ns = 0.f, g_t_hop_ns = 0.f, g_t_team_solo_ns = 0.f, g_t_team_cluster_ns = 0.f;
+// Time per in-edge gathered on one SM in one level (ns): a level's gather is bound by the SM's
+// rate of scattered key loads, so a wide level costs more than the chain's one-task level.
+// Measured on a wide calibration graph (512 levels of 256 tasks, 4 in-edges each) against the
+// chain: level-sync (one CTA per 256 tasks), team on one CTA, team on a 4-CTA cluster.
+static float g_r_level_ns = 0.f, g_r_team_ns = 0.f, g_r_cluster_ns = 0.f;
 // host link (GB/s): host to device, device to host, and both directions at once (bytes of both
 // copies over their common time)
 static float g_link_gbs[3] = {0.f, 0.f, 0.f};
@@ -2079,8 +2084,55 @@ static hf_status calibrate(cudaStream_t s) {
     }
     if (p) plan_destroy(p);
     hf_graph_destroy(g);
+    // the wide graph: level l's task i has its first in-edge from level l - 1, three more from
+    // anywhere earlier (a fixed hash), delays 1
+    const int32_t W = 256, LW = 512, FW = 4;
+    float tlw = 0.f, tsw = 0.f, tcw = 0.f;
+    hf_graph* gw = nullptr;
+    Plan* pw = nullptr;
+    if (st == HF_OK) st = hf_graph_create(&gw, (int64_t)W * LW, (int64_t)W * LW * FW);
+    if (st == HF_OK) st = hf_add_tasks_bulk(gw, (int64_t)W * LW, nullptr, nullptr);
+    if (st == HF_OK) {
+        std::vector<int32_t> es, ed;
+        uint64_t h = 0x9e3779b97f4a7c15ull;
+        for (int32_t l = 1; l < LW; ++l)
+            for (int32_t i = 0; i < W; ++i)
+                for (int32_t j = 0; j < FW; ++j) {
+                    h ^= h >> 33;
+                    h *= 0xff51afd7ed558ccdull;
+                    h ^= h >> 29;
+                    h += 0x632be59bd9b4e5f5ull;
+                    es.push_back(j == 0 ? (l - 1) * W + (int32_t)(h % W) : (int32_t)(h % (uint64_t)(l * W)));
+                    ed.push_back(l * W + i);
+                }
+        std::vector<float> dl(es.size(), 1.0f);
+        st = hf_precede_bulk(gw, (int64_t)es.size(), es.data(), ed.data(), dl.data());
+    }
+    if (st == HF_OK) st = hf_finalize(gw);
+    if (st == HF_OK) {
+        std::vector<hf_graph*> one{gw};
+        st = plan_build(one, &pw);
+    }
+    if (st == HF_OK) {
+        hf_run_opts o;
+        hf_run_opts_default(&o);
+        o.mode = HF_MODE_LEVELSYNC;
+        st = time_runs(pw, s, o, 1, &tlw);
+        hf_run_opts_default(&o);
+        o.mode = HF_MODE_TEAM;
+        o.team_size = 1;
+        if (st == HF_OK) st = time_runs(pw, s, o, 1, &tsw);
+        o.team_size = 4;
+        if (st == HF_OK) st = time_runs(pw, s, o, 1, &tcw);
+    }
+    if (pw) plan_destroy(pw);
+    if (gw) hf_graph_destroy(gw);
     if (st == HF_OK) st = measure_link(s);
     if (st != HF_OK) return st;
+    const float e_lvl = (float)(W * FW);
+    g_r_level_ns = std::max(0.f, 1e6f * tlw / (float)LW - 1e6f * tl / (float)n) / e_lvl;
+    g_r_team_ns = std::max(0.f, 1e6f * tsw / (float)LW - 1e6f * ts / (float)n) / e_lvl;
+    g_r_cluster_ns = std::max(0.f, 1e6f * tcw / (float)LW - 1e6f * tc / (float)n) / (e_lvl / 4.f);
     g_t_level_ns = 1e6f * tl / (float)n;
     g_t_hop_ns = 1e6f * tp / (float)n;
     g_t_team_solo_ns = 1e6f * ts / (float)n;
@@ -2099,6 +2151,9 @@ hf_status plan_calibration(cudaStream_t s, float* out) {
     out[4] = g_link_gbs[0];
     out[5] = g_link_gbs[1];
     out[6] = g_link_gbs[2];
+    out[7] = g_r_level_ns;
+    out[8] = g_r_team_ns;
+    out[9] = g_r_cluster_ns;
     return HF_OK;
 }
 
@@ -2172,7 +2227,18 @@ hf_status plan_predict(Plan* p, int32_t priority, const hf_costmodel* cm, cudaSt
     cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
     const double ls_bytes = 8.0 * (double)p->m + 8.0 * (double)p->n;
     const double dram = ls_bytes > 0.5 * (double)l2 ? 2.5 : 1.0;
-    *ls_ms = (float)(std::max((double)p->levels * dram * g_t_level_ns + lsum, link_ns) / 1e6);
+    // a merged level's gather: its in-edges over the SMs its CTAs (256 tasks each) occupy
+    std::vector<double> lw((size_t)std::max(p->levels, 1), 0.0), le((size_t)std::max(p->levels, 1), 0.0);
+    for (int32_t gi = 0; gi < p->ngraphs; ++gi)
+        for (int32_t l = 0; l < p->glevels[(size_t)gi] && (size_t)l < lw.size(); ++l) {
+            const int4& sg = p->h_seg[(size_t)(p->seg_first[(size_t)gi] + l)];
+            lw[(size_t)l] += (double)(sg.y - sg.x);
+            le[(size_t)l] += (double)(sg.w - sg.z);
+        }
+    double gather = 0.0;
+    for (size_t l = 0; l < lw.size(); ++l)
+        gather += le[l] / std::max(1.0, std::min(std::ceil(lw[l] / 256.0), (double)p->num_sms));
+    *ls_ms = (float)(std::max((double)p->levels * dram * g_t_level_ns + g_r_level_ns * gather + lsum, link_ns) / 1e6);
     *p_ms = (float)(std::max(cp + (double)p->levels * g_t_hop_ns + work / warps, link_ns) / 1e6);
     // team executor: its own plan under the same cost source (host tasks: not available)
     *t_ms = INFINITY;
@@ -2191,14 +2257,16 @@ hf_status plan_predict(Plan* p, int32_t priority, const hf_costmodel* cm, cudaSt
 }
 
 // Team executor: predicted time of graph g on a team of k CTAs (ns),
-//   T_g(k) = sum over levels l of  t_lvl(k) * ceil(w_l / (256 k)) + P_l / (8 k),
-// w_l the level's task count, P_l the summed predicted cost (warp-ns) of its payload tasks,
-// t_lvl the measured time of a one-task level (CTA barrier for k = 1, cluster barrier else).
+//   T_g(k) = sum over levels l of  t_lvl(k) * ceil(w_l / (256 k)) + r(k) * E_l / k + P_l / (8 k),
+// w_l the level's task count, E_l its in-edges, P_l the summed predicted cost (warp-ns) of its
+// payload tasks, t_lvl the measured time of a one-task level (CTA barrier for k = 1, cluster
+// barrier else), r(k) the measured time per in-edge gathered on one SM.
 constexpr int kTeamMaxCluster = 16;  // above 8 is a non-portable cluster size
 
 static double team_time(const Plan* p, const std::vector<double>& pay_ns, int32_t g, int k, double scale = 1.0) {
     double t = 0.0;
     const double tl = k == 1 ? g_t_team_solo_ns : g_t_team_cluster_ns;
+    const double re = k == 1 ? g_r_team_ns : g_r_cluster_ns;  // per in-edge gathered on one SM
     const int32_t s0 = p->seg_first[(size_t)g];
     for (int32_t l = 0; l < p->glevels[(size_t)g]; ++l) {
         const int4& sg = p->h_seg[(size_t)(s0 + l)];
@@ -2206,7 +2274,8 @@ static double team_time(const Plan* p, const std::vector<double>& pay_ns, int32_
         // a level too large to stage reads its task list, row starts and in-edges from memory:
         // three dependent round trips instead of one
         const double stage = (w <= p->stage_n && sg.w - sg.z <= p->stage_e) ? 1.0 : 2.5;
-        t += stage * tl * (double)((w + 256LL * k - 1) / (256LL * k)) + scale * pay_ns[(size_t)(s0 + l)] / (8.0 * k);
+        t += stage * tl * (double)((w + 256LL * k - 1) / (256LL * k)) + re * (double)(sg.w - sg.z) / k +
+             scale * pay_ns[(size_t)(s0 + l)] / (8.0 * k);
     }
     return t;
 }
@@ -2284,8 +2353,9 @@ static int team_capacity(const Plan* p, int k, size_t smem, bool csk) {
 // Team plan under a cost source: a team size k_g in {1, 2, 4, 8, 16} per graph (k > 1: a
 // thread-block cluster, resident for the whole run). Predicted makespan
 //   M = max( longest T_g(k_g),  sum of T_g(1) over single-CTA graphs / CTAs left to them ).
-// Every graph starts on one CTA; the graph with the longest predicted time doubles its team
-// while that lowers M (and the clusters fit); the first time it does not, the plan is final.
+// Every graph starts on one CTA; the graph with the longest predicted time moves to the larger
+// team (of those that fit) that lowers M most, while one does; the first time none does, the
+// plan is final.
 // `order` lists the graphs in decreasing predicted time. Planning multiplies the payload costs
 // by `scale` (the slowdown of memory traffic when all graphs stream together); *M_out is the
 // plan's makespan in unscaled costs, comparable with the other executors' predictions. FIFO:
@@ -2351,18 +2421,31 @@ static hf_status team_decide(Plan* p, int32_t prio, int32_t ctas_opt, double sca
     while (!heap.empty()) {
         const Item top = heap.top();
         const int32_t g = top.second;
-        const int k0 = k[(size_t)g], k1 = fold_k > 0 ? (k0 == 1 ? fold_k : 2 * kTeamMaxCluster) : 2 * k0;
-        if (k1 > kTeamMaxCluster || (inclass[k1] + 1) * k1 > capk[k1]) break;
-        const int cl1 = cl_ctas + k1 - (k0 > 1 ? k0 : 0);
-        const int ns1 = nsolo - (k0 == 1 ? 1 : 0);
-        if (cl1 > cap1 - (ns1 > 0 ? 1 : 0)) break;
-        const double t1 = team_time(p, pay_ns, g, k1, scale);
+        const int k0 = k[(size_t)g];
         heap.pop();
         const double next = heap.empty() ? 0.0 : heap.top().first;
+        const int ns1 = nsolo - (k0 == 1 ? 1 : 0);
         const double ss1 = solo_sum - (k0 == 1 ? T[(size_t)g] : 0.0);
         const double m0 = makespan(top.first, solo_sum, cap1 - cl_ctas, nsolo);
-        const double m1 = makespan(std::max(next, t1), ss1, cap1 - cl1, ns1);
-        if (!(m1 < m0)) {  // doubling the longest graph's team does not shorten the makespan
+        // every larger team that fits (a level's gather spreads over more SMs, but the first
+        // doubling may not pay for the cluster barrier where a larger team does); the best one
+        int k1 = 0, cl1 = 0;
+        double t1 = 0.0, m1 = m0;
+        for (int kk = fold_k > 0 ? (k0 == 1 ? fold_k : 2 * kTeamMaxCluster) : 2 * k0; kk <= kTeamMaxCluster;
+             kk = fold_k > 0 ? 2 * kTeamMaxCluster : 2 * kk) {
+            if ((inclass[kk] + 1) * kk > capk[kk]) continue;
+            const int c = cl_ctas + kk - (k0 > 1 ? k0 : 0);
+            if (c > cap1 - (ns1 > 0 ? 1 : 0)) continue;
+            const double tk = team_time(p, pay_ns, g, kk, scale);
+            const double mk = makespan(std::max(next, tk), ss1, cap1 - c, ns1);
+            if (mk < m1) {
+                k1 = kk;
+                cl1 = c;
+                t1 = tk;
+                m1 = mk;
+            }
+        }
+        if (k1 == 0) {  // no larger team of the longest graph shortens the makespan
             heap.push(top);
             break;
         }

@@ -553,8 +553,9 @@ def hf_batch_team_keys(b, ngraphs):
 
 def hf_calibration(stream=None):
     """(level-sync ns/level, persistent ns/hop, team ns/level on one CTA, on a cluster,
-    host link GB/s host to device, device to host, both directions at once)."""
-    out = np.zeros(7, np.float32)
+    host link GB/s host to device, device to host, both directions at once,
+    ns per in-edge gathered on one SM: level-sync, team on one CTA, team on a cluster)."""
+    out = np.zeros(10, np.float32)
     _check(load().hf_calibration(_stream_handle(stream), out.ctypes.data), "hf_calibration")
     return tuple(float(x) for x in out)
 
