@@ -58,6 +58,8 @@ def parse():
                     help="headline executor (auto: the cost model's choice)")
     ap.add_argument("--no-learned", action="store_true", help="headline without the cost model (heuristic)")
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--team-size", type=int, default=0,
+                    help="team executor: every graph on teams of this many CTAs (0: the planner's choice)")
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -200,14 +202,15 @@ def train_workloads(name, seeds):
     return [S.config(name, seed=s) for s in seeds]
 
 
-def headline_plan(bd, wl, stream, workload, executor="auto", learned=True, tune=True, rank=0):
+def headline_plan(bd, wl, stream, workload, executor="auto", learned=True, tune=True, rank=0, team_size=0):
     """The plan the benchmark times on batch `bd` (a workload.BatchOnDevice of workload `wl`):
 
     * learned part: a cost model trained on timings recorded from two other seeds of the same
       workload family (the benchmark's own batch stays held out), attached to the batch;
     * executor: the cost model's choice (the library's HF_MODE_AUTO rule from
       hf_batch_predict), or the one forced by `executor`;
-    * launch parameters: autotuned for the executor that runs.
+    * launch parameters: autotuned for the executor that runs (team_size > 0: every graph of a
+      team-executor run on teams of that many CTAs, not tuned).
 
     Returns a dict: opts (hf_run_opts fields of a timed run), chosen (executor), prio, cm (the
     model or None; the caller destroys it), learned (training report), predicted_ms, tuned_ms.
@@ -244,10 +247,10 @@ def headline_plan(bd, wl, stream, workload, executor="auto", learned=True, tune=
             chosen = hf.HF_MODE_TEAM
     else:
         chosen = forced[executor]
-    base = hf.hf_run_opts_default(priority=prio, mode=chosen)
+    base = hf.hf_run_opts_default(priority=prio, mode=chosen, team_size=team_size)
     tuned_ms = None
     best = base
-    if tune and chosen in (hf.HF_MODE_PERSISTENT, hf.HF_MODE_TEAM):
+    if tune and chosen in (hf.HF_MODE_PERSISTENT, hf.HF_MODE_TEAM) and not (team_size and chosen == hf.HF_MODE_TEAM):
         best, tuned_ms = hf.hf_batch_autotune(bd.b, stream, base)
     opts = {k: v for k, v in hf.opts_dict(best).items() if k not in ("time_kernel", "instrument", "validate")}
     opts.update(mode=forced[executor], priority=prio)
@@ -433,7 +436,8 @@ def main():
             torch.distributed.barrier()
 
     # ---- the headline plan: learned costs (trained on other seeds), executor choice, autotuning
-    hp = headline_plan(bd, wl, stream, args.workload, args.executor, not args.no_learned, not args.no_tune, rank)
+    hp = headline_plan(bd, wl, stream, args.workload, args.executor, not args.no_learned, not args.no_tune, rank,
+                       args.team_size)
     head, chosen, prio, cm, learned = hp["opts"], hp["chosen"], hp["prio"], hp["cm"], hp["learned"]
     tuned_ms = hp["tuned_ms"]
     bd.reset_y()
