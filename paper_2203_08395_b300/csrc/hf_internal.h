@@ -189,6 +189,12 @@ struct ResetArgs {
 // level's key loads are in flight: pays where the keys come from L2, not where they fit in L1)
 constexpr int32_t kJobSharedKeys = 1;
 constexpr int32_t kJobPipelined = 2;
+// kJobPayloadLocal: no payload task of the graph touches memory another one writes (checked on
+// the host from the payloads' address ranges; graphs with host tasks never qualify), so no task
+// of the graph can observe another's payload data: a cluster level then releases only its
+// arrival keys (an explicit cluster fence by the threads that stored them) and the level's
+// cluster barrier need not wait for the payload stores to be acknowledged
+constexpr int32_t kJobPayloadLocal = 4;
 // graphs of at least this many tasks run pipelined (their keys outgrow an SM's L1)
 constexpr int32_t kPipeMinTasks = 32768;
 

@@ -45,6 +45,7 @@ struct Plan {
     std::vector<DevPayload> hpay;   // payload table (task-ordered by creation)
     std::vector<int32_t> pay_task;  // payload -> task
     std::vector<int32_t> pay_level; // payload -> level
+    std::vector<uint8_t> pay_local; // graph -> 1: no payload touches memory another payload writes
     std::vector<int32_t> hpidx;     // task -> payload or -1
     std::vector<uint8_t> hpdir;     // payload -> 0, or 1 for a pull copy, 2 for a push copy
     std::vector<int32_t> pay_succ_level;  // payload -> its task's successors' lowest level (-1: none)
@@ -540,6 +541,59 @@ hf_status plan_build(const std::vector<hf_graph*>& graphs, Plan** out) {
             }
         }
         p->npay = (int32_t)p->hpay.size();
+        // per graph: payload memory ranges pairwise disjoint wherever one of them is written
+        // (saxpy writes y and reads x and y; a copy writes dst and reads src; a host task may
+        // touch anything)
+        p->pay_local.assign((size_t)p->ngraphs, 1);
+        {
+            struct Rng {
+                uint64_t a, b;
+                int32_t owner;
+                bool write;
+            };
+            std::vector<std::vector<Rng>> per((size_t)p->ngraphs);
+            for (int32_t q = 0; q < p->npay; ++q) {
+                const int32_t t = p->pay_task[(size_t)q];
+                const int32_t gi = (int32_t)(std::upper_bound(p->task_off.begin(), p->task_off.end(), t) -
+                                             p->task_off.begin()) - 1;
+                const DevPayload& d = p->hpay[(size_t)q];
+                if (d.op == kPayHost) {
+                    p->pay_local[(size_t)gi] = 0;
+                    continue;
+                }
+                const uint64_t bytes = d.op == kPayCopy ? (uint64_t)d.n : 4ull * (uint64_t)d.n;
+                if (bytes == 0) continue;
+                per[(size_t)gi].push_back(Rng{(uint64_t)d.dst, (uint64_t)d.dst + bytes, q, true});
+                if (d.src) per[(size_t)gi].push_back(Rng{(uint64_t)d.src, (uint64_t)d.src + bytes, q, false});
+            }
+            for (int32_t gi = 0; gi < p->ngraphs; ++gi) {
+                std::vector<Rng>& r = per[(size_t)gi];
+                std::vector<Rng> w;
+                for (const Rng& x : r)
+                    if (x.write) w.push_back(x);
+                std::sort(w.begin(), w.end(), [](const Rng& x, const Rng& y) { return x.a < y.a; });
+                // written ranges of different payloads must not overlap each other or any range
+                // another payload reads: for each range, the written ranges starting before its
+                // end, scanned back while they could still reach it (ends below the running
+                // maximum are skipped by the check, not by the scan)
+                std::vector<uint64_t> wmax(w.size());
+                for (size_t i = 0; i < w.size(); ++i) wmax[i] = std::max<uint64_t>(i ? wmax[i - 1] : 0, w[i].b);
+                for (size_t k = 0; k < r.size() && p->pay_local[(size_t)gi]; ++k) {
+                    const Rng& x = r[k];
+                    size_t hi = (size_t)(std::lower_bound(w.begin(), w.end(), x.b,
+                                                          [](const Rng& y, uint64_t v) { return y.a < v; }) -
+                                         w.begin());
+                    while (hi > 0 && wmax[hi - 1] > x.a) {
+                        const Rng& y = w[hi - 1];
+                        if (y.b > x.a && y.owner != x.owner) {
+                            p->pay_local[(size_t)gi] = 0;
+                            break;
+                        }
+                        --hi;
+                    }
+                }
+            }
+        }
         // cost-model inputs kept on the host until first use
         p->h_level.resize((size_t)n);
         p->h_cat.resize((size_t)n);
@@ -2558,8 +2612,10 @@ static hf_status plan_team_jobs(Plan* p, const hf_run_opts& o, cudaStream_t s) {
         }
     }
     if (p->tclass.size() > 5) return fail(HF_ENOTSUP, "too many team classes");
-    for (TeamJob& j : jobs)
+    for (TeamJob& j : jobs) {
         if (p->task_off[(size_t)j.graph + 1] - p->task_off[(size_t)j.graph] >= kPipeMinTasks) j.flags |= kJobPipelined;
+        if (p->pay_local[(size_t)j.graph]) j.flags |= kJobPayloadLocal;
+    }
     // Keys in distributed shared memory (team.cuh), per cluster class of a power-of-two size, in
     // batches without payloads, the largest clusters first. A key table of `cap` entries per CTA
     // must leave every CTA of the class resident and the shared memory of all classes' CTAs

@@ -316,6 +316,15 @@ __device__ __forceinline__ void cluster_sync() {
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
+// The same barrier with a relaxed arrive: it orders nothing by itself; a thread whose writes other
+// CTAs read after the barrier releases them first with fence_cluster (the fence and the arrive
+// form the release), and the wait still acquires
+__device__ __forceinline__ void cluster_sync_relaxed() {
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_cluster() { asm volatile("fence.acq_rel.cluster;" ::: "memory"); }
+
 // store a job into CTA `rank`'s copy of the shared variable `local`
 __device__ __forceinline__ void st_cluster_job(TeamJob* local, unsigned rank, const TeamJob j) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(local);
@@ -344,6 +353,7 @@ __device__ __noinline__ void team_fail(const TeamArgs& a, int* s_fail, int k, in
         asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(d) : "r"(s), "r"(r));
         asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(d), "r"(1) : "memory");
     }
+    fence_cluster();  // (released before the level's barrier, whose arrive may be relaxed)
 }
 
 // ---------------------------------------------------------------- one level
@@ -533,6 +543,9 @@ __device__ __forceinline__ bool team_run_graph(const TeamArgs& a, const TeamJob&
     bool pvalid = false;
     const int2* pin = nullptr;  // the read-ahead task's in-edges (its level's stage buffer)
     const bool pipe = (job.flags & kJobPipelined) != 0;
+    // cluster jobs whose payloads touch disjoint memory (kJobPayloadLocal): a level releases its
+    // arrival keys alone (each thread that stored one fences), not the pieces' stores
+    const bool plocal = PAY && !SOLO && (job.flags & kJobPayloadLocal) != 0;
     const uint64_t pol = l2_keep_policy();
     // segment descriptors and item ranges ride a ring in shared memory, fetched by the lead
     // thread kRingAhead levels ahead (the first kRingAhead here); level l uses stage buffer
@@ -632,6 +645,7 @@ __device__ __forceinline__ bool team_run_graph(const TeamArgs& a, const TeamJob&
                 }
             };
             int p = team_slice(s0.x, s0.y - s0.x, rank, k, lk) + t;
+            const bool stored = t < kTeamThreads && p < p1;  // this thread stores at least one key
             if (!pipe) {
                 // (jobs that are not pipelined keep the plain loop: with the pipelined path compiled
                 // in their levels measured slower, keys in L1 leaving nothing to hide)
@@ -688,6 +702,7 @@ __device__ __forceinline__ bool team_run_graph(const TeamArgs& a, const TeamJob&
             pe0 = ne0;
             pe1 = ne1;
             pin = nin;
+            if (plocal && stored) fence_cluster();  // the keys, before this thread's pieces
         }
         // this CTA's slice of the level's payload pieces: each warp takes the next piece from a
         // shared counter, the warps without arrivals at once, the others after them. In cluster
@@ -724,8 +739,14 @@ __device__ __forceinline__ bool team_run_graph(const TeamArgs& a, const TeamJob&
         // the ring group of level l - 1 (entry l - 1 + kRingAhead, staged at level l + 1); this
         // level's own group stays in flight across the barrier
         if (t == kTeamLead) cp_async_wait_group1();
-        if (SOLO) __syncthreads();
-        else cluster_sync();
+        if (SOLO) {
+            __syncthreads();
+        } else if (plocal) {  // the CTA's shared state (piece counter, ring) by the CTA barrier
+            __syncthreads();
+            cluster_sync_relaxed();
+        } else {
+            cluster_sync();
+        }
         if (*(volatile int*)s_fail) {  // the same value in every thread of the team (see team_fail)
             if (t == kTeamLead) {      // stage and ring copies still in flight land before the CTA ends
                 for (int q = 0; q < kTeamBufs; ++q)
