@@ -534,10 +534,12 @@ __device__ __forceinline__ bool team_run_graph(const TeamArgs& a, const TeamJob&
     const int kbase = SK ? __ldg(a.task_off + job.graph) : 0;
     const unsigned skey_s = SK ? (unsigned)__cvta_generic_to_shared(skey) : 0u;
     unsigned inflight = 0;  // lead thread: stage buffers with a copy issued and not yet seen complete
-    // Software pipelining across levels: while its first task's key loads are in flight, a thread
-    // tests (without waiting) whether the next level's stage buffer has landed and, if so, reads
-    // its first task of that level (id and in-edge range) from it. `seen`: buffers whose current
-    // completion this thread has already observed; pv/pe0/pe1 (valid: pvalid): the task read ahead.
+    // Software pipelining across levels (pipe: jobs flagged kJobPipelined): while its first task's
+    // key loads are in flight, a thread tests (without waiting) whether the next level's stage
+    // buffer has landed and, if so, reads its first task of that level (id, in-edge range, stage
+    // pointer) from it; the kernel without payloads then issues that task's first eight key loads
+    // as the very first thing of the next level. `seen`: buffers whose current completion this
+    // thread has already observed; pv/pe0/pe1/pin (valid: pvalid): the task read ahead.
     unsigned seen = 0;
     int pv = 0, pe0 = 0, pe1 = 0;
     bool pvalid = false;
