@@ -361,6 +361,15 @@ hf_status hf_batch_team_plan(hf_batch* b, int32_t* team_size);
  * batch's graph count (see hf_run_opts::team_global_keys). HF_ESTATE before the first
  * team-executor run. */
 hf_status hf_batch_team_keys(hf_batch* b, int32_t* shared);
+/* How each graph of the batch ran in the last team-executor run, as bits into a host array of
+ * the batch's graph count: 1 its keys lived in its cluster's distributed shared memory (as
+ * hf_batch_team_keys); 2 its levels were software-pipelined (graphs of at least 32,768 tasks:
+ * each thread reads its next level's task during the current level's gather); 4 its payload
+ * tasks touch pairwise disjoint memory wherever one of them writes (checked on the host from
+ * the payloads' address ranges: saxpy writes y and reads x and y, a copy writes its destination
+ * and reads its source; a graph with host tasks never qualifies), so its cluster levels release
+ * only the arrival keys. HF_ESTATE before the first team-executor run. */
+hf_status hf_batch_team_flags(hf_batch* b, int32_t* flags);
 /* As hf_set_delays for every graph of the batch: delay holds the graphs' edge delays
  * concatenated in batch order (sum of their edge counts). */
 hf_status hf_batch_set_delays(hf_batch* b, const float* delay, int on_device, void* stream);

@@ -958,6 +958,12 @@ hf_status hf_batch_team_keys(hf_batch* b, int32_t* shared) {
     return plan_team_keys(b->plan, shared);
 }
 
+hf_status hf_batch_team_flags(hf_batch* b, int32_t* flags) {
+    if (!b || !flags) return fail(HF_EINVAL, "NULL argument");
+    if (!b->plan) return fail(HF_ESTATE, "batch has not run");
+    return plan_team_flags(b->plan, flags);
+}
+
 hf_status hf_batch_kernel_ms(hf_batch* b, float* ms) {
     if (!b || !ms) return fail(HF_EINVAL, "NULL argument");
     if (!b->plan) return fail(HF_ESTATE, "batch has not run");

@@ -369,6 +369,7 @@ hf_status plan_last_launches(Plan* p, int32_t* n);
 hf_status plan_get_task_costs(Plan* p, int32_t gi, float* out);
 hf_status plan_team_plan(Plan* p, int32_t* team_size);
 hf_status plan_team_keys(Plan* p, int32_t* shared);
+hf_status plan_team_flags(Plan* p, int32_t* flags);
 hf_status plan_set_delays(Plan* p, const float* delay, int on_device, cudaStream_t s);
 hf_status plan_run_host(Plan* p, cudaStream_t s, const hf_run_opts& o, const float* delay, float* arr_out);
 hf_status plan_features(Plan* p, float* X, cudaStream_t s);

@@ -1635,6 +1635,17 @@ hf_status plan_team_keys(Plan* p, int32_t* shared) {
     return HF_OK;
 }
 
+hf_status plan_team_flags(Plan* p, int32_t* flags) {
+    if (p->team_sk.size() != (size_t)p->ngraphs) return fail(HF_ESTATE, "no team-executor run yet");
+    for (int32_t g = 0; g < p->ngraphs; ++g) {
+        int32_t f = p->team_sk[(size_t)g] ? kJobSharedKeys : 0;
+        if (p->task_off[(size_t)g + 1] - p->task_off[(size_t)g] >= kPipeMinTasks) f |= kJobPipelined;
+        if (p->pay_local[(size_t)g]) f |= kJobPayloadLocal;
+        flags[g] = f;
+    }
+    return HF_OK;
+}
+
 hf_status plan_kernel_ms(Plan* p, float* ms) {
     if (!p->ran || !p->last_timed) return fail(HF_ESTATE, "last run was not a time_kernel run");
     cudaError_t e = cudaEventSynchronize(p->kev1);

@@ -150,6 +150,7 @@ def load():
         "hf_batch_last_launches": [vp, P(i32)],
         "hf_batch_team_plan": [vp, vp],
         "hf_batch_team_keys": [vp, vp],
+        "hf_batch_team_flags": [vp, vp],
         "hf_calibration": [vp, vp],
         "hf_dump": [vp, ctypes.c_char_p],
         "hf_place": [vp, i32, vp, vp],
@@ -542,6 +543,16 @@ def hf_batch_team_plan(b, ngraphs):
     k = np.zeros(ngraphs, np.int32)
     _check(load().hf_batch_team_plan(b, k.ctypes.data), "hf_batch_team_plan")
     return k
+
+
+TEAM_SHARED_KEYS, TEAM_PIPELINED, TEAM_PAYLOAD_LOCAL = 1, 2, 4
+
+
+def hf_batch_team_flags(b, ngraphs):
+    """How each graph ran in the last team-executor run (int32 array of TEAM_* bits)."""
+    f = np.zeros(ngraphs, np.int32)
+    _check(load().hf_batch_team_flags(b, f.ctypes.data), "hf_batch_team_flags")
+    return f
 
 
 def hf_batch_team_keys(b, ngraphs):

@@ -110,3 +110,81 @@ def test_cluster_payload_order(shared, opts):
         np.testing.assert_array_equal(arr.view(np.uint32), ref, err_msg=str(opts))
     hf.hf_graph_destroy(g)
     del xs
+
+
+def _chain(bufs_x, bufs_y, a, extra=None):
+    """One saxpy task per level (y_l = a_l * x_l + y_l), each after the one before, beside 50
+    max-plus tasks per level; extra(g, ids) may add tasks. Returns (graph, task ids)."""
+    g = hf.hf_graph_create()
+    ids = []
+    prev = None
+    for lv, (x, y) in enumerate(zip(bufs_x, bufs_y)):
+        m = hf.hf_add_tasks_bulk(g, 50)
+        p = hf.hf_saxpy_payload(op=hf.HF_K_SAXPY_F32, a_f=float(a[lv]), n=int(y.numel()), x_pull=-1, y_pull=-1,
+                                x_dev=x.data_ptr(), y_dev=y.data_ptr())
+        s = hf.hf_add_task(g, hf.HF_KERNEL, p)
+        if prev is not None:
+            for t in list(range(m, m + 50)) + [s]:
+                hf.hf_precede(g, prev, t)
+        prev = s
+        ids.append(s)
+    if extra:
+        extra(g, ids)
+    return g, ids
+
+
+def test_payload_local_classification_and_overlapping_views():
+    """The host check behind the relaxed cluster barrier, through hf_batch_team_flags: private
+    buffers qualify; a shared y, overlapping views of one buffer, one task's y read as another's
+    x, and a graph with a host task do not. The overlapping-view chain also runs exactly on
+    clusters (each update sees the one before)."""
+    rng = np.random.default_rng(21)
+    dev = torch.device("cuda")
+    L, n = 12, 4000
+    a = rng.choice(np.array([0.5, 2.0, -1.0], np.float32), L)
+
+    def tens(k):
+        return [torch.tensor(rng.integers(-8, 9, n).astype(np.float32), device=dev) for _ in range(k)]
+
+    keep = []
+    xs_p, ys_p = tens(L), tens(L)  # private
+    base = torch.tensor(rng.integers(-50, 51, (L + 1) * n // 2).astype(np.float32), device=dev)
+    ys_v = [base[lv * n // 2: lv * n // 2 + n] for lv in range(L)]  # each overlaps the next by half
+    xs_v = tens(L)
+    ys_r, xs_r = tens(L), None  # task l reads task l-1's y as its x
+    xs_r = [tens(1)[0]] + [ys_r[lv - 1] for lv in range(1, L)]
+    xs_h, ys_h = tens(L), tens(L)
+    calls = []
+    host_fn = hf.HOST_FN(lambda arg: calls.append(1))
+    keep += [host_fn]
+
+    def add_host(g, ids):
+        h = hf.hf_add_task(g, hf.HF_HOST, hf.hf_host_payload(fn=host_fn, arg=None))
+        hf.hf_precede(g, ids[-1], h)
+
+    start_v = base.clone()
+    graphs = [_chain(xs_p, ys_p, a)[0], _chain(xs_v, ys_v, a)[0], _chain(xs_r, ys_r, a)[0],
+              _chain(xs_h, ys_h, a, add_host)[0]]
+    b = hf.hf_batch_create()
+    for g in graphs:
+        hf.hf_batch_add(b, g)
+    # expected overlapping-view result: the updates in chain order, float64 of exact values
+    want = start_v.cpu().numpy().astype(np.float64)
+    for lv in range(L):
+        lo = lv * n // 2
+        want[lo:lo + n] = float(a[lv]) * xs_v[lv].cpu().numpy().astype(np.float64) + want[lo:lo + n]
+    for ts in (2, 4):
+        base.copy_(start_v)
+        torch.cuda.synchronize()
+        hf.hf_batch_run(b, None, hf.hf_run_opts_default(mode=hf.HF_MODE_TEAM, team_size=ts))
+        hf.hf_batch_sync_status(b)
+        torch.cuda.synchronize()
+        flags = hf.hf_batch_team_flags(b, len(graphs))
+        local = [(int(f) & hf.TEAM_PAYLOAD_LOCAL) != 0 for f in flags]
+        assert local == [True, False, False, False], (ts, flags)
+        assert all((int(f) & hf.TEAM_PIPELINED) == 0 for f in flags)  # (small graphs)
+        np.testing.assert_array_equal(base.cpu().numpy(), want.astype(np.float32), err_msg=str(ts))
+    hf.hf_batch_destroy(b)
+    for g in graphs:
+        hf.hf_graph_destroy(g)
+    del keep, xs_p, ys_p, xs_v, ys_v, xs_r, ys_r, xs_h, ys_h
