@@ -197,13 +197,13 @@ def algorithmic_bytes(wl):
 
 
 def train_workloads(name, seeds):
-    """Training graphs for the cost model: the same family as the benchmark workload with other
-    seeds and fewer graphs (the benchmark's own seed stays held out)."""
+    """Training graphs for the cost model: the benchmark workload's own recipe and size with other
+    seeds (the benchmark's own seed stays held out). Full size matters for batches: a task's
+    recorded cost includes the memory contention of the batch it ran in, and 48-graph batches
+    recorded payload costs low enough that the planner left the heaviest graphs of the 256-graph
+    batch on 4-CTA clusters."""
     from paper_2203_08395_b300 import synth as S
 
-    if name.startswith("batch"):
-        frac = 0.10 if name.endswith("mixed") else 0.0
-        return [S.batch(s, graphs=48, frac_saxpy=frac) for s in seeds]
     return [S.config(name, seed=s) for s in seeds]
 
 
